@@ -1,0 +1,410 @@
+#!/usr/bin/env python3
+"""Benchmark of the 2D radix-2 DIT FFT on GB300: 4096x4096 complex64 images.
+
+One step = forward 2D FFT then inverse 2D FFT of each of B resident images
+(per rank).  ``value`` counts 2D transforms per second (a forward and an
+inverse each count as one image transform), summed over ranks; inputs are
+already in HBM when the timed region starts.  The working set (B images x
+2 buffers x 128 MiB) is far larger than L2, so no image is L2-resident when
+it is revisited.
+
+Prints ONE JSON line on rank 0.  ``--impl reference`` times the FP64 CPU
+oracle (the only other implementation of this path) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "2D FFT images/s & HBM GB/s vs peak at 4096²; serving p50/p99 latency"
+UNIT = "images/s"
+SIDE = 4096
+BYTES_PER_PX_PASS = 16          # one read + one write of a complex64 pixel
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--images", type=int, default=4, help="resident images per rank")
+    ap.add_argument("--side", type=int, default=SIDE)
+    ap.add_argument("--e2e-steps", type=int, default=6)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="bound on the CPU-baseline sample (wall seconds)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-parity", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(ws, backend):
+    if ws <= 1:
+        return None
+    import torch.distributed as dist
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def max_over_ranks(x: float, dist, device=None) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback 6.8 TB/s (MEASURED_PEAKS.json absent)"
+
+
+def kernel_source_hash() -> str:
+    """Hash of the CUDA sources the timed kernels are built from."""
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1505_08019_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None when the kernels changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    v = d.get("kernels", {}).get(kernel, {}).get("dram_bytes_per_launch_full_size")
+    return float(v) if v is not None else None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = []
+        for rec in csv.reader(io.StringIO(out)):
+            rec = [r.strip() for r in rec]
+            if len(rec) < 9:
+                continue
+            if self.uuid and rec[0] != self.uuid:
+                continue
+            try:
+                rows.append((float(rec[1]), float(rec[2]), rec[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, v in enumerate(fl)
+                          if v.lower().startswith("active")})
+        sm = [r[0] for r in rows]
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+# ------------------------------------------------------------- CPU oracle
+def cpu_oracle_sample(side, seconds, threads):
+    """Forward+inverse 4096^2 transforms by the FP64 oracle on host threads,
+    repeated while the wall-clock bound allows (at least one pair)."""
+    import synth
+    from oracle import oracle
+    orc = oracle.get()
+    x = synth.blob_image(side, side, seed=0).astype(np.complex128)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        X = orc.fft2d(x, threads=threads)
+        orc.fft2d(X, inverse=True, threads=threads)
+        n += 2
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = init_dist(ws, "nccl")
+
+    from paper_1505_08019_gb300 import build as _b
+    if not os.path.exists(_b.LIB):
+        _b.build()
+    import paper_1505_08019_gb300 as fft
+    import synth
+
+    side, B = args.side, args.images
+    imgs = [synth.blob_image(side, side, seed=rank * 1000 + i) for i in range(B)]
+    xs = [torch.from_numpy(im).to(dev) for im in imgs]
+    Xs = [torch.empty_like(x) for x in xs]
+    pf = fft.fft2d_plan(side, side, fft.FFT2D_C64, fft.FFT2D_FORWARD)
+    pi = fft.fft2d_plan(side, side, fft.FFT2D_C64, fft.FFT2D_INVERSE)
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    ROWS, COLS = fft.FFT2D_PASS_ROWS, fft.FFT2D_PASS_COLS
+    exec_pass = fft.fft2d_exec_pass
+
+    def step(evs=None):
+        # forward then inverse of every resident image; with `evs`, an event
+        # brackets every kernel launch (rows fwd, cols fwd, rows inv, cols inv)
+        for x, X in zip(xs, Xs):
+            if evs is None:
+                exec_pass(pf, ROWS, x, X, sptr)
+                exec_pass(pf, COLS, X, X, sptr)
+                exec_pass(pi, ROWS, X, X, sptr)
+                exec_pass(pi, COLS, X, X, sptr)
+            else:
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+                e[0].record(stream)
+                exec_pass(pf, ROWS, x, X, sptr)
+                e[1].record(stream)
+                exec_pass(pf, COLS, X, X, sptr)
+                e[2].record(stream)
+                exec_pass(pi, ROWS, X, X, sptr)
+                e[3].record(stream)
+                exec_pass(pi, COLS, X, X, sptr)
+                e[4].record(stream)
+                evs.append(e)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    evs = []
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_start.record(stream)
+    for _ in range(args.steps):
+        step(evs)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    ms_local = t_start.elapsed_time(t_end)
+    ms = max_over_ranks(ms_local, dist, dev)
+
+    # per-kernel durations over the timed region
+    d = np.array([[e[k].elapsed_time(e[k + 1]) for k in range(4)] for e in evs])   # ms
+    names = ["row_pass_fwd", "col_pass_fwd", "row_pass_inv", "col_pass_inv"]
+    per = {n: float(d[:, k].mean()) for k, n in enumerate(names)}
+    pass_bytes = BYTES_PER_PX_PASS * side * side
+    row_ms = float(d[:, [0, 2]].mean())
+    col_ms = float(d[:, [1, 3]].mean())
+    dom, dom_ms = ("col_pass", col_ms) if col_ms >= row_ms else ("row_pass", row_ms)
+    peak, peak_src = measured_hbm_peak()
+    achieved = pass_bytes / (dom_ms * 1e-3) / 1e9
+    transforms = 2 * B * args.steps * ws
+    value = transforms / (ms * 1e-3)
+
+    # end to end through the public host-buffer call: H2D, both passes, D2H
+    hin = [torch.from_numpy(im).pin_memory() for im in imgs]
+    hout = [torch.empty_like(h).pin_memory() for h in hin]
+    fft.fft2d_exec_host(pf, hin[0], hout[0], sptr)          # allocate staging
+    fft.fft2d_exec_host(pi, hout[0], hout[0], sptr)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        for h, o in zip(hin, hout):
+            fft.fft2d_exec_host(pf, h, o, sptr)
+            fft.fft2d_exec_host(pi, o, o, sptr)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    img_bytes = side * side * 8
+    e2e = {"value": 2 * B * args.e2e_steps * ws / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": 2 * B * img_bytes, "d2h_bytes_per_step": 2 * B * img_bytes,
+           "steps": args.e2e_steps, "call": "fft2d_exec_host (pinned host buffers)"}
+
+    parity = None
+    if rank == 0 and not args.no_parity:
+        from oracle import oracle
+        orc = oracle.get()
+        X = torch.empty_like(xs[0])
+        fft.fft2d_exec(pf, xs[0], X, sptr)
+        Y = torch.empty_like(X)
+        fft.fft2d_exec(pi, X, Y, sptr)
+        torch.cuda.synchronize()
+        Xh, Yh = X.cpu().numpy(), Y.cpu().numpy()
+        th = host_cores()
+        want = orc.fft2d(imgs[0], threads=th)
+        back = orc.fft2d(Xh, inverse=True, threads=th)
+        rl = lambda a, b: float(np.linalg.norm((a.astype(np.complex128) - b).ravel())
+                                / np.linalg.norm(b.ravel()))
+        parity = {"fwd_rel_l2": rl(Xh, want), "inv_rel_l2": rl(Yh, back),
+                  "round_trip_rel_l2": rl(Yh, imgs[0].astype(np.complex128)),
+                  "tolerance": 1e-5, "image": "blob 4096x4096 seed 0"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        th = host_cores()
+        v, n, dt = cpu_oracle_sample(side, args.cpu_seconds, th)
+        cpu = {"value": v, "unit": UNIT, "cores": th, "kind": "oracle",
+               "sample": f"{n} transforms ({n // 2} forward+inverse pairs) of one "
+                         f"{side}x{side} blob image, FP64 C oracle on {th} threads, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic (seeded Gaussian-blob + U[0,1) gray images)",
+            "config": {"workload": f"{side}x{side} complex64 2D FFT, forward+inverse of "
+                                   f"{B} resident images per GPU per step",
+                       "side": side, "images_per_gpu": B, "parallelism": f"replicas x{ws}",
+                       "l2": f"inputs larger than L2 ({B} images x 2 buffers x "
+                             f"{img_bytes >> 20} MiB rotated)",
+                       "transform_counting": "forward and inverse each count as one image"},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak,
+                         "peak_source": peak_src,
+                         "algorithmic_bytes_per_launch": pass_bytes,
+                         "avg_launch_ms": dom_ms,
+                         "traffic": ncu_traffic(dom)},
+            "passes_ms": per,
+            "whole_transform_hbm_frac": (2 * pass_bytes / ((row_ms + col_ms) * 1e-3) / 1e9) / peak,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": 4 * B * args.steps,
+            "clocks": clk,
+            "parity": parity,
+        }
+        print(json.dumps(line), flush=True)
+    for p in (pf, pi):
+        fft.fft2d_destroy(p)
+    if dist:
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------- reference arm
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    th = host_cores()
+    import synth
+    from oracle import oracle
+    orc = oracle.get()
+    side = args.side
+    x = synth.blob_image(side, side, seed=0).astype(np.complex128)
+    # one untimed forward+inverse pair pages the data and the library in
+    X = orc.fft2d(x, threads=th)
+    orc.fft2d(X, inverse=True, threads=th)
+    steps = args.steps
+    # each step: one forward + one inverse of one image (a bounded sample of
+    # the GPU step); steps stop early once the wall-clock budget is spent so
+    # the run ends within minutes whatever --steps asks for
+    budget_s = 90.0
+    t0 = time.perf_counter()
+    done = 0
+    for _ in range(steps):
+        X = orc.fft2d(x, threads=th)
+        orc.fft2d(X, inverse=True, threads=th)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    value = 2 * done / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": done, "warmup": 1, "ms_per_step": dt / done * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded Gaussian-blob + U[0,1) gray image)",
+        "config": {"workload": f"{side}x{side} complex64 2D FFT, forward+inverse; each "
+                               f"step one image (bounded sample)", "side": side},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": th, "kind": "oracle",
+                         "sample": f"{done} forward+inverse pairs of one {side}x{side} image"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * fft2d.h -- C ABI of a GB300 (sm_103a) library for the 2D forward and
+ * inverse complex FFT of an image by radix-2 decimation in time.
+ *
+ * Method (Shen et al., "Research on the fast Fourier transform of image
+ * based on GPU"):
+ *   - Section 2, eq. 1: X(k) = sum_{n<N} x(n) W_N^{nk}.
+ *   - Section 2, eqs. 2-3: the radix-2 DIT recurrence X(k) = Xe(k) + W_N^k Xo(k),
+ *     X(k+N/2) = Xe(k) - W_N^k Xo(k), applied over log2(N) stages of N/2
+ *     independent butterflies.
+ *   - Section 3.1, eq. 4: the butterfly X(k) = X1(k) + W * X2(k), with
+ *     rotation factors precomputed once per size.
+ *   - Section 3.2: a bit-reversal scramble before the stages, so that they
+ *     run in place; 2D = every row, then every column, each axis scrambled
+ *     along itself.
+ *
+ * Conventions (readings of points the paper leaves open):
+ *   - W_N = exp(-2*pi*i/N) forward, exp(+2*pi*i/N) inverse.
+ *   - Forward unscaled, inverse multiplied by 1/(rows*cols).
+ *   - Rows first, then columns.
+ *
+ * Data layout: a rows x cols image is row-major, with interleaved complex
+ * values: FFT2D_C64 is (float re, float im), 8 bytes per pixel, the layout of
+ * torch.complex64 / numpy.complex64.
+ *
+ * Ownership: image buffers (device or host) belong to the caller.  A plan
+ * owns its device twiddle tables and any staging buffer it allocates; all of
+ * them are released by fft2d_destroy.  Every fft2d_exec* call is
+ * asynchronous on the given CUDA stream (NULL = the legacy default stream)
+ * except where noted.
+ *
+ * Errors: argument errors are returned synchronously and nothing is
+ * launched.  A launch failure returns FFT2D_ERR_CUDA; fft2d_last_error()
+ * gives the CUDA error text of the calling thread's last failure.  Calls must
+ * be made with the plan's device current.
+ */
+#ifndef FFT2D_H
+#define FFT2D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define FFT2D_API __attribute__((visibility("default")))
+#else
+#define FFT2D_API
+#endif
+
+typedef struct fft2d_plan_s *fft2d_plan_t;
+
+/* Storage types (dtype argument). */
+#define FFT2D_C64 0  /* complex64: float2 per pixel, FP32 arithmetic */
+
+/* Directions (dir argument). */
+#define FFT2D_FORWARD (-1)
+#define FFT2D_INVERSE 1
+
+/* Passes (fft2d_exec_pass). */
+#define FFT2D_PASS_ROWS 0
+#define FFT2D_PASS_COLS 1
+
+/* Largest side accepted (2^14). */
+#define FFT2D_MAX_SIDE 16384
+
+typedef enum {
+    FFT2D_OK = 0,
+    FFT2D_ERR_ARG = 1,         /* null pointer, bad enum, bad stage count   */
+    FFT2D_ERR_NOT_POW2 = 2,    /* a side is not a power of two (or < 1)     */
+    FFT2D_ERR_TOO_LARGE = 3,   /* a side exceeds FFT2D_MAX_SIDE             */
+    FFT2D_ERR_OOM = 4,         /* device or host allocation failed          */
+    FFT2D_ERR_CUDA = 5,        /* a CUDA call or launch failed              */
+    FFT2D_ERR_TIMEOUT = 6,     /* a bounded device wait ran out             */
+    FFT2D_ERR_BUDGET = 7,      /* request does not fit the memory budget    */
+    FFT2D_ERR_UNSUPPORTED = 8  /* valid but not provided by this build      */
+} fft2d_status;
+
+/*
+ * Create a plan for a rows x cols transform (1 <= side <= FFT2D_MAX_SIDE,
+ * powers of two; 1 means that axis is left unchanged).  Builds the per-stage
+ * rotation-factor tables of both axes on the host in FP64 (Section 3.1:
+ * "calculated in advance ... not changed") and uploads them, rounded to FP32,
+ * to the current device.  *out receives the plan; on error it is set to NULL.
+ */
+FFT2D_API fft2d_status fft2d_plan(int rows, int cols, int dtype, int dir, fft2d_plan_t *out);
+
+/* Release a plan and everything it owns.  NULL is accepted (no-op). */
+FFT2D_API fft2d_status fft2d_destroy(fft2d_plan_t plan);
+
+/* Report the parameters a plan was created with (any pointer may be NULL). */
+FFT2D_API fft2d_status fft2d_plan_info(fft2d_plan_t plan, int *rows, int *cols, int *dtype, int *dir);
+
+/*
+ * Whole 2D transform on device buffers: the row pass (scramble fused into the
+ * load, all log2(cols) stages in one launch), then the column pass (scramble
+ * fused, all log2(rows) stages, inverse scale fused into the store).
+ * in and out are device pointers to rows*cols pixels; in == out is allowed
+ * (in place).  Partial overlap of in and out is not allowed.  Two launches.
+ */
+FFT2D_API fft2d_status fft2d_exec(fft2d_plan_t plan, const void *in, void *out, void *stream);
+
+/*
+ * One of the two passes of fft2d_exec: FFT2D_PASS_ROWS reads `in` and writes
+ * `out`; FFT2D_PASS_COLS reads `in` and writes `out` and applies the inverse
+ * scale.  fft2d_exec(p, x, y) == pass(ROWS, x, y) then pass(COLS, y, y).
+ * One launch.
+ */
+FFT2D_API fft2d_status fft2d_exec_pass(fft2d_plan_t plan, int pass, const void *in, void *out,
+                             void *stream);
+
+/*
+ * Debug view of partial execution: like fft2d_exec, but each axis stops
+ * after row_stages (0..log2 cols) and col_stages (0..log2 rows) butterfly
+ * stages, leaving the data in the scrambled position order that the
+ * in-place stages use.  With 0 stages an axis is only scrambled (Section 3.2),
+ * an exact permutation.  The inverse scale is applied only when both axes run
+ * every stage.  Two launches.
+ */
+FFT2D_API fft2d_status fft2d_exec_stages(fft2d_plan_t plan, const void *in, void *out, int row_stages,
+                               int col_stages, void *stream);
+
+/*
+ * Whole transform of HOST buffers (the paper's upload / render / read-back
+ * cycle, Section 1.1): copies in_host to a plan-owned device buffer
+ * (allocated on first use), runs fft2d_exec in place there, copies the
+ * result to out_host and waits for the stream.  Synchronous.  Pinned host
+ * memory gives the full copy bandwidth; pageable memory is accepted.
+ * in_host == out_host is allowed.
+ */
+FFT2D_API fft2d_status fft2d_exec_host(fft2d_plan_t plan, const void *in_host, void *out_host,
+                             void *stream);
+
+/*
+ * n independent transforms, possibly of different plans (sizes, directions),
+ * issued on one stream: image i is transformed with plans[i] from in[i] to
+ * out[i] (device pointers; in[i] == out[i] allowed).
+ */
+FFT2D_API fft2d_status fft2d_exec_batched(int n, const fft2d_plan_t *plans, const void *const *in,
+                                void *const *out, void *stream);
+
+/*
+ * Host-only: write the rotation-factor table that a plan uploads for an axis
+ * of 2^L points (0 <= L <= 14) into out[0 .. 2*(2^L - 1)), as (re, im) float
+ * pairs.  Stage s (1..L) occupies entries [2^(s-1) - 1, 2^s - 1) and entry
+ * 2^(s-1) - 1 + j holds W_{2^s}^j = exp(-+2*pi*i*j/2^s) (minus sign for
+ * FFT2D_FORWARD), computed in FP64 with exact quarter-turn values and rounded
+ * to FP32 -- the paper's per-stage "secondary texture" (Section 3.1), one row
+ * per stage, compacted to the entries a stage uses.  Needs no GPU.
+ */
+FFT2D_API fft2d_status fft2d_stage_table(int L, int dir, float *out);
+
+/* Static text for a status code. */
+FFT2D_API const char *fft2d_strerror(int status);
+
+/* Text of the calling thread's last CUDA failure ("" if none). */
+FFT2D_API const char *fft2d_last_error(void);
+
+/* ABI version (major * 100 + minor). */
+FFT2D_API int fft2d_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFT2D_H */

@@ -1,0 +1,372 @@
+// fft2d_api.cpp -- the C ABI declared in include/fft2d.h: plans, rotation
+// factor tables, and the two-launch execution of the 2D transform.
+#include "fft2d.h"
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "passes.h"
+
+struct fft2d_plan_s {
+    int rows, cols, Lr, Lc, dtype, dir, device;
+    // Per-stage rotation factors of each axis (stage s: W_{2^s}^j, j < 2^(s-1),
+    // at offset 2^(s-1)-1), already conjugated for the inverse direction.
+    float2 *tw_rows;   // table for the row pass: lines of cols points
+    float2 *tw_cols;   // table for the column pass: lines of rows points
+    void *staging;     // device image buffer for fft2d_exec_host (lazy)
+};
+
+namespace {
+
+thread_local char g_last_error[256] = "";
+
+fft2d_status cuda_fail(cudaError_t e, const char *what)
+{
+    std::snprintf(g_last_error, sizeof g_last_error, "%s: %s", what, cudaGetErrorString(e));
+    return FFT2D_ERR_CUDA;
+}
+
+int log2_exact(int n)
+{
+    int L = 0;
+    while ((1 << L) < n)
+        L++;
+    return L;
+}
+
+// W_M^j = exp(-2*pi*i*j/M) in FP64 with exact symmetry: the angle is reduced
+// to the first octant with integer arithmetic, so quarter turns are exact
+// (1, -i, -1, i) and symmetric entries are bitwise mirror images.
+void twiddle_fp64(long long j, long long M, double *c, double *s)
+{
+    j %= M;
+    // n in [0, M): fold by symmetries of cos/sin of 2*pi*n/M
+    long long n = j;
+    double sgn_s = 1.0, sgn_c = 1.0;
+    bool swap = false;
+    if (2 * n > M) {          // (pi, 2pi): sin negative
+        n = M - n;
+        sgn_s = -1.0;
+    }
+    if (4 * n > M) {          // (pi/2, pi]: cos negative
+        n = M / 2 - n;        // M is even whenever 4n > M can hold with n <= M/2
+        sgn_c = -1.0;
+    }
+    if (8 * n > M) {          // (pi/4, pi/2]: swap cos and sin
+        n = M / 4 - n;
+        swap = true;
+    }
+    double cc, ss;
+    if (n == 0) {
+        cc = 1.0;
+        ss = 0.0;
+    } else {
+        const double ang = 2.0 * 3.14159265358979323846264338327950288 * (double)n / (double)M;
+        cc = std::cos(ang);
+        ss = std::sin(ang);
+    }
+    if (swap) {
+        double t = cc;
+        cc = ss;
+        ss = t;
+    }
+    *c = sgn_c * cc;
+    *s = sgn_s * ss;
+}
+
+// Per-stage table for an axis of 2^L points: N-1 entries.  Forward entries
+// are W = cos(theta) - i sin(theta); inverse entries are the conjugates.
+std::vector<float2> stage_table(int L, int dir)
+{
+    const long long N = 1LL << L;
+    std::vector<float2> t((size_t)(N > 1 ? N - 1 : 1));
+    for (int s = 1; s <= L; s++) {
+        const long long half = 1LL << (s - 1);
+        for (long long j = 0; j < half; j++) {
+            double c, sn;
+            twiddle_fp64(j, 1LL << s, &c, &sn);
+            const double im = (dir == FFT2D_FORWARD) ? -sn : sn;
+            t[(size_t)(half - 1 + j)] = make_float2((float)c, (float)im);
+        }
+    }
+    return t;
+}
+
+fft2d_status check_shape(int rows, int cols)
+{
+    if (rows < 1 || cols < 1 || (rows & (rows - 1)) || (cols & (cols - 1)))
+        return FFT2D_ERR_NOT_POW2;
+    if (rows > FFT2D_MAX_SIDE || cols > FFT2D_MAX_SIDE)
+        return FFT2D_ERR_TOO_LARGE;
+    return FFT2D_OK;
+}
+
+fft2d_status check_device(const fft2d_plan_s *p)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaGetDevice");
+    if (dev != p->device) {
+        std::snprintf(g_last_error, sizeof g_last_error,
+                      "plan belongs to device %d, current device is %d", p->device, dev);
+        return FFT2D_ERR_ARG;
+    }
+    return FFT2D_OK;
+}
+
+// One pass over the image.  nst < 0: all stages of that axis.
+fft2d_status run_pass(const fft2d_plan_s *p, int pass, const void *in, void *out, int nst,
+                      bool allow_scale, cudaStream_t st)
+{
+    fft2d::PassArgs a;
+    a.in = static_cast<const float2 *>(in);
+    a.out = static_cast<float2 *>(out);
+    a.rows = p->rows;
+    a.cols = p->cols;
+    a.ld = p->cols;
+    a.scale = 1.0f;
+    const int L = (pass == FFT2D_PASS_ROWS) ? p->Lc : p->Lr;
+    a.nst = nst < 0 ? L : nst;
+    a.partial = a.nst < L;
+    if (L == 0) {
+        // A length-1 axis is the identity.  The inverse scale is applied by the
+        // other axis's pass (the row pass when rows == 1, see below).
+        if (in != out) {
+            cudaError_t e = cudaMemcpyAsync(out, in, (size_t)p->rows * p->cols * sizeof(float2),
+                                            cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess)
+                return cuda_fail(e, "cudaMemcpyAsync");
+        }
+        return FFT2D_OK;
+    }
+    cudaError_t e;
+    if (pass == FFT2D_PASS_ROWS) {
+        a.tw = p->tw_rows;
+        // inverse of an image with one row: the row pass is the last pass
+        if (p->Lr == 0 && p->dir == FFT2D_INVERSE && allow_scale)
+            a.scale = 1.0f / (float)((double)p->rows * p->cols);
+        e = fft2d::launch_row_pass(L, a, st);
+    } else {
+        a.tw = p->tw_cols;
+        if (p->dir == FFT2D_INVERSE && allow_scale)
+            a.scale = (float)(1.0 / ((double)p->rows * (double)p->cols));
+        e = fft2d::launch_col_pass(L, a, st);
+    }
+    if (e != cudaSuccess)
+        return cuda_fail(e, pass == FFT2D_PASS_ROWS ? "row pass launch" : "column pass launch");
+    return FFT2D_OK;
+}
+
+fft2d_status exec_impl(const fft2d_plan_s *p, const void *in, void *out, int rs, int cs,
+                       cudaStream_t st)
+{
+    const bool full = (rs < 0 || rs == p->Lc) && (cs < 0 || cs == p->Lr);
+    fft2d_status s = run_pass(p, FFT2D_PASS_ROWS, in, out, rs, full, st);
+    if (s != FFT2D_OK)
+        return s;
+    if (p->Lr == 0)
+        return FFT2D_OK;   // one row: nothing along the columns
+    return run_pass(p, FFT2D_PASS_COLS, out, out, cs, full, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int fft2d_version(void) { return 100; }
+
+const char *fft2d_strerror(int status)
+{
+    switch (status) {
+    case FFT2D_OK: return "ok";
+    case FFT2D_ERR_ARG: return "invalid argument";
+    case FFT2D_ERR_NOT_POW2: return "image side is not a power of two";
+    case FFT2D_ERR_TOO_LARGE: return "image side exceeds FFT2D_MAX_SIDE";
+    case FFT2D_ERR_OOM: return "out of memory";
+    case FFT2D_ERR_CUDA: return "CUDA error";
+    case FFT2D_ERR_TIMEOUT: return "bounded device wait timed out";
+    case FFT2D_ERR_BUDGET: return "request exceeds the memory budget";
+    case FFT2D_ERR_UNSUPPORTED: return "not supported by this build";
+    default: return "unknown status";
+    }
+}
+
+const char *fft2d_last_error(void) { return g_last_error; }
+
+fft2d_status fft2d_plan(int rows, int cols, int dtype, int dir, fft2d_plan_t *out)
+{
+    if (!out)
+        return FFT2D_ERR_ARG;
+    *out = nullptr;
+    fft2d_status st = check_shape(rows, cols);
+    if (st != FFT2D_OK)
+        return st;
+    if (dir != FFT2D_FORWARD && dir != FFT2D_INVERSE)
+        return FFT2D_ERR_ARG;
+    if (dtype != FFT2D_C64)
+        return dtype == 1 ? FFT2D_ERR_UNSUPPORTED : FFT2D_ERR_ARG;
+    fft2d_plan_s *p = new (std::nothrow) fft2d_plan_s();
+    if (!p)
+        return FFT2D_ERR_OOM;
+    p->rows = rows;
+    p->cols = cols;
+    p->Lr = log2_exact(rows);
+    p->Lc = log2_exact(cols);
+    p->dtype = dtype;
+    p->dir = dir;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    std::vector<float2> tr = stage_table(p->Lc, dir), tc = stage_table(p->Lr, dir);
+    e = cudaMalloc(&p->tw_rows, tr.size() * sizeof(float2));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&p->tw_cols, tc.size() * sizeof(float2));
+    if (e != cudaSuccess) {
+        cudaFree(p->tw_rows);
+        delete p;
+        cuda_fail(e, "cudaMalloc twiddles");
+        return FFT2D_ERR_OOM;
+    }
+    e = cudaMemcpy(p->tw_rows, tr.data(), tr.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->tw_cols, tc.data(), tc.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(p->tw_rows);
+        cudaFree(p->tw_cols);
+        delete p;
+        return cuda_fail(e, "cudaMemcpy twiddles");
+    }
+    *out = p;
+    return FFT2D_OK;
+}
+
+fft2d_status fft2d_destroy(fft2d_plan_t p)
+{
+    if (!p)
+        return FFT2D_OK;
+    cudaFree(p->tw_rows);
+    cudaFree(p->tw_cols);
+    if (p->staging)
+        cudaFree(p->staging);
+    delete p;
+    return FFT2D_OK;
+}
+
+fft2d_status fft2d_stage_table(int L, int dir, float *out)
+{
+    if (!out || L < 0 || L > 14 || (dir != FFT2D_FORWARD && dir != FFT2D_INVERSE))
+        return FFT2D_ERR_ARG;
+    std::vector<float2> t = stage_table(L, dir);
+    const size_t n = (L > 0) ? ((size_t)1 << L) - 1 : 0;
+    std::memcpy(out, t.data(), n * sizeof(float2));
+    return FFT2D_OK;
+}
+
+fft2d_status fft2d_plan_info(fft2d_plan_t p, int *rows, int *cols, int *dtype, int *dir)
+{
+    if (!p)
+        return FFT2D_ERR_ARG;
+    if (rows)
+        *rows = p->rows;
+    if (cols)
+        *cols = p->cols;
+    if (dtype)
+        *dtype = p->dtype;
+    if (dir)
+        *dir = p->dir;
+    return FFT2D_OK;
+}
+
+fft2d_status fft2d_exec(fft2d_plan_t p, const void *in, void *out, void *stream)
+{
+    if (!p || !in || !out)
+        return FFT2D_ERR_ARG;
+    fft2d_status s = check_device(p);
+    if (s != FFT2D_OK)
+        return s;
+    return exec_impl(p, in, out, -1, -1, static_cast<cudaStream_t>(stream));
+}
+
+fft2d_status fft2d_exec_pass(fft2d_plan_t p, int pass, const void *in, void *out, void *stream)
+{
+    if (!p || !in || !out || (pass != FFT2D_PASS_ROWS && pass != FFT2D_PASS_COLS))
+        return FFT2D_ERR_ARG;
+    fft2d_status s = check_device(p);
+    if (s != FFT2D_OK)
+        return s;
+    return run_pass(p, pass, in, out, -1, true, static_cast<cudaStream_t>(stream));
+}
+
+fft2d_status fft2d_exec_stages(fft2d_plan_t p, const void *in, void *out, int row_stages,
+                               int col_stages, void *stream)
+{
+    if (!p || !in || !out)
+        return FFT2D_ERR_ARG;
+    if (row_stages < 0 || row_stages > p->Lc || col_stages < 0 || col_stages > p->Lr)
+        return FFT2D_ERR_ARG;
+    fft2d_status s = check_device(p);
+    if (s != FFT2D_OK)
+        return s;
+    return exec_impl(p, in, out, row_stages, col_stages, static_cast<cudaStream_t>(stream));
+}
+
+fft2d_status fft2d_exec_host(fft2d_plan_t p, const void *in_host, void *out_host, void *stream)
+{
+    if (!p || !in_host || !out_host)
+        return FFT2D_ERR_ARG;
+    fft2d_status s = check_device(p);
+    if (s != FFT2D_OK)
+        return s;
+    const size_t bytes = (size_t)p->rows * p->cols * sizeof(float2);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!p->staging) {
+        cudaError_t e = cudaMalloc(&p->staging, bytes);
+        if (e != cudaSuccess) {
+            p->staging = nullptr;
+            cuda_fail(e, "cudaMalloc staging");
+            return FFT2D_ERR_OOM;
+        }
+    }
+    cudaError_t e = cudaMemcpyAsync(p->staging, in_host, bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync H2D");
+    s = exec_impl(p, p->staging, p->staging, -1, -1, st);
+    if (s != FFT2D_OK)
+        return s;
+    e = cudaMemcpyAsync(out_host, p->staging, bytes, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync D2H");
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaStreamSynchronize");
+    return FFT2D_OK;
+}
+
+fft2d_status fft2d_exec_batched(int n, const fft2d_plan_t *plans, const void *const *in,
+                                void *const *out, void *stream)
+{
+    if (n < 0 || (n > 0 && (!plans || !in || !out)))
+        return FFT2D_ERR_ARG;
+    for (int i = 0; i < n; i++)
+        if (!plans[i] || !in[i] || !out[i])
+            return FFT2D_ERR_ARG;
+    for (int i = 0; i < n; i++) {
+        fft2d_status s = check_device(plans[i]);
+        if (s != FFT2D_OK)
+            return s;
+        s = exec_impl(plans[i], in[i], out[i], -1, -1, static_cast<cudaStream_t>(stream));
+        if (s != FFT2D_OK)
+            return s;
+    }
+    return FFT2D_OK;
+}
+
+}  // extern "C"

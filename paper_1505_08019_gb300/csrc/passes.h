@@ -1,0 +1,28 @@
+// passes.h -- host-side entry points of the row and column pass kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace fft2d {
+
+// Arguments common to both passes (complex64 storage, FP32 arithmetic).
+struct PassArgs {
+    const float2 *in;    // device, first pixel of the image
+    float2 *out;         // device, may equal in
+    const float2 *tw;    // device, per-stage rotation factors of this axis
+    int rows, cols;      // image shape
+    long long ld;        // row pitch in pixels (== cols for a dense image)
+    float scale;         // multiplies every stored value (1 or 1/(rows*cols))
+    int nst;             // stages to run on this axis (partial debug view)
+    bool partial;        // nst < log2(axis length)
+};
+
+// Lines per CTA of the row pass and interleaved columns per CTA of the
+// column pass for an axis of 2^L points.
+int row_lines_per_cta(int L);
+int col_width(int L);
+
+cudaError_t launch_row_pass(int L, const PassArgs &a, cudaStream_t s);
+cudaError_t launch_col_pass(int L, const PassArgs &a, cudaStream_t s);
+
+}  // namespace fft2d

@@ -1,0 +1,215 @@
+"""ctypes binding of ``libfft2d.so`` (the C ABI in ``include/fft2d.h``).
+
+Argument marshalling only: every function below forwards to the C entry
+point of the same name; all the work runs in the library's CUDA kernels.
+Device buffers may be given as torch tensors (contiguous, complex64, on the
+plan's device) or as raw integer device pointers.  A stream may be a
+``torch.cuda.Stream``, a raw ``cudaStream_t`` integer, or ``None`` for the
+current torch stream of the current device.
+
+If the library has not been built, importing this module raises
+``ImportError``: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libfft2d.so")
+
+FFT2D_C64 = 0
+FFT2D_FORWARD = -1
+FFT2D_INVERSE = 1
+FFT2D_PASS_ROWS = 0
+FFT2D_PASS_COLS = 1
+FFT2D_MAX_SIDE = 16384
+
+FFT2D_OK = 0
+FFT2D_ERR_ARG = 1
+FFT2D_ERR_NOT_POW2 = 2
+FFT2D_ERR_TOO_LARGE = 3
+FFT2D_ERR_OOM = 4
+FFT2D_ERR_CUDA = 5
+FFT2D_ERR_TIMEOUT = 6
+FFT2D_ERR_BUDGET = 7
+FFT2D_ERR_UNSUPPORTED = 8
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"fft2d CUDA library not built ({LIB_PATH} missing); run "
+        "`python -c 'import __graft_entry__ as g; g.build()'` or "
+        "`python paper_1505_08019_gb300/build.py`")
+
+lib = ctypes.CDLL(LIB_PATH)
+
+_P, _I = ctypes.c_void_p, ctypes.c_int
+_sigs = {
+    "fft2d_plan": ([_I, _I, _I, _I, ctypes.POINTER(ctypes.c_void_p)], _I),
+    "fft2d_destroy": ([_P], _I),
+    "fft2d_plan_info": ([_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                         ctypes.POINTER(_I)], _I),
+    "fft2d_exec": ([_P, _P, _P, _P], _I),
+    "fft2d_exec_pass": ([_P, _I, _P, _P, _P], _I),
+    "fft2d_exec_stages": ([_P, _P, _P, _I, _I, _P], _I),
+    "fft2d_exec_host": ([_P, _P, _P, _P], _I),
+    "fft2d_exec_batched": ([_I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
+                           _I),
+    "fft2d_stage_table": ([_I, _I, _P], _I),
+    "fft2d_strerror": ([_I], ctypes.c_char_p),
+    "fft2d_last_error": ([], ctypes.c_char_p),
+    "fft2d_version": ([], _I),
+}
+for _name, (_args, _res) in _sigs.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+class FFT2DError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib.fft2d_strerror(status).decode()
+        detail = lib.fft2d_last_error().decode()
+        super().__init__(f"{where}: {msg} (status {status})" + (f" [{detail}]" if detail else ""))
+
+
+def _check(status: int, where: str) -> None:
+    if status != FFT2D_OK:
+        raise FFT2DError(status, where)
+
+
+def _dptr(x) -> int:
+    """Device pointer of a torch tensor (checked) or a raw integer."""
+    if isinstance(x, int):
+        return x
+    if not x.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not x.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return x.data_ptr()
+
+
+def _hptr(x) -> int:
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if x.is_cuda:
+            raise ValueError("expected a host tensor")
+        if not x.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return x.data_ptr()
+    return x.ctypes.data   # numpy array
+
+
+def _stream(s) -> int:
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+# ---------------------------------------------------------------- C ABI mirror
+def fft2d_plan(rows: int, cols: int, dtype: int = FFT2D_C64, dir: int = FFT2D_FORWARD) -> int:
+    h = ctypes.c_void_p()
+    _check(lib.fft2d_plan(rows, cols, dtype, dir, ctypes.byref(h)), "fft2d_plan")
+    return h.value
+
+
+def fft2d_destroy(plan: int) -> None:
+    _check(lib.fft2d_destroy(plan), "fft2d_destroy")
+
+
+def fft2d_plan_info(plan: int) -> tuple[int, int, int, int]:
+    r, c, d, s = _I(), _I(), _I(), _I()
+    _check(lib.fft2d_plan_info(plan, ctypes.byref(r), ctypes.byref(c), ctypes.byref(d),
+                               ctypes.byref(s)), "fft2d_plan_info")
+    return r.value, c.value, d.value, s.value
+
+
+def fft2d_exec(plan: int, inp, out, stream=None) -> None:
+    _check(lib.fft2d_exec(plan, _dptr(inp), _dptr(out), _stream(stream)), "fft2d_exec")
+
+
+def fft2d_exec_pass(plan: int, pass_: int, inp, out, stream=None) -> None:
+    _check(lib.fft2d_exec_pass(plan, pass_, _dptr(inp), _dptr(out), _stream(stream)),
+           "fft2d_exec_pass")
+
+
+def fft2d_exec_stages(plan: int, inp, out, row_stages: int, col_stages: int,
+                      stream=None) -> None:
+    _check(lib.fft2d_exec_stages(plan, _dptr(inp), _dptr(out), row_stages, col_stages,
+                                 _stream(stream)), "fft2d_exec_stages")
+
+
+def fft2d_exec_host(plan: int, inp_host, out_host, stream=None) -> None:
+    _check(lib.fft2d_exec_host(plan, _hptr(inp_host), _hptr(out_host), _stream(stream)),
+           "fft2d_exec_host")
+
+
+def fft2d_exec_batched(plans, inps, outs, stream=None) -> None:
+    n = len(plans)
+    if len(inps) != n or len(outs) != n:
+        raise ValueError("plans, inputs and outputs must have the same length")
+    arr = ctypes.c_void_p * max(n, 1)
+    P = arr(*plans)
+    I_ = arr(*[_dptr(x) for x in inps])
+    O_ = arr(*[_dptr(x) for x in outs])
+    _check(lib.fft2d_exec_batched(n, P, I_, O_, _stream(stream)), "fft2d_exec_batched")
+
+
+def fft2d_stage_table(L: int, dir: int = FFT2D_FORWARD):
+    """The per-stage rotation-factor table a plan uploads (numpy complex64)."""
+    import numpy as np
+    n = (1 << L) - 1
+    out = np.zeros(max(n, 1), dtype=np.complex64)
+    _check(lib.fft2d_stage_table(L, dir, out.ctypes.data), "fft2d_stage_table")
+    return out[:n]
+
+
+def fft2d_strerror(status: int) -> str:
+    return lib.fft2d_strerror(status).decode()
+
+
+def fft2d_last_error() -> str:
+    return lib.fft2d_last_error().decode()
+
+
+def fft2d_version() -> int:
+    return lib.fft2d_version()
+
+
+# ------------------------------------------------------------ convenience
+class Plan:
+    """Owning wrapper of an fft2d plan handle."""
+
+    def __init__(self, rows: int, cols: int, dir: int = FFT2D_FORWARD, dtype: int = FFT2D_C64):
+        self.rows, self.cols, self.dir, self.dtype = rows, cols, dir, dtype
+        self.handle = fft2d_plan(rows, cols, dtype, dir)
+
+    def __call__(self, inp, out=None, stream=None):
+        """Transform device tensor ``inp`` into ``out`` (new tensor if None)."""
+        if out is None:
+            import torch
+            out = torch.empty_like(inp)
+        fft2d_exec(self.handle, inp, out, stream)
+        return out
+
+    def close(self):
+        if self.handle:
+            fft2d_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

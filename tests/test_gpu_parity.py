@@ -1,0 +1,249 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerance (the accuracy target for the FP32 complex64 path): relative L2
+error <= 1e-5 against the FP64 oracle on the same seeded input.  Integer and
+permutation work (scramble-only and exactly representable stages) must be
+bit-exact.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def env(orc):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1505_08019_gb300 import build
+    build.build()
+    import paper_1505_08019_gb300 as fft
+    return torch, fft, orc
+
+
+def rel(a, b):
+    a = np.asarray(a, np.complex128)
+    b = np.asarray(b, np.complex128)
+    d = np.linalg.norm(b.ravel())
+    return float(np.linalg.norm((a - b).ravel()) / (d if d > 0 else 1.0))
+
+
+def gpu_fft(env, x, direction, inplace=False, stages=None):
+    torch, fft, _ = env
+    R, C = x.shape
+    plan = fft.fft2d_plan(R, C, fft.FFT2D_C64, direction)
+    try:
+        dx = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        out = dx if inplace else torch.empty_like(dx)
+        if stages is None:
+            fft.fft2d_exec(plan, dx, out)
+        else:
+            fft.fft2d_exec_stages(plan, dx, out, stages[0], stages[1])
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+    finally:
+        fft.fft2d_destroy(plan)
+
+
+def report(name, err):
+    print(f"[parity] {name}: rel_l2={err:.3e}")
+
+
+# ------------------------------------------------------------------ configs
+def test_256_gray_forward(env):
+    """256x256, real part U[0,1), imaginary 0, forward, plain path."""
+    _, _, orc = env
+    x = synth.uniform_real(256, 256, seed=0)
+    got = gpu_fft(env, x, -1)
+    want = orc.fft2d(x)
+    err = rel(got, want)
+    report("256x256 fwd", err)
+    assert err <= TOL
+    # crops of the input through the direct double sum (eq. 1): the GPU's
+    # 16x16 transform of the crop must match too
+    for r0, c0 in ((0, 0), (120, 120)):
+        crop = np.ascontiguousarray(x[r0:r0 + 16, c0:c0 + 16])
+        assert rel(gpu_fft(env, crop, -1), orc.dft2d(crop)) <= TOL
+
+
+@pytest.mark.parametrize("side", [1024, 4096])
+def test_blob_forward_inverse(env, side):
+    """Forward + inverse on the Gaussian-blob image at the paper's size and at
+    4096x4096 (the benchmarked workload), whole outputs compared."""
+    _, _, orc = env
+    x = synth.blob_image(side, side, seed=0)
+    X = gpu_fft(env, x, -1)
+    Xo = orc.fft2d(x, threads=16)
+    e_fwd = rel(X, Xo)
+    y = gpu_fft(env, X, 1)
+    e_inv = rel(y, orc.fft2d(X, inverse=True, threads=16))
+    e_rt = rel(y, x)
+    report(f"{side}^2 fwd", e_fwd)
+    report(f"{side}^2 inv(of gpu fwd)", e_inv)
+    report(f"{side}^2 round trip", e_rt)
+    assert e_fwd <= TOL and e_inv <= TOL and e_rt <= TOL
+
+
+SHAPES = [(1, 1), (1, 2), (2, 1), (2, 2), (4, 8), (8, 4), (16, 16), (32, 64), (64, 32),
+          (128, 256), (256, 128), (512, 512), (2048, 128), (128, 2048), (256, 1024),
+          (1024, 256), (2048, 2048), (16, 4096), (4096, 16), (64, 8192), (8192, 64),
+          (16, 16384), (16384, 16), (1, 4096), (4096, 1), (2, 16384), (16384, 2)]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"{s[0]}x{s[1]}")
+def test_shapes_both_directions(env, shape):
+    _, _, orc = env
+    R, C = shape
+    x = synth.uniform_complex(R, C, seed=R * 7 + C)
+    for d, inv in ((-1, False), (1, True)):
+        err = rel(gpu_fft(env, x, d), orc.fft2d(x, inverse=inv, threads=8))
+        report(f"{R}x{C} {'inv' if inv else 'fwd'}", err)
+        assert err <= TOL
+
+
+# ---------------------------------------------------------- bit-exact plumbing
+@pytest.mark.parametrize("shape", [(8, 8), (64, 256), (512, 32), (4096, 4096), (16, 16384)],
+                         ids=lambda s: f"{s[0]}x{s[1]}")
+def test_scramble_only_is_exact_permutation(env, shape):
+    """Zero butterfly stages: the fused scramble alone (Section 3.2) must equal
+    the oracle's bit-reversal permutation bit for bit."""
+    _, _, orc = env
+    R, C = shape
+    x = synth.uniform_complex(R, C, seed=5)
+    got = gpu_fft(env, x, -1, stages=(0, 0))
+    want = orc.fft2d(x, row_stages=0, col_stages=0).astype(np.complex64)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("shape,stages", [((16, 16), (2, 2)), ((256, 64), (1, 2)),
+                                          ((1024, 1024), (2, 1)), ((64, 4096), (2, 2)),
+                                          ((4096, 4096), (2, 2)), ((4, 4), (2, 2)),
+                                          ((2, 4), (2, 1))])
+def test_exact_stages_on_integers(env, shape, stages):
+    """Stages 1-2 use only the rotation factors 1 and -i; on small-integer
+    images every sum is exact in FP32, so the GPU must match the oracle bit
+    for bit (this checks the scramble, the pairing of every butterfly, the
+    stage order and the position order of partial results)."""
+    _, _, orc = env
+    R, C = shape
+    x = synth.integer_image(R, C, seed=9)
+    rs, cs = min(stages[0], C.bit_length() - 1), min(stages[1], R.bit_length() - 1)
+    got = gpu_fft(env, x, -1, stages=(rs, cs))
+    want = orc.fft2d(x, row_stages=rs, col_stages=cs)
+    assert np.array_equal(got.astype(np.complex128), want)
+
+
+@pytest.mark.parametrize("shape,stages", [((64, 128), (3, 5)), ((2048, 256), (7, 4)),
+                                          ((4096, 4096), (9, 10)), ((32, 16384), (13, 2))])
+def test_partial_stages_match_oracle(env, shape, stages):
+    _, _, orc = env
+    R, C = shape
+    x = synth.uniform_complex(R, C, seed=3)
+    got = gpu_fft(env, x, -1, stages=stages)
+    want = orc.fft2d(x, row_stages=stages[0], col_stages=stages[1], threads=8)
+    assert rel(got, want) <= TOL
+
+
+# --------------------------------------------------------------- API plumbing
+def test_inplace_equals_out_of_place(env):
+    x = synth.uniform_complex(1024, 512, seed=1)
+    a = gpu_fft(env, x, -1)
+    b = gpu_fft(env, x, -1, inplace=True)
+    assert np.array_equal(a, b)
+
+
+def test_passes_compose_to_exec_and_runs_are_deterministic(env):
+    torch, fft, _ = env
+    x = torch.from_numpy(synth.blob_image(2048, 1024, seed=2)).cuda()
+    plan = fft.fft2d_plan(2048, 1024, fft.FFT2D_C64, fft.FFT2D_INVERSE)
+    try:
+        a = torch.empty_like(x)
+        b = torch.empty_like(x)
+        fft.fft2d_exec(plan, x, a)
+        fft.fft2d_exec_pass(plan, fft.FFT2D_PASS_ROWS, x, b)
+        fft.fft2d_exec_pass(plan, fft.FFT2D_PASS_COLS, b, b)
+        c = torch.empty_like(x)
+        fft.fft2d_exec(plan, x, c)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
+        assert torch.equal(a, c)
+    finally:
+        fft.fft2d_destroy(plan)
+
+
+def test_exec_host_matches_device_exec(env):
+    torch, fft, _ = env
+    x = synth.uniform_real(512, 2048, seed=4)
+    want = gpu_fft(env, x, -1)
+    plan = fft.fft2d_plan(512, 2048, fft.FFT2D_C64, fft.FFT2D_FORWARD)
+    try:
+        hin = torch.from_numpy(x).pin_memory()
+        hout = torch.empty_like(hin).pin_memory()
+        fft.fft2d_exec_host(plan, hin, hout)
+        assert np.array_equal(hout.numpy(), want)
+        # pageable numpy buffers, in place
+        buf = x.copy()
+        fft.fft2d_exec_host(plan, buf, buf)
+        assert np.array_equal(buf, want)
+    finally:
+        fft.fft2d_destroy(plan)
+
+
+def test_batched_uneven_equals_solo(env):
+    torch, fft, _ = env
+    shapes = synth.batch_shapes(12, seed=0)
+    imgs = synth.batch_images(shapes, seed=0)
+    plans = [fft.fft2d_plan(r, c, fft.FFT2D_C64, fft.FFT2D_FORWARD) for r, c in shapes]
+    try:
+        ins = [torch.from_numpy(im).cuda() for im in imgs]
+        outs = [torch.empty_like(t) for t in ins]
+        fft.fft2d_exec_batched(plans, ins, outs)
+        torch.cuda.synchronize()
+        for im, o in zip(imgs, outs):
+            assert np.array_equal(o.cpu().numpy(), gpu_fft(env, im, -1))
+        fft.fft2d_exec_batched([], [], [])
+    finally:
+        for p in plans:
+            fft.fft2d_destroy(p)
+
+
+def test_errors_are_reported_not_launched(env):
+    torch, fft, _ = env
+    plan = fft.fft2d_plan(64, 64, fft.FFT2D_C64, fft.FFT2D_FORWARD)
+    try:
+        x = torch.zeros(64, 64, dtype=torch.complex64, device="cuda")
+        with pytest.raises(fft.FFT2DError):
+            fft.fft2d_exec_stages(plan, x, x, 7, 0)          # 7 > log2(64)
+        with pytest.raises(fft.FFT2DError):
+            fft.fft2d_exec_pass(plan, 5, x, x)
+        assert fft.fft2d_plan_info(plan) == (64, 64, 0, -1)
+    finally:
+        fft.fft2d_destroy(plan)
+
+
+def test_16384_square_properties(env):
+    """16384x16384 (2 GiB per buffer): round trip and Parseval hold at any size."""
+    torch, fft, _ = env
+    R = C = 16384
+    x = torch.from_numpy(synth.uniform_complex(R, C, seed=8)).cuda()
+    pf = fft.fft2d_plan(R, C, fft.FFT2D_C64, fft.FFT2D_FORWARD)
+    pi = fft.fft2d_plan(R, C, fft.FFT2D_C64, fft.FFT2D_INVERSE)
+    try:
+        X = torch.empty_like(x)
+        fft.fft2d_exec(pf, x, X)
+        px = (x.abs().double() ** 2).sum().item()
+        pX = (X.abs().double() ** 2).sum().item() / (R * C)
+        assert abs(px - pX) <= 1e-5 * px
+        y = torch.empty_like(x)
+        fft.fft2d_exec(pi, X, y)
+        err = ((y - x).abs().double().norm() / x.abs().double().norm()).item()
+        report("16384^2 round trip", err)
+        assert err <= TOL
+    finally:
+        fft.fft2d_destroy(pf)
+        fft.fft2d_destroy(pi)
