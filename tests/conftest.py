@@ -20,3 +20,13 @@ def pytest_configure(config):
 def orc():
     from oracle import oracle
     return oracle.get()
+
+
+def build_lib():
+    """Build libfft2d.so (if stale) without importing the package first."""
+    import importlib.util
+    path = os.path.join(ROOT, "paper_1505_08019_gb300", "build.py")
+    spec = importlib.util.spec_from_file_location("_fft2d_build", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod.build()

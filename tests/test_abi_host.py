@@ -12,8 +12,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="session")
 def fft():
-    from paper_1505_08019_gb300 import build
-    build.build()
+    from conftest import build_lib
+    build_lib()
     import paper_1505_08019_gb300 as fft
     return fft
 

@@ -20,8 +20,8 @@ def env(orc):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    from paper_1505_08019_gb300 import build
-    build.build()
+    from conftest import build_lib
+    build_lib()
     import paper_1505_08019_gb300 as fft
     return torch, fft, orc
 
