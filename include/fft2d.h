@@ -87,6 +87,24 @@ typedef enum {
  */
 FFT2D_API fft2d_status fft2d_plan(int rows, int cols, int dtype, int dir, fft2d_plan_t *out);
 
+/*
+ * Wait for all work on the device, then report device-side failures of this
+ * plan's kernels since the last call: FFT2D_ERR_TIMEOUT when a bounded wait
+ * inside a kernel (a TMA transfer that never completed) gave up, in which
+ * case that launch's output is incomplete.  Clears the status.  A CUDA error
+ * of the context is returned as FFT2D_ERR_CUDA.
+ */
+FFT2D_API fft2d_status fft2d_sync_status(fft2d_plan_t plan);
+
+/*
+ * Self-test of the device failure path: one small kernel waits on an mbarrier
+ * phase that nothing completes, gives up after about 20 ms with the same
+ * bounded wait the TMA pipeline uses, and records the timeout in the plan's
+ * status word, which the next fft2d_sync_status reports as FFT2D_ERR_TIMEOUT.
+ * Touches no image data and leaves the context usable.  Asynchronous.
+ */
+FFT2D_API fft2d_status fft2d_selftest_timeout(fft2d_plan_t plan, void *stream);
+
 /* Release a plan and everything it owns.  NULL is accepted (no-op). */
 FFT2D_API fft2d_status fft2d_destroy(fft2d_plan_t plan);
 

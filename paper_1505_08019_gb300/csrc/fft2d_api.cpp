@@ -19,6 +19,7 @@ struct fft2d_plan_s {
     float2 *tw_rows;   // table for the row pass: lines of cols points
     float2 *tw_cols;   // table for the column pass: lines of rows points
     void *staging;     // device image buffer for fft2d_exec_host (lazy)
+    int *dev_err;      // device status word set by bounded waits in the kernels
 };
 
 namespace {
@@ -131,6 +132,7 @@ fft2d_status run_pass(const fft2d_plan_s *p, int pass, const void *in, void *out
     a.cols = p->cols;
     a.ld = p->cols;
     a.scale = 1.0f;
+    a.err = p->dev_err;
     const int L = (pass == FFT2D_PASS_ROWS) ? p->Lc : p->Lr;
     a.nst = nst < 0 ? L : nst;
     a.partial = a.nst < L;
@@ -235,12 +237,23 @@ fft2d_status fft2d_plan(int rows, int cols, int dtype, int dir, fft2d_plan_t *ou
         cuda_fail(e, "cudaMalloc twiddles");
         return FFT2D_ERR_OOM;
     }
-    e = cudaMemcpy(p->tw_rows, tr.data(), tr.size() * sizeof(float2), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(p->tw_cols, tc.data(), tc.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    e = cudaMalloc(&p->dev_err, sizeof(int));
     if (e != cudaSuccess) {
         cudaFree(p->tw_rows);
         cudaFree(p->tw_cols);
+        delete p;
+        cuda_fail(e, "cudaMalloc status word");
+        return FFT2D_ERR_OOM;
+    }
+    e = cudaMemcpy(p->tw_rows, tr.data(), tr.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->tw_cols, tc.data(), tc.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemset(p->dev_err, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaFree(p->tw_rows);
+        cudaFree(p->tw_cols);
+        cudaFree(p->dev_err);
         delete p;
         return cuda_fail(e, "cudaMemcpy twiddles");
     }
@@ -254,9 +267,45 @@ fft2d_status fft2d_destroy(fft2d_plan_t p)
         return FFT2D_OK;
     cudaFree(p->tw_rows);
     cudaFree(p->tw_cols);
+    cudaFree(p->dev_err);
     if (p->staging)
         cudaFree(p->staging);
     delete p;
+    return FFT2D_OK;
+}
+
+fft2d_status fft2d_selftest_timeout(fft2d_plan_t p, void *stream)
+{
+    if (!p)
+        return FFT2D_ERR_ARG;
+    fft2d_status s = check_device(p);
+    if (s != FFT2D_OK)
+        return s;
+    cudaError_t e = fft2d::launch_selftest_timeout(p->dev_err, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess)
+        return cuda_fail(e, "self-test launch");
+    return FFT2D_OK;
+}
+
+fft2d_status fft2d_sync_status(fft2d_plan_t p)
+{
+    if (!p)
+        return FFT2D_ERR_ARG;
+    fft2d_status s = check_device(p);
+    if (s != FFT2D_OK)
+        return s;
+    int h = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = cudaMemcpy(&h, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "fft2d_sync_status");
+    if (h != 0) {
+        cudaMemset(p->dev_err, 0, sizeof(int));
+        std::snprintf(g_last_error, sizeof g_last_error,
+                      "a bounded device wait gave up (code %d)", h);
+        return FFT2D_ERR_TIMEOUT;
+    }
     return FFT2D_OK;
 }
 

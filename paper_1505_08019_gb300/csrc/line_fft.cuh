@@ -32,8 +32,11 @@
 //    a group after the first, lanes read consecutive entries.
 #pragma once
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include "async_copy.cuh"
 
 namespace fft2d {
 
@@ -44,6 +47,17 @@ __host__ __device__ constexpr int brev_c(int v, int bits)
         if (v & (1 << b))
             r |= 1 << (bits - 1 - b);
     return r;
+}
+
+// Image data is read exactly once: keep it out of L1 so that the rotation
+// factor table, which every CTA re-reads, stays resident there.
+__device__ __forceinline__ float2 ld_stream(const float2 *p)
+{
+    float2 v;
+    asm volatile("ld.global.L1::no_allocate.v2.f32 {%0, %1}, [%2];"
+                 : "=f"(v.x), "=f"(v.y)
+                 : "l"(p));
+    return v;
 }
 
 __device__ __forceinline__ int brev_rt(int v, int bits)
@@ -65,19 +79,27 @@ struct LineCfg {
     static constexpr int K = KW >= 4 ? 0 : 4 - KW;
     static constexpr bool SWZ = K > 0 && L >= 2 * K;
     static constexpr int SMEM_BYTES = NG > 1 ? E * 8 : 0;
+    // resident CTAs per SM asked of the register allocator (64 registers a
+    // thread for CTAs of up to 256 threads)
+    static constexpr int MINB = T <= 256 ? 4 : (T <= 512 ? 2 : 1);
     static_assert(L >= 1 && L <= 14, "line length out of range");
     static_assert(E >= 16, "CTA must hold at least 16 values");
 };
 
-// Group GI of the stage groups: bits [S0, S0 + G) of p.
-template <class C, int GI>
-struct Grp {
-    static constexpr int S0 = 4 * GI;
-    static constexpr int G = (C::L - S0) < 4 ? (C::L - S0) : 4;
+// A group of G consecutive stages S0+1 .. S0+G (bits [S0, S0 + G) of p) on
+// lines of 2^L points.
+template <int L, int S0_, int G_>
+struct GrpSG {
+    static constexpr int S0 = S0_;
+    static constexpr int G = G_;
     static constexpr int R = 1 << G;             // values per unit
     static constexpr int V = 16 / R;             // units per thread
-    static constexpr int HB = C::L - S0 - G;     // bits above the group
+    static constexpr int HB = L - S0 - G;        // bits above the group
 };
+
+// Group GI of the stage groups of a CTA config: bits [4 GI, 4 GI + G).
+template <class C, int GI>
+struct Grp : GrpSG<C::L, 4 * GI, ((C::L - 4 * GI) < 4 ? (C::L - 4 * GI) : 4)> {};
 
 // Shared-memory slot of (line block lb, position p, interleaved line w).
 template <class C>
@@ -91,11 +113,10 @@ __device__ __forceinline__ int sidx(int lb, int p, int w)
 
 // Stages S0+1 .. S0+G on unit v of a[]: pairs (r, r + 2^t) at stage S0+1+t use
 // W_{2^s}^j with j = lo + (r mod 2^t) 2^S0.
-template <class C, int GI, bool GENERIC>
-__device__ __forceinline__ void run_stages(float2 (&a)[16], int v, int lo,
-                                           const float2 *__restrict__ tw, int nst)
+template <class Gp, bool FIRST, bool GENERIC>
+__device__ __forceinline__ void run_stages_g(float2 (&a)[16], int v, int lo,
+                                             const float2 *__restrict__ tw, int nst)
 {
-    using Gp = Grp<C, GI>;
 #pragma unroll
     for (int t = 0; t < Gp::G; t++) {
         const int s = Gp::S0 + 1 + t;
@@ -110,7 +131,7 @@ __device__ __forceinline__ void run_stages(float2 (&a)[16], int v, int lo,
             float2 &x0 = a[v * Gp::R + r];
             float2 &x1 = a[v * Gp::R + (r | (1 << t))];
             float2 m;
-            if (GI == 0 && jc == 0) {
+            if (FIRST && jc == 0) {
                 m = x1;   // W = 1
             } else {
                 const float2 w = __ldg(tws + lo + jc);
@@ -121,6 +142,13 @@ __device__ __forceinline__ void run_stages(float2 (&a)[16], int v, int lo,
             x0 = make_float2(x0.x + m.x, x0.y + m.y);
         }
     }
+}
+
+template <class C, int GI, bool GENERIC>
+__device__ __forceinline__ void run_stages(float2 (&a)[16], int v, int lo,
+                                           const float2 *__restrict__ tw, int nst)
+{
+    run_stages_g<Grp<C, GI>, GI == 0, GENERIC>(a, v, lo, tw, nst);
 }
 
 // Group 0: scrambled global load, first stages, then either the final store
@@ -145,7 +173,7 @@ __device__ __forceinline__ void group_first(float2 (&a)[16], float2 *sm, const f
 #pragma unroll
         for (int r = 0; r < Gp::R; r++) {
             const int off = brev_c(r, Gp::G) << Gp::HB;
-            a[v * Gp::R + r] = ok ? src[ROW ? (long long)off : (long long)off * ld]
+            a[v * Gp::R + r] = ok ? ld_stream(src + (ROW ? (long long)off : (long long)off * ld))
                                   : make_float2(0.f, 0.f);
         }
     }
@@ -182,7 +210,10 @@ __device__ __forceinline__ void group_first(float2 (&a)[16], float2 *sm, const f
 
 // Group GI >= 1: read units from shared memory, run the group's stages, then
 // write back in place (middle group) or store to global memory (last group).
-template <class C, int GI, bool ROW, bool GENERIC>
+// With TO_SMEM the last group does not store to global memory: it leaves the
+// finished lines in shared memory in natural order, slot k*W + w (used by the
+// cluster column pass, whose last stages run across CTAs).
+template <class C, int GI, bool ROW, bool GENERIC, bool TO_SMEM = false>
 __device__ __forceinline__ void group_smem(float2 (&a)[16], float2 *sm, float2 *out,
                                            const float2 *__restrict__ tw, long long ld,
                                            float scale, int nst, long long nvalid)
@@ -208,6 +239,11 @@ __device__ __forceinline__ void group_smem(float2 (&a)[16], float2 *sm, float2 *
         const int lo = (u >> C::KW) & ((1 << Gp::S0) - 1);
         run_stages<C, GI, GENERIC>(a, v, lo, tw, nst);
     }
+    if constexpr (LAST && TO_SMEM) {
+        // the natural-order slots differ from the swizzled ones just read
+        if constexpr (C::SWZ)
+            __syncthreads();
+    }
 #pragma unroll
     for (int v = 0; v < Gp::V; v++) {
         const int u = tid + v * C::T;
@@ -216,7 +252,11 @@ __device__ __forceinline__ void group_smem(float2 (&a)[16], float2 *sm, float2 *
         const int lo = u2 & ((1 << Gp::S0) - 1);
         const int hi = (u2 >> Gp::S0) & ((1 << Gp::HB) - 1);
         const int lb = u2 >> (Gp::S0 + Gp::HB);
-        if constexpr (LAST) {
+        if constexpr (LAST && TO_SMEM) {
+#pragma unroll
+            for (int r = 0; r < Gp::R; r++)
+                sm[((lo | (r << Gp::S0)) << C::KW) | w] = a[v * Gp::R + r];
+        } else if constexpr (LAST) {
             const bool ok = !GENERIC || (ROW ? lb < nvalid : w < nvalid);
             if (ok) {
                 float2 *dst = ROW ? out + (long long)lb * ld + lo : out + (long long)lo * ld + w;
@@ -265,7 +305,7 @@ __device__ __forceinline__ void line_fft(const float2 *in, float2 *out,
 
 // Row pass: CTA b transforms rows [b*LB, b*LB + LB).  ld = row pitch.
 template <class C, bool GENERIC>
-__global__ void __launch_bounds__(C::T) row_pass_kernel(const float2 *in, float2 *out,
+__global__ void __launch_bounds__(C::T, C::MINB) row_pass_kernel(const float2 *in, float2 *out,
                                                         const float2 *__restrict__ tw,
                                                         int rows, long long ld, float scale,
                                                         int nst)
@@ -277,13 +317,268 @@ __global__ void __launch_bounds__(C::T) row_pass_kernel(const float2 *in, float2
 // Column pass: CTA b transforms columns [b*W, b*W + W), each of `rows`=2^L
 // points spaced ld apart.
 template <class C, bool GENERIC>
-__global__ void __launch_bounds__(C::T) col_pass_kernel(const float2 *in, float2 *out,
+__global__ void __launch_bounds__(C::T, C::MINB) col_pass_kernel(const float2 *in, float2 *out,
                                                         const float2 *__restrict__ tw,
                                                         int cols, long long ld, float scale,
                                                         int nst)
 {
     const long long c0 = (long long)blockIdx.x * C::W;
     line_fft<C, false, GENERIC>(in + c0, out + c0, tw, ld, scale, nst, cols - c0);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent column pass fed by TMA.
+//
+// One CTA per SM walks over column tiles (W adjacent whole columns).  Each
+// tile arrives in shared memory by TMA tensor loads (boxes of W x 256 rows),
+// in natural order; group 0 gathers it in scrambled order straight from
+// there (the fused scramble), the tile is then reused as the exchange buffer,
+// and as soon as the last group has read its values into registers the TMA
+// load of the CTA's next tile is issued, so that transfer overlaps the last
+// stages and the stores of the current tile.
+
+// Group 0 from a natural-order tile in shared memory, slot i*W + w for line
+// element i of interleaved line w; ends with the swizzled exchange layout in
+// the same buffer.
+template <class C, bool GENERIC>
+__device__ __forceinline__ void group_first_smem(float2 (&a)[16], float2 *sm,
+                                                 const float2 *__restrict__ tw, int nst)
+{
+    using Gp = Grp<C, 0>;
+    static_assert(C::NG >= 2 && C::LB == 1, "tile engine needs two groups, one line block");
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int v = 0; v < Gp::V; v++) {
+        const int u = tid + v * C::T;
+        const int w = u & (C::W - 1);
+        const int hib = (u >> C::KW) & ((1 << Gp::HB) - 1);
+#pragma unroll
+        for (int r = 0; r < Gp::R; r++) {
+            const int i = (brev_c(r, Gp::G) << Gp::HB) | hib;
+            a[v * Gp::R + r] = sm[(i << C::KW) | w];
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < Gp::V; v++)
+        run_stages<C, 0, GENERIC>(a, v, 0, tw, nst);
+    __syncthreads();   // every natural-order slot has been read
+#pragma unroll
+    for (int v = 0; v < Gp::V; v++) {
+        const int u = tid + v * C::T;
+        const int w = u & (C::W - 1);
+        const int hib = (u >> C::KW) & ((1 << Gp::HB) - 1);
+        const int hi = brev_rt(hib, Gp::HB);
+#pragma unroll
+        for (int r = 0; r < Gp::R; r++)
+            sm[sidx<C>(0, r | (hi << Gp::G), w)] = a[v * Gp::R + r];
+    }
+}
+
+// Last group, split in two so the caller can recycle shared memory in
+// between: read the units into registers ...
+template <class C>
+__device__ __forceinline__ void group_last_read(float2 (&a)[16], const float2 *sm)
+{
+    using Gp = Grp<C, C::NG - 1>;
+    static_assert(Gp::HB == 0, "last group");
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int v = 0; v < Gp::V; v++) {
+        const int u = tid + v * C::T;
+        const int w = u & (C::W - 1);
+        const int lo = (u >> C::KW) & ((1 << Gp::S0) - 1);
+#pragma unroll
+        for (int r = 0; r < Gp::R; r++)
+            a[v * Gp::R + r] = sm[sidx<C>(0, lo | (r << Gp::S0), w)];
+    }
+}
+
+// ... then run its stages and store rows lo + r 2^S0 of the tile.
+__device__ __forceinline__ void st_stream(float2 *p, float2 v)
+{
+    asm volatile("st.global.cs.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v.x), "f"(v.y) : "memory");
+}
+
+template <class C, bool GENERIC>
+__device__ __forceinline__ void group_last_finish(float2 (&a)[16], float2 *out,
+                                                  const float2 *__restrict__ tw, long long ld,
+                                                  float scale, int nst)
+{
+    using Gp = Grp<C, C::NG - 1>;
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int v = 0; v < Gp::V; v++) {
+        const int u = tid + v * C::T;
+        const int lo = (u >> C::KW) & ((1 << Gp::S0) - 1);
+        run_stages<C, C::NG - 1, GENERIC>(a, v, lo, tw, nst);
+    }
+#pragma unroll
+    for (int v = 0; v < Gp::V; v++) {
+        const int u = tid + v * C::T;
+        const int w = u & (C::W - 1);
+        const int lo = (u >> C::KW) & ((1 << Gp::S0) - 1);
+        float2 *dst = out + (long long)lo * ld + w;
+#pragma unroll
+        for (int r = 0; r < Gp::R; r++) {
+            const float2 x = a[v * Gp::R + r];
+            st_stream(dst + (long long)(r << Gp::S0) * ld, make_float2(x.x * scale, x.y * scale));
+        }
+    }
+}
+
+// map: 2D tensor map over the column-pass input (inner dimension = columns,
+// 8-byte elements, box W x min(256, N)).  cols must be a multiple of W.
+// err: device status word; a lost TMA transfer sets kDevErrTmaTimeout.
+template <class C>
+__global__ void __launch_bounds__(C::T, C::T <= 512 ? 2 : 1) col_tma_kernel(const __grid_constant__ CUtensorMap map,
+                                                          float2 *out,
+                                                          const float2 *__restrict__ tw,
+                                                          int cols, long long ld, float scale,
+                                                          int *err)
+{
+    extern __shared__ __align__(1024) float2 sm[];
+    __shared__ __align__(8) uint64_t bar;
+    constexpr int BOX = C::N < 256 ? C::N : 256;
+    constexpr int NBOX = C::N / BOX;
+    constexpr uint32_t TILE_BYTES = (uint32_t)C::E * 8u;
+    const int ntiles = cols / C::W;
+    const int tid = threadIdx.x;
+    int tile = blockIdx.x;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0 && tile < ntiles) {
+        mbar_arrive_expect_tx(&bar, TILE_BYTES);
+        for (int k = 0; k < NBOX; k++)
+            tma_load_2d(sm + k * BOX * C::W, &map, tile * C::W, k * BOX, &bar);
+    }
+    uint32_t parity = 0;
+    float2 a[16];
+    for (; tile < ntiles; tile += gridDim.x) {
+        const int lost = mbar_wait_bounded(&bar, parity) ? 0 : 1;
+        if (__syncthreads_or(lost)) {
+            if (tid == 0)
+                atomicExch(err, kDevErrTmaTimeout);
+            mbar_wait_bounded(&bar, parity);   // let a late transfer land before leaving
+            return;
+        }
+        parity ^= 1;
+        group_first_smem<C, false>(a, sm, tw, C::L);
+        __syncthreads();
+        if constexpr (C::NG >= 3) {
+            group_smem<C, 1, false, false>(a, sm, nullptr, tw, ld, 1.0f, C::L, 0);
+            __syncthreads();
+        }
+        if constexpr (C::NG >= 4) {
+            group_smem<C, 2, false, false>(a, sm, nullptr, tw, ld, 1.0f, C::L, 0);
+            __syncthreads();
+        }
+        group_last_read<C>(a, sm);
+        fence_proxy_async_smem();
+        __syncthreads();   // the tile buffer is free
+        const int next = tile + gridDim.x;
+        if (tid == 0 && next < ntiles) {
+            mbar_arrive_expect_tx(&bar, TILE_BYTES);
+            for (int k = 0; k < NBOX; k++)
+                tma_load_2d(sm + k * BOX * C::W, &map, next * C::W, k * BOX, &bar);
+        }
+        group_last_finish<C, false>(a, out + (long long)tile * C::W, tw, ld, scale, C::L);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Column pass split over a thread-block cluster of CS = 2^c CTAs.
+//
+// A tile of W adjacent columns of 2^L rows is too large for one CTA when the
+// tile is wide enough for full 64-128 byte row segments.  The DIT structure
+// splits it without any extra pass over memory: after the scramble, the
+// positions p in [b 2^(L-c), (b+1) 2^(L-c)) hold exactly the rows
+// m = CS m' + rev_c(b), in the order p = b 2^(L-c) + rev_{L-c}(m').  So CTA
+// b of the cluster loads every CS-th row (starting at rev_c(b)), runs stages
+// 1 .. L-c on them locally (the ordinary engine with a CS-times row pitch)
+// and leaves its 2^(L-c)-point results in shared memory in natural order.
+// Stages L-c+1 .. L pair positions that differ only in their top c bits,
+// i.e. values held by different CTAs: after a cluster barrier each CTA
+// gathers, through distributed shared memory, the CS values of its share of
+// the output rows (lo in [b 2^(L-2c), (b+1) 2^(L-2c))), runs those last c
+// stages in registers and stores rows lo + r 2^(L-c), r < CS.
+template <int L_, int KW_, int C_>
+struct ClusterColCfg {
+    static constexpr int L = L_, KW = KW_, c = C_;
+    static constexpr int CS = 1 << c;
+    using Local = LineCfg<L - c, KW, 0>;
+    using Cross = GrpSG<L, L - c, c>;
+    static constexpr int T = Local::T;
+    static constexpr int W = Local::W;
+    static constexpr int NL = Local::N;          // rows held by one CTA
+    static constexpr int SMEM_BYTES = Local::E * 8;
+    static_assert(c >= 1 && c <= 4, "cluster of 2 to 16 CTAs");
+    static_assert(Local::NG >= 2, "local line must span at least two groups");
+};
+
+template <class CC, bool GENERIC>
+__global__ void __launch_bounds__(CC::T) col_cluster_kernel(const float2 *in, float2 *out,
+                                                            const float2 *__restrict__ tw,
+                                                            int cols, long long ld,
+                                                            float scale, int nst)
+{
+    namespace cg = cooperative_groups;
+    using LC = typename CC::Local;
+    using X = typename CC::Cross;
+    extern __shared__ float2 sm[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int b = (int)cluster.block_rank();
+    const long long c0 = (long long)(blockIdx.x / CC::CS) * CC::W;
+    const long long nvalid = cols - c0;
+    const long long lld = ld * CC::CS;
+    const float2 *lin = in + c0 + (long long)brev_rt(b, CC::c) * ld;
+    float2 a[16];
+
+    // stages 1 .. L-c on this CTA's rows
+    group_first<LC, false, GENERIC>(a, sm, lin, nullptr, tw, lld, 1.0f, nst, nvalid);
+    __syncthreads();
+    if constexpr (LC::NG >= 3) {
+        group_smem<LC, 1, false, GENERIC>(a, sm, nullptr, tw, lld, 1.0f, nst, nvalid);
+        __syncthreads();
+    }
+    if constexpr (LC::NG >= 4) {
+        group_smem<LC, 2, false, GENERIC>(a, sm, nullptr, tw, lld, 1.0f, nst, nvalid);
+        __syncthreads();
+    }
+    group_smem<LC, LC::NG - 1, false, GENERIC, true>(a, sm, nullptr, tw, lld, 1.0f, nst, nvalid);
+    cluster.sync();
+
+    // stages L-c+1 .. L across the cluster
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int v = 0; v < X::V; v++) {
+        const int u = tid + v * CC::T;
+        const int w = u & (CC::W - 1);
+        const int lo = b * (CC::NL / CC::CS) + (u >> CC::KW);
+#pragma unroll
+        for (int r = 0; r < CC::CS; r++) {
+            const float2 *peer = cluster.map_shared_rank(sm, r);
+            a[v * X::R + r] = peer[lo * CC::W + w];
+        }
+    }
+    cluster.sync();   // no CTA leaves while a peer may still read its smem
+#pragma unroll
+    for (int v = 0; v < X::V; v++) {
+        const int u = tid + v * CC::T;
+        const int w = u & (CC::W - 1);
+        const int lo = b * (CC::NL / CC::CS) + (u >> CC::KW);
+        run_stages_g<X, false, GENERIC>(a, v, lo, tw, nst);
+        if (!GENERIC || w < nvalid) {
+            float2 *dst = out + c0 + (long long)lo * ld + w;
+#pragma unroll
+            for (int r = 0; r < CC::CS; r++) {
+                const float2 x = a[v * X::R + r];
+                dst[(long long)r * CC::NL * ld] = make_float2(x.x * scale, x.y * scale);
+            }
+        }
+    }
 }
 
 }  // namespace fft2d

@@ -15,6 +15,7 @@ struct PassArgs {
     float scale;         // multiplies every stored value (1 or 1/(rows*cols))
     int nst;             // stages to run on this axis (partial debug view)
     bool partial;        // nst < log2(axis length)
+    int *err;            // device status word (bounded-wait timeouts)
 };
 
 // Lines per CTA of the row pass and interleaved columns per CTA of the
@@ -23,6 +24,7 @@ int row_lines_per_cta(int L);
 int col_width(int L);
 
 cudaError_t launch_row_pass(int L, const PassArgs &a, cudaStream_t s);
+cudaError_t launch_selftest_timeout(int *err, cudaStream_t s);
 cudaError_t launch_col_pass(int L, const PassArgs &a, cudaStream_t s);
 
 }  // namespace fft2d

@@ -47,6 +47,8 @@ _P, _I = ctypes.c_void_p, ctypes.c_int
 _sigs = {
     "fft2d_plan": ([_I, _I, _I, _I, ctypes.POINTER(ctypes.c_void_p)], _I),
     "fft2d_destroy": ([_P], _I),
+    "fft2d_sync_status": ([_P], _I),
+    "fft2d_selftest_timeout": ([_P, _P], _I),
     "fft2d_plan_info": ([_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                          ctypes.POINTER(_I)], _I),
     "fft2d_exec": ([_P, _P, _P, _P], _I),
@@ -120,6 +122,15 @@ def fft2d_plan(rows: int, cols: int, dtype: int = FFT2D_C64, dir: int = FFT2D_FO
 
 def fft2d_destroy(plan: int) -> None:
     _check(lib.fft2d_destroy(plan), "fft2d_destroy")
+
+
+def fft2d_sync_status(plan: int) -> None:
+    """Wait for the device; raise FFT2DError if a kernel's bounded wait gave up."""
+    _check(lib.fft2d_sync_status(plan), "fft2d_sync_status")
+
+
+def fft2d_selftest_timeout(plan: int, stream=None) -> None:
+    _check(lib.fft2d_selftest_timeout(plan, _stream(stream)), "fft2d_selftest_timeout")
 
 
 def fft2d_plan_info(plan: int) -> tuple[int, int, int, int]:

@@ -247,3 +247,45 @@ def test_16384_square_properties(env):
     finally:
         fft.fft2d_destroy(pf)
         fft.fft2d_destroy(pi)
+
+
+def test_unaligned_buffers_take_the_plain_path(env):
+    """A buffer that is only 8-byte aligned cannot feed TMA; the result must
+    still match (the plain column kernel serves it)."""
+    torch, fft, orc = env
+    R = C = 1024
+    x = synth.uniform_complex(R, C, seed=12)
+    flat = torch.zeros(R * C + 1, dtype=torch.complex64, device="cuda")
+    src = flat[1:].view(R, C)
+    assert src.data_ptr() % 16 == 8
+    src.copy_(torch.from_numpy(x))
+    plan = fft.fft2d_plan(R, C, fft.FFT2D_C64, fft.FFT2D_FORWARD)
+    try:
+        fft.fft2d_exec(plan, src, src)
+        fft.fft2d_sync_status(plan)
+        assert rel(src.cpu().numpy(), orc.fft2d(x, threads=8)) <= TOL
+    finally:
+        fft.fft2d_destroy(plan)
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(env):
+    """Failure path of the TMA pipeline: a wait on an mbarrier that nothing
+    completes gives up (about 20 ms), the host reads FFT2D_ERR_TIMEOUT, the
+    status clears, and the next transform is still correct."""
+    torch, fft, orc = env
+    plan = fft.fft2d_plan(256, 256, fft.FFT2D_C64, fft.FFT2D_FORWARD)
+    try:
+        fft.fft2d_sync_status(plan)                      # clean to start with
+        fft.fft2d_selftest_timeout(plan)
+        with pytest.raises(fft.FFT2DError) as ei:
+            fft.fft2d_sync_status(plan)
+        assert ei.value.status == fft.FFT2D_ERR_TIMEOUT
+        fft.fft2d_sync_status(plan)                      # cleared
+        x = synth.uniform_real(256, 256, seed=0)
+        dx = torch.from_numpy(x).cuda()
+        out = torch.empty_like(dx)
+        fft.fft2d_exec(plan, dx, out)
+        fft.fft2d_sync_status(plan)
+        assert rel(out.cpu().numpy(), orc.fft2d(x)) <= TOL
+    finally:
+        fft.fft2d_destroy(plan)
