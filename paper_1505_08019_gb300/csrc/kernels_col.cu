@@ -120,16 +120,17 @@ static cudaError_t col_launch_tma(const PassArgs &a, cudaStream_t s, bool *used)
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
         return cudaSuccess;   // not expressible as a tensor map: plain kernel
-    auto k = col_tma_kernel<C>;
+    auto k = col_tma2_kernel<C>;
+    constexpr int SMEM = TmaSplit<C>::SMEM_BYTES;
     static int occ[kMaxDev] = {};
     const int d = current_device();
     if (!occ[d]) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             C::SMEM_BYTES);
+                                             SMEM);
         if (e != cudaSuccess)
             return e;
         int o = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, C::T, C::SMEM_BYTES);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, C::T, SMEM);
         if (e != cudaSuccess)
             return e;
         occ[d] = o > 0 ? o : 1;
@@ -138,7 +139,7 @@ static cudaError_t col_launch_tma(const PassArgs &a, cudaStream_t s, bool *used)
     int grid = sm_count() * occ[d];
     if (grid > ntiles)
         grid = ntiles;
-    k<<<grid, C::T, C::SMEM_BYTES, s>>>(map, a.out, a.tw, a.cols, a.ld, a.scale, a.err);
+    k<<<grid, C::T, SMEM, s>>>(map, a.out, a.tw, a.cols, a.ld, a.scale, a.err);
     *used = true;
     return cudaGetLastError();
 }
@@ -147,7 +148,7 @@ template <int L>
 static cudaError_t col_dispatch(const PassArgs &a, cudaStream_t s)
 {
     const bool generic = a.partial || a.cols < col_width(L);
-    if constexpr (L >= 5 && L <= 12) {
+    if constexpr (L >= 9 && L <= 12) {
         if (!generic && a.err) {
             bool used = false;
             cudaError_t e = col_launch_tma<L>(a, s, &used);

@@ -489,6 +489,154 @@ __global__ void __launch_bounds__(C::T, C::T <= 512 ? 2 : 1) col_tma_kernel(cons
 }
 
 // ---------------------------------------------------------------------------
+// Column pass with an early prefetch.  Shared memory holds the tile region
+// (the exchange buffer, one tile) and a prefetch region of NB boxes.  Boxes
+// 0..NB-1 of the NEXT tile land in the prefetch region as soon as group 0 has
+// gathered the current tile into registers -- while the remaining groups
+// still work -- and boxes NB.. land at the start of the tile region once the
+// last group has read it.  Group 0 of a tile finds box k in the prefetch
+// region (k < NB) or in the tile region (k >= NB); k depends only on the
+// register index, so the split costs no extra address arithmetic.
+template <class C>
+struct TmaSplit {
+    static constexpr int BOX = C::N < 256 ? C::N : 256;             // rows per box
+    static constexpr int NBOX = C::N / BOX;
+    static constexpr int BOX_VALS = BOX * C::W;
+    static constexpr int PREF_LIMIT = 96 * 1024;                    // prefetch region
+    static constexpr int NB0 = PREF_LIMIT / (BOX_VALS * 8);
+    static constexpr int NB = NB0 < NBOX - 1 ? NB0 : NBOX - 1;       // early boxes
+    static constexpr int SMEM_BYTES = (C::E + NB * BOX_VALS) * 8;
+    static constexpr uint32_t EARLY_BYTES = (uint32_t)NB * BOX_VALS * 8u;
+    static constexpr uint32_t LATE_BYTES = (uint32_t)(NBOX - NB) * BOX_VALS * 8u;
+    static_assert(NB >= 1, "tile must span at least two boxes");
+    static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
+};
+
+template <class C>
+__device__ __forceinline__ void split_issue_early(float2 *sm, const CUtensorMap *map, int tile,
+                                                  uint64_t *bar)
+{
+    using S = TmaSplit<C>;
+    float2 *pref = sm + C::E;
+    mbar_arrive_expect_tx(bar, S::EARLY_BYTES);
+    for (int k = 0; k < S::NB; k++)
+        tma_load_2d(pref + k * S::BOX_VALS, map, tile * C::W, k * S::BOX, bar);
+}
+
+template <class C>
+__device__ __forceinline__ void split_issue_late(float2 *sm, const CUtensorMap *map, int tile,
+                                                 uint64_t *bar)
+{
+    using S = TmaSplit<C>;
+    mbar_arrive_expect_tx(bar, S::LATE_BYTES);
+    for (int k = S::NB; k < S::NBOX; k++)
+        tma_load_2d(sm + (k - S::NB) * S::BOX_VALS, map, tile * C::W, k * S::BOX, bar);
+}
+
+// Group 0 from the split tile (see above), ending with the swizzled exchange
+// layout in the tile region.  `after_reads` runs once every thread has
+// gathered its values (the prefetch region is then free).
+template <class C, class F>
+__device__ __forceinline__ void group_first_split(float2 (&a)[16], float2 *sm,
+                                                  const float2 *__restrict__ tw, F after_reads)
+{
+    using Gp = Grp<C, 0>;
+    using S = TmaSplit<C>;
+    static_assert(C::NG >= 2 && C::LB == 1, "tile engine needs two groups, one line block");
+    static_assert((1 << Gp::HB) <= S::BOX, "box index must depend on the register only");
+    const float2 *pref = sm + C::E;
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int v = 0; v < Gp::V; v++) {
+        const int u = tid + v * C::T;
+        const int w = u & (C::W - 1);
+        const int hib = (u >> C::KW) & ((1 << Gp::HB) - 1);
+#pragma unroll
+        for (int r = 0; r < Gp::R; r++) {
+            const int top = brev_c(r, Gp::G) << Gp::HB;     // compile-time
+            const int k = top / S::BOX;
+            const int in_box = ((top % S::BOX) | hib) * C::W + w;
+            const float2 *bx = k < S::NB ? pref + k * S::BOX_VALS : sm + (k - S::NB) * S::BOX_VALS;
+            a[v * Gp::R + r] = bx[in_box];
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < Gp::V; v++)
+        run_stages<C, 0, false>(a, v, 0, tw, C::L);
+    fence_proxy_async_smem();
+    __syncthreads();   // every slot of both regions has been read
+    after_reads();
+#pragma unroll
+    for (int v = 0; v < Gp::V; v++) {
+        const int u = tid + v * C::T;
+        const int w = u & (C::W - 1);
+        const int hib = (u >> C::KW) & ((1 << Gp::HB) - 1);
+        const int hi = brev_rt(hib, Gp::HB);
+#pragma unroll
+        for (int r = 0; r < Gp::R; r++)
+            sm[sidx<C>(0, r | (hi << Gp::G), w)] = a[v * Gp::R + r];
+    }
+}
+
+template <class C>
+__global__ void __launch_bounds__(C::T, 1) col_tma2_kernel(const __grid_constant__ CUtensorMap map,
+                                                           float2 *out,
+                                                           const float2 *__restrict__ tw,
+                                                           int cols, long long ld, float scale,
+                                                           int *err)
+{
+    extern __shared__ __align__(1024) float2 sm[];
+    __shared__ __align__(8) uint64_t bar_early, bar_late;
+    const int ntiles = cols / C::W;
+    const int tid = threadIdx.x;
+    int tile = blockIdx.x;
+    if (tid == 0) {
+        mbar_init(&bar_early, 1);
+        mbar_init(&bar_late, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0 && tile < ntiles) {
+        split_issue_early<C>(sm, &map, tile, &bar_early);
+        split_issue_late<C>(sm, &map, tile, &bar_late);
+    }
+    uint32_t parity = 0;
+    float2 a[16];
+    for (; tile < ntiles; tile += gridDim.x) {
+        const int next = tile + gridDim.x;
+        const bool ok = mbar_wait_bounded(&bar_early, parity) && mbar_wait_bounded(&bar_late, parity);
+        if (__syncthreads_or(ok ? 0 : 1)) {
+            if (tid == 0)
+                atomicExch(err, kDevErrTmaTimeout);
+            // let late transfers land before the CTA leaves
+            mbar_wait_bounded(&bar_early, parity);
+            mbar_wait_bounded(&bar_late, parity);
+            return;
+        }
+        parity ^= 1;
+        group_first_split<C>(a, sm, tw, [&] {
+            if (tid == 0 && next < ntiles)
+                split_issue_early<C>(sm, &map, next, &bar_early);
+        });
+        __syncthreads();
+        if constexpr (C::NG >= 3) {
+            group_smem<C, 1, false, false>(a, sm, nullptr, tw, ld, 1.0f, C::L, 0);
+            __syncthreads();
+        }
+        if constexpr (C::NG >= 4) {
+            group_smem<C, 2, false, false>(a, sm, nullptr, tw, ld, 1.0f, C::L, 0);
+            __syncthreads();
+        }
+        group_last_read<C>(a, sm);
+        fence_proxy_async_smem();
+        __syncthreads();   // the tile region is free
+        if (tid == 0 && next < ntiles)
+            split_issue_late<C>(sm, &map, next, &bar_late);
+        group_last_finish<C, false>(a, out + (long long)tile * C::W, tw, ld, scale, C::L);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Column pass split over a thread-block cluster of CS = 2^c CTAs.
 //
 // A tile of W adjacent columns of 2^L rows is too large for one CTA when the
