@@ -111,9 +111,20 @@ __device__ __forceinline__ int sidx(int lb, int p, int w)
     return (((lb << C::L) | q) << C::KW) | w;
 }
 
+// Rotation factor load: from global memory through the read-only path, or
+// from a copy of the table in shared memory (TWS).
+template <bool TWS>
+__device__ __forceinline__ float2 ld_tw(const float2 *p)
+{
+    if constexpr (TWS)
+        return *p;
+    else
+        return __ldg(p);
+}
+
 // Stages S0+1 .. S0+G on unit v of a[]: pairs (r, r + 2^t) at stage S0+1+t use
 // W_{2^s}^j with j = lo + (r mod 2^t) 2^S0.
-template <class Gp, bool FIRST, bool GENERIC>
+template <class Gp, bool FIRST, bool GENERIC, bool TWS = false>
 __device__ __forceinline__ void run_stages_g(float2 (&a)[16], int v, int lo,
                                              const float2 *__restrict__ tw, int nst)
 {
@@ -134,7 +145,7 @@ __device__ __forceinline__ void run_stages_g(float2 (&a)[16], int v, int lo,
             if (FIRST && jc == 0) {
                 m = x1;   // W = 1
             } else {
-                const float2 w = __ldg(tws + lo + jc);
+                const float2 w = ld_tw<TWS>(tws + lo + jc);
                 m.x = w.x * x1.x - w.y * x1.y;
                 m.y = w.x * x1.y + w.y * x1.x;
             }
@@ -144,11 +155,11 @@ __device__ __forceinline__ void run_stages_g(float2 (&a)[16], int v, int lo,
     }
 }
 
-template <class C, int GI, bool GENERIC>
+template <class C, int GI, bool GENERIC, bool TWS = false>
 __device__ __forceinline__ void run_stages(float2 (&a)[16], int v, int lo,
                                            const float2 *__restrict__ tw, int nst)
 {
-    run_stages_g<Grp<C, GI>, GI == 0, GENERIC>(a, v, lo, tw, nst);
+    run_stages_g<Grp<C, GI>, GI == 0, GENERIC, TWS>(a, v, lo, tw, nst);
 }
 
 // Group 0: scrambled global load, first stages, then either the final store
@@ -213,7 +224,7 @@ __device__ __forceinline__ void group_first(float2 (&a)[16], float2 *sm, const f
 // With TO_SMEM the last group does not store to global memory: it leaves the
 // finished lines in shared memory in natural order, slot k*W + w (used by the
 // cluster column pass, whose last stages run across CTAs).
-template <class C, int GI, bool ROW, bool GENERIC, bool TO_SMEM = false>
+template <class C, int GI, bool ROW, bool GENERIC, bool TO_SMEM = false, bool TWS = false>
 __device__ __forceinline__ void group_smem(float2 (&a)[16], float2 *sm, float2 *out,
                                            const float2 *__restrict__ tw, long long ld,
                                            float scale, int nst, long long nvalid)
@@ -237,7 +248,7 @@ __device__ __forceinline__ void group_smem(float2 (&a)[16], float2 *sm, float2 *
     for (int v = 0; v < Gp::V; v++) {
         const int u = tid + v * C::T;
         const int lo = (u >> C::KW) & ((1 << Gp::S0) - 1);
-        run_stages<C, GI, GENERIC>(a, v, lo, tw, nst);
+        run_stages<C, GI, GENERIC, TWS>(a, v, lo, tw, nst);
     }
     if constexpr (LAST && TO_SMEM) {
         // the natural-order slots differ from the swizzled ones just read
@@ -399,7 +410,7 @@ __device__ __forceinline__ void st_stream(float2 *p, float2 v)
     asm volatile("st.global.cs.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v.x), "f"(v.y) : "memory");
 }
 
-template <class C, bool GENERIC>
+template <class C, bool GENERIC, bool TWS = false>
 __device__ __forceinline__ void group_last_finish(float2 (&a)[16], float2 *out,
                                                   const float2 *__restrict__ tw, long long ld,
                                                   float scale, int nst)
@@ -410,7 +421,7 @@ __device__ __forceinline__ void group_last_finish(float2 (&a)[16], float2 *out,
     for (int v = 0; v < Gp::V; v++) {
         const int u = tid + v * C::T;
         const int lo = (u >> C::KW) & ((1 << Gp::S0) - 1);
-        run_stages<C, C::NG - 1, GENERIC>(a, v, lo, tw, nst);
+        run_stages<C, C::NG - 1, GENERIC, TWS>(a, v, lo, tw, nst);
     }
 #pragma unroll
     for (int v = 0; v < Gp::V; v++) {
@@ -502,10 +513,12 @@ struct TmaSplit {
     static constexpr int BOX = C::N < 256 ? C::N : 256;             // rows per box
     static constexpr int NBOX = C::N / BOX;
     static constexpr int BOX_VALS = BOX * C::W;
-    static constexpr int PREF_LIMIT = 96 * 1024;                    // prefetch region
+    static constexpr int PREF_LIMIT = 64 * 1024;                    // prefetch region
     static constexpr int NB0 = PREF_LIMIT / (BOX_VALS * 8);
     static constexpr int NB = NB0 < NBOX - 1 ? NB0 : NBOX - 1;       // early boxes
-    static constexpr int SMEM_BYTES = (C::E + NB * BOX_VALS) * 8;
+    static constexpr int TW_VALS = C::N - 1;                         // twiddle table copy
+    static constexpr int TW_OFF = C::E + NB * BOX_VALS;
+    static constexpr int SMEM_BYTES = (TW_OFF + TW_VALS + 1) * 8;
     static constexpr uint32_t EARLY_BYTES = (uint32_t)NB * BOX_VALS * 8u;
     static constexpr uint32_t LATE_BYTES = (uint32_t)(NBOX - NB) * BOX_VALS * 8u;
     static_assert(NB >= 1, "tile must span at least two boxes");
@@ -562,7 +575,7 @@ __device__ __forceinline__ void group_first_split(float2 (&a)[16], float2 *sm,
     }
 #pragma unroll
     for (int v = 0; v < Gp::V; v++)
-        run_stages<C, 0, false>(a, v, 0, tw, C::L);
+        run_stages<C, 0, false, true>(a, v, 0, tw, C::L);
     fence_proxy_async_smem();
     __syncthreads();   // every slot of both regions has been read
     after_reads();
@@ -600,6 +613,11 @@ __global__ void __launch_bounds__(C::T, 1) col_tma2_kernel(const __grid_constant
         split_issue_early<C>(sm, &map, tile, &bar_early);
         split_issue_late<C>(sm, &map, tile, &bar_late);
     }
+    // the rotation factors stay in shared memory for the CTA's whole life
+    float2 *stw = sm + TmaSplit<C>::TW_OFF;
+    for (int i = tid; i < TmaSplit<C>::TW_VALS; i += C::T)
+        stw[i] = __ldg(tw + i);
+    __syncthreads();
     uint32_t parity = 0;
     float2 a[16];
     for (; tile < ntiles; tile += gridDim.x) {
@@ -614,17 +632,17 @@ __global__ void __launch_bounds__(C::T, 1) col_tma2_kernel(const __grid_constant
             return;
         }
         parity ^= 1;
-        group_first_split<C>(a, sm, tw, [&] {
+        group_first_split<C>(a, sm, stw, [&] {
             if (tid == 0 && next < ntiles)
                 split_issue_early<C>(sm, &map, next, &bar_early);
         });
         __syncthreads();
         if constexpr (C::NG >= 3) {
-            group_smem<C, 1, false, false>(a, sm, nullptr, tw, ld, 1.0f, C::L, 0);
+            group_smem<C, 1, false, false, false, true>(a, sm, nullptr, stw, ld, 1.0f, C::L, 0);
             __syncthreads();
         }
         if constexpr (C::NG >= 4) {
-            group_smem<C, 2, false, false>(a, sm, nullptr, tw, ld, 1.0f, C::L, 0);
+            group_smem<C, 2, false, false, false, true>(a, sm, nullptr, stw, ld, 1.0f, C::L, 0);
             __syncthreads();
         }
         group_last_read<C>(a, sm);
@@ -632,7 +650,7 @@ __global__ void __launch_bounds__(C::T, 1) col_tma2_kernel(const __grid_constant
         __syncthreads();   // the tile region is free
         if (tid == 0 && next < ntiles)
             split_issue_late<C>(sm, &map, next, &bar_late);
-        group_last_finish<C, false>(a, out + (long long)tile * C::W, tw, ld, scale, C::L);
+        group_last_finish<C, false, true>(a, out + (long long)tile * C::W, stw, ld, scale, C::L);
     }
 }
 
