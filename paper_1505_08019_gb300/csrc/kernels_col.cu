@@ -30,17 +30,22 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-int current_device()
+int current_device() { return device_current(); }
+int sm_count() { return device_sm_count(); }
+
+}  // namespace
+
+int device_current()
 {
     int d = 0;
     cudaGetDevice(&d);
     return d < 0 || d >= kMaxDev ? 0 : d;
 }
 
-int sm_count()
+int device_sm_count()
 {
     static int cache[kMaxDev] = {};
-    const int d = current_device();
+    const int d = device_current();
     if (!cache[d]) {
         int n = 0;
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d);
@@ -48,8 +53,6 @@ int sm_count()
     }
     return cache[d];
 }
-
-}  // namespace
 
 // 2^14 values (128 KB of shared memory) per CTA from 1024-point columns up;
 // 16 to 64 columns per CTA below.

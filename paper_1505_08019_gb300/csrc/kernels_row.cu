@@ -27,10 +27,51 @@ static cudaError_t row_launch(const PassArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Persistent TMA-fed variant (row_tma_kernel): whole blocks of LB rows only,
+// input 16-byte aligned, row pitch a multiple of 16 bytes.
+template <int L>
+static cudaError_t row_launch_tma(const PassArgs &a, cudaStream_t s, bool *used)
+{
+    using C = LineCfg<L, 0, row_kb(L)>;
+    constexpr int SMEM = RowTma<C>::SMEM_BYTES;
+    *used = false;
+    if ((reinterpret_cast<uintptr_t>(a.in) & 15) || ((a.ld * 8) & 15) || a.rows % C::LB)
+        return cudaSuccess;
+    auto k = row_tma_kernel<C>;
+    constexpr int kMaxDev = 64;
+    static int occ[kMaxDev] = {};
+    const int d = device_current();
+    if (!occ[d]) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (e != cudaSuccess)
+            return e;
+        int o = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, C::T, SMEM);
+        if (e != cudaSuccess)
+            return e;
+        occ[d] = o > 0 ? o : 1;
+    }
+    const int ntiles = a.rows / C::LB;
+    int grid = device_sm_count() * occ[d];
+    if (grid > ntiles)
+        grid = ntiles;
+    k<<<grid, C::T, SMEM, s>>>(a.in, a.out, a.tw, a.rows, a.ld, a.scale, a.err);
+    *used = true;
+    return cudaGetLastError();
+}
+
 template <int L>
 static cudaError_t row_dispatch(const PassArgs &a, cudaStream_t s)
 {
     const bool generic = a.partial || a.rows < row_lines_per_cta(L);
+    if constexpr (L >= 5 && L <= 13) {
+        if (!generic && a.err) {
+            bool used = false;
+            cudaError_t e = row_launch_tma<L>(a, s, &used);
+            if (e != cudaSuccess || used)
+                return e;
+        }
+    }
     return generic ? row_launch<L, true>(a, s) : row_launch<L, false>(a, s);
 }
 

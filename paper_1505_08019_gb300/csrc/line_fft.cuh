@@ -348,40 +348,44 @@ __global__ void __launch_bounds__(C::T, C::MINB) col_pass_kernel(const float2 *i
 // load of the CTA's next tile is issued, so that transfer overlaps the last
 // stages and the stores of the current tile.
 
-// Group 0 from a natural-order tile in shared memory, slot i*W + w for line
-// element i of interleaved line w; ends with the swizzled exchange layout in
-// the same buffer.
-template <class C, bool GENERIC>
+// Group 0 from a natural-order tile in shared memory, slot
+// ((lb << L) | i) * W + w for element i of interleaved line w of line block
+// lb; ends with the swizzled exchange layout in the same buffer.
+template <class C, bool GENERIC, bool TWS = false>
 __device__ __forceinline__ void group_first_smem(float2 (&a)[16], float2 *sm,
                                                  const float2 *__restrict__ tw, int nst)
 {
     using Gp = Grp<C, 0>;
-    static_assert(C::NG >= 2 && C::LB == 1, "tile engine needs two groups, one line block");
+    static_assert(C::NG >= 2, "tile engine needs two groups");
     const int tid = threadIdx.x;
 #pragma unroll
     for (int v = 0; v < Gp::V; v++) {
         const int u = tid + v * C::T;
         const int w = u & (C::W - 1);
-        const int hib = (u >> C::KW) & ((1 << Gp::HB) - 1);
+        const int u2 = u >> C::KW;
+        const int hib = u2 & ((1 << Gp::HB) - 1);
+        const int lb = u2 >> Gp::HB;
 #pragma unroll
         for (int r = 0; r < Gp::R; r++) {
             const int i = (brev_c(r, Gp::G) << Gp::HB) | hib;
-            a[v * Gp::R + r] = sm[(i << C::KW) | w];
+            a[v * Gp::R + r] = sm[(((lb << C::L) | i) << C::KW) | w];
         }
     }
 #pragma unroll
     for (int v = 0; v < Gp::V; v++)
-        run_stages<C, 0, GENERIC>(a, v, 0, tw, nst);
+        run_stages<C, 0, GENERIC, TWS>(a, v, 0, tw, nst);
     __syncthreads();   // every natural-order slot has been read
 #pragma unroll
     for (int v = 0; v < Gp::V; v++) {
         const int u = tid + v * C::T;
         const int w = u & (C::W - 1);
-        const int hib = (u >> C::KW) & ((1 << Gp::HB) - 1);
+        const int u2 = u >> C::KW;
+        const int hib = u2 & ((1 << Gp::HB) - 1);
+        const int lb = u2 >> Gp::HB;
         const int hi = brev_rt(hib, Gp::HB);
 #pragma unroll
         for (int r = 0; r < Gp::R; r++)
-            sm[sidx<C>(0, r | (hi << Gp::G), w)] = a[v * Gp::R + r];
+            sm[sidx<C>(lb, r | (hi << Gp::G), w)] = a[v * Gp::R + r];
     }
 }
 
@@ -496,6 +500,91 @@ __global__ void __launch_bounds__(C::T, C::T <= 512 ? 2 : 1) col_tma_kernel(cons
                 tma_load_2d(sm + k * BOX * C::W, &map, next * C::W, k * BOX, &bar);
         }
         group_last_finish<C, false>(a, out + (long long)tile * C::W, tw, ld, scale, C::L);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent row pass fed by TMA bulk copies, double buffered: while a CTA
+// transforms its current block of LB rows in one shared-memory buffer, the
+// next block streams into the other.  The block's rows arrive in natural
+// order and group 0 gathers them scrambled from shared memory.
+template <class C>
+struct RowTma {
+    static constexpr int SMEM_BYTES = 2 * C::E * 8;
+    static constexpr uint32_t ROW_BYTES = (uint32_t)C::N * 8u;
+    static constexpr uint32_t TILE_BYTES = (uint32_t)C::E * 8u;
+};
+
+template <class C>
+__device__ __forceinline__ void row_issue(float2 *buf, const float2 *in, long long ld, int tile,
+                                          uint64_t *bar)
+{
+    mbar_arrive_expect_tx(bar, RowTma<C>::TILE_BYTES);
+    const float2 *src = in + (long long)tile * C::LB * ld;
+    if (ld == C::N) {
+        bulk_load(buf, src, RowTma<C>::TILE_BYTES, bar);   // dense rows: one copy
+    } else {
+        for (int lb = 0; lb < C::LB; lb++)
+            bulk_load(buf + lb * C::N, src + lb * ld, RowTma<C>::ROW_BYTES, bar);
+    }
+}
+
+// in must be 16-byte aligned, ld even, rows a multiple of LB.
+template <class C>
+__global__ void __launch_bounds__(C::T, C::MINB) row_tma_kernel(const float2 *in, float2 *out,
+                                                                const float2 *__restrict__ tw,
+                                                                int rows, long long ld,
+                                                                float scale, int *err)
+{
+    extern __shared__ __align__(1024) float2 sm[];
+    __shared__ __align__(8) uint64_t bar[2];
+    const int ntiles = rows / C::LB;
+    const int tid = threadIdx.x;
+    int tile = blockIdx.x;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (tile < ntiles)
+            row_issue<C>(sm, in, ld, tile, &bar[0]);
+        if (tile + (int)gridDim.x < ntiles)
+            row_issue<C>(sm + C::E, in, ld, tile + gridDim.x, &bar[1]);
+    }
+    float2 a[16];
+    for (int it = 0; tile < ntiles; tile += gridDim.x, it++) {
+        const int b = it & 1;
+        const uint32_t parity = (it >> 1) & 1;
+        float2 *buf = sm + b * C::E;
+        const int lost = mbar_wait_bounded(&bar[b], parity) ? 0 : 1;
+        if (__syncthreads_or(lost)) {
+            if (tid == 0)
+                atomicExch(err, kDevErrTmaTimeout);
+            // let transfers in flight land before the CTA leaves
+            mbar_wait_bounded(&bar[b], parity);
+            if (tile + (int)gridDim.x < ntiles)
+                mbar_wait_bounded(&bar[b ^ 1], ((it + 1) >> 1) & 1);
+            return;
+        }
+        float2 *o = out + (long long)tile * C::LB * ld;
+        group_first_smem<C, false>(a, buf, tw, C::L);
+        __syncthreads();
+        if constexpr (C::NG >= 3) {
+            group_smem<C, 1, true, false>(a, buf, o, tw, ld, 1.0f, C::L, C::LB);
+            __syncthreads();
+        }
+        if constexpr (C::NG >= 4) {
+            group_smem<C, 2, true, false>(a, buf, o, tw, ld, 1.0f, C::L, C::LB);
+            __syncthreads();
+        }
+        group_smem<C, C::NG - 1, true, false>(a, buf, o, tw, ld, scale, C::L, C::LB);
+        fence_proxy_async_smem();
+        __syncthreads();   // this buffer is free again
+        const int nn = tile + 2 * (int)gridDim.x;
+        if (tid == 0 && nn < ntiles)
+            row_issue<C>(buf, in, ld, nn, &bar[b]);
     }
 }
 

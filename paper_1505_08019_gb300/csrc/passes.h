@@ -24,6 +24,10 @@ int row_lines_per_cta(int L);
 int col_width(int L);
 
 cudaError_t launch_row_pass(int L, const PassArgs &a, cudaStream_t s);
+
+// Streaming multiprocessors of the current device (cached per device).
+int device_sm_count();
+int device_current();
 cudaError_t launch_selftest_timeout(int *err, cudaStream_t s);
 cudaError_t launch_col_pass(int L, const PassArgs &a, cudaStream_t s);
 
