@@ -60,12 +60,16 @@ static cudaError_t row_launch_tma(const PassArgs &a, cudaStream_t s, bool *used)
     return cudaGetLastError();
 }
 
+// The plain kernel keeps 4 CTAs of 256 threads on every SM, which already
+// overlaps loads with compute; the TMA variant's double buffer costs one CTA
+// per SM and measured slower at 4096 points, so it serves only on request
+// (row_variant == 1).
 template <int L>
 static cudaError_t row_dispatch(const PassArgs &a, cudaStream_t s)
 {
     const bool generic = a.partial || a.rows < row_lines_per_cta(L);
     if constexpr (L >= 5 && L <= 13) {
-        if (!generic && a.err) {
+        if (!generic && a.err && a.variant == 1) {
             bool used = false;
             cudaError_t e = row_launch_tma<L>(a, s, &used);
             if (e != cudaSuccess || used)

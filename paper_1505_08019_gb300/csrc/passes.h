@@ -16,6 +16,7 @@ struct PassArgs {
     int nst;             // stages to run on this axis (partial debug view)
     bool partial;        // nst < log2(axis length)
     int *err;            // device status word (bounded-wait timeouts)
+    int variant = 0;     // kernel variant (0 = default for this size)
 };
 
 // Lines per CTA of the row pass and interleaved columns per CTA of the
