@@ -103,10 +103,14 @@ static cudaError_t col_launch(const PassArgs &a, cudaStream_t s)
 
 // Persistent TMA-fed variant (see col_tma_kernel): whole tiles only, input
 // 16-byte aligned, row pitch a multiple of 16 bytes.
+// Values per thread of the TMA column kernel: 32 for tiles of 2^14 values
+// (512 threads of up to 128 registers), 16 below.
+static constexpr int col_tma_ept(int L) { return L >= 10 ? 32 : 16; }
+
 template <int L>
 static cudaError_t col_launch_tma(const PassArgs &a, cudaStream_t s, bool *used)
 {
-    using C = LineCfg<L, col_kw(L), 0>;
+    using C = LineCfg<L, col_kw(L), 0, col_tma_ept(L)>;
     *used = false;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc || (reinterpret_cast<uintptr_t>(a.in) & 15) || ((a.ld * 8) & 15))

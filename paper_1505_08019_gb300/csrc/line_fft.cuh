@@ -67,39 +67,41 @@ __device__ __forceinline__ int brev_rt(int v, int bits)
 
 // Geometry of one CTA's work: lines of 2^L points, 2^KW interleaved lines
 // (adjacent in memory: the column pass), 2^KB separate line blocks (the row
-// pass), 16 values per thread.
-template <int L_, int KW_, int KB_>
+// pass), EPT (16 or 32) values per thread.
+template <int L_, int KW_, int KB_, int EPT_ = 16>
 struct LineCfg {
-    static constexpr int L = L_, KW = KW_, KB = KB_;
+    static constexpr int L = L_, KW = KW_, KB = KB_, EPT = EPT_;
     static constexpr int N = 1 << L, W = 1 << KW, LB = 1 << KB;
     static constexpr int E = N * W * LB;
-    static constexpr int T = E / 16;
+    static constexpr int T = E / EPT;
     static constexpr int NG = (L + 3) / 4;
     // lanes of a half-warp that are not spent on the interleave index
     static constexpr int K = KW >= 4 ? 0 : 4 - KW;
     static constexpr bool SWZ = K > 0 && L >= 2 * K;
     static constexpr int SMEM_BYTES = NG > 1 ? E * 8 : 0;
-    // resident CTAs per SM asked of the register allocator (64 registers a
-    // thread for CTAs of up to 256 threads)
-    static constexpr int MINB = T <= 256 ? 4 : (T <= 512 ? 2 : 1);
+    // resident CTAs per SM asked of the register allocator: 64 registers a
+    // thread with 16 values, 128 with 32
+    static constexpr int REGS = EPT == 16 ? 64 : 128;
+    static constexpr int MINB = 65536 / (T * REGS) > 0 ? 65536 / (T * REGS) : 1;
     static_assert(L >= 1 && L <= 14, "line length out of range");
-    static_assert(E >= 16, "CTA must hold at least 16 values");
+    static_assert(E >= EPT, "CTA must hold at least one thread's values");
+    static_assert(EPT == 16 || EPT == 32, "16 or 32 values per thread");
 };
 
 // A group of G consecutive stages S0+1 .. S0+G (bits [S0, S0 + G) of p) on
 // lines of 2^L points.
-template <int L, int S0_, int G_>
+template <int L, int S0_, int G_, int EPT = 16>
 struct GrpSG {
     static constexpr int S0 = S0_;
     static constexpr int G = G_;
     static constexpr int R = 1 << G;             // values per unit
-    static constexpr int V = 16 / R;             // units per thread
+    static constexpr int V = EPT / R;            // units per thread
     static constexpr int HB = L - S0 - G;        // bits above the group
 };
 
 // Group GI of the stage groups of a CTA config: bits [4 GI, 4 GI + G).
 template <class C, int GI>
-struct Grp : GrpSG<C::L, 4 * GI, ((C::L - 4 * GI) < 4 ? (C::L - 4 * GI) : 4)> {};
+struct Grp : GrpSG<C::L, 4 * GI, ((C::L - 4 * GI) < 4 ? (C::L - 4 * GI) : 4), C::EPT> {};
 
 // Shared-memory slot of (line block lb, position p, interleaved line w).
 template <class C>
@@ -124,8 +126,8 @@ __device__ __forceinline__ float2 ld_tw(const float2 *p)
 
 // Stages S0+1 .. S0+G on unit v of a[]: pairs (r, r + 2^t) at stage S0+1+t use
 // W_{2^s}^j with j = lo + (r mod 2^t) 2^S0.
-template <class Gp, bool FIRST, bool GENERIC, bool TWS = false>
-__device__ __forceinline__ void run_stages_g(float2 (&a)[16], int v, int lo,
+template <class Gp, bool FIRST, bool GENERIC, bool TWS = false, int NA>
+__device__ __forceinline__ void run_stages_g(float2 (&a)[NA], int v, int lo,
                                              const float2 *__restrict__ tw, int nst)
 {
 #pragma unroll
@@ -156,7 +158,7 @@ __device__ __forceinline__ void run_stages_g(float2 (&a)[16], int v, int lo,
 }
 
 template <class C, int GI, bool GENERIC, bool TWS = false>
-__device__ __forceinline__ void run_stages(float2 (&a)[16], int v, int lo,
+__device__ __forceinline__ void run_stages(float2 (&a)[C::EPT], int v, int lo,
                                            const float2 *__restrict__ tw, int nst)
 {
     run_stages_g<Grp<C, GI>, GI == 0, GENERIC, TWS>(a, v, lo, tw, nst);
@@ -165,7 +167,7 @@ __device__ __forceinline__ void run_stages(float2 (&a)[16], int v, int lo,
 // Group 0: scrambled global load, first stages, then either the final store
 // (single group, L <= 4) or the write to shared memory.
 template <class C, bool ROW, bool GENERIC>
-__device__ __forceinline__ void group_first(float2 (&a)[16], float2 *sm, const float2 *in,
+__device__ __forceinline__ void group_first(float2 (&a)[C::EPT], float2 *sm, const float2 *in,
                                             float2 *out, const float2 *__restrict__ tw,
                                             long long ld, float scale, int nst,
                                             long long nvalid)
@@ -225,7 +227,7 @@ __device__ __forceinline__ void group_first(float2 (&a)[16], float2 *sm, const f
 // finished lines in shared memory in natural order, slot k*W + w (used by the
 // cluster column pass, whose last stages run across CTAs).
 template <class C, int GI, bool ROW, bool GENERIC, bool TO_SMEM = false, bool TWS = false>
-__device__ __forceinline__ void group_smem(float2 (&a)[16], float2 *sm, float2 *out,
+__device__ __forceinline__ void group_smem(float2 (&a)[C::EPT], float2 *sm, float2 *out,
                                            const float2 *__restrict__ tw, long long ld,
                                            float scale, int nst, long long nvalid)
 {
@@ -298,7 +300,7 @@ __device__ __forceinline__ void line_fft(const float2 *in, float2 *out,
                                          float scale, int nst, long long nvalid)
 {
     extern __shared__ float2 sm[];
-    float2 a[16];
+    float2 a[C::EPT];
     group_first<C, ROW, GENERIC>(a, sm, in, out, tw, ld, scale, nst, nvalid);
     if constexpr (C::NG >= 2) {
         __syncthreads();
@@ -352,7 +354,7 @@ __global__ void __launch_bounds__(C::T, C::MINB) col_pass_kernel(const float2 *i
 // ((lb << L) | i) * W + w for element i of interleaved line w of line block
 // lb; ends with the swizzled exchange layout in the same buffer.
 template <class C, bool GENERIC, bool TWS = false>
-__device__ __forceinline__ void group_first_smem(float2 (&a)[16], float2 *sm,
+__device__ __forceinline__ void group_first_smem(float2 (&a)[C::EPT], float2 *sm,
                                                  const float2 *__restrict__ tw, int nst)
 {
     using Gp = Grp<C, 0>;
@@ -392,7 +394,7 @@ __device__ __forceinline__ void group_first_smem(float2 (&a)[16], float2 *sm,
 // Last group, split in two so the caller can recycle shared memory in
 // between: read the units into registers ...
 template <class C>
-__device__ __forceinline__ void group_last_read(float2 (&a)[16], const float2 *sm)
+__device__ __forceinline__ void group_last_read(float2 (&a)[C::EPT], const float2 *sm)
 {
     using Gp = Grp<C, C::NG - 1>;
     static_assert(Gp::HB == 0, "last group");
@@ -415,7 +417,7 @@ __device__ __forceinline__ void st_stream(float2 *p, float2 v)
 }
 
 template <class C, bool GENERIC, bool TWS = false>
-__device__ __forceinline__ void group_last_finish(float2 (&a)[16], float2 *out,
+__device__ __forceinline__ void group_last_finish(float2 (&a)[C::EPT], float2 *out,
                                                   const float2 *__restrict__ tw, long long ld,
                                                   float scale, int nst)
 {
@@ -470,7 +472,7 @@ __global__ void __launch_bounds__(C::T, C::T <= 512 ? 2 : 1) col_tma_kernel(cons
             tma_load_2d(sm + k * BOX * C::W, &map, tile * C::W, k * BOX, &bar);
     }
     uint32_t parity = 0;
-    float2 a[16];
+    float2 a[C::EPT];
     for (; tile < ntiles; tile += gridDim.x) {
         const int lost = mbar_wait_bounded(&bar, parity) ? 0 : 1;
         if (__syncthreads_or(lost)) {
@@ -553,7 +555,7 @@ __global__ void __launch_bounds__(C::T, C::MINB) row_tma_kernel(const float2 *in
         if (tile + (int)gridDim.x < ntiles)
             row_issue<C>(sm + C::E, in, ld, tile + gridDim.x, &bar[1]);
     }
-    float2 a[16];
+    float2 a[C::EPT];
     for (int it = 0; tile < ntiles; tile += gridDim.x, it++) {
         const int b = it & 1;
         const uint32_t parity = (it >> 1) & 1;
@@ -639,7 +641,7 @@ __device__ __forceinline__ void split_issue_late(float2 *sm, const CUtensorMap *
 // layout in the tile region.  `after_reads` runs once every thread has
 // gathered its values (the prefetch region is then free).
 template <class C, class F>
-__device__ __forceinline__ void group_first_split(float2 (&a)[16], float2 *sm,
+__device__ __forceinline__ void group_first_split(float2 (&a)[C::EPT], float2 *sm,
                                                   const float2 *__restrict__ tw, F after_reads)
 {
     using Gp = Grp<C, 0>;
@@ -708,7 +710,7 @@ __global__ void __launch_bounds__(C::T, 1) col_tma2_kernel(const __grid_constant
         stw[i] = __ldg(tw + i);
     __syncthreads();
     uint32_t parity = 0;
-    float2 a[16];
+    float2 a[C::EPT];
     for (; tile < ntiles; tile += gridDim.x) {
         const int next = tile + gridDim.x;
         const bool ok = mbar_wait_bounded(&bar_early, parity) && mbar_wait_bounded(&bar_late, parity);
@@ -789,7 +791,7 @@ __global__ void __launch_bounds__(CC::T) col_cluster_kernel(const float2 *in, fl
     const long long nvalid = cols - c0;
     const long long lld = ld * CC::CS;
     const float2 *lin = in + c0 + (long long)brev_rt(b, CC::c) * ld;
-    float2 a[16];
+    float2 a[CC::Local::EPT];
 
     // stages 1 .. L-c on this CTA's rows
     group_first<LC, false, GENERIC>(a, sm, lin, nullptr, tw, lld, 1.0f, nst, nvalid);
