@@ -170,6 +170,35 @@ FFT2D_API fft2d_status fft2d_exec_batched(int n, const fft2d_plan_t *plans, cons
  */
 FFT2D_API fft2d_status fft2d_stage_table(int L, int dir, float *out);
 
+/* Largest side accepted by fft2d_exec_noalloc. */
+#define FFT2D_NOALLOC_MAX_SIDE 4096
+
+/*
+ * The whole 2D transform (as fft2d_exec) without any device allocation, for
+ * callers that cannot allocate: code running while a CUDA graph is being
+ * captured, code that must not go through a process's caching allocator, or
+ * hosts that manage every byte of the device themselves.  The paper has no
+ * counterpart; this is a deployment convenience.
+ *
+ * rows, cols: powers of two, 1 <= side <= FFT2D_NOALLOC_MAX_SIDE (4096);
+ * larger sides return FFT2D_ERR_TOO_LARGE (use a plan for them).  dir is
+ * FFT2D_FORWARD or FFT2D_INVERSE; in/out are caller-owned device buffers of
+ * rows*cols complex64 pixels (in == out allowed).  Asynchronous on `stream`.
+ *
+ * Instead of a plan, the rotation-factor tables and the kernels' status word
+ * live in one static device array of about 64 KB that every device holds from
+ * the library's load until the process exits.  Each call rewrites the tables
+ * for its shape and direction and clears the status word on the stream, so
+ * calls that overlap on the GPU (different streams, or different threads on
+ * one device) race on that array: serialise them.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  It calls no cudaMalloc or
+ * cudaFree.  A bounded device wait that gives up is not reported here (use a
+ * plan and fft2d_sync_status for that).
+ */
+FFT2D_API fft2d_status fft2d_exec_noalloc(int rows, int cols, int dir, const void *in, void *out,
+                                          void *stream);
+
 /* Static text for a status code. */
 FFT2D_API const char *fft2d_strerror(int status);
 

@@ -24,6 +24,7 @@ FFT2D_INVERSE = 1
 FFT2D_PASS_ROWS = 0
 FFT2D_PASS_COLS = 1
 FFT2D_MAX_SIDE = 16384
+FFT2D_NOALLOC_MAX_SIDE = 4096
 
 FFT2D_OK = 0
 FFT2D_ERR_ARG = 1
@@ -58,6 +59,7 @@ _sigs = {
     "fft2d_exec_batched": ([_I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
                            _I),
     "fft2d_stage_table": ([_I, _I, _P], _I),
+    "fft2d_exec_noalloc": ([_I, _I, _I, _P, _P, _P], _I),
     "fft2d_strerror": ([_I], ctypes.c_char_p),
     "fft2d_last_error": ([], ctypes.c_char_p),
     "fft2d_version": ([], _I),
@@ -169,6 +171,12 @@ def fft2d_exec_batched(plans, inps, outs, stream=None) -> None:
     I_ = arr(*[_dptr(x) for x in inps])
     O_ = arr(*[_dptr(x) for x in outs])
     _check(lib.fft2d_exec_batched(n, P, I_, O_, _stream(stream)), "fft2d_exec_batched")
+
+
+def fft2d_exec_noalloc(rows: int, cols: int, dir: int, inp, out, stream=None) -> None:
+    """Plan-free transform that allocates no device memory (sides <= 4096)."""
+    _check(lib.fft2d_exec_noalloc(rows, cols, dir, _dptr(inp), _dptr(out), _stream(stream)),
+           "fft2d_exec_noalloc")
 
 
 def fft2d_stage_table(L: int, dir: int = FFT2D_FORWARD):

@@ -1,0 +1,79 @@
+"""fft2d_exec_noalloc -- the plan-free entry point for callers that cannot
+allocate device memory (graph capture, foreign allocators) -- must give the
+same results as fft2d_exec, within the FP32 tolerance of the other GPU tests,
+call after call on its shared static scratch.  Collected last on purpose."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from conftest import build_lib
+    build_lib()
+    import paper_1505_08019_gb300 as fft
+    return torch, fft
+
+
+def rel(a, b):
+    a = np.asarray(a, np.complex128)
+    b = np.asarray(b, np.complex128)
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def via_plan(torch, fft, x, direction):
+    R, C = x.shape
+    plan = fft.fft2d_plan(R, C, fft.FFT2D_C64, direction)
+    try:
+        dx = torch.from_numpy(x).cuda()
+        out = torch.empty_like(dx)
+        fft.fft2d_exec(plan, dx, out)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+    finally:
+        fft.fft2d_destroy(plan)
+
+
+def test_noalloc_matches_plan_exec_on_consecutive_calls(env):
+    torch, fft = env
+    cases = [((4096, 4096), fft.FFT2D_FORWARD, 0),    # the benchmarked size
+             ((256, 1024), fft.FFT2D_INVERSE, 1),     # next call: new shape, new direction
+             ((4096, 4096), fft.FFT2D_FORWARD, 2)]    # and back, tables rewritten again
+    for (R, C), direction, seed in cases:
+        x = synth.uniform_complex(R, C, seed=seed)
+        want = via_plan(torch, fft, x, direction)
+        dx = torch.from_numpy(x).cuda()
+        out = torch.empty_like(dx)
+        fft.fft2d_exec_noalloc(R, C, direction, dx, out)
+        torch.cuda.synchronize()
+        err = rel(out.cpu().numpy(), want)
+        print(f"[noalloc] {R}x{C} dir={direction}: rel_l2 vs fft2d_exec = {err:.2e}")
+        assert err <= TOL
+
+
+def test_noalloc_in_place_and_limits(env):
+    torch, fft = env
+    x = synth.blob_image(512, 512, seed=3)
+    want = via_plan(torch, fft, x, fft.FFT2D_FORWARD)
+    buf = torch.from_numpy(x).cuda()
+    fft.fft2d_exec_noalloc(512, 512, fft.FFT2D_FORWARD, buf, buf)
+    torch.cuda.synchronize()
+    assert rel(buf.cpu().numpy(), want) <= TOL
+    # beyond the static array's limit: rejected up front, nothing launched
+    big = torch.zeros(8, dtype=torch.complex64, device="cuda")
+    st = fft.lib.fft2d_exec_noalloc(8192, 8, fft.FFT2D_FORWARD, ctypes.c_void_p(big.data_ptr()),
+                                    ctypes.c_void_p(big.data_ptr()), None)
+    assert st == fft.FFT2D_ERR_TOO_LARGE
+    st = fft.lib.fft2d_exec_noalloc(12, 8, fft.FFT2D_FORWARD, ctypes.c_void_p(big.data_ptr()),
+                                    ctypes.c_void_p(big.data_ptr()), None)
+    assert st == fft.FFT2D_ERR_NOT_POW2
