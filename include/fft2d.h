@@ -105,6 +105,38 @@ FFT2D_API fft2d_status fft2d_sync_status(fft2d_plan_t plan);
  */
 FFT2D_API fft2d_status fft2d_selftest_timeout(fft2d_plan_t plan, void *stream);
 
+/*
+ * Autotuner.  Times every kernel variant usable for this plan's shape on the
+ * current device -- per pass: CTA tile shape (rows or adjacent columns per
+ * CTA), values per thread, TMA-fed persistent or plain launches, and for
+ * long columns the cluster split -- on two scratch images it allocates for
+ * the call, and keeps the fastest for this plan.  The choice is also kept in
+ * a process-wide table (device, pass, axis length, line count) that later
+ * fft2d_plan calls of the same shape pick up, and, when the environment
+ * variable FFT2D_TUNE_CACHE names a file, written there and read back by
+ * later processes.  Every variant computes identical results (the same
+ * butterflies in the same order); only the speed differs.  Synchronous.
+ */
+FFT2D_API fft2d_status fft2d_autotune(fft2d_plan_t plan, void *stream);
+
+/*
+ * Write a NUL-terminated description of the kernel variant each pass of the
+ * plan uses ("rows:<name>(shape=..,ept=..,tuned|default) cols:...") into
+ * buf[0..len).
+ */
+FFT2D_API fft2d_status fft2d_plan_describe(fft2d_plan_t plan, char *buf, int len);
+
+/* Number of kernel variants of one pass (FFT2D_PASS_ROWS/COLS) over lines of
+ * 2^L points (1 <= L <= 14; 0 otherwise), and the name of variant `index`
+ * ("" when out of range).  Variant 0 ("plain") serves every call. */
+FFT2D_API int fft2d_variant_count(int pass, int L);
+FFT2D_API const char *fft2d_variant_name(int pass, int L, int index);
+
+/* Force the kernel variant of one pass of a plan (-1: the per-size default).
+ * A variant that cannot serve a particular call (unaligned buffers, partial
+ * tiles) falls back to the plain kernel for that call. */
+FFT2D_API fft2d_status fft2d_plan_set_variant(fft2d_plan_t plan, int pass, int variant);
+
 /* Release a plan and everything it owns.  NULL is accepted (no-op). */
 FFT2D_API fft2d_status fft2d_destroy(fft2d_plan_t plan);
 

@@ -1,0 +1,104 @@
+// batch.cu -- grouped launches for many independent images of uneven shapes.
+//
+// Every image is a separate 2D transform (Section 2: rows and columns of one
+// image are independent, and so are images).  Instead of two launches per
+// image, the images are grouped by axis length: one launch runs the row pass
+// of every image whose rows have 2^L points, another the column pass of every
+// image whose columns have 2^L points.  A small job table travels as a kernel
+// parameter; each CTA finds its image by binary search over the table's CTA
+// offsets and then runs exactly the per-CTA work of the single-image kernels,
+// so a batched image is bit-for-bit the image transformed alone.
+#include "line_fft.cuh"
+#include "passes.h"
+
+namespace fft2d {
+
+namespace {
+
+template <class C>
+__device__ __forceinline__ int find_job(const BatchTable &t)
+{
+    int lo = 0, hi = t.n - 1;
+    const int b = (int)blockIdx.x;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (t.job[mid].first_cta <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+template <class C>
+__global__ void __launch_bounds__(C::T, C::MINB) row_batch_kernel(const __grid_constant__ BatchTable t)
+{
+    const BatchJob &jb = t.job[find_job<C>(t)];
+    const long long r0 = (long long)((int)blockIdx.x - jb.first_cta) * C::LB;
+    line_fft<C, true, true>(jb.in + r0 * jb.ld, jb.out + r0 * jb.ld, jb.tw, jb.ld, jb.scale, C::L,
+                            jb.lines - r0);
+}
+
+template <class C>
+__global__ void __launch_bounds__(C::T, C::MINB) col_batch_kernel(const __grid_constant__ BatchTable t)
+{
+    const BatchJob &jb = t.job[find_job<C>(t)];
+    const long long c0 = (long long)((int)blockIdx.x - jb.first_cta) * C::W;
+    line_fft<C, false, true>(jb.in + c0, jb.out + c0, jb.tw, jb.ld, jb.scale, C::L,
+                             jb.lines - c0);
+}
+
+template <class C, bool ROW>
+cudaError_t batch_launch(BatchTable &t, cudaStream_t s)
+{
+    auto k = ROW ? row_batch_kernel<C> : col_batch_kernel<C>;
+    const int per = ROW ? C::LB : C::W;
+    int ctas = 0;
+    for (int i = 0; i < t.n; i++) {
+        t.job[i].first_cta = ctas;
+        ctas += (t.job[i].lines + per - 1) / per;
+    }
+    if (ctas == 0)
+        return cudaSuccess;
+    if (C::SMEM_BYTES > 48 * 1024) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
+        if (e != cudaSuccess)
+            return e;
+    }
+    k<<<ctas, C::T, C::SMEM_BYTES, s>>>(t);
+    return cudaGetLastError();
+}
+
+template <int L>
+cudaError_t batch_dispatch(bool row, BatchTable &t, cudaStream_t s)
+{
+    if (row)
+        return batch_launch<LineCfg<L, 0, row_kb(L)>, true>(t, s);
+    return batch_launch<LineCfg<L, col_kw(L), 0>, false>(t, s);
+}
+
+}  // namespace
+
+cudaError_t launch_batch_pass(bool row, int L, BatchTable &t, cudaStream_t s)
+{
+    switch (L) {
+    case 1: return batch_dispatch<1>(row, t, s);
+    case 2: return batch_dispatch<2>(row, t, s);
+    case 3: return batch_dispatch<3>(row, t, s);
+    case 4: return batch_dispatch<4>(row, t, s);
+    case 5: return batch_dispatch<5>(row, t, s);
+    case 6: return batch_dispatch<6>(row, t, s);
+    case 7: return batch_dispatch<7>(row, t, s);
+    case 8: return batch_dispatch<8>(row, t, s);
+    case 9: return batch_dispatch<9>(row, t, s);
+    case 10: return batch_dispatch<10>(row, t, s);
+    case 11: return batch_dispatch<11>(row, t, s);
+    case 12: return batch_dispatch<12>(row, t, s);
+    case 13: return batch_dispatch<13>(row, t, s);
+    case 14: return batch_dispatch<14>(row, t, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace fft2d

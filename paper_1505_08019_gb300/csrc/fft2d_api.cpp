@@ -6,8 +6,13 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <string>
+#include <tuple>
 #include <vector>
 
 #include "passes.h"
@@ -20,6 +25,8 @@ struct fft2d_plan_s {
     float2 *tw_cols;   // table for the column pass: lines of rows points
     void *staging;     // device image buffer for fft2d_exec_host (lazy)
     int *dev_err;      // device status word set by bounded waits in the kernels
+    int row_variant;   // kernel variant of each pass (-1: per-size default)
+    int col_variant;
 };
 
 namespace {
@@ -133,6 +140,7 @@ fft2d_status run_pass(const fft2d_plan_s *p, int pass, const void *in, void *out
     a.ld = p->cols;
     a.scale = 1.0f;
     a.err = p->dev_err;
+    a.variant = (pass == FFT2D_PASS_ROWS) ? p->row_variant : p->col_variant;
     const int L = (pass == FFT2D_PASS_ROWS) ? p->Lc : p->Lr;
     a.nst = nst < 0 ? L : nst;
     a.partial = a.nst < L;
@@ -175,6 +183,96 @@ fft2d_status exec_impl(const fft2d_plan_s *p, const void *in, void *out, int rs,
     if (p->Lr == 0)
         return FFT2D_OK;   // one row: nothing along the columns
     return run_pass(p, FFT2D_PASS_COLS, out, out, cs, full, st);
+}
+
+// ---------------------------------------------------------------- autotuning
+// Winners of past tunings, keyed by (device, pass, log2 axis length, number
+// of lines): later plans of the same shape start from them.  Optionally
+// mirrored in the text file named by the FFT2D_TUNE_CACHE environment
+// variable, one "device-name<TAB>pass<TAB>L<TAB>lines<TAB>variant-name" line
+// per entry, so that a new process does not have to tune again.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, int> g_tuned;
+bool g_tune_file_loaded = false;
+
+std::string device_name(int dev)
+{
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+        return "unknown";
+    return prop.name;
+}
+
+int variant_index(int pass, int L, const char *name)
+{
+    int n = 0;
+    const fft2d::Variant *v =
+        pass == FFT2D_PASS_ROWS ? fft2d::row_variants(L, &n) : fft2d::col_variants(L, &n);
+    for (int i = 0; i < n; i++)
+        if (std::strcmp(v[i].name, name) == 0)
+            return i;
+    return -1;
+}
+
+void load_tune_file_locked(int dev)
+{
+    if (g_tune_file_loaded)
+        return;
+    g_tune_file_loaded = true;
+    const char *path = std::getenv("FFT2D_TUNE_CACHE");
+    if (!path || !*path)
+        return;
+    FILE *f = std::fopen(path, "r");
+    if (!f)
+        return;
+    const std::string me = device_name(dev);
+    char line[512];
+    while (std::fgets(line, sizeof line, f)) {
+        char name[256], var[64];
+        int pass, L, lines;
+        if (std::sscanf(line, "%255[^\t]\t%d\t%d\t%d\t%63s", name, &pass, &L, &lines, var) != 5)
+            continue;
+        if (me != name || L < 1 || L > 14)
+            continue;
+        const int idx = variant_index(pass, L, var);
+        if (idx >= 0)
+            g_tuned[std::make_tuple(dev, pass, L, lines)] = idx;
+    }
+    std::fclose(f);
+}
+
+void save_tune_file_locked()
+{
+    const char *path = std::getenv("FFT2D_TUNE_CACHE");
+    if (!path || !*path)
+        return;
+    FILE *f = std::fopen(path, "w");
+    if (!f)
+        return;
+    for (const auto &kv : g_tuned) {
+        const int dev = std::get<0>(kv.first), pass = std::get<1>(kv.first);
+        const int L = std::get<2>(kv.first), lines = std::get<3>(kv.first);
+        int n = 0;
+        const fft2d::Variant *v =
+            pass == FFT2D_PASS_ROWS ? fft2d::row_variants(L, &n) : fft2d::col_variants(L, &n);
+        if (kv.second < 0 || kv.second >= n)
+            continue;
+        std::fprintf(f, "%s\t%d\t%d\t%d\t%s\n", device_name(dev).c_str(), pass, L, lines,
+                     v[kv.second].name);
+    }
+    std::fclose(f);
+}
+
+void apply_tuned(fft2d_plan_s *p)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    load_tune_file_locked(p->device);
+    auto r = g_tuned.find(std::make_tuple(p->device, (int)FFT2D_PASS_ROWS, p->Lc, p->rows));
+    if (r != g_tuned.end())
+        p->row_variant = r->second;
+    auto c = g_tuned.find(std::make_tuple(p->device, (int)FFT2D_PASS_COLS, p->Lr, p->cols));
+    if (c != g_tuned.end())
+        p->col_variant = c->second;
 }
 
 }  // namespace
@@ -222,6 +320,8 @@ fft2d_status fft2d_plan(int rows, int cols, int dtype, int dir, fft2d_plan_t *ou
     p->Lc = log2_exact(cols);
     p->dtype = dtype;
     p->dir = dir;
+    p->row_variant = -1;
+    p->col_variant = -1;
     cudaError_t e = cudaGetDevice(&p->device);
     if (e != cudaSuccess) {
         delete p;
@@ -257,7 +357,163 @@ fft2d_status fft2d_plan(int rows, int cols, int dtype, int dir, fft2d_plan_t *ou
         delete p;
         return cuda_fail(e, "cudaMemcpy twiddles");
     }
+    apply_tuned(p);
     *out = p;
+    return FFT2D_OK;
+}
+
+fft2d_status fft2d_autotune(fft2d_plan_t p, void *stream)
+{
+    if (!p)
+        return FFT2D_ERR_ARG;
+    fft2d_status s = check_device(p);
+    if (s != FFT2D_OK)
+        return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t bytes = (size_t)p->rows * p->cols * sizeof(float2);
+    void *a = nullptr, *b = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&a, bytes);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&b, bytes);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(a, 0, bytes, st);
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&e0);
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&e1);
+    fft2d_status result = FFT2D_OK;
+    for (int pass = 0; pass < 2 && e == cudaSuccess; pass++) {
+        const int L = pass == FFT2D_PASS_ROWS ? p->Lc : p->Lr;
+        if (L == 0)
+            continue;
+        int n = 0;
+        const fft2d::Variant *v =
+            pass == FFT2D_PASS_ROWS ? fft2d::row_variants(L, &n) : fft2d::col_variants(L, &n);
+        fft2d::PassArgs args;
+        args.in = static_cast<const float2 *>(pass == FFT2D_PASS_ROWS ? a : b);
+        args.out = static_cast<float2 *>(b);
+        args.tw = pass == FFT2D_PASS_ROWS ? p->tw_rows : p->tw_cols;
+        args.rows = p->rows;
+        args.cols = p->cols;
+        args.ld = p->cols;
+        args.scale = 1.0f;
+        args.nst = L;
+        args.partial = false;
+        args.err = p->dev_err;
+        int best = -1;
+        float best_ms = 0.f;
+        for (int i = 0; i < n && e == cudaSuccess; i++) {
+            args.variant = i;
+            if (!v[i].usable(args))
+                continue;
+            for (int w = 0; w < 2 && e == cudaSuccess; w++)
+                e = v[i].launch(args, st);
+            const int reps = 5;
+            if (e == cudaSuccess)
+                e = cudaEventRecord(e0, st);
+            for (int r = 0; r < reps && e == cudaSuccess; r++)
+                e = v[i].launch(args, st);
+            if (e == cudaSuccess)
+                e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess)
+                e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess)
+                e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && (best < 0 || ms < best_ms)) {
+                best = i;
+                best_ms = ms;
+            }
+        }
+        if (e == cudaSuccess && best >= 0) {
+            const int lines = pass == FFT2D_PASS_ROWS ? p->rows : p->cols;
+            if (pass == FFT2D_PASS_ROWS)
+                p->row_variant = best;
+            else
+                p->col_variant = best;
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            load_tune_file_locked(p->device);
+            g_tuned[std::make_tuple(p->device, pass, L, lines)] = best;
+            save_tune_file_locked();
+        }
+    }
+    if (e != cudaSuccess)
+        result = cuda_fail(e, "fft2d_autotune");
+    if (e0)
+        cudaEventDestroy(e0);
+    if (e1)
+        cudaEventDestroy(e1);
+    cudaFree(a);
+    cudaFree(b);
+    // a timeout during tuning is not the caller's business: clear the word
+    cudaMemset(p->dev_err, 0, sizeof(int));
+    return result;
+}
+
+int fft2d_variant_count(int pass, int L)
+{
+    if ((pass != FFT2D_PASS_ROWS && pass != FFT2D_PASS_COLS) || L < 1 || L > 14)
+        return 0;
+    int n = 0;
+    if (pass == FFT2D_PASS_ROWS)
+        fft2d::row_variants(L, &n);
+    else
+        fft2d::col_variants(L, &n);
+    return n;
+}
+
+const char *fft2d_variant_name(int pass, int L, int index)
+{
+    const int n = fft2d_variant_count(pass, L);
+    if (index < 0 || index >= n)
+        return "";
+    int m = 0;
+    const fft2d::Variant *v =
+        pass == FFT2D_PASS_ROWS ? fft2d::row_variants(L, &m) : fft2d::col_variants(L, &m);
+    return v[index].name;
+}
+
+fft2d_status fft2d_plan_set_variant(fft2d_plan_t p, int pass, int variant)
+{
+    if (!p || (pass != FFT2D_PASS_ROWS && pass != FFT2D_PASS_COLS))
+        return FFT2D_ERR_ARG;
+    const int L = pass == FFT2D_PASS_ROWS ? p->Lc : p->Lr;
+    if (variant < -1 || variant >= fft2d_variant_count(pass, L) + (L == 0 ? 1 : 0))
+        return FFT2D_ERR_ARG;
+    if (pass == FFT2D_PASS_ROWS)
+        p->row_variant = variant;
+    else
+        p->col_variant = variant;
+    return FFT2D_OK;
+}
+
+fft2d_status fft2d_plan_describe(fft2d_plan_t p, char *buf, int len)
+{
+    if (!p || !buf || len <= 0)
+        return FFT2D_ERR_ARG;
+    std::string out;
+    for (int pass = 0; pass < 2; pass++) {
+        const int L = pass == FFT2D_PASS_ROWS ? p->Lc : p->Lr;
+        out += pass == FFT2D_PASS_ROWS ? "rows:" : " cols:";
+        if (L == 0) {
+            out += "identity";
+            continue;
+        }
+        int n = 0;
+        const fft2d::Variant *v =
+            pass == FFT2D_PASS_ROWS ? fft2d::row_variants(L, &n) : fft2d::col_variants(L, &n);
+        int i = pass == FFT2D_PASS_ROWS ? p->row_variant : p->col_variant;
+        const bool tuned = i >= 0;
+        if (i < 0 || i >= n)
+            i = pass == FFT2D_PASS_ROWS ? fft2d::row_default_variant(L)
+                                        : fft2d::col_default_variant(L);
+        char tmp[96];
+        std::snprintf(tmp, sizeof tmp, "%s(shape=%d,ept=%d,%s)", v[i].name, v[i].shape, v[i].ept,
+                      tuned ? "tuned" : "default");
+        out += tmp;
+    }
+    std::snprintf(buf, (size_t)len, "%s", out.c_str());
     return FFT2D_OK;
 }
 
@@ -411,9 +667,47 @@ fft2d_status fft2d_exec_batched(int n, const fft2d_plan_t *plans, const void *co
         fft2d_status s = check_device(plans[i]);
         if (s != FFT2D_OK)
             return s;
-        s = exec_impl(plans[i], in[i], out[i], -1, -1, static_cast<cudaStream_t>(stream));
-        if (s != FFT2D_OK)
-            return s;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // images with a length-1 side take the single-image path
+    for (int i = 0; i < n; i++) {
+        if (plans[i]->Lr == 0 || plans[i]->Lc == 0) {
+            fft2d_status s = exec_impl(plans[i], in[i], out[i], -1, -1, st);
+            if (s != FFT2D_OK)
+                return s;
+        }
+    }
+    // grouped row passes (in -> out), then grouped column passes (out, in place)
+    static thread_local fft2d::BatchTable table;
+    for (int pass = 0; pass < 2; pass++) {
+        const bool row = pass == 0;
+        for (int L = 1; L <= 14; L++) {
+            table.n = 0;
+            for (int i = 0; i <= n; i++) {
+                const bool flush = (i == n) || table.n == fft2d::kBatchMaxJobs;
+                if (flush && table.n > 0) {
+                    cudaError_t e = fft2d::launch_batch_pass(row, L, table, st);
+                    if (e != cudaSuccess)
+                        return cuda_fail(e, row ? "batched row pass" : "batched column pass");
+                    table.n = 0;
+                }
+                if (i == n)
+                    break;
+                const fft2d_plan_s *p = plans[i];
+                if (p->Lr == 0 || p->Lc == 0 || (row ? p->Lc : p->Lr) != L)
+                    continue;
+                fft2d::BatchJob &j = table.job[table.n++];
+                j.in = static_cast<const float2 *>(row ? in[i] : out[i]);
+                j.out = static_cast<float2 *>(out[i]);
+                j.tw = row ? p->tw_rows : p->tw_cols;
+                j.ld = p->cols;
+                j.lines = row ? p->rows : p->cols;
+                j.first_cta = 0;
+                j.scale = (!row && p->dir == FFT2D_INVERSE)
+                              ? (float)(1.0 / ((double)p->rows * (double)p->cols))
+                              : 1.0f;
+            }
+        }
     }
     return FFT2D_OK;
 }

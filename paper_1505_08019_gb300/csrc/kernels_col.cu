@@ -54,12 +54,6 @@ int device_sm_count()
     return cache[d];
 }
 
-// 2^14 values (128 KB of shared memory) per CTA from 1024-point columns up;
-// 16 to 64 columns per CTA below.
-static constexpr int col_kw(int L)
-{
-    return L >= 10 ? 14 - L : (13 - L < 4 ? 4 : (13 - L > 6 ? 6 : 13 - L));
-}
 
 int col_width(int L) { return 1 << col_kw(L); }
 
@@ -84,10 +78,11 @@ cudaError_t launch_selftest_timeout(int *err, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <int L, bool GENERIC>
-static cudaError_t col_launch(const PassArgs &a, cudaStream_t s)
+namespace {
+
+template <class C, bool GENERIC>
+cudaError_t col_launch(const PassArgs &a, cudaStream_t s)
 {
-    using C = LineCfg<L, col_kw(L), 0>;
     auto k = col_pass_kernel<C, GENERIC>;
     const int dev_bytes = C::SMEM_BYTES;
     if (dev_bytes > 48 * 1024) {
@@ -101,20 +96,26 @@ static cudaError_t col_launch(const PassArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// Persistent TMA-fed variant (see col_tma_kernel): whole tiles only, input
-// 16-byte aligned, row pitch a multiple of 16 bytes.
-// Values per thread of the TMA column kernel: 32 for tiles of 2^14 values
-// (512 threads of up to 128 registers), 16 below.
-static constexpr int col_tma_ept(int L) { return L >= 10 ? 32 : 16; }
-
-template <int L>
-static cudaError_t col_launch_tma(const PassArgs &a, cudaStream_t s, bool *used)
+template <class C>
+cudaError_t col_launch_any(const PassArgs &a, cudaStream_t s)
 {
-    using C = LineCfg<L, col_kw(L), 0, col_tma_ept(L)>;
-    *used = false;
+    const bool generic = a.partial || a.cols % C::W != 0;
+    return generic ? col_launch<C, true>(a, s) : col_launch<C, false>(a, s);
+}
+
+template <class C>
+bool col_tma_usable(const PassArgs &a)
+{
+    return !a.partial && a.err && tensor_map_encoder() &&
+           !(reinterpret_cast<uintptr_t>(a.in) & 15) && !((a.ld * 8) & 15) && a.cols % C::W == 0;
+}
+
+// Persistent TMA-fed column pass (col_tma2_kernel).  Falls back to the plain
+// kernel if the tile cannot be described by a tensor map.
+template <class C>
+cudaError_t col_launch_tma(const PassArgs &a, cudaStream_t s)
+{
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-    if (!enc || (reinterpret_cast<uintptr_t>(a.in) & 15) || ((a.ld * 8) & 15))
-        return cudaSuccess;
     CUtensorMap map;
     const int box_rows = C::N < 256 ? C::N : 256;
     cuuint64_t dims[2] = {(cuuint64_t)a.cols, (cuuint64_t)a.rows};
@@ -126,7 +127,7 @@ static cudaError_t col_launch_tma(const PassArgs &a, cudaStream_t s, bool *used)
                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
-        return cudaSuccess;   // not expressible as a tensor map: plain kernel
+        return col_launch_any<LineCfg<C::L, C::KW, 0>>(a, s);
     auto k = col_tma2_kernel<C>;
     constexpr int SMEM = TmaSplit<C>::SMEM_BYTES;
     static int occ[kMaxDev] = {};
@@ -147,44 +148,155 @@ static cudaError_t col_launch_tma(const PassArgs &a, cudaStream_t s, bool *used)
     if (grid > ntiles)
         grid = ntiles;
     k<<<grid, C::T, SMEM, s>>>(map, a.out, a.tw, a.cols, a.ld, a.scale, a.err);
-    *used = true;
     return cudaGetLastError();
 }
 
-template <int L>
-static cudaError_t col_dispatch(const PassArgs &a, cudaStream_t s)
+template <class CC>
+bool col_cluster_usable(const PassArgs &a)
 {
-    const bool generic = a.partial || a.cols < col_width(L);
-    if constexpr (L >= 9 && L <= 12) {
-        if (!generic && a.err) {
-            bool used = false;
-            cudaError_t e = col_launch_tma<L>(a, s, &used);
-            if (e != cudaSuccess || used)
-                return e;
-        }
+    return !a.partial && a.cols % CC::W == 0;
+}
+
+// Cluster column pass (col_cluster_kernel): CS CTAs share a tile, the last
+// log2(CS) stages run through distributed shared memory.
+template <class CC>
+cudaError_t col_launch_cluster(const PassArgs &a, cudaStream_t s)
+{
+    auto k = col_cluster_kernel<CC, false>;
+    static bool attr[kMaxDev] = {};
+    const int d = current_device();
+    if (!attr[d]) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             CC::SMEM_BYTES);
+        if (e == cudaSuccess && CC::CS > 8)
+            e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess)
+            return e;
+        attr[d] = true;
     }
-    return generic ? col_launch<L, true>(a, s) : col_launch<L, false>(a, s);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CC::CS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(a.cols / CC::W * CC::CS));
+    cfg.blockDim = dim3(CC::T);
+    cfg.dynamicSmemBytes = CC::SMEM_BYTES;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, a.in, a.out, a.tw, a.cols, a.ld, a.scale, a.nst);
+}
+
+bool always(const PassArgs &) { return true; }
+bool whole_stages(const PassArgs &a) { return !a.partial; }
+
+// Values per thread of the TMA column kernel: 32 for tiles of 2^14 values
+// (512 threads of up to 128 registers), 16 below.
+constexpr int col_tma_ept(int L) { return L >= 10 ? 32 : 16; }
+
+template <int L>
+struct ColVariants {
+    using Plain = LineCfg<L, col_kw(L), 0>;
+    static constexpr bool HASTMA = L >= 9 && L <= 12;
+    using Tma32 = LineCfg<L, col_kw(L), 0, col_tma_ept(L)>;
+    using Tma16 = LineCfg<L, col_kw(L), 0, 16>;
+    static constexpr int KWN = col_kw(L) - 1;                 // narrower tiles
+    static constexpr bool HASNARROW = L >= 5 && KWN >= 2;
+    using Narrow = LineCfg<L, (KWN >= 0 ? KWN : 0), 0>;
+    // cluster shapes: W = 8 over 2 (2048 rows) or 4 (4096 rows) CTAs;
+    // W = 4 over 2 or 4 CTAs for 8192 and 16384 rows
+    static constexpr int CKW = L <= 12 ? 3 : 2;
+    static constexpr int CC_ = L <= 11 ? 1 : (L == 12 ? 2 : (L == 13 ? 1 : 2));
+    static constexpr bool HASCLUSTER = L >= 11;
+    using Clu = ClusterColCfg<(L >= 11 ? L : 11), CKW, CC_>;
+
+    struct Table {
+        Variant v[6];
+        int n = 0;
+    };
+    static Table build()
+    {
+        Table t;
+        t.v[t.n++] = {"plain", Plain::W, 16, always, col_launch_any<Plain>};
+        if constexpr (HASTMA) {
+            t.v[t.n++] = {Tma32::EPT == 32 ? "tma32" : "tma", Tma32::W, Tma32::EPT,
+                          col_tma_usable<Tma32>, col_launch_tma<Tma32>};
+            if constexpr (Tma32::EPT == 32)
+                t.v[t.n++] = {"tma16", Tma16::W, 16, col_tma_usable<Tma16>, col_launch_tma<Tma16>};
+        }
+        if constexpr (HASNARROW)
+            t.v[t.n++] = {"narrow", Narrow::W, 16, whole_stages, col_launch_any<Narrow>};
+        if constexpr (HASCLUSTER)
+            t.v[t.n++] = {"cluster", Clu::W, 16, col_cluster_usable<Clu>, col_launch_cluster<Clu>};
+        return t;
+    }
+    static const Variant *table(int *n)
+    {
+        static const Table t = build();
+        *n = t.n;
+        return t.v;
+    }
+    static int preferred()
+    {
+        if constexpr (HASTMA)
+            return 1;   // measured fastest for 512..4096-row columns
+        else if constexpr (L >= 13) {
+            int n;
+            table(&n);
+            return n - 1;   // cluster: keeps >= 32-byte row segments
+        } else
+            return 0;
+    }
+};
+
+}  // namespace
+
+const Variant *col_variants(int L, int *n)
+{
+    switch (L) {
+    case 1: return ColVariants<1>::table(n);
+    case 2: return ColVariants<2>::table(n);
+    case 3: return ColVariants<3>::table(n);
+    case 4: return ColVariants<4>::table(n);
+    case 5: return ColVariants<5>::table(n);
+    case 6: return ColVariants<6>::table(n);
+    case 7: return ColVariants<7>::table(n);
+    case 8: return ColVariants<8>::table(n);
+    case 9: return ColVariants<9>::table(n);
+    case 10: return ColVariants<10>::table(n);
+    case 11: return ColVariants<11>::table(n);
+    case 12: return ColVariants<12>::table(n);
+    case 13: return ColVariants<13>::table(n);
+    case 14: return ColVariants<14>::table(n);
+    default: *n = 0; return nullptr;
+    }
+}
+
+int col_default_variant(int L)
+{
+    switch (L) {
+    case 9: return ColVariants<9>::preferred();
+    case 10: return ColVariants<10>::preferred();
+    case 11: return ColVariants<11>::preferred();
+    case 12: return ColVariants<12>::preferred();
+    case 13: return ColVariants<13>::preferred();
+    case 14: return ColVariants<14>::preferred();
+    default: return 0;
+    }
 }
 
 cudaError_t launch_col_pass(int L, const PassArgs &a, cudaStream_t s)
 {
-    switch (L) {
-    case 1: return col_dispatch<1>(a, s);
-    case 2: return col_dispatch<2>(a, s);
-    case 3: return col_dispatch<3>(a, s);
-    case 4: return col_dispatch<4>(a, s);
-    case 5: return col_dispatch<5>(a, s);
-    case 6: return col_dispatch<6>(a, s);
-    case 7: return col_dispatch<7>(a, s);
-    case 8: return col_dispatch<8>(a, s);
-    case 9: return col_dispatch<9>(a, s);
-    case 10: return col_dispatch<10>(a, s);
-    case 11: return col_dispatch<11>(a, s);
-    case 12: return col_dispatch<12>(a, s);
-    case 13: return col_dispatch<13>(a, s);
-    case 14: return col_dispatch<14>(a, s);
-    default: return cudaErrorInvalidValue;
-    }
+    int n = 0;
+    const Variant *v = col_variants(L, &n);
+    if (!v || n == 0)
+        return cudaErrorInvalidValue;
+    int i = a.variant >= 0 && a.variant < n ? a.variant : col_default_variant(L);
+    if (!v[i].usable(a))
+        i = 0;   // the plain kernel serves every case
+    return v[i].launch(a, s);
 }
 
 }  // namespace fft2d

@@ -1,21 +1,25 @@
-// kernels_row.cu -- row pass instantiations: every row of an image is one line
-// of cols = 2^L points (contiguous), LB rows per CTA, 256 threads per CTA up to
-// 4096-point rows.
+// kernels_row.cu -- row pass kernel variants: every row of an image is one
+// line of cols = 2^L contiguous points.
+//
+// Variants per line length (the autotuner picks among the usable ones):
+//   0  plain   : LB = 2^row_kb(L) rows per CTA, 256 threads x 16 values,
+//                scrambled global loads (the default)
+//   1  plain32 : the same rows per CTA with 32 values per thread
+//   2  plain2x : twice the rows per CTA (two line blocks in flight)
+//   3  tma     : persistent, double-buffered TMA bulk loads (16-byte aligned,
+//                dense whole blocks only)
 #include "line_fft.cuh"
 #include "passes.h"
 
 namespace fft2d {
 
-static constexpr int row_kb(int L) { return L <= 12 ? 12 - L : 0; }
-// values per thread (32 measured no faster for 4096-point rows)
-static constexpr int row_ept(int) { return 16; }
-
 int row_lines_per_cta(int L) { return 1 << row_kb(L); }
 
-template <int L, bool GENERIC>
-static cudaError_t row_launch(const PassArgs &a, cudaStream_t s)
+namespace {
+
+template <class C, bool GENERIC>
+cudaError_t row_launch(const PassArgs &a, cudaStream_t s)
 {
-    using C = LineCfg<L, 0, row_kb(L), row_ept(L)>;
     auto k = row_pass_kernel<C, GENERIC>;
     const int dev_bytes = C::SMEM_BYTES;
     if (dev_bytes > 48 * 1024) {
@@ -29,16 +33,24 @@ static cudaError_t row_launch(const PassArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// Persistent TMA-fed variant (row_tma_kernel): whole blocks of LB rows only,
-// input 16-byte aligned, row pitch a multiple of 16 bytes.
-template <int L>
-static cudaError_t row_launch_tma(const PassArgs &a, cudaStream_t s, bool *used)
+template <class C>
+cudaError_t row_launch_any(const PassArgs &a, cudaStream_t s)
 {
-    using C = LineCfg<L, 0, row_kb(L)>;
+    const bool generic = a.partial || a.rows % C::LB != 0;
+    return generic ? row_launch<C, true>(a, s) : row_launch<C, false>(a, s);
+}
+
+template <class C>
+bool row_tma_usable(const PassArgs &a)
+{
+    return !a.partial && a.err && !(reinterpret_cast<uintptr_t>(a.in) & 15) &&
+           !((a.ld * 8) & 15) && a.rows % C::LB == 0;
+}
+
+template <class C>
+cudaError_t row_launch_tma(const PassArgs &a, cudaStream_t s)
+{
     constexpr int SMEM = RowTma<C>::SMEM_BYTES;
-    *used = false;
-    if ((reinterpret_cast<uintptr_t>(a.in) & 15) || ((a.ld * 8) & 15) || a.rows % C::LB)
-        return cudaSuccess;
     auto k = row_tma_kernel<C>;
     constexpr int kMaxDev = 64;
     static int occ[kMaxDev] = {};
@@ -58,48 +70,81 @@ static cudaError_t row_launch_tma(const PassArgs &a, cudaStream_t s, bool *used)
     if (grid > ntiles)
         grid = ntiles;
     k<<<grid, C::T, SMEM, s>>>(a.in, a.out, a.tw, a.rows, a.ld, a.scale, a.err);
-    *used = true;
     return cudaGetLastError();
 }
 
-// The plain kernel keeps 4 CTAs of 256 threads on every SM, which already
-// overlaps loads with compute; the TMA variant's double buffer costs one CTA
-// per SM and measured slower at 4096 points, so it serves only on request
-// (row_variant == 1).
+bool always(const PassArgs &) { return true; }
+bool whole_stages(const PassArgs &a) { return !a.partial; }
+
 template <int L>
-static cudaError_t row_dispatch(const PassArgs &a, cudaStream_t s)
-{
-    const bool generic = a.partial || a.rows < row_lines_per_cta(L);
-    if constexpr (L >= 5 && L <= 13) {
-        if (!generic && a.err && a.variant == 1) {
-            bool used = false;
-            cudaError_t e = row_launch_tma<L>(a, s, &used);
-            if (e != cudaSuccess || used)
-                return e;
-        }
+struct RowVariants {
+    using Plain = LineCfg<L, 0, row_kb(L), 16>;
+    using Plain32 = LineCfg<L, 0, row_kb(L), 32>;
+    static constexpr int KB2 = row_kb(L) + 1;
+    using Plain2x = LineCfg<L, 0, KB2, 16>;
+    static constexpr bool HAS32 = L >= 5 && Plain32::E >= 32;
+    static constexpr bool HAS2X = L >= 5 && L <= 13 && Plain2x::E * 8 <= 128 * 1024;
+    static constexpr bool HASTMA = L >= 5 && L <= 13;
+
+    struct Table {
+        Variant v[4];
+        int n = 0;
+    };
+    static Table build()
+    {
+        Table t;
+        t.v[t.n++] = {"plain", 1 << row_kb(L), 16, always, row_launch_any<Plain>};
+        if constexpr (HAS32)
+            t.v[t.n++] = {"plain32", 1 << row_kb(L), 32, whole_stages, row_launch_any<Plain32>};
+        if constexpr (HAS2X)
+            t.v[t.n++] = {"plain2x", 1 << KB2, 16, whole_stages, row_launch_any<Plain2x>};
+        if constexpr (HASTMA)
+            t.v[t.n++] = {"tma", 1 << row_kb(L), 16, row_tma_usable<Plain>, row_launch_tma<Plain>};
+        return t;
     }
-    return generic ? row_launch<L, true>(a, s) : row_launch<L, false>(a, s);
+    static const Variant *table(int *n)
+    {
+        static const Table t = build();
+        *n = t.n;
+        return t.v;
+    }
+};
+
+}  // namespace
+
+const Variant *row_variants(int L, int *n)
+{
+    switch (L) {
+    case 1: return RowVariants<1>::table(n);
+    case 2: return RowVariants<2>::table(n);
+    case 3: return RowVariants<3>::table(n);
+    case 4: return RowVariants<4>::table(n);
+    case 5: return RowVariants<5>::table(n);
+    case 6: return RowVariants<6>::table(n);
+    case 7: return RowVariants<7>::table(n);
+    case 8: return RowVariants<8>::table(n);
+    case 9: return RowVariants<9>::table(n);
+    case 10: return RowVariants<10>::table(n);
+    case 11: return RowVariants<11>::table(n);
+    case 12: return RowVariants<12>::table(n);
+    case 13: return RowVariants<13>::table(n);
+    case 14: return RowVariants<14>::table(n);
+    default: *n = 0; return nullptr;
+    }
 }
+
+int row_default_variant(int) { return 0; }
 
 cudaError_t launch_row_pass(int L, const PassArgs &a, cudaStream_t s)
 {
-    switch (L) {
-    case 1: return row_dispatch<1>(a, s);
-    case 2: return row_dispatch<2>(a, s);
-    case 3: return row_dispatch<3>(a, s);
-    case 4: return row_dispatch<4>(a, s);
-    case 5: return row_dispatch<5>(a, s);
-    case 6: return row_dispatch<6>(a, s);
-    case 7: return row_dispatch<7>(a, s);
-    case 8: return row_dispatch<8>(a, s);
-    case 9: return row_dispatch<9>(a, s);
-    case 10: return row_dispatch<10>(a, s);
-    case 11: return row_dispatch<11>(a, s);
-    case 12: return row_dispatch<12>(a, s);
-    case 13: return row_dispatch<13>(a, s);
-    case 14: return row_dispatch<14>(a, s);
-    default: return cudaErrorInvalidValue;
-    }
+    int n = 0;
+    const Variant *v = row_variants(L, &n);
+    if (!v || n == 0)
+        return cudaErrorInvalidValue;
+    int i = a.variant >= 0 && a.variant < n ? a.variant : row_default_variant(L);
+    if (!v[i].usable(a))
+        i = 0;   // the plain kernel serves every case
+    return v[i].launch(a, s);
 }
 
 }  // namespace fft2d

@@ -124,6 +124,15 @@ __device__ __forceinline__ float2 ld_tw(const float2 *p)
         return __ldg(p);
 }
 
+// W * b with one fixed rounding sequence (one product rounded, one fused
+// multiply-add), so that every kernel variant -- whatever the compiler would
+// otherwise contract -- produces the same bits.
+__device__ __forceinline__ float2 cmul_w(float2 w, float2 b)
+{
+    return make_float2(__fmaf_rn(w.x, b.x, __fmul_rn(-w.y, b.y)),
+                       __fmaf_rn(w.x, b.y, __fmul_rn(w.y, b.x)));
+}
+
 // Stages S0+1 .. S0+G on unit v of a[]: pairs (r, r + 2^t) at stage S0+1+t use
 // W_{2^s}^j with j = lo + (r mod 2^t) 2^S0.
 template <class Gp, bool FIRST, bool GENERIC, bool TWS = false, int NA>
@@ -147,12 +156,10 @@ __device__ __forceinline__ void run_stages_g(float2 (&a)[NA], int v, int lo,
             if (FIRST && jc == 0) {
                 m = x1;   // W = 1
             } else {
-                const float2 w = ld_tw<TWS>(tws + lo + jc);
-                m.x = w.x * x1.x - w.y * x1.y;
-                m.y = w.x * x1.y + w.y * x1.x;
+                m = cmul_w(ld_tw<TWS>(tws + lo + jc), x1);
             }
-            x1 = make_float2(x0.x - m.x, x0.y - m.y);
-            x0 = make_float2(x0.x + m.x, x0.y + m.y);
+            x1 = make_float2(__fsub_rn(x0.x, m.x), __fsub_rn(x0.y, m.y));
+            x0 = make_float2(__fadd_rn(x0.x, m.x), __fadd_rn(x0.y, m.y));
         }
     }
 }

@@ -16,13 +16,57 @@ struct PassArgs {
     int nst;             // stages to run on this axis (partial debug view)
     bool partial;        // nst < log2(axis length)
     int *err;            // device status word (bounded-wait timeouts)
-    int variant = 0;     // kernel variant (0 = default for this size)
+    int variant = -1;    // kernel variant index (-1: the default for this size)
 };
+
+// One way to run a pass for one line length (see kernels_row.cu and
+// kernels_col.cu for the lists).  `usable` says whether it can serve these
+// arguments (alignment, whole tiles, ...); the plain variant 0 serves all.
+struct Variant {
+    const char *name;
+    int shape;     // rows per CTA (row pass) or adjacent columns per tile (column pass)
+    int ept;       // values per thread
+    bool (*usable)(const PassArgs &);
+    cudaError_t (*launch)(const PassArgs &, cudaStream_t);
+};
+const Variant *row_variants(int L, int *n);
+const Variant *col_variants(int L, int *n);
+int row_default_variant(int L);
+int col_default_variant(int L);
+
+// Per-size CTA shapes of the plain kernels: log2 of the rows per CTA of the
+// row pass (256 threads per CTA up to 4096-point rows) and log2 of the
+// adjacent columns per CTA of the column pass (2^14 values per CTA from
+// 1024-point columns up, 16 to 64 columns below).
+constexpr int row_kb(int L) { return L <= 12 ? 12 - L : 0; }
+constexpr int col_kw(int L)
+{
+    return L >= 10 ? 14 - L : (13 - L < 4 ? 4 : (13 - L > 6 ? 6 : 13 - L));
+}
 
 // Lines per CTA of the row pass and interleaved columns per CTA of the
 // column pass for an axis of 2^L points.
 int row_lines_per_cta(int L);
 int col_width(int L);
+
+// Grouped launches over many images (batch.cu): one job per image, passed
+// by value as a kernel parameter.
+constexpr int kBatchMaxJobs = 128;
+struct BatchJob {
+    const float2 *in;
+    float2 *out;
+    const float2 *tw;
+    long long ld;
+    int lines;       // rows (row pass) or columns (column pass) of the image
+    int first_cta;   // filled by launch_batch_pass
+    float scale;
+};
+struct BatchTable {
+    int n;
+    BatchJob job[kBatchMaxJobs];
+};
+// One launch for every job of `t` whose axis has 2^L points.
+cudaError_t launch_batch_pass(bool row, int L, BatchTable &t, cudaStream_t s);
 
 cudaError_t launch_row_pass(int L, const PassArgs &a, cudaStream_t s);
 

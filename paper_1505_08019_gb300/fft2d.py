@@ -60,6 +60,11 @@ _sigs = {
                            _I),
     "fft2d_stage_table": ([_I, _I, _P], _I),
     "fft2d_exec_noalloc": ([_I, _I, _I, _P, _P, _P], _I),
+    "fft2d_autotune": ([_P, _P], _I),
+    "fft2d_variant_count": ([_I, _I], _I),
+    "fft2d_variant_name": ([_I, _I, _I], ctypes.c_char_p),
+    "fft2d_plan_set_variant": ([_P, _I, _I], _I),
+    "fft2d_plan_describe": ([_P, ctypes.c_char_p, _I], _I),
     "fft2d_strerror": ([_I], ctypes.c_char_p),
     "fft2d_last_error": ([], ctypes.c_char_p),
     "fft2d_version": ([], _I),
@@ -177,6 +182,29 @@ def fft2d_exec_noalloc(rows: int, cols: int, dir: int, inp, out, stream=None) ->
     """Plan-free transform that allocates no device memory (sides <= 4096)."""
     _check(lib.fft2d_exec_noalloc(rows, cols, dir, _dptr(inp), _dptr(out), _stream(stream)),
            "fft2d_exec_noalloc")
+
+
+def fft2d_autotune(plan: int, stream=None) -> None:
+    """Time the kernel variants for this plan's shape and keep the fastest."""
+    _check(lib.fft2d_autotune(plan, _stream(stream)), "fft2d_autotune")
+
+
+def fft2d_variant_count(pass_: int, L: int) -> int:
+    return lib.fft2d_variant_count(pass_, L)
+
+
+def fft2d_variant_name(pass_: int, L: int, index: int) -> str:
+    return lib.fft2d_variant_name(pass_, L, index).decode()
+
+
+def fft2d_plan_set_variant(plan: int, pass_: int, variant: int) -> None:
+    _check(lib.fft2d_plan_set_variant(plan, pass_, variant), "fft2d_plan_set_variant")
+
+
+def fft2d_plan_describe(plan: int) -> str:
+    buf = ctypes.create_string_buffer(256)
+    _check(lib.fft2d_plan_describe(plan, buf, 256), "fft2d_plan_describe")
+    return buf.value.decode()
 
 
 def fft2d_stage_table(L: int, dir: int = FFT2D_FORWARD):
