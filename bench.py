@@ -476,7 +476,8 @@ def run_batched(args):
                      "frac": gbs / peak, "peak_source": peak_src,
                      "algorithmic_bytes_per_step": 32 * px},
         "rel_l2_samples": errs, "tolerance": 1e-5,
-        "gpu_launches_per_step": None,
+        "gpu_launches_per_step": len({c for _, c in shapes}) + len({r for r, _ in shapes}),
+        "gpu_launches_per_step_single": 2 * len(shapes),
     }
     print(json.dumps(line), flush=True)
 
