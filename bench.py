@@ -41,9 +41,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["fft4096", "batched"], default="fft4096",
+    ap.add_argument("--workload", choices=["fft4096", "batched", "fp16"], default="fft4096",
                     help="fft4096: the 4096x4096 forward+inverse benchmark (default); "
-                         "batched: 64 uneven images through the grouped executor")
+                         "batched: 64 uneven images through the grouped executor; "
+                         "fp16: half2 storage vs complex64 at 8192^2 and 16384^2")
     ap.add_argument("--images", type=int, default=4, help="resident images per rank")
     ap.add_argument("--side", type=int, default=SIDE)
     ap.add_argument("--e2e-steps", type=int, default=6)
@@ -482,12 +483,100 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ fp16 workload
+def run_fp16(args):
+    """8192^2 and 16384^2 forward transforms of re, im ~ U[-1,1): half2
+    storage with per-line exponents (fft2d_exec_h16) beside complex64
+    (fft2d_exec) on the same GPU, with the relative L2 error of each against
+    the FP64 oracle."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1505_08019_gb300 as fft
+    import synth
+    from oracle import oracle
+    orc = oracle.get()
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    peak, peak_src = measured_hbm_peak()
+    results = {}
+    for side in (8192, 16384):
+        x = synth.uniform_complex(side, side, seed=side)
+        dx = torch.from_numpy(x).cuda()
+        y = torch.empty_like(dx)
+        p32 = fft.fft2d_plan(side, side, fft.FFT2D_C64, fft.FFT2D_FORWARD)
+        p16 = fft.fft2d_plan(side, side, fft.FFT2D_C32H, fft.FFT2D_FORWARD)
+        q = torch.empty((side, side, 2), dtype=torch.float16, device="cuda")
+        qe = torch.empty(side, dtype=torch.int32, device="cuda")
+        fft.fft2d_h16_pack(side, side, dx, q, qe, sptr)
+        qo = torch.empty_like(q)
+        oe = torch.empty(side, dtype=torch.int32, device="cuda")
+
+        def t(fn, n):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(n):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / n
+
+        reps = 20 if side == 8192 else 8
+        ms32 = t(lambda: fft.fft2d_exec(p32, dx, y, sptr), reps)
+        ms16 = t(lambda: fft.fft2d_exec_h16(p16, q, qe, fft.FFT2D_PASS_ROWS, qo, oe, sptr), reps)
+        # accuracy against the FP64 oracle (of the input each path saw)
+        th = host_cores()
+        xin = torch.empty_like(dx)
+        fft.fft2d_h16_unpack(side, side, q, qe, fft.FFT2D_PASS_ROWS, xin, sptr)
+        got16 = torch.empty_like(dx)
+        fft.fft2d_h16_unpack(side, side, qo, oe, fft.FFT2D_PASS_COLS, got16, sptr)
+        torch.cuda.synchronize()
+        want32 = orc.fft2d(x, threads=th)
+        e32 = float(np.linalg.norm(y.cpu().numpy().astype(np.complex128) - want32)
+                    / np.linalg.norm(want32))
+        del want32
+        want16 = orc.fft2d(xin.cpu().numpy(), threads=th)
+        e16 = float(np.linalg.norm(got16.cpu().numpy().astype(np.complex128) - want16)
+                    / np.linalg.norm(want16))
+        del want16
+        px = side * side
+        results[f"{side}x{side}"] = {
+            "fp16_ms": ms16, "fp32_ms": ms32, "speedup_fp16_vs_fp32": ms32 / ms16,
+            "fp16_images_per_s": 1e3 / ms16, "fp32_images_per_s": 1e3 / ms32,
+            "fp16_hbm_frac": (16.0 * px / (ms16 * 1e-3) / 1e9) / peak,
+            "fp32_hbm_frac": (32.0 * px / (ms32 * 1e-3) / 1e9) / peak,
+            "fp16_rel_l2_vs_fp64_oracle": e16, "fp32_rel_l2_vs_fp64_oracle": e32,
+            "tolerance_fp16": 5e-3, "tolerance_fp32": 1e-5}
+        for p in (p32, p16):
+            fft.fft2d_destroy(p)
+        del dx, y, q, qo, xin, got16
+        torch.cuda.empty_cache()
+    big = results["16384x16384"]
+    line = {"metric": "2D FFT images/s, FP16 half2 storage vs complex64 (8192^2, 16384^2)",
+            "value": big["fp16_images_per_s"], "unit": "images/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32 (half2 storage)",
+            "data": "synthetic (seeded re, im ~ U[-1,1))",
+            "config": {"workload": "forward 2D FFT at 8192x8192 and 16384x16384; value = "
+                                   "16384^2 FP16 images/s"},
+            "roofline": {"bound": "hbm", "peak": peak, "unit": "GB/s", "peak_source": peak_src,
+                         "algorithmic_bytes_per_px": {"fp16": 16, "fp32": 32}},
+            "per_size": results}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "fp16":
+        run_fp16(args)
     else:
         run_ours(args)
 

@@ -54,6 +54,7 @@ typedef struct fft2d_plan_s *fft2d_plan_t;
 
 /* Storage types (dtype argument). */
 #define FFT2D_C64 0  /* complex64: float2 per pixel, FP32 arithmetic */
+#define FFT2D_C32H 1 /* half2 per pixel + a power-of-two exponent per line, FP32 arithmetic */
 
 /* Directions (dir argument). */
 #define FFT2D_FORWARD (-1)
@@ -190,6 +191,34 @@ FFT2D_API fft2d_status fft2d_exec_host(fft2d_plan_t plan, const void *in_host, v
  */
 FFT2D_API fft2d_status fft2d_exec_batched(int n, const fft2d_plan_t *plans, const void *const *in,
                                 void *const *out, void *stream);
+
+/*
+ * Half2 storage (plans created with FFT2D_C32H, sides >= 2).  A pixel is
+ * stored as q = (re, im) in IEEE half precision, and its value is q * 2^e
+ * where e is an int exponent shared by its whole row or whole column.  Each
+ * pass computes in FP32 (the same butterflies and rotation factors as the
+ * complex64 path) and, for every line it writes, picks e from the line's
+ * largest component magnitude M = f 2^k (f in [0.5, 1)) as e = k - 14, so
+ * that every stored |q| < 2^14.  Global traffic is half that of complex64.
+ *
+ * in: rows*cols half2 with exponents in_exp, one per row (in_axis =
+ * FFT2D_PASS_ROWS) or one per column (in_axis = FFT2D_PASS_COLS).
+ * out: rows*cols half2 (in == out allowed) with exponents written to
+ * out_exp, one per COLUMN (the column pass owns whole columns).  The row
+ * pass's per-row exponents live in the plan.  Asynchronous.
+ */
+FFT2D_API fft2d_status fft2d_exec_h16(fft2d_plan_t plan, const void *in, const int *in_exp,
+                                      int in_axis, void *out, int *out_exp, void *stream);
+
+/* complex64 -> half2 with one exponent per row (same rule as the passes);
+ * out_exp receives `rows` ints.  Device buffers, asynchronous. */
+FFT2D_API fft2d_status fft2d_h16_pack(int rows, int cols, const void *in, void *out,
+                                      int *out_exp, void *stream);
+
+/* half2 + exponents (one per row for axis FFT2D_PASS_ROWS, per column for
+ * FFT2D_PASS_COLS) -> complex64.  Device buffers, asynchronous. */
+FFT2D_API fft2d_status fft2d_h16_unpack(int rows, int cols, const void *in, const int *exps,
+                                        int axis, void *out, void *stream);
 
 /*
  * Host-only: write the rotation-factor table that a plan uploads for an axis

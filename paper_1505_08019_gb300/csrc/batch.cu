@@ -35,8 +35,8 @@ __global__ void __launch_bounds__(C::T, C::MINB) row_batch_kernel(const __grid_c
 {
     const BatchJob &jb = t.job[find_job<C>(t)];
     const long long r0 = (long long)((int)blockIdx.x - jb.first_cta) * C::LB;
-    line_fft<C, true, true>(jb.in + r0 * jb.ld, jb.out + r0 * jb.ld, jb.tw, jb.ld, jb.scale, C::L,
-                            jb.lines - r0);
+    line_fft<C, true, true, StoreC64>(StoreC64{jb.in, jb.out}, Geo{r0, 1, 0, jb.ld}, jb.tw,
+                                      jb.scale, C::L, jb.lines - r0);
 }
 
 template <class C>
@@ -44,8 +44,8 @@ __global__ void __launch_bounds__(C::T, C::MINB) col_batch_kernel(const __grid_c
 {
     const BatchJob &jb = t.job[find_job<C>(t)];
     const long long c0 = (long long)((int)blockIdx.x - jb.first_cta) * C::W;
-    line_fft<C, false, true>(jb.in + c0, jb.out + c0, jb.tw, jb.ld, jb.scale, C::L,
-                             jb.lines - c0);
+    line_fft<C, false, true, StoreC64>(StoreC64{jb.in, jb.out}, Geo{0, 1, c0, jb.ld}, jb.tw,
+                                       jb.scale, C::L, jb.lines - c0);
 }
 
 template <class C, bool ROW>

@@ -27,6 +27,7 @@ struct fft2d_plan_s {
     int *dev_err;      // device status word set by bounded waits in the kernels
     int row_variant;   // kernel variant of each pass (-1: per-size default)
     int col_variant;
+    int *exp_rows;     // half2 plans: exponents of the row pass output, one per row
 };
 
 namespace {
@@ -309,8 +310,10 @@ fft2d_status fft2d_plan(int rows, int cols, int dtype, int dir, fft2d_plan_t *ou
         return st;
     if (dir != FFT2D_FORWARD && dir != FFT2D_INVERSE)
         return FFT2D_ERR_ARG;
-    if (dtype != FFT2D_C64)
-        return dtype == 1 ? FFT2D_ERR_UNSUPPORTED : FFT2D_ERR_ARG;
+    if (dtype != FFT2D_C64 && dtype != FFT2D_C32H)
+        return FFT2D_ERR_ARG;
+    if (dtype == FFT2D_C32H && (rows < 2 || cols < 2))
+        return FFT2D_ERR_UNSUPPORTED;
     fft2d_plan_s *p = new (std::nothrow) fft2d_plan_s();
     if (!p)
         return FFT2D_ERR_OOM;
@@ -356,6 +359,17 @@ fft2d_status fft2d_plan(int rows, int cols, int dtype, int dir, fft2d_plan_t *ou
         cudaFree(p->dev_err);
         delete p;
         return cuda_fail(e, "cudaMemcpy twiddles");
+    }
+    if (dtype == FFT2D_C32H) {
+        e = cudaMalloc(&p->exp_rows, sizeof(int) * (size_t)rows);
+        if (e != cudaSuccess) {
+            cudaFree(p->tw_rows);
+            cudaFree(p->tw_cols);
+            cudaFree(p->dev_err);
+            delete p;
+            cuda_fail(e, "cudaMalloc exponents");
+            return FFT2D_ERR_OOM;
+        }
     }
     apply_tuned(p);
     *out = p;
@@ -451,6 +465,69 @@ fft2d_status fft2d_autotune(fft2d_plan_t p, void *stream)
     return result;
 }
 
+fft2d_status fft2d_exec_h16(fft2d_plan_t p, const void *in, const int *in_exp, int in_axis,
+                            void *out, int *out_exp, void *stream)
+{
+    if (!p || !in || !in_exp || !out || !out_exp || p->dtype != FFT2D_C32H ||
+        (in_axis != FFT2D_PASS_ROWS && in_axis != FFT2D_PASS_COLS))
+        return FFT2D_ERR_ARG;
+    fft2d_status s = check_device(p);
+    if (s != FFT2D_OK)
+        return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    fft2d::H16PassArgs a;
+    a.rows = p->rows;
+    a.cols = p->cols;
+    a.ld = p->cols;
+    // row pass: in -> out, per-row exponents into the plan
+    a.in = static_cast<const __half2 *>(in);
+    a.out = static_cast<__half2 *>(out);
+    a.tw = p->tw_rows;
+    a.scale = 1.0f;
+    a.nst = p->Lc;
+    a.in_exp = in_exp;
+    a.in_axis = in_axis;
+    a.out_exp = p->exp_rows;
+    cudaError_t e = fft2d::launch_pass_h16(true, p->Lc, a, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "half2 row pass");
+    // column pass: out -> out, per-column exponents to the caller
+    a.in = static_cast<const __half2 *>(out);
+    a.tw = p->tw_cols;
+    a.scale = p->dir == FFT2D_INVERSE ? (float)(1.0 / ((double)p->rows * (double)p->cols)) : 1.0f;
+    a.nst = p->Lr;
+    a.in_exp = p->exp_rows;
+    a.in_axis = FFT2D_PASS_ROWS;
+    a.out_exp = out_exp;
+    e = fft2d::launch_pass_h16(false, p->Lr, a, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "half2 column pass");
+    return FFT2D_OK;
+}
+
+fft2d_status fft2d_h16_pack(int rows, int cols, const void *in, void *out, int *out_exp,
+                            void *stream)
+{
+    if (!in || !out || !out_exp || rows < 1 || cols < 1)
+        return FFT2D_ERR_ARG;
+    cudaError_t e = fft2d::launch_h16_pack(static_cast<const float2 *>(in),
+                                           static_cast<__half2 *>(out), out_exp, rows, cols,
+                                           static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? FFT2D_OK : cuda_fail(e, "fft2d_h16_pack");
+}
+
+fft2d_status fft2d_h16_unpack(int rows, int cols, const void *in, const int *exps, int axis,
+                              void *out, void *stream)
+{
+    if (!in || !exps || !out || rows < 1 || cols < 1 ||
+        (axis != FFT2D_PASS_ROWS && axis != FFT2D_PASS_COLS))
+        return FFT2D_ERR_ARG;
+    cudaError_t e = fft2d::launch_h16_unpack(static_cast<const __half2 *>(in), exps, axis,
+                                             static_cast<float2 *>(out), rows, cols,
+                                             static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? FFT2D_OK : cuda_fail(e, "fft2d_h16_unpack");
+}
+
 int fft2d_variant_count(int pass, int L)
 {
     if ((pass != FFT2D_PASS_ROWS && pass != FFT2D_PASS_COLS) || L < 1 || L > 14)
@@ -524,6 +601,8 @@ fft2d_status fft2d_destroy(fft2d_plan_t p)
     cudaFree(p->tw_rows);
     cudaFree(p->tw_cols);
     cudaFree(p->dev_err);
+    if (p->exp_rows)
+        cudaFree(p->exp_rows);
     if (p->staging)
         cudaFree(p->staging);
     delete p;
@@ -592,7 +671,7 @@ fft2d_status fft2d_plan_info(fft2d_plan_t p, int *rows, int *cols, int *dtype, i
 
 fft2d_status fft2d_exec(fft2d_plan_t p, const void *in, void *out, void *stream)
 {
-    if (!p || !in || !out)
+    if (!p || !in || !out || p->dtype != FFT2D_C64)
         return FFT2D_ERR_ARG;
     fft2d_status s = check_device(p);
     if (s != FFT2D_OK)
@@ -602,7 +681,8 @@ fft2d_status fft2d_exec(fft2d_plan_t p, const void *in, void *out, void *stream)
 
 fft2d_status fft2d_exec_pass(fft2d_plan_t p, int pass, const void *in, void *out, void *stream)
 {
-    if (!p || !in || !out || (pass != FFT2D_PASS_ROWS && pass != FFT2D_PASS_COLS))
+    if (!p || !in || !out || (pass != FFT2D_PASS_ROWS && pass != FFT2D_PASS_COLS) ||
+        p->dtype != FFT2D_C64)
         return FFT2D_ERR_ARG;
     fft2d_status s = check_device(p);
     if (s != FFT2D_OK)
@@ -613,7 +693,7 @@ fft2d_status fft2d_exec_pass(fft2d_plan_t p, int pass, const void *in, void *out
 fft2d_status fft2d_exec_stages(fft2d_plan_t p, const void *in, void *out, int row_stages,
                                int col_stages, void *stream)
 {
-    if (!p || !in || !out)
+    if (!p || !in || !out || p->dtype != FFT2D_C64)
         return FFT2D_ERR_ARG;
     if (row_stages < 0 || row_stages > p->Lc || col_stages < 0 || col_stages > p->Lr)
         return FFT2D_ERR_ARG;
@@ -625,7 +705,7 @@ fft2d_status fft2d_exec_stages(fft2d_plan_t p, const void *in, void *out, int ro
 
 fft2d_status fft2d_exec_host(fft2d_plan_t p, const void *in_host, void *out_host, void *stream)
 {
-    if (!p || !in_host || !out_host)
+    if (!p || !in_host || !out_host || p->dtype != FFT2D_C64)
         return FFT2D_ERR_ARG;
     fft2d_status s = check_device(p);
     if (s != FFT2D_OK)
@@ -661,7 +741,7 @@ fft2d_status fft2d_exec_batched(int n, const fft2d_plan_t *plans, const void *co
     if (n < 0 || (n > 0 && (!plans || !in || !out)))
         return FFT2D_ERR_ARG;
     for (int i = 0; i < n; i++)
-        if (!plans[i] || !in[i] || !out[i])
+        if (!plans[i] || !in[i] || !out[i] || plans[i]->dtype != FFT2D_C64)
             return FFT2D_ERR_ARG;
     for (int i = 0; i < n; i++) {
         fft2d_status s = check_device(plans[i]);

@@ -83,8 +83,8 @@ namespace {
 template <class C, bool GENERIC>
 cudaError_t col_launch(const PassArgs &a, cudaStream_t s)
 {
-    auto k = col_pass_kernel<C, GENERIC>;
-    const int dev_bytes = C::SMEM_BYTES;
+    auto k = col_pass_kernel<C, GENERIC, StoreC64>;
+    const int dev_bytes = LineSmem<C, false, StoreC64>::BYTES;
     if (dev_bytes > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              dev_bytes);
@@ -92,7 +92,7 @@ cudaError_t col_launch(const PassArgs &a, cudaStream_t s)
             return e;
     }
     const unsigned grid = (unsigned)((a.cols + C::W - 1) / C::W);
-    k<<<grid, C::T, dev_bytes, s>>>(a.in, a.out, a.tw, a.cols, a.ld, a.scale, a.nst);
+    k<<<grid, C::T, dev_bytes, s>>>(StoreC64{a.in, a.out}, a.tw, a.cols, a.ld, a.scale, a.nst);
     return cudaGetLastError();
 }
 

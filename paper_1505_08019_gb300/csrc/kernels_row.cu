@@ -20,8 +20,8 @@ namespace {
 template <class C, bool GENERIC>
 cudaError_t row_launch(const PassArgs &a, cudaStream_t s)
 {
-    auto k = row_pass_kernel<C, GENERIC>;
-    const int dev_bytes = C::SMEM_BYTES;
+    auto k = row_pass_kernel<C, GENERIC, StoreC64>;
+    const int dev_bytes = LineSmem<C, true, StoreC64>::BYTES;
     if (dev_bytes > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              dev_bytes);
@@ -29,7 +29,7 @@ cudaError_t row_launch(const PassArgs &a, cudaStream_t s)
             return e;
     }
     const unsigned grid = (unsigned)((a.rows + C::LB - 1) / C::LB);
-    k<<<grid, C::T, dev_bytes, s>>>(a.in, a.out, a.tw, a.rows, a.ld, a.scale, a.nst);
+    k<<<grid, C::T, dev_bytes, s>>>(StoreC64{a.in, a.out}, a.tw, a.rows, a.ld, a.scale, a.nst);
     return cudaGetLastError();
 }
 

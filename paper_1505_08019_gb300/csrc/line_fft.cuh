@@ -33,6 +33,7 @@
 #pragma once
 
 #include <cooperative_groups.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -171,13 +172,143 @@ __device__ __forceinline__ void run_stages(float2 (&a)[C::EPT], int v, int lo,
     run_stages_g<Grp<C, GI>, GI == 0, GENERIC, TWS>(a, v, lo, tw, nst);
 }
 
+// ---------------------------------------------------------------------------
+// Global-memory storage of the image, used by the load of group 0 and the
+// store of the last group (everything in between is FP32 in registers and
+// shared memory).
+//
+//  * StoreC64: complex64, float2 per pixel.
+//  * StoreH16: half2 per pixel, each line carrying a power-of-two exponent:
+//    pixel = q * 2^e.  The input's exponents are per row (in_axis 0) or per
+//    column (in_axis 1); the pass writes one exponent per line it owns (row
+//    pass: per row, column pass: per column), chosen from that line's largest
+//    component magnitude M as e = k - 14 where M = f 2^k, f in [0.5, 1), so
+//    every stored |q| < 2^14, well inside half precision's range.
+struct StoreC64 {
+    static constexpr bool H16 = false;
+    using T = float2;
+    const float2 *in;
+    float2 *out;
+};
+
+struct StoreH16 {
+    static constexpr bool H16 = true;
+    using T = __half2;
+    const __half2 *in;
+    __half2 *out;
+    const int *in_exp;   // exponents of the input lines
+    int in_axis;         // 0: one per row, 1: one per column
+    int *out_exp;        // exponents of this pass's output lines
+};
+
+// 2^e as a float (exact), e clamped to the normal range.
+__device__ __forceinline__ float pow2f(int e)
+{
+    e = e < -126 ? -126 : (e > 127 ? 127 : e);
+    return __int_as_float((127 + e) << 23);
+}
+
+// Exponent of a line from its largest component magnitude (see StoreH16).
+__device__ __forceinline__ int line_exponent(float m)
+{
+    const int bits = __float_as_int(m);
+    const int ebits = (bits >> 23) & 0xff;
+    if (ebits == 0)
+        return 0;                       // zero (or subnormal) line
+    return (ebits - 126) - 14;          // m = f 2^(ebits-126), f in [0.5, 1)
+}
+
+// Where the CTA's elements live: element i of line lb (row pass) is pixel
+// (r0 + lb, i); element i of interleaved line w (column pass) is pixel
+// (r0 + i * rstep, c0 + w).  ld = row pitch in pixels.
+struct Geo {
+    long long r0, rstep, c0, ld;
+};
+
+template <bool ROW>
+__device__ __forceinline__ long long pix(const Geo &g, int lb, int i, int w)
+{
+    return ROW ? (g.r0 + lb) * g.ld + i : (g.r0 + (long long)i * g.rstep) * g.ld + g.c0 + w;
+}
+
+template <class IO, bool ROW>
+__device__ __forceinline__ float2 load_pix(const IO &io, const Geo &g, int lb, int i, int w)
+{
+    const long long k = pix<ROW>(g, lb, i, w);
+    if constexpr (IO::H16) {
+        const float2 q = __half22float2(io.in[k]);
+        const long long line = io.in_axis == 0 ? (ROW ? g.r0 + lb : g.r0 + (long long)i * g.rstep)
+                                               : (ROW ? (long long)i : g.c0 + w);
+        const float f = pow2f(io.in_exp[line]);
+        return make_float2(q.x * f, q.y * f);
+    } else {
+        return ld_stream(io.in + k);
+    }
+}
+
+// Store the units of a finished line group.  For half2 storage each line's
+// exponent is chosen first: the largest |component| of every line is
+// max-reduced in shared memory (sred, one int per line, zeroed at kernel
+// start), which costs one barrier; the thread holding position 0 of a line
+// writes its exponent.  pos(v, r) is the position of value r of unit v.
+template <class C, bool ROW, bool GENERIC, class IO, class Gp, class Pos>
+__device__ __forceinline__ void store_units(float2 (&a)[C::EPT], const IO &io, const Geo &g,
+                                            float scale, long long nvalid, int *sred,
+                                            Pos pos)
+{
+    const int tid = threadIdx.x;
+    if constexpr (IO::H16) {
+#pragma unroll
+        for (int v = 0; v < Gp::V; v++) {
+            const int u = tid + v * C::T;
+            const int w = u & (C::W - 1);
+            const int lb = ROW ? pos(v, 0) >> C::L : 0;
+            const bool ok = !GENERIC || (ROW ? lb < nvalid : w < nvalid);
+            float m = 0.f;
+#pragma unroll
+            for (int r = 0; r < Gp::R; r++)
+                m = fmaxf(m, fmaxf(fabsf(a[v * Gp::R + r].x), fabsf(a[v * Gp::R + r].y)));
+            if (ok)
+                atomicMax(sred + (ROW ? lb : w), __float_as_int(m * scale));
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int v = 0; v < Gp::V; v++) {
+        const int u = tid + v * C::T;
+        const int w = u & (C::W - 1);
+        const int lb = ROW ? pos(v, 0) >> C::L : 0;
+        const bool ok = !GENERIC || (ROW ? lb < nvalid : w < nvalid);
+        if (!ok)
+            continue;
+        float f = scale;
+        int e = 0;
+        if constexpr (IO::H16) {
+            e = line_exponent(__int_as_float(sred[ROW ? lb : w]));
+            f = scale * pow2f(-e);
+        }
+#pragma unroll
+        for (int r = 0; r < Gp::R; r++) {
+            const int p = pos(v, r) & (C::N - 1);
+            const float2 x = a[v * Gp::R + r];
+            const long long k = pix<ROW>(g, lb, p, w);
+            if constexpr (IO::H16) {
+                io.out[k] = __floats2half2_rn(x.x * f, x.y * f);
+                if (p == 0)
+                    io.out_exp[ROW ? g.r0 + lb : g.c0 + w] = e;
+            } else {
+                io.out[k] = make_float2(x.x * f, x.y * f);
+            }
+        }
+    }
+}
+
 // Group 0: scrambled global load, first stages, then either the final store
 // (single group, L <= 4) or the write to shared memory.
-template <class C, bool ROW, bool GENERIC>
-__device__ __forceinline__ void group_first(float2 (&a)[C::EPT], float2 *sm, const float2 *in,
-                                            float2 *out, const float2 *__restrict__ tw,
-                                            long long ld, float scale, int nst,
-                                            long long nvalid)
+template <class C, bool ROW, bool GENERIC, class IO>
+__device__ __forceinline__ void group_first(float2 (&a)[C::EPT], float2 *sm, const IO &io,
+                                            const Geo &g, const float2 *__restrict__ tw,
+                                            float scale, int nst, long long nvalid, int *sred)
 {
     using Gp = Grp<C, 0>;
     const int tid = threadIdx.x;
@@ -189,37 +320,30 @@ __device__ __forceinline__ void group_first(float2 (&a)[C::EPT], float2 *sm, con
         const int hib = u2 & ((1 << Gp::HB) - 1);
         const int lb = u2 >> Gp::HB;
         const bool ok = !GENERIC || (ROW ? lb < nvalid : w < nvalid);
-        const float2 *src = ROW ? in + (long long)lb * ld + hib : in + (long long)hib * ld + w;
 #pragma unroll
         for (int r = 0; r < Gp::R; r++) {
-            const int off = brev_c(r, Gp::G) << Gp::HB;
-            a[v * Gp::R + r] = ok ? ld_stream(src + (ROW ? (long long)off : (long long)off * ld))
-                                  : make_float2(0.f, 0.f);
+            const int i = (brev_c(r, Gp::G) << Gp::HB) | hib;
+            a[v * Gp::R + r] = ok ? load_pix<IO, ROW>(io, g, lb, i, w) : make_float2(0.f, 0.f);
         }
     }
 #pragma unroll
     for (int v = 0; v < Gp::V; v++)
         run_stages<C, 0, GENERIC>(a, v, 0, tw, nst);
+    if constexpr (C::NG == 1) {
+        // the whole line is in one unit: positions p = r are the output order
+        store_units<C, ROW, GENERIC, IO, Gp>(a, io, g, scale, nvalid, sred, [&](int v, int r) {
+            const int u = tid + v * C::T;
+            const int lb = (u >> C::KW) >> Gp::HB;
+            return (lb << C::L) | r;
+        });
+    } else {
 #pragma unroll
-    for (int v = 0; v < Gp::V; v++) {
-        const int u = tid + v * C::T;
-        const int w = u & (C::W - 1);
-        const int u2 = u >> C::KW;
-        const int hib = u2 & ((1 << Gp::HB) - 1);
-        const int lb = u2 >> Gp::HB;
-        if constexpr (C::NG == 1) {
-            // whole line in this unit: positions p = r are the output order
-            const bool ok = !GENERIC || (ROW ? lb < nvalid : w < nvalid);
-            if (ok) {
-                float2 *dst = ROW ? out + (long long)lb * ld : out + w;
-#pragma unroll
-                for (int r = 0; r < Gp::R; r++) {
-                    const float2 x = a[v * Gp::R + r];
-                    dst[ROW ? (long long)r : (long long)r * ld] =
-                        make_float2(x.x * scale, x.y * scale);
-                }
-            }
-        } else {
+        for (int v = 0; v < Gp::V; v++) {
+            const int u = tid + v * C::T;
+            const int w = u & (C::W - 1);
+            const int u2 = u >> C::KW;
+            const int hib = u2 & ((1 << Gp::HB) - 1);
+            const int lb = u2 >> Gp::HB;
             const int hi = brev_rt(hib, Gp::HB);
 #pragma unroll
             for (int r = 0; r < Gp::R; r++)
@@ -228,18 +352,17 @@ __device__ __forceinline__ void group_first(float2 (&a)[C::EPT], float2 *sm, con
     }
 }
 
-// Group GI >= 1: read units from shared memory, run the group's stages, then
-// write back in place (middle group) or store to global memory (last group).
-// With TO_SMEM the last group does not store to global memory: it leaves the
-// finished lines in shared memory in natural order, slot k*W + w (used by the
-// cluster column pass, whose last stages run across CTAs).
-template <class C, int GI, bool ROW, bool GENERIC, bool TO_SMEM = false, bool TWS = false>
-__device__ __forceinline__ void group_smem(float2 (&a)[C::EPT], float2 *sm, float2 *out,
-                                           const float2 *__restrict__ tw, long long ld,
-                                           float scale, int nst, long long nvalid)
+// Group GI >= 1 that stays in shared memory: read units, run the group's
+// stages, write back in place (a middle group) or, for the last group with
+// TO_SMEM, leave the finished lines in natural order, slot k*W + w (used by
+// the cluster column pass, whose last stages run across CTAs).
+template <class C, int GI, bool GENERIC, bool TO_SMEM = false, bool TWS = false>
+__device__ __forceinline__ void group_smem(float2 (&a)[C::EPT], float2 *sm,
+                                           const float2 *__restrict__ tw, int nst)
 {
     using Gp = Grp<C, GI>;
     constexpr bool LAST = (GI == C::NG - 1);
+    static_assert(!LAST || TO_SMEM, "the last group with a global store is group_last");
     const int tid = threadIdx.x;
 #pragma unroll
     for (int v = 0; v < Gp::V; v++) {
@@ -272,22 +395,10 @@ __device__ __forceinline__ void group_smem(float2 (&a)[C::EPT], float2 *sm, floa
         const int lo = u2 & ((1 << Gp::S0) - 1);
         const int hi = (u2 >> Gp::S0) & ((1 << Gp::HB) - 1);
         const int lb = u2 >> (Gp::S0 + Gp::HB);
-        if constexpr (LAST && TO_SMEM) {
+        if constexpr (LAST) {
 #pragma unroll
             for (int r = 0; r < Gp::R; r++)
                 sm[((lo | (r << Gp::S0)) << C::KW) | w] = a[v * Gp::R + r];
-        } else if constexpr (LAST) {
-            const bool ok = !GENERIC || (ROW ? lb < nvalid : w < nvalid);
-            if (ok) {
-                float2 *dst = ROW ? out + (long long)lb * ld + lo : out + (long long)lo * ld + w;
-#pragma unroll
-                for (int r = 0; r < Gp::R; r++) {
-                    const int off = r << Gp::S0;
-                    const float2 x = a[v * Gp::R + r];
-                    dst[ROW ? (long long)off : (long long)off * ld] =
-                        make_float2(x.x * scale, x.y * scale);
-                }
-            }
         } else {
 #pragma unroll
             for (int r = 0; r < Gp::R; r++)
@@ -297,53 +408,104 @@ __device__ __forceinline__ void group_smem(float2 (&a)[C::EPT], float2 *sm, floa
     }
 }
 
-// The whole line transform of one CTA.  in/out point at the CTA's first line
-// (row pass: first row of its block; column pass: first column of its tile).
-// ld is the image row pitch in complex elements.  nvalid (GENERIC only) is the
-// number of line blocks (ROW) or interleaved lines (column pass) that exist.
-template <class C, bool ROW, bool GENERIC>
-__device__ __forceinline__ void line_fft(const float2 *in, float2 *out,
-                                         const float2 *__restrict__ tw, long long ld,
-                                         float scale, int nst, long long nvalid)
+// The last group (GI = NG-1 >= 1): read units from shared memory, run the
+// group's stages, store natural-order positions p = lo | r << S0 to global.
+template <class C, bool ROW, bool GENERIC, class IO, bool TWS = false>
+__device__ __forceinline__ void group_last(float2 (&a)[C::EPT], float2 *sm, const IO &io,
+                                           const Geo &g, const float2 *__restrict__ tw,
+                                           float scale, int nst, long long nvalid, int *sred)
+{
+    using Gp = Grp<C, C::NG - 1>;
+    static_assert(Gp::HB == 0, "last group");
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int v = 0; v < Gp::V; v++) {
+        const int u = tid + v * C::T;
+        const int w = u & (C::W - 1);
+        const int u2 = u >> C::KW;
+        const int lo = u2 & ((1 << Gp::S0) - 1);
+        const int lb = u2 >> Gp::S0;
+#pragma unroll
+        for (int r = 0; r < Gp::R; r++)
+            a[v * Gp::R + r] = sm[sidx<C>(lb, lo | (r << Gp::S0), w)];
+    }
+#pragma unroll
+    for (int v = 0; v < Gp::V; v++) {
+        const int u = tid + v * C::T;
+        const int lo = (u >> C::KW) & ((1 << Gp::S0) - 1);
+        run_stages<C, C::NG - 1, GENERIC, TWS>(a, v, lo, tw, nst);
+    }
+    store_units<C, ROW, GENERIC, IO, Gp>(a, io, g, scale, nvalid, sred, [&](int v, int r) {
+        const int u = tid + v * C::T;
+        const int u2 = u >> C::KW;
+        const int lo = u2 & ((1 << Gp::S0) - 1);
+        const int lb = u2 >> Gp::S0;
+        return (lb << C::L) | lo | (r << Gp::S0);
+    });
+}
+
+// Shared memory of a line_fft CTA: the exchange buffer, then (half2 storage)
+// one int per output line for the exponent reduction.
+template <class C, bool ROW, class IO>
+struct LineSmem {
+    static constexpr int RED_INTS = IO::H16 ? (ROW ? C::LB : C::W) : 0;
+    static constexpr int BYTES = C::SMEM_BYTES + RED_INTS * 4;
+};
+
+// The whole line transform of one CTA.  nvalid (GENERIC only) is the number
+// of line blocks (ROW) or interleaved lines (column pass) that exist.
+template <class C, bool ROW, bool GENERIC, class IO>
+__device__ __forceinline__ void line_fft(const IO &io, const Geo &g,
+                                         const float2 *__restrict__ tw, float scale, int nst,
+                                         long long nvalid)
 {
     extern __shared__ float2 sm[];
+    int *sred = reinterpret_cast<int *>(sm + C::E * (C::NG > 1 ? 1 : 0));
+    if constexpr (IO::H16) {
+        for (int i = threadIdx.x; i < LineSmem<C, ROW, IO>::RED_INTS; i += C::T)
+            sred[i] = 0;
+        if constexpr (C::NG == 1)
+            __syncthreads();
+    }
     float2 a[C::EPT];
-    group_first<C, ROW, GENERIC>(a, sm, in, out, tw, ld, scale, nst, nvalid);
+    group_first<C, ROW, GENERIC, IO>(a, sm, io, g, tw, scale, nst, nvalid, sred);
     if constexpr (C::NG >= 2) {
         __syncthreads();
         if constexpr (C::NG >= 3) {
-            group_smem<C, 1, ROW, GENERIC>(a, sm, out, tw, ld, scale, nst, nvalid);
+            group_smem<C, 1, GENERIC>(a, sm, tw, nst);
             __syncthreads();
         }
         if constexpr (C::NG >= 4) {
-            group_smem<C, 2, ROW, GENERIC>(a, sm, out, tw, ld, scale, nst, nvalid);
+            group_smem<C, 2, GENERIC>(a, sm, tw, nst);
             __syncthreads();
         }
-        group_smem<C, C::NG - 1, ROW, GENERIC>(a, sm, out, tw, ld, scale, nst, nvalid);
+        group_last<C, ROW, GENERIC, IO>(a, sm, io, g, tw, scale, nst, nvalid, sred);
     }
 }
 
 // Row pass: CTA b transforms rows [b*LB, b*LB + LB).  ld = row pitch.
-template <class C, bool GENERIC>
-__global__ void __launch_bounds__(C::T, C::MINB) row_pass_kernel(const float2 *in, float2 *out,
-                                                        const float2 *__restrict__ tw,
-                                                        int rows, long long ld, float scale,
-                                                        int nst)
+template <class C, bool GENERIC, class IO = StoreC64>
+__global__ void __launch_bounds__(C::T, C::MINB) row_pass_kernel(const IO io,
+                                                                 const float2 *__restrict__ tw,
+                                                                 int rows, long long ld,
+                                                                 float scale, int nst)
 {
     const long long r0 = (long long)blockIdx.x * C::LB;
-    line_fft<C, true, GENERIC>(in + r0 * ld, out + r0 * ld, tw, ld, scale, nst, rows - r0);
+    const Geo g{r0, 1, 0, ld};
+    line_fft<C, true, GENERIC, IO>(io, g, tw, scale, nst, rows - r0);
 }
 
 // Column pass: CTA b transforms columns [b*W, b*W + W), each of `rows`=2^L
 // points spaced ld apart.
-template <class C, bool GENERIC>
-__global__ void __launch_bounds__(C::T, C::MINB) col_pass_kernel(const float2 *in, float2 *out,
-                                                        const float2 *__restrict__ tw,
-                                                        int cols, long long ld, float scale,
-                                                        int nst)
+template <class C, bool GENERIC, class IO = StoreC64>
+__global__ void __launch_bounds__(C::T, C::MINB) col_pass_kernel(const IO io,
+                                                                 const float2 *__restrict__ tw,
+                                                                 int cols, long long ld,
+                                                                 float scale, int nst)
 {
     const long long c0 = (long long)blockIdx.x * C::W;
-    line_fft<C, false, GENERIC>(in + c0, out + c0, tw, ld, scale, nst, cols - c0);
+    const Geo g{0, 1, c0, ld};
+    line_fft<C, false, GENERIC, IO>(io, g, tw, scale, nst, cols - c0);
 }
 
 // ---------------------------------------------------------------------------
@@ -492,11 +654,11 @@ __global__ void __launch_bounds__(C::T, C::T <= 512 ? 2 : 1) col_tma_kernel(cons
         group_first_smem<C, false>(a, sm, tw, C::L);
         __syncthreads();
         if constexpr (C::NG >= 3) {
-            group_smem<C, 1, false, false>(a, sm, nullptr, tw, ld, 1.0f, C::L, 0);
+            group_smem<C, 1, false>(a, sm, tw, C::L);
             __syncthreads();
         }
         if constexpr (C::NG >= 4) {
-            group_smem<C, 2, false, false>(a, sm, nullptr, tw, ld, 1.0f, C::L, 0);
+            group_smem<C, 2, false>(a, sm, tw, C::L);
             __syncthreads();
         }
         group_last_read<C>(a, sm);
@@ -577,18 +739,19 @@ __global__ void __launch_bounds__(C::T, C::MINB) row_tma_kernel(const float2 *in
                 mbar_wait_bounded(&bar[b ^ 1], ((it + 1) >> 1) & 1);
             return;
         }
-        float2 *o = out + (long long)tile * C::LB * ld;
         group_first_smem<C, false>(a, buf, tw, C::L);
         __syncthreads();
         if constexpr (C::NG >= 3) {
-            group_smem<C, 1, true, false>(a, buf, o, tw, ld, 1.0f, C::L, C::LB);
+            group_smem<C, 1, false>(a, buf, tw, C::L);
             __syncthreads();
         }
         if constexpr (C::NG >= 4) {
-            group_smem<C, 2, true, false>(a, buf, o, tw, ld, 1.0f, C::L, C::LB);
+            group_smem<C, 2, false>(a, buf, tw, C::L);
             __syncthreads();
         }
-        group_smem<C, C::NG - 1, true, false>(a, buf, o, tw, ld, scale, C::L, C::LB);
+        group_last<C, true, false, StoreC64>(a, buf, StoreC64{in, out},
+                                             Geo{(long long)tile * C::LB, 1, 0, ld}, tw, scale,
+                                             C::L, C::LB, nullptr);
         fence_proxy_async_smem();
         __syncthreads();   // this buffer is free again
         const int nn = tile + 2 * (int)gridDim.x;
@@ -736,11 +899,11 @@ __global__ void __launch_bounds__(C::T, 1) col_tma2_kernel(const __grid_constant
         });
         __syncthreads();
         if constexpr (C::NG >= 3) {
-            group_smem<C, 1, false, false, false, true>(a, sm, nullptr, stw, ld, 1.0f, C::L, 0);
+            group_smem<C, 1, false, false, true>(a, sm, stw, C::L);
             __syncthreads();
         }
         if constexpr (C::NG >= 4) {
-            group_smem<C, 2, false, false, false, true>(a, sm, nullptr, stw, ld, 1.0f, C::L, 0);
+            group_smem<C, 2, false, false, true>(a, sm, stw, C::L);
             __syncthreads();
         }
         group_last_read<C>(a, sm);
@@ -796,22 +959,22 @@ __global__ void __launch_bounds__(CC::T) col_cluster_kernel(const float2 *in, fl
     const int b = (int)cluster.block_rank();
     const long long c0 = (long long)(blockIdx.x / CC::CS) * CC::W;
     const long long nvalid = cols - c0;
-    const long long lld = ld * CC::CS;
-    const float2 *lin = in + c0 + (long long)brev_rt(b, CC::c) * ld;
     float2 a[CC::Local::EPT];
 
     // stages 1 .. L-c on this CTA's rows
-    group_first<LC, false, GENERIC>(a, sm, lin, nullptr, tw, lld, 1.0f, nst, nvalid);
+    group_first<LC, false, GENERIC, StoreC64>(a, sm, StoreC64{in, nullptr},
+                                              Geo{(long long)brev_rt(b, CC::c), CC::CS, c0, ld},
+                                              tw, 1.0f, nst, nvalid, nullptr);
     __syncthreads();
     if constexpr (LC::NG >= 3) {
-        group_smem<LC, 1, false, GENERIC>(a, sm, nullptr, tw, lld, 1.0f, nst, nvalid);
+        group_smem<LC, 1, GENERIC>(a, sm, tw, nst);
         __syncthreads();
     }
     if constexpr (LC::NG >= 4) {
-        group_smem<LC, 2, false, GENERIC>(a, sm, nullptr, tw, lld, 1.0f, nst, nvalid);
+        group_smem<LC, 2, GENERIC>(a, sm, tw, nst);
         __syncthreads();
     }
-    group_smem<LC, LC::NG - 1, false, GENERIC, true>(a, sm, nullptr, tw, lld, 1.0f, nst, nvalid);
+    group_smem<LC, LC::NG - 1, GENERIC, true>(a, sm, tw, nst);
     cluster.sync();
 
     // stages L-c+1 .. L across the cluster

@@ -1,6 +1,7 @@
 // passes.h -- host-side entry points of the row and column pass kernels.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace fft2d {
@@ -48,6 +49,25 @@ constexpr int col_kw(int L)
 // column pass for an axis of 2^L points.
 int row_lines_per_cta(int L);
 int col_width(int L);
+
+// Half2 storage with one power-of-two exponent per line (kernels_h16.cu).
+struct H16PassArgs {
+    const __half2 *in;
+    __half2 *out;
+    const float2 *tw;
+    int rows, cols;
+    long long ld;
+    float scale;
+    int nst;
+    const int *in_exp;   // input exponents, one per row (in_axis 0) or column (1)
+    int in_axis;
+    int *out_exp;        // output exponents: per row (row pass) or column (column pass)
+};
+cudaError_t launch_pass_h16(bool row, int L, const H16PassArgs &a, cudaStream_t s);
+cudaError_t launch_h16_pack(const float2 *in, __half2 *out, int *exp_rows, int rows, int cols,
+                            cudaStream_t s);
+cudaError_t launch_h16_unpack(const __half2 *in, const int *exps, int axis, float2 *out,
+                              int rows, int cols, cudaStream_t s);
 
 // Grouped launches over many images (batch.cu): one job per image, passed
 // by value as a kernel parameter.

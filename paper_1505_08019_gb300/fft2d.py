@@ -19,6 +19,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_lib", "libfft2d.so")
 
 FFT2D_C64 = 0
+FFT2D_C32H = 1
 FFT2D_FORWARD = -1
 FFT2D_INVERSE = 1
 FFT2D_PASS_ROWS = 0
@@ -61,6 +62,9 @@ _sigs = {
     "fft2d_stage_table": ([_I, _I, _P], _I),
     "fft2d_exec_noalloc": ([_I, _I, _I, _P, _P, _P], _I),
     "fft2d_autotune": ([_P, _P], _I),
+    "fft2d_exec_h16": ([_P, _P, _P, _I, _P, _P, _P], _I),
+    "fft2d_h16_pack": ([_I, _I, _P, _P, _P, _P], _I),
+    "fft2d_h16_unpack": ([_I, _I, _P, _P, _I, _P, _P], _I),
     "fft2d_variant_count": ([_I, _I], _I),
     "fft2d_variant_name": ([_I, _I, _I], ctypes.c_char_p),
     "fft2d_plan_set_variant": ([_P, _I, _I], _I),
@@ -182,6 +186,24 @@ def fft2d_exec_noalloc(rows: int, cols: int, dir: int, inp, out, stream=None) ->
     """Plan-free transform that allocates no device memory (sides <= 4096)."""
     _check(lib.fft2d_exec_noalloc(rows, cols, dir, _dptr(inp), _dptr(out), _stream(stream)),
            "fft2d_exec_noalloc")
+
+
+def fft2d_exec_h16(plan: int, inp, in_exp, in_axis: int, out, out_exp, stream=None) -> None:
+    """half2 transform: inp/out are (rows, cols) half2 buffers (e.g. torch
+    float16 tensors of shape (rows, cols, 2)), in_exp / out_exp int32 device
+    vectors (input per row or column, output per column)."""
+    _check(lib.fft2d_exec_h16(plan, _dptr(inp), _dptr(in_exp), in_axis, _dptr(out),
+                              _dptr(out_exp), _stream(stream)), "fft2d_exec_h16")
+
+
+def fft2d_h16_pack(rows: int, cols: int, inp, out, out_exp, stream=None) -> None:
+    _check(lib.fft2d_h16_pack(rows, cols, _dptr(inp), _dptr(out), _dptr(out_exp),
+                              _stream(stream)), "fft2d_h16_pack")
+
+
+def fft2d_h16_unpack(rows: int, cols: int, inp, exps, axis: int, out, stream=None) -> None:
+    _check(lib.fft2d_h16_unpack(rows, cols, _dptr(inp), _dptr(exps), axis, _dptr(out),
+                                _stream(stream)), "fft2d_h16_unpack")
 
 
 def fft2d_autotune(plan: int, stream=None) -> None:
