@@ -506,6 +506,7 @@ def run_fp16(args):
         dx = torch.from_numpy(x).cuda()
         y = torch.empty_like(dx)
         p32 = fft.fft2d_plan(side, side, fft.FFT2D_C64, fft.FFT2D_FORWARD)
+        fft.fft2d_autotune(p32)
         p16 = fft.fft2d_plan(side, side, fft.FFT2D_C32H, fft.FFT2D_FORWARD)
         q = torch.empty((side, side, 2), dtype=torch.float16, device="cuda")
         qe = torch.empty(side, dtype=torch.int32, device="cuda")
@@ -551,6 +552,7 @@ def run_fp16(args):
             "fp16_hbm_frac": (16.0 * px / (ms16 * 1e-3) / 1e9) / peak,
             "fp32_hbm_frac": (32.0 * px / (ms32 * 1e-3) / 1e9) / peak,
             "fp16_rel_l2_vs_fp64_oracle": e16, "fp32_rel_l2_vs_fp64_oracle": e32,
+            "fp32_kernels": fft.fft2d_plan_describe(p32),
             "tolerance_fp16": 5e-3, "tolerance_fp32": 1e-5}
         for p in (p32, p16):
             fft.fft2d_destroy(p)

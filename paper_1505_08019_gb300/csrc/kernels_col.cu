@@ -162,31 +162,8 @@ bool col_cluster_usable(const PassArgs &a)
 template <class CC>
 cudaError_t col_launch_cluster(const PassArgs &a, cudaStream_t s)
 {
-    auto k = col_cluster_kernel<CC, false>;
-    static bool attr[kMaxDev] = {};
-    const int d = current_device();
-    if (!attr[d]) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             CC::SMEM_BYTES);
-        if (e == cudaSuccess && CC::CS > 8)
-            e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess)
-            return e;
-        attr[d] = true;
-    }
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = CC::CS;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3((unsigned)(a.cols / CC::W * CC::CS));
-    cfg.blockDim = dim3(CC::T);
-    cfg.dynamicSmemBytes = CC::SMEM_BYTES;
-    cfg.stream = s;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k, a.in, a.out, a.tw, a.cols, a.ld, a.scale, a.nst);
+    return launch_cluster_kernel<CC, StoreC64>(StoreC64{a.in, a.out}, a.tw, a.cols, a.ld, a.scale,
+                                               a.nst, s);
 }
 
 bool always(const PassArgs &) { return true; }
@@ -211,9 +188,12 @@ struct ColVariants {
     static constexpr int CC_ = L <= 11 ? 1 : (L == 12 ? 2 : (L == 13 ? 1 : 2));
     static constexpr bool HASCLUSTER = L >= 11;
     using Clu = ClusterColCfg<(L >= 11 ? L : 11), CKW, CC_>;
+    // 8-column tiles over 4 or 8 CTAs for 8192 and 16384 rows
+    static constexpr bool HASCLUSTER8 = L >= 13;
+    using Clu8 = ClusterColCfg<(L >= 13 ? L : 13), 3, (L >= 13 ? L - 11 : 2)>;
 
     struct Table {
-        Variant v[6];
+        Variant v[7];
         int n = 0;
     };
     static Table build()
@@ -230,6 +210,9 @@ struct ColVariants {
             t.v[t.n++] = {"narrow", Narrow::W, 16, whole_stages, col_launch_any<Narrow>};
         if constexpr (HASCLUSTER)
             t.v[t.n++] = {"cluster", Clu::W, 16, col_cluster_usable<Clu>, col_launch_cluster<Clu>};
+        if constexpr (HASCLUSTER8)
+            t.v[t.n++] = {"cluster8", Clu8::W, 16, col_cluster_usable<Clu8>,
+                          col_launch_cluster<Clu8>};
         return t;
     }
     static const Variant *table(int *n)
@@ -245,7 +228,7 @@ struct ColVariants {
         else if constexpr (L >= 13) {
             int n;
             table(&n);
-            return n - 1;   // cluster: keeps >= 32-byte row segments
+            return n - 2;   // cluster of 4-column tiles: keeps 32-byte row segments
         } else
             return 0;
     }

@@ -37,6 +37,16 @@ cudaError_t h16_dispatch(bool row, const H16PassArgs &a, cudaStream_t s)
         return a.rows % C::LB ? h16_launch<C, true, true>(a, s) : h16_launch<C, true, false>(a, s);
     }
     using C = LineCfg<L, col_kw(L), 0>;
+    if constexpr (L >= 12) {
+        // from 4096 rows the single-CTA tile would be 2 or fewer columns
+        // wide (8 bytes of half2 per row): split 8-column tiles over a
+        // cluster of 2, 4 or 8 CTAs instead (32-byte row segments)
+        using CC = ClusterColCfg<L, 3, L - 11>;
+        if (a.cols % CC::W == 0) {
+            StoreH16 io{a.in, a.out, a.in_exp, a.in_axis, a.out_exp};
+            return launch_cluster_kernel<CC, StoreH16>(io, a.tw, a.cols, a.ld, a.scale, a.nst, s);
+        }
+    }
     return a.cols % C::W ? h16_launch<C, false, true>(a, s) : h16_launch<C, false, false>(a, s);
 }
 

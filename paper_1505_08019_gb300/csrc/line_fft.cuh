@@ -945,8 +945,15 @@ struct ClusterColCfg {
     static_assert(Local::NG >= 2, "local line must span at least two groups");
 };
 
-template <class CC, bool GENERIC>
-__global__ void __launch_bounds__(CC::T) col_cluster_kernel(const float2 *in, float2 *out,
+// Shared memory of a cluster CTA: its rows of the tile, then (half2
+// storage) one int per column for the cluster-wide exponent reduction.
+template <class CC, class IO>
+struct ClusterSmem {
+    static constexpr int BYTES = CC::SMEM_BYTES + (IO::H16 ? CC::W * 4 : 0);
+};
+
+template <class CC, bool GENERIC, class IO = StoreC64>
+__global__ void __launch_bounds__(CC::T) col_cluster_kernel(const IO io,
                                                             const float2 *__restrict__ tw,
                                                             int cols, long long ld,
                                                             float scale, int nst)
@@ -955,16 +962,22 @@ __global__ void __launch_bounds__(CC::T) col_cluster_kernel(const float2 *in, fl
     using LC = typename CC::Local;
     using X = typename CC::Cross;
     extern __shared__ float2 sm[];
+    int *sred = reinterpret_cast<int *>(sm + LC::E);
     cg::cluster_group cluster = cg::this_cluster();
     const int b = (int)cluster.block_rank();
     const long long c0 = (long long)(blockIdx.x / CC::CS) * CC::W;
     const long long nvalid = cols - c0;
+    const int tid = threadIdx.x;
     float2 a[CC::Local::EPT];
+    if constexpr (IO::H16) {
+        for (int i = tid; i < CC::W; i += CC::T)
+            sred[i] = 0;
+    }
 
     // stages 1 .. L-c on this CTA's rows
-    group_first<LC, false, GENERIC, StoreC64>(a, sm, StoreC64{in, nullptr},
-                                              Geo{(long long)brev_rt(b, CC::c), CC::CS, c0, ld},
-                                              tw, 1.0f, nst, nvalid, nullptr);
+    group_first<LC, false, GENERIC, IO>(a, sm, io,
+                                        Geo{(long long)brev_rt(b, CC::c), CC::CS, c0, ld}, tw,
+                                        1.0f, nst, nvalid, nullptr);
     __syncthreads();
     if constexpr (LC::NG >= 3) {
         group_smem<LC, 1, GENERIC>(a, sm, tw, nst);
@@ -978,7 +991,6 @@ __global__ void __launch_bounds__(CC::T) col_cluster_kernel(const float2 *in, fl
     cluster.sync();
 
     // stages L-c+1 .. L across the cluster
-    const int tid = threadIdx.x;
 #pragma unroll
     for (int v = 0; v < X::V; v++) {
         const int u = tid + v * CC::T;
@@ -990,22 +1002,92 @@ __global__ void __launch_bounds__(CC::T) col_cluster_kernel(const float2 *in, fl
             a[v * X::R + r] = peer[lo * CC::W + w];
         }
     }
-    cluster.sync();   // no CTA leaves while a peer may still read its smem
+    if constexpr (!IO::H16)
+        cluster.sync();   // no CTA leaves while a peer may still read its smem
+#pragma unroll
+    for (int v = 0; v < X::V; v++) {
+        const int u = tid + v * CC::T;
+        const int lo = b * (CC::NL / CC::CS) + (u >> CC::KW);
+        run_stages_g<X, false, GENERIC>(a, v, lo, tw, nst);
+    }
+    if constexpr (IO::H16) {
+        // a column's exponent depends on all CS CTAs' rows of it: each CTA
+        // max-reduces its part into sred, then reads every peer's value
+#pragma unroll
+        for (int v = 0; v < X::V; v++) {
+            const int u = tid + v * CC::T;
+            const int w = u & (CC::W - 1);
+            float m = 0.f;
+#pragma unroll
+            for (int r = 0; r < CC::CS; r++)
+                m = fmaxf(m, fmaxf(fabsf(a[v * X::R + r].x), fabsf(a[v * X::R + r].y)));
+            if (!GENERIC || w < nvalid)
+                atomicMax(sred + w, __float_as_int(m * scale));
+        }
+        cluster.sync();   // gathers done, partial maxima final
+    }
 #pragma unroll
     for (int v = 0; v < X::V; v++) {
         const int u = tid + v * CC::T;
         const int w = u & (CC::W - 1);
         const int lo = b * (CC::NL / CC::CS) + (u >> CC::KW);
-        run_stages_g<X, false, GENERIC>(a, v, lo, tw, nst);
-        if (!GENERIC || w < nvalid) {
-            float2 *dst = out + c0 + (long long)lo * ld + w;
+        if (GENERIC && w >= nvalid)
+            continue;
+        float f = scale;
+        int e = 0;
+        if constexpr (IO::H16) {
+            int mb = 0;
 #pragma unroll
             for (int r = 0; r < CC::CS; r++) {
-                const float2 x = a[v * X::R + r];
-                dst[(long long)r * CC::NL * ld] = make_float2(x.x * scale, x.y * scale);
+                const int *peer = cluster.map_shared_rank(sred, r);
+                mb = max(mb, peer[w]);
+            }
+            e = line_exponent(__int_as_float(mb));
+            f = scale * pow2f(-e);
+        }
+#pragma unroll
+        for (int r = 0; r < CC::CS; r++) {
+            const float2 x = a[v * X::R + r];
+            const long long k = ((long long)lo + (long long)r * CC::NL) * ld + c0 + w;
+            if constexpr (IO::H16) {
+                io.out[k] = __floats2half2_rn(x.x * f, x.y * f);
+                if (lo == 0 && r == 0)
+                    io.out_exp[c0 + w] = e;
+            } else {
+                io.out[k] = make_float2(x.x * f, x.y * f);
             }
         }
     }
+    if constexpr (IO::H16)
+        cluster.sync();   // peers are done reading this CTA's maxima
+}
+
+// Host-side launch of a cluster column pass (cluster dimension attribute,
+// shared-memory opt-in).  Defined here so both storage formats share it.
+template <class CC, class IO>
+inline cudaError_t launch_cluster_kernel(const IO &io, const float2 *tw, int cols, long long ld,
+                                         float scale, int nst, cudaStream_t s)
+{
+    auto k = col_cluster_kernel<CC, false, IO>;
+    constexpr int SMEM = ClusterSmem<CC, IO>::BYTES;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    if (e == cudaSuccess && CC::CS > 8)
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess)
+        return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CC::CS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(cols / CC::W * CC::CS));
+    cfg.blockDim = dim3(CC::T);
+    cfg.dynamicSmemBytes = SMEM;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, io, tw, cols, ld, scale, nst);
 }
 
 }  // namespace fft2d
