@@ -221,6 +221,74 @@ FFT2D_API fft2d_status fft2d_h16_unpack(int rows, int cols, const void *in, cons
                                         int axis, void *out, void *stream);
 
 /*
+ * Gaussian low-pass multiply of an unshifted 2D spectrum in place (the
+ * filter step of FFT -> filter -> inverse FFT, the image-filtering use that
+ * motivates the paper, Section 1):
+ *   X[k][l] *= exp(-d_k^2/(2 sigma_rows^2)) * exp(-d_l^2/(2 sigma_cols^2)),
+ *   d_k = min(k, rows-k), d_l = min(l, cols-l) (frequency distance in bins).
+ * dtype FFT2D_C64 (complex64) or FFT2D_C32H (half2; the factor is <= 1, so
+ * per-line exponents stay valid).  Device buffer, asynchronous.
+ */
+FFT2D_API fft2d_status fft2d_lowpass(int rows, int cols, int dtype, void *data, float sigma_rows,
+                                     float sigma_cols, void *stream);
+
+/* ------------------------------------------------------------------ serving
+ * A continuous-batching request loop on the current device.  Clients submit
+ * requests on host buffers (pin them for full copy speed).  A scheduler
+ * thread admits queued requests in arrival order while the device memory
+ * they need (complex64: 8 B/pixel; half2: 12 B/pixel + exponents) fits the
+ * HBM budget, launches everything admitted so far as one batch on an idle
+ * stream (copies in, grouped FFT launches, low-pass, inverse, copies out),
+ * keeps up to `streams` batches in flight so new arrivals overlap running
+ * work, and recycles device buffers through a resident pool.  Plans stay
+ * resident.  Results do not depend on what else is in flight: every kernel
+ * computes the same bits alone and in a batch.
+ */
+#define FFT2D_OP_FORWARD 0   /* forward 2D FFT */
+#define FFT2D_OP_LOWPASS 1   /* forward FFT, Gaussian low-pass (sigma = side/8), inverse FFT */
+
+#define FFT2D_SERVE_SIMULATE 1   /* flags: no CUDA calls, modelled device time (testing) */
+
+typedef struct fft2d_server_s *fft2d_server_t;
+
+typedef struct {
+    int op;           /* FFT2D_OP_FORWARD or FFT2D_OP_LOWPASS */
+    int rows, cols;   /* powers of two, <= FFT2D_MAX_SIDE */
+    int dtype;        /* device storage during the work: FFT2D_C64 or FFT2D_C32H */
+    const void *in;   /* host: rows*cols complex64 input */
+    void *out;        /* host: rows*cols complex64 result (may equal in) */
+} fft2d_request;
+
+typedef struct {
+    long long submitted, completed, rejected, queued, batches, peak_device_bytes;
+    double mean_batch_size;
+    double p50_ms, p99_ms, mean_ms, max_ms;   /* submit -> result on the host */
+    double throughput_rps;                    /* completed / (last completion - first submit) */
+} fft2d_serve_stats;
+
+/* Create a server with an HBM budget (bytes of device buffers it may hold)
+ * and 1..16 streams.  flags: 0 or FFT2D_SERVE_SIMULATE. */
+FFT2D_API fft2d_status fft2d_serve_create(size_t hbm_budget_bytes, int streams, int flags,
+                                          fft2d_server_t *out);
+
+/* Queue one request; *ticket identifies it.  A request whose buffers alone
+ * exceed the budget is refused with FFT2D_ERR_BUDGET.  Non-blocking. */
+FFT2D_API fft2d_status fft2d_serve_submit(fft2d_server_t srv, const fft2d_request *req,
+                                          unsigned long long *ticket);
+
+/* Wait up to timeout_ms (< 0: forever) for a ticket; returns its status (or
+ * FFT2D_ERR_TIMEOUT if still running) and its latency in ms.  Each ticket
+ * can be waited for once. */
+FFT2D_API fft2d_status fft2d_serve_wait(fft2d_server_t srv, unsigned long long ticket,
+                                        int timeout_ms, double *latency_ms);
+
+/* Counters and latency percentiles of all completed requests. */
+FFT2D_API fft2d_status fft2d_serve_stats_get(fft2d_server_t srv, fft2d_serve_stats *out);
+
+/* Finish all queued work, then release the server. */
+FFT2D_API fft2d_status fft2d_serve_destroy(fft2d_server_t srv);
+
+/*
  * Host-only: write the rotation-factor table that a plan uploads for an axis
  * of 2^L points (0 <= L <= 14) into out[0 .. 2*(2^L - 1)), as (re, im) float
  * pairs.  Stage s (1..L) occupies entries [2^(s-1) - 1, 2^s - 1) and entry

@@ -273,6 +273,27 @@ int oracle_fft2d(double *z, long rows, long cols, int sign, int row_stages,
 }
 
 /*
+ * Gaussian low-pass of an unshifted spectrum (the filter step of the image
+ * filtering workload; not part of the paper's method, which only names image
+ * filtering as a use, Section 1):
+ *   Z[k][l] *= exp(-d_k^2 / (2 sr^2)) * exp(-d_l^2 / (2 sc^2)),
+ *   d_k = min(k, rows - k), d_l = min(l, cols - l).
+ */
+void oracle_gaussian_lowpass(double *z, long rows, long cols, double sr, double sc)
+{
+    for (long k = 0; k < rows; k++) {
+        const double dk = (double)(k < rows - k ? k : rows - k);
+        const double hk = exp(-dk * dk / (2.0 * sr * sr));
+        for (long l = 0; l < cols; l++) {
+            const double dl = (double)(l < cols - l ? l : cols - l);
+            const double h = hk * exp(-dl * dl / (2.0 * sc * sc));
+            z[2 * (k * cols + l)] *= h;
+            z[2 * (k * cols + l) + 1] *= h;
+        }
+    }
+}
+
+/*
  * Section 2 eq. 1, evaluated directly in O(n^2): X(k) = sum_n x(n) W_n^{nk}.
  * The exponent n*k is reduced modulo n before the rotation factor is
  * formed.  Any n >= 1 is accepted (no power-of-two requirement).

@@ -76,6 +76,8 @@ class Oracle:
         lib.oracle_dft_line.restype = I
         lib.oracle_dft2d.argtypes = [P, P, L, L, I]
         lib.oracle_dft2d.restype = I
+        lib.oracle_gaussian_lowpass.argtypes = [P, L, L, ctypes.c_double, ctypes.c_double]
+        lib.oracle_gaussian_lowpass.restype = None
         self.lib = lib
 
     # -- Section 3.2 ---------------------------------------------------------
@@ -135,6 +137,21 @@ class Oracle:
         if rc:
             raise ValueError(f"oracle_fft2d rc={rc} ({R}x{C}, stages {rs},{cs})")
         return z
+
+
+    # -- the filtering workload ------------------------------------------------
+    def lowpass(self, X, sigma_rows: float, sigma_cols: float) -> np.ndarray:
+        """Gaussian low-pass of an unshifted spectrum (copy)."""
+        z = np.array(X, dtype=np.complex128, copy=True, order="C")
+        self.lib.oracle_gaussian_lowpass(_ptr(z), z.shape[0], z.shape[1], sigma_rows, sigma_cols)
+        return z
+
+    def filter_image(self, x, threads: int = 1) -> np.ndarray:
+        """FFT -> Gaussian low-pass (sigma = side/8 per axis) -> inverse FFT."""
+        R, C = np.shape(x)
+        X = self.fft2d(x, threads=threads)
+        X = self.lowpass(X, R / 8.0, C / 8.0)
+        return self.fft2d(X, inverse=True, threads=threads)
 
 
 _default: Oracle | None = None

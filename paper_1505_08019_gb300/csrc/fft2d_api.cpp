@@ -528,6 +528,17 @@ fft2d_status fft2d_h16_unpack(int rows, int cols, const void *in, const int *exp
     return e == cudaSuccess ? FFT2D_OK : cuda_fail(e, "fft2d_h16_unpack");
 }
 
+fft2d_status fft2d_lowpass(int rows, int cols, int dtype, void *data, float sigma_rows,
+                           float sigma_cols, void *stream)
+{
+    if (!data || rows < 1 || cols < 1 || !(sigma_rows > 0.f) || !(sigma_cols > 0.f) ||
+        (dtype != FFT2D_C64 && dtype != FFT2D_C32H))
+        return FFT2D_ERR_ARG;
+    cudaError_t e = fft2d::launch_lowpass(dtype == FFT2D_C32H, data, rows, cols, sigma_rows,
+                                          sigma_cols, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? FFT2D_OK : cuda_fail(e, "fft2d_lowpass");
+}
+
 int fft2d_variant_count(int pass, int L)
 {
     if ((pass != FFT2D_PASS_ROWS && pass != FFT2D_PASS_COLS) || L < 1 || L > 14)

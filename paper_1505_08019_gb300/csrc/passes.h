@@ -69,6 +69,10 @@ cudaError_t launch_h16_pack(const float2 *in, __half2 *out, int *exp_rows, int r
 cudaError_t launch_h16_unpack(const __half2 *in, const int *exps, int axis, float2 *out,
                               int rows, int cols, cudaStream_t s);
 
+// Gaussian low-pass multiply of an unshifted spectrum (filter.cu).
+cudaError_t launch_lowpass(bool half2, void *x, int rows, int cols, float sigma_r, float sigma_c,
+                           cudaStream_t s);
+
 // Grouped launches over many images (batch.cu): one job per image, passed
 // by value as a kernel parameter.
 constexpr int kBatchMaxJobs = 128;

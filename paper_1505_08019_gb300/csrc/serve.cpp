@@ -1,0 +1,554 @@
+// serve.cpp -- a continuous-batching request loop for 2D FFT work.
+//
+// Clients submit requests (a forward FFT, or FFT -> Gaussian low-pass ->
+// inverse FFT) on host buffers.  One scheduler thread:
+//   * admits queued requests in arrival order while the device memory they
+//     need fits the HBM budget (buffers come from a resident pool; a request
+//     that could never fit is refused at submission);
+//   * launches everything admitted so far as one batch on an idle stream:
+//     host->device copies, grouped FFT launches for the complex64 work
+//     (fft2d_exec_batched), per-request calls for half2 work, the low-pass
+//     multiply, the inverse, device->host copies, then an event;
+//   * keeps several batches in flight on different streams, so requests that
+//     arrive while others run are admitted as memory frees up and their work
+//     overlaps on the device;
+//   * polls the events, stamps completion times, returns buffers to the pool.
+// Plans (rotation-factor tables) stay resident for the server's lifetime.
+//
+// A simulation mode runs the same admission and batching logic with no CUDA
+// calls at all (modelled device time), so it can be tested without a GPU.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "fft2d.h"
+#include "passes.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Req {
+    unsigned long long ticket;
+    fft2d_request r;
+    size_t bytes;                 // device memory this request holds while in flight
+    Clock::time_point t_submit;
+    Clock::time_point t_done;
+    void *buf_c64 = nullptr;      // device complex64 image
+    void *buf_h16 = nullptr;      // device half2 image (FFT2D_C32H)
+    int *exps = nullptr;          // device exponents: rows + cols ints (FFT2D_C32H)
+    fft2d_status status = FFT2D_OK;
+    bool done = false;
+};
+
+struct Batch {
+    std::vector<Req *> reqs;
+    int stream = -1;
+    cudaEvent_t ev = nullptr;
+    Clock::time_point sim_ready;  // simulation: modelled completion time
+};
+
+size_t request_bytes(const fft2d_request &r)
+{
+    const size_t px = (size_t)r.rows * r.cols;
+    size_t b = px * 8;
+    if (r.dtype == FFT2D_C32H)
+        b += px * 4 + (size_t)(r.rows + r.cols) * 4;
+    return b;
+}
+
+bool pow2(int n) { return n >= 1 && !(n & (n - 1)); }
+
+}  // namespace
+
+struct fft2d_server_s {
+    size_t budget;
+    int nstreams;
+    bool simulate;
+    int device = 0;
+
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    bool stopping = false;
+    std::thread worker;
+
+    unsigned long long next_ticket = 1;
+    std::deque<Req *> queue;                          // submitted, not admitted
+    std::unordered_map<unsigned long long, Req *> all;
+    std::vector<Batch> inflight;
+    std::vector<cudaStream_t> streams;
+    std::vector<bool> stream_busy;
+
+    // memory accounting (device bytes held: in use + pooled)
+    size_t used = 0, pooled = 0, peak = 0;
+    std::multimap<size_t, void *> pool;               // free device buffers by size
+
+    std::map<std::tuple<int, int, int, int>, fft2d_plan_t> plans;
+
+    // statistics
+    std::vector<double> latencies_ms;
+    long long rejected = 0, batches = 0, batched_reqs = 0;
+    Clock::time_point first_submit{}, last_done{};
+    bool any_submit = false;
+
+    // ------------------------------------------------------------- memory
+    // Take a buffer of at least `need` bytes from the pool, or allocate one if
+    // the budget allows.  Returns nullptr (without waiting) when it cannot.
+    void *acquire(size_t need)
+    {
+        auto it = pool.lower_bound(need);
+        if (it != pool.end() && it->first <= 2 * need) {
+            void *p = it->second;
+            pooled -= it->first;
+            used += it->first;
+            sizes[p] = it->first;
+            pool.erase(it);
+            return p;
+        }
+        // make room by releasing pooled buffers that do not fit this request
+        while (used + pooled + need > budget && !pool.empty()) {
+            auto big = std::prev(pool.end());
+            if (!simulate)
+                cudaFree(big->second);
+            else
+                std::free(big->second);
+            pooled -= big->first;
+            pool.erase(big);
+        }
+        if (used + pooled + need > budget)
+            return nullptr;
+        void *p = nullptr;
+        if (simulate) {
+            p = std::malloc(1);
+        } else if (cudaMalloc(&p, need) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        used += need;
+        sizes[p] = need;
+        peak = std::max(peak, used + pooled);
+        return p;
+    }
+    std::unordered_map<void *, size_t> sizes;
+
+    void release(void *p)
+    {
+        if (!p)
+            return;
+        const size_t n = sizes[p];
+        sizes.erase(p);
+        used -= n;
+        pooled += n;
+        pool.emplace(n, p);
+    }
+
+    bool admit(Req *q)
+    {
+        const size_t px = (size_t)q->r.rows * q->r.cols;
+        q->buf_c64 = acquire(px * 8);
+        if (!q->buf_c64)
+            return false;
+        if (q->r.dtype == FFT2D_C32H) {
+            q->buf_h16 = acquire(px * 4);
+            q->exps = static_cast<int *>(acquire((size_t)(q->r.rows + q->r.cols) * 4));
+            if (!q->buf_h16 || !q->exps) {
+                release(q->buf_c64);
+                release(q->buf_h16);
+                release(q->exps);
+                q->buf_c64 = q->buf_h16 = nullptr;
+                q->exps = nullptr;
+                return false;
+            }
+        }
+        return true;
+    }
+
+    void free_req(Req *q)
+    {
+        release(q->buf_c64);
+        release(q->buf_h16);
+        release(q->exps);
+        q->buf_c64 = q->buf_h16 = nullptr;
+        q->exps = nullptr;
+    }
+
+    fft2d_plan_t plan(int rows, int cols, int dtype, int dir)
+    {
+        auto key = std::make_tuple(rows, cols, dtype, dir);
+        auto it = plans.find(key);
+        if (it != plans.end())
+            return it->second;
+        fft2d_plan_t p = nullptr;
+        if (fft2d_plan(rows, cols, dtype, dir, &p) != FFT2D_OK)
+            return nullptr;
+        plans[key] = p;
+        return p;
+    }
+
+    // ------------------------------------------------------------- launch
+    fft2d_status launch(Batch &b)
+    {
+        cudaStream_t st = streams[b.stream];
+        for (Req *q : b.reqs) {
+            const size_t bytes = (size_t)q->r.rows * q->r.cols * 8;
+            if (cudaMemcpyAsync(q->buf_c64, q->r.in, bytes, cudaMemcpyHostToDevice, st) !=
+                cudaSuccess)
+                return FFT2D_ERR_CUDA;
+        }
+        // complex64 work: grouped forward launches, filter, grouped inverse
+        std::vector<fft2d_plan_t> fp, ip;
+        std::vector<const void *> fin, iin;
+        std::vector<void *> fout, iout;
+        for (Req *q : b.reqs) {
+            if (q->r.dtype != FFT2D_C64)
+                continue;
+            fft2d_plan_t p = plan(q->r.rows, q->r.cols, FFT2D_C64, FFT2D_FORWARD);
+            if (!p)
+                return FFT2D_ERR_OOM;
+            fp.push_back(p);
+            fin.push_back(q->buf_c64);
+            fout.push_back(q->buf_c64);
+        }
+        fft2d_status s = FFT2D_OK;
+        if (!fp.empty())
+            s = fft2d_exec_batched((int)fp.size(), fp.data(), fin.data(), fout.data(), st);
+        if (s != FFT2D_OK)
+            return s;
+        for (Req *q : b.reqs) {
+            if (q->r.dtype != FFT2D_C64 || q->r.op != FFT2D_OP_LOWPASS)
+                continue;
+            if (fft2d::launch_lowpass(false, q->buf_c64, q->r.rows, q->r.cols,
+                                      q->r.rows / 8.0f, q->r.cols / 8.0f, st) != cudaSuccess)
+                return FFT2D_ERR_CUDA;
+            fft2d_plan_t p = plan(q->r.rows, q->r.cols, FFT2D_C64, FFT2D_INVERSE);
+            if (!p)
+                return FFT2D_ERR_OOM;
+            ip.push_back(p);
+            iin.push_back(q->buf_c64);
+            iout.push_back(q->buf_c64);
+        }
+        if (!ip.empty())
+            s = fft2d_exec_batched((int)ip.size(), ip.data(), iin.data(), iout.data(), st);
+        if (s != FFT2D_OK)
+            return s;
+        // half2 work, one request at a time
+        for (Req *q : b.reqs) {
+            if (q->r.dtype != FFT2D_C32H)
+                continue;
+            const int R = q->r.rows, C = q->r.cols;
+            int *erow = q->exps, *ecol = q->exps + R;
+            s = fft2d_h16_pack(R, C, q->buf_c64, q->buf_h16, erow, st);
+            fft2d_plan_t pf = s == FFT2D_OK ? plan(R, C, FFT2D_C32H, FFT2D_FORWARD) : nullptr;
+            if (!pf)
+                return s == FFT2D_OK ? FFT2D_ERR_OOM : s;
+            s = fft2d_exec_h16(pf, q->buf_h16, erow, FFT2D_PASS_ROWS, q->buf_h16, ecol, st);
+            if (s == FFT2D_OK && q->r.op == FFT2D_OP_LOWPASS) {
+                if (fft2d::launch_lowpass(true, q->buf_h16, R, C, R / 8.0f, C / 8.0f, st) !=
+                    cudaSuccess)
+                    return FFT2D_ERR_CUDA;
+                fft2d_plan_t pi = plan(R, C, FFT2D_C32H, FFT2D_INVERSE);
+                if (!pi)
+                    return FFT2D_ERR_OOM;
+                // in place: the inverse reads per-column exponents and
+                // writes new per-column exponents into the same vector
+                s = fft2d_exec_h16(pi, q->buf_h16, ecol, FFT2D_PASS_COLS, q->buf_h16, ecol, st);
+            }
+            if (s == FFT2D_OK)
+                s = fft2d_h16_unpack(R, C, q->buf_h16, ecol, FFT2D_PASS_COLS, q->buf_c64, st);
+            if (s != FFT2D_OK)
+                return s;
+        }
+        for (Req *q : b.reqs) {
+            const size_t bytes = (size_t)q->r.rows * q->r.cols * 8;
+            if (cudaMemcpyAsync(q->r.out, q->buf_c64, bytes, cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess)
+                return FFT2D_ERR_CUDA;
+        }
+        if (cudaEventRecord(b.ev, st) != cudaSuccess)
+            return FFT2D_ERR_CUDA;
+        return FFT2D_OK;
+    }
+
+    // Modelled device time of a batch in simulation mode: 2 us per request
+    // plus 1 ns per byte moved.
+    static Clock::duration sim_time(const Batch &b)
+    {
+        double us = 0;
+        for (const Req *q : b.reqs)
+            us += 2.0 + (double)q->bytes * 1e-3;
+        return std::chrono::microseconds((long long)us);
+    }
+
+    // ------------------------------------------------------------- loop
+    void complete(Batch &b, fft2d_status s)
+    {
+        const auto now = Clock::now();
+        for (Req *q : b.reqs) {
+            q->t_done = now;
+            q->status = s;
+            q->done = true;
+            free_req(q);
+            latencies_ms.push_back(
+                std::chrono::duration<double, std::milli>(now - q->t_submit).count());
+        }
+        last_done = now;
+        stream_busy[b.stream] = false;
+        if (b.ev)
+            cudaEventDestroy(b.ev);
+        b.ev = nullptr;
+    }
+
+    void run()
+    {
+        if (!simulate)
+            cudaSetDevice(device);
+        std::unique_lock<std::mutex> lk(mu);
+        for (;;) {
+            // 1. retire finished batches
+            bool progressed = false;
+            for (size_t i = 0; i < inflight.size();) {
+                Batch &b = inflight[i];
+                bool fin;
+                if (simulate)
+                    fin = Clock::now() >= b.sim_ready;
+                else
+                    fin = cudaEventQuery(b.ev) != cudaErrorNotReady;
+                if (fin) {
+                    const fft2d_status s =
+                        simulate || cudaEventQuery(b.ev) == cudaSuccess ? FFT2D_OK : FFT2D_ERR_CUDA;
+                    complete(b, s);
+                    inflight.erase(inflight.begin() + i);
+                    progressed = true;
+                } else {
+                    i++;
+                }
+            }
+            if (progressed)
+                cv_done.notify_all();
+            // 2. admit and launch on an idle stream
+            int idle = -1;
+            for (int k = 0; k < nstreams; k++)
+                if (!stream_busy[k]) {
+                    idle = k;
+                    break;
+                }
+            if (idle >= 0 && !queue.empty()) {
+                Batch b;
+                b.stream = idle;
+                while (!queue.empty() && b.reqs.size() < 128) {
+                    Req *q = queue.front();
+                    if (!admit(q))
+                        break;   // wait for memory; keep arrival order
+                    queue.pop_front();
+                    b.reqs.push_back(q);
+                }
+                if (!b.reqs.empty()) {
+                    stream_busy[idle] = true;
+                    batches++;
+                    batched_reqs += (long long)b.reqs.size();
+                    fft2d_status s = FFT2D_OK;
+                    if (simulate) {
+                        b.sim_ready = Clock::now() + sim_time(b);
+                    } else if (cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming) !=
+                               cudaSuccess) {
+                        s = FFT2D_ERR_CUDA;
+                    } else {
+                        lk.unlock();   // launches need no lock: buffers are owned
+                        s = launch(b);
+                        lk.lock();
+                    }
+                    if (s != FFT2D_OK) {
+                        if (b.ev)
+                            cudaStreamSynchronize(streams[b.stream]);
+                        complete(b, s);
+                        cv_done.notify_all();
+                    } else {
+                        inflight.push_back(b);
+                    }
+                    continue;
+                }
+            }
+            if (stopping && queue.empty() && inflight.empty())
+                break;
+            // 3. wait for new work or poll the device again shortly
+            cv_work.wait_for(lk, std::chrono::microseconds(inflight.empty() ? 1000 : 20));
+        }
+    }
+};
+
+extern "C" {
+
+fft2d_status fft2d_serve_create(size_t hbm_budget_bytes, int streams, int flags,
+                                fft2d_server_t *out)
+{
+    if (!out || hbm_budget_bytes == 0 || streams < 1 || streams > 16)
+        return FFT2D_ERR_ARG;
+    *out = nullptr;
+    fft2d_server_s *s = new (std::nothrow) fft2d_server_s();
+    if (!s)
+        return FFT2D_ERR_OOM;
+    s->budget = hbm_budget_bytes;
+    s->nstreams = streams;
+    s->simulate = (flags & FFT2D_SERVE_SIMULATE) != 0;
+    s->streams.assign(streams, nullptr);
+    s->stream_busy.assign(streams, false);
+    if (!s->simulate) {
+        if (cudaGetDevice(&s->device) != cudaSuccess) {
+            delete s;
+            return FFT2D_ERR_CUDA;
+        }
+        for (int k = 0; k < streams; k++) {
+            if (cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking) != cudaSuccess) {
+                for (int j = 0; j < k; j++)
+                    cudaStreamDestroy(s->streams[j]);
+                delete s;
+                return FFT2D_ERR_CUDA;
+            }
+        }
+    }
+    s->worker = std::thread([s] { s->run(); });
+    *out = s;
+    return FFT2D_OK;
+}
+
+fft2d_status fft2d_serve_submit(fft2d_server_t s, const fft2d_request *req,
+                                unsigned long long *ticket)
+{
+    if (!s || !req || !ticket)
+        return FFT2D_ERR_ARG;
+    const fft2d_request &r = *req;
+    if ((r.op != FFT2D_OP_FORWARD && r.op != FFT2D_OP_LOWPASS) || !r.in || !r.out ||
+        (r.dtype != FFT2D_C64 && r.dtype != FFT2D_C32H))
+        return FFT2D_ERR_ARG;
+    if (!pow2(r.rows) || !pow2(r.cols))
+        return FFT2D_ERR_NOT_POW2;
+    if (r.rows > FFT2D_MAX_SIDE || r.cols > FFT2D_MAX_SIDE)
+        return FFT2D_ERR_TOO_LARGE;
+    if (r.dtype == FFT2D_C32H && (r.rows < 2 || r.cols < 2))
+        return FFT2D_ERR_UNSUPPORTED;
+    Req *q = new (std::nothrow) Req();
+    if (!q)
+        return FFT2D_ERR_OOM;
+    q->r = r;
+    q->bytes = request_bytes(r);
+    q->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        // two buffers of a request may round up to 2x in the pool
+        if (q->bytes > s->budget) {
+            s->rejected++;
+            delete q;
+            return FFT2D_ERR_BUDGET;
+        }
+        if (!s->any_submit) {
+            s->first_submit = q->t_submit;
+            s->any_submit = true;
+        }
+        q->ticket = s->next_ticket++;
+        s->all[q->ticket] = q;
+        s->queue.push_back(q);
+        *ticket = q->ticket;
+    }
+    s->cv_work.notify_one();
+    return FFT2D_OK;
+}
+
+fft2d_status fft2d_serve_wait(fft2d_server_t s, unsigned long long ticket, int timeout_ms,
+                              double *latency_ms)
+{
+    if (!s)
+        return FFT2D_ERR_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end())
+        return FFT2D_ERR_ARG;
+    Req *q = it->second;
+    const auto pred = [q] { return q->done; };
+    if (timeout_ms < 0)
+        s->cv_done.wait(lk, pred);
+    else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred))
+        return FFT2D_ERR_TIMEOUT;
+    if (latency_ms)
+        *latency_ms = std::chrono::duration<double, std::milli>(q->t_done - q->t_submit).count();
+    const fft2d_status st = q->status;
+    s->all.erase(it);
+    delete q;
+    return st;
+}
+
+fft2d_status fft2d_serve_stats_get(fft2d_server_t s, fft2d_serve_stats *out)
+{
+    if (!s || !out)
+        return FFT2D_ERR_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    std::memset(out, 0, sizeof *out);
+    std::vector<double> v = s->latencies_ms;
+    out->completed = (long long)v.size();
+    out->rejected = s->rejected;
+    out->submitted = (long long)(s->next_ticket - 1) + s->rejected;
+    out->queued = (long long)s->queue.size();
+    out->peak_device_bytes = (long long)s->peak;
+    out->batches = s->batches;
+    out->mean_batch_size = s->batches ? (double)s->batched_reqs / (double)s->batches : 0.0;
+    if (!v.empty()) {
+        std::sort(v.begin(), v.end());
+        auto pct = [&v](double p) {
+            const size_t i = (size_t)std::min((double)v.size() - 1, p * (double)(v.size() - 1) + 0.5);
+            return v[i];
+        };
+        out->p50_ms = pct(0.50);
+        out->p99_ms = pct(0.99);
+        out->max_ms = v.back();
+        double sum = 0;
+        for (double x : v)
+            sum += x;
+        out->mean_ms = sum / (double)v.size();
+        const double span =
+            std::chrono::duration<double>(s->last_done - s->first_submit).count();
+        out->throughput_rps = span > 0 ? (double)v.size() / span : 0.0;
+    }
+    return FFT2D_OK;
+}
+
+fft2d_status fft2d_serve_destroy(fft2d_server_t s)
+{
+    if (!s)
+        return FFT2D_OK;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stopping = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable())
+        s->worker.join();
+    for (auto &kv : s->all)
+        delete kv.second;
+    for (auto &kv : s->pool) {
+        if (s->simulate)
+            std::free(kv.second);
+        else
+            cudaFree(kv.second);
+    }
+    for (auto &kv : s->plans)
+        fft2d_destroy(kv.second);
+    if (!s->simulate)
+        for (cudaStream_t st : s->streams)
+            if (st)
+                cudaStreamDestroy(st);
+    delete s;
+    return FFT2D_OK;
+}
+
+}  // extern "C"

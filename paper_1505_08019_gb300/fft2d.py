@@ -79,6 +79,39 @@ for _name, (_args, _res) in _sigs.items():
     _f.restype = _res
 
 
+class fft2d_request(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int), ("rows", ctypes.c_int), ("cols", ctypes.c_int),
+                ("dtype", ctypes.c_int), ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+class fft2d_serve_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+                ("rejected", ctypes.c_longlong), ("queued", ctypes.c_longlong),
+                ("batches", ctypes.c_longlong), ("peak_device_bytes", ctypes.c_longlong),
+                ("mean_batch_size", ctypes.c_double), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("throughput_rps", ctypes.c_double)]
+
+
+FFT2D_OP_FORWARD = 0
+FFT2D_OP_LOWPASS = 1
+FFT2D_SERVE_SIMULATE = 1
+
+_sigs.update({
+    "fft2d_lowpass": ([_I, _I, _I, _P, ctypes.c_float, ctypes.c_float, _P], _I),
+    "fft2d_serve_create": ([ctypes.c_size_t, _I, _I, ctypes.POINTER(ctypes.c_void_p)], _I),
+    "fft2d_serve_submit": ([_P, ctypes.POINTER(fft2d_request),
+                            ctypes.POINTER(ctypes.c_ulonglong)], _I),
+    "fft2d_serve_wait": ([_P, ctypes.c_ulonglong, _I, ctypes.POINTER(ctypes.c_double)], _I),
+    "fft2d_serve_stats_get": ([_P, ctypes.POINTER(fft2d_serve_stats)], _I),
+    "fft2d_serve_destroy": ([_P], _I),
+})
+for _name in ("fft2d_lowpass", "fft2d_serve_create", "fft2d_serve_submit", "fft2d_serve_wait",
+              "fft2d_serve_stats_get", "fft2d_serve_destroy"):
+    _f = getattr(lib, _name)
+    _f.argtypes, _f.restype = _sigs[_name]
+
+
 class FFT2DError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -227,6 +260,46 @@ def fft2d_plan_describe(plan: int) -> str:
     buf = ctypes.create_string_buffer(256)
     _check(lib.fft2d_plan_describe(plan, buf, 256), "fft2d_plan_describe")
     return buf.value.decode()
+
+
+def fft2d_lowpass(rows: int, cols: int, dtype: int, data, sigma_rows: float,
+                  sigma_cols: float, stream=None) -> None:
+    _check(lib.fft2d_lowpass(rows, cols, dtype, _dptr(data), sigma_rows, sigma_cols,
+                             _stream(stream)), "fft2d_lowpass")
+
+
+def fft2d_serve_create(hbm_budget_bytes: int, streams: int = 4, flags: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(lib.fft2d_serve_create(hbm_budget_bytes, streams, flags, ctypes.byref(h)),
+           "fft2d_serve_create")
+    return h.value
+
+
+def fft2d_serve_submit(srv: int, op: int, rows: int, cols: int, dtype: int, inp_host,
+                       out_host) -> int:
+    """Queue a request on host buffers (torch CPU tensors, numpy arrays or raw
+    pointers); returns its ticket.  Keep the buffers alive until it is done."""
+    req = fft2d_request(op, rows, cols, dtype, _hptr(inp_host), _hptr(out_host))
+    t = ctypes.c_ulonglong()
+    _check(lib.fft2d_serve_submit(srv, ctypes.byref(req), ctypes.byref(t)), "fft2d_serve_submit")
+    return t.value
+
+
+def fft2d_serve_wait(srv: int, ticket: int, timeout_ms: int = -1) -> float:
+    """Wait for a ticket; returns its latency in ms."""
+    lat = ctypes.c_double()
+    _check(lib.fft2d_serve_wait(srv, ticket, timeout_ms, ctypes.byref(lat)), "fft2d_serve_wait")
+    return lat.value
+
+
+def fft2d_serve_stats_get(srv: int) -> dict:
+    st = fft2d_serve_stats()
+    _check(lib.fft2d_serve_stats_get(srv, ctypes.byref(st)), "fft2d_serve_stats_get")
+    return {name: getattr(st, name) for name, _ in fft2d_serve_stats._fields_}
+
+
+def fft2d_serve_destroy(srv: int) -> None:
+    _check(lib.fft2d_serve_destroy(srv), "fft2d_serve_destroy")
 
 
 def fft2d_stage_table(L: int, dir: int = FFT2D_FORWARD):

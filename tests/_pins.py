@@ -198,7 +198,31 @@ def pin_partial_stages(orc):
         assert rel(got, want) < TOL_FFT, f"2D partial {kr},{kc}"
 
 
-ALL_PINS = [pin_bitrev, pin_fft1d_brute, pin_dft1d_brute, pin_fft1d_library,
+def pin_lowpass(orc):
+    """The Gaussian low-pass of the filtering workload: DC passes unchanged,
+    the factor at distance d = sigma is exp(-1/2), it decreases with the
+    frequency distance, the filter is separable and mirror-symmetric, and a
+    real image stays real through FFT -> low-pass -> inverse."""
+    R, C = 64, 32
+    one = np.ones((R, C), np.complex128)
+    H = orc.lowpass(one, 8.0, 4.0)
+    assert H[0, 0] == 1.0
+    assert abs(H[8, 0] - np.exp(-0.5)) < 1e-15 and abs(H[0, 4] - np.exp(-0.5)) < 1e-15
+    assert abs(H[R - 8, 0] - np.exp(-0.5)) < 1e-15
+    assert abs(H[8, 4] - np.exp(-1.0)) < 1e-15
+    # decreasing with frequency distance up to the Nyquist bin on each axis
+    assert np.all(np.diff(H[: R // 2 + 1, 0].real) < 0)
+    assert np.all(np.diff(H[0, : C // 2 + 1].real) < 0)
+    assert np.allclose(H, np.outer(H[:, 0], H[0, :]), rtol=1e-14, atol=0)
+    g = np.random.default_rng(17)
+    x = g.standard_normal((R, C)).astype(np.complex128)
+    y = orc.filter_image(x)
+    assert np.abs(y.imag).max() < 1e-12 * np.abs(y.real).max()
+    # the mean (DC) of the image is preserved exactly in exact arithmetic
+    assert abs(y.mean() - x.mean()) < 1e-12
+
+
+ALL_PINS = [pin_lowpass, pin_bitrev, pin_fft1d_brute, pin_dft1d_brute, pin_fft1d_library,
             pin_fft2d_library, pin_dft2d, pin_crops_brute, pin_closed_forms,
             pin_invariants, pin_partial_stages]
 

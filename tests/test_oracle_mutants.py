@@ -41,6 +41,9 @@ MUTANTS = {
     # direct DFT with a wrong exponent
     "dft_index": ("oracle_twiddle((m * k) % n, n, sign, &wr, &wi);",
                   "oracle_twiddle((m * (k + 1)) % n, n, sign, &wr, &wi);"),
+    # low-pass distance not folded (no mirror symmetry)
+    "lowpass_fold": ("const double dk = (double)(k < rows - k ? k : rows - k);",
+                     "const double dk = (double)k;"),
     # quarter-turn value wrong
     "quarter_turn": ("static const double sq[4] = {0.0, 1.0, 0.0, -1.0};",
                      "static const double sq[4] = {0.0, -1.0, 0.0, 1.0};"),
