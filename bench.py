@@ -620,15 +620,6 @@ def run_serve(args):
     budget = 40 << 30
     srv = fft.fft2d_serve_create(budget, 4)
     # warm up: resident plans and pooled buffers for every shape and type
-    warm = []
-    for sh in shapes:
-        for op in (0, 1):
-            for dt in (0, 1):
-                warm.append(fft.fft2d_serve_submit(srv, op, sh[0], sh[1], dt, inp[sh], outb[sh]))
-    for t in warm:
-        fft.fft2d_serve_wait(srv, t)
-    fft.fft2d_serve_destroy(srv)
-    srv = fft.fft2d_serve_create(budget, 4)
     for sh in shapes:
         for op in (0, 1):
             for dt in (0, 1):
