@@ -533,6 +533,8 @@ def run_fp16(args):
 
         reps = 20 if side == 8192 else 8
         ms32 = t(lambda: fft.fft2d_exec(p32, dx, y, sptr), reps)
+        ms32_rows = t(lambda: fft.fft2d_exec_pass(p32, fft.FFT2D_PASS_ROWS, dx, y, sptr), reps)
+        ms32_cols = t(lambda: fft.fft2d_exec_pass(p32, fft.FFT2D_PASS_COLS, y, y, sptr), reps)
         ms16 = t(lambda: fft.fft2d_exec_h16(p16, q, qe, fft.FFT2D_PASS_ROWS, qo, oe, sptr), reps)
         # accuracy against the FP64 oracle (of the input each path saw)
         th = host_cores()
@@ -552,6 +554,7 @@ def run_fp16(args):
         px = side * side
         results[f"{side}x{side}"] = {
             "fp16_ms": ms16, "fp32_ms": ms32, "speedup_fp16_vs_fp32": ms32 / ms16,
+            "fp32_row_pass_ms": ms32_rows, "fp32_col_pass_ms": ms32_cols,
             "fp16_images_per_s": 1e3 / ms16, "fp32_images_per_s": 1e3 / ms32,
             "fp16_hbm_frac": (16.0 * px / (ms16 * 1e-3) / 1e9) / peak,
             "fp32_hbm_frac": (32.0 * px / (ms32 * 1e-3) / 1e9) / peak,
