@@ -536,7 +536,9 @@ def run_fp16(args):
         ms32_rows = t(lambda: fft.fft2d_exec_pass(p32, fft.FFT2D_PASS_ROWS, dx, y, sptr), reps)
         ms32_cols = t(lambda: fft.fft2d_exec_pass(p32, fft.FFT2D_PASS_COLS, y, y, sptr), reps)
         ms16 = t(lambda: fft.fft2d_exec_h16(p16, q, qe, fft.FFT2D_PASS_ROWS, qo, oe, sptr), reps)
-        # accuracy against the FP64 oracle (of the input each path saw)
+        # accuracy against the FP64 oracle (of the input each path saw); the
+        # per-pass timings above overwrote y, so transform once more
+        fft.fft2d_exec(p32, dx, y, sptr)
         th = host_cores()
         xin = torch.empty_like(dx)
         fft.fft2d_h16_unpack(side, side, q, qe, fft.FFT2D_PASS_ROWS, xin, sptr)
