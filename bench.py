@@ -463,6 +463,13 @@ def run_batched(args):
             fft.fft2d_exec(p, x, o, sptr)
 
     steps = max(args.steps // 10, 20)
+    ms_default = timed(batched, steps, max(args.warmup, 3))
+    fft.fft2d_autotune_batched(plans, ins, outs, sptr)
+    R, C = fft.FFT2D_PASS_ROWS, fft.FFT2D_PASS_COLS
+    chosen = {f"{1 << L}": [fft.fft2d_batch_variant_name(R, fft.fft2d_batch_get_variant(R, L)),
+                            fft.fft2d_batch_variant_name(C, fft.fft2d_batch_get_variant(C, L))]
+              for L in sorted({(r.bit_length() - 1) for r, _ in shapes}
+                              | {(c.bit_length() - 1) for _, c in shapes})}
     ms_b = timed(batched, steps, max(args.warmup, 3))
     ms_s = timed(single, steps, max(args.warmup, 3))
     peak, peak_src = measured_hbm_peak()
@@ -487,6 +494,8 @@ def run_batched(args):
         "single_image_path": {"value": len(shapes) / (ms_s * 1e-3), "ms_per_step": ms_s,
                               "call": "fft2d_exec per image (autotuned plans)"},
         "speedup_vs_single": ms_s / ms_b,
+        "default_variants_ms_per_step": ms_default,
+        "tuned_variants": chosen,
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                      "frac": gbs / peak, "peak_source": peak_src,
                      "algorithmic_bytes_per_step": 32 * px},

@@ -187,7 +187,12 @@ FFT2D_API fft2d_status fft2d_exec_host(fft2d_plan_t plan, const void *in_host, v
 /*
  * n independent transforms, possibly of different plans (sizes, directions),
  * issued on one stream: image i is transformed with plans[i] from in[i] to
- * out[i] (device pointers; in[i] == out[i] allowed).
+ * out[i] (device pointers; in[i] == out[i] allowed; different images must not
+ * overlap).  Images are grouped by axis length and direction: one launch per
+ * group runs the row pass of all its images (a job table travels as a kernel
+ * parameter), then one launch per group the column pass -- a handful of
+ * launches for any number of images.  Every image's result is bit for bit
+ * the one fft2d_exec gives.  complex64 plans only.
  */
 FFT2D_API fft2d_status fft2d_exec_batched(int n, const fft2d_plan_t *plans, const void *const *in,
                                 void *const *out, void *stream);
@@ -327,6 +332,31 @@ FFT2D_API fft2d_status fft2d_stage_table(int L, int dir, float *out);
  */
 FFT2D_API fft2d_status fft2d_exec_noalloc(int rows, int cols, int dir, const void *in, void *out,
                                           void *stream);
+
+/*
+ * Batch autotuner: for every group of fft2d_exec_batched's grouped launches
+ * in this batch (pass, axis length, direction), time each grouped-kernel
+ * variant (rows: plain, 32 values per thread; columns: plain, half-width
+ * tiles, persistent TMA-fed) and keep the fastest per (pass, axis length) in
+ * the process-wide tuning table (and FFT2D_TUNE_CACHE).  Later
+ * fft2d_exec_batched calls use the winners.  The buffers are overwritten
+ * with intermediate results (the passes run several times).  Synchronous.
+ */
+FFT2D_API fft2d_status fft2d_autotune_batched(int n, const fft2d_plan_t *plans,
+                                              const void *const *in, void *const *out,
+                                              void *stream);
+
+/* Grouped-kernel variants of fft2d_exec_batched: how many a pass has, the
+ * name of variant `index` ("" when out of range), the variant the calling
+ * thread's current device uses for a pass over lines of 2^L points (-1 on a
+ * bad argument or no device), and forcing one (-1: back to the default).  A
+ * forced choice goes into the same process-wide table as a tuned winner.  A
+ * variant that cannot serve a group (e.g. the TMA column kernel on an image
+ * whose width is not a whole number of tiles) falls back to "plain". */
+FFT2D_API int fft2d_batch_variant_count(int pass);
+FFT2D_API const char *fft2d_batch_variant_name(int pass, int index);
+FFT2D_API int fft2d_batch_get_variant(int pass, int L);
+FFT2D_API fft2d_status fft2d_batch_set_variant(int pass, int L, int variant);
 
 /* Static text for a status code. */
 FFT2D_API const char *fft2d_strerror(int status);

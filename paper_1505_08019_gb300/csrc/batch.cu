@@ -70,33 +70,111 @@ cudaError_t batch_launch(BatchTable &t, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <int L>
-cudaError_t batch_dispatch(bool row, BatchTable &t, cudaStream_t s)
+// Grouped persistent TMA column pass: one tensor map per image; false when
+// some image cannot be described by one (alignment, partial tiles).
+template <class C>
+cudaError_t batch_launch_tma(const BatchTable &t, int *err, cudaStream_t s, bool *used)
 {
-    if (row)
+    *used = false;
+    static thread_local BatchTmaTable tt;
+    if (t.n > kBatchTmaMaxJobs || !err)
+        return cudaSuccess;
+    int tiles = 0;
+    for (int i = 0; i < t.n; i++) {
+        const BatchJob &j = t.job[i];
+        if (j.lines % C::W != 0 ||
+            !encode_col_map(&tt.map[i], j.in, C::N, j.lines, j.ld, C::W, C::N < 256 ? C::N : 256))
+            return cudaSuccess;
+        tt.out[i] = j.out;
+        tt.ld[i] = j.ld;
+        tt.scale[i] = j.scale;
+        tt.first_tile[i] = tiles;
+        tiles += j.lines / C::W;
+    }
+    tt.first_tile[t.n] = tiles;
+    tt.n = t.n;
+    if (tiles == 0) {
+        *used = true;
+        return cudaSuccess;
+    }
+    auto k = col_tma2_batch_kernel<C>;
+    constexpr int SMEM = TmaSplit<C>::SMEM_BYTES;
+    constexpr int kMaxDev = 64;
+    static int occ[kMaxDev] = {};
+    const int d = device_current();
+    if (!occ[d]) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (e != cudaSuccess)
+            return e;
+        int o = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, C::T, SMEM);
+        if (e != cudaSuccess)
+            return e;
+        occ[d] = o > 0 ? o : 1;
+    }
+    int grid = device_sm_count() * occ[d];
+    if (grid > tiles)
+        grid = tiles;
+    k<<<grid, C::T, SMEM, s>>>(tt, t.job[0].tw, err);
+    *used = true;
+    return cudaGetLastError();
+}
+
+template <int L>
+cudaError_t batch_dispatch(bool row, BatchTable &t, int variant, int *err, cudaStream_t s)
+{
+    if (row) {
+        if (variant == 1 && L >= 5)
+            return batch_launch<LineCfg<L, 0, row_kb(L), 32>, true>(t, s);
         return batch_launch<LineCfg<L, 0, row_kb(L)>, true>(t, s);
+    }
+    if constexpr (L >= 9 && L <= 12) {
+        if (variant == 2) {
+            bool used = false;
+            cudaError_t e =
+                batch_launch_tma<LineCfg<L, col_kw(L), 0, col_tma_ept(L)>>(t, err, s, &used);
+            if (e != cudaSuccess || used)
+                return e;
+        }
+    }
+    if constexpr (L >= 5 && col_kw(L) >= 3) {
+        if (variant == 1)
+            return batch_launch<LineCfg<L, col_kw(L) - 1, 0>, false>(t, s);
+    }
     return batch_launch<LineCfg<L, col_kw(L), 0>, false>(t, s);
 }
 
 }  // namespace
 
-cudaError_t launch_batch_pass(bool row, int L, BatchTable &t, cudaStream_t s)
+int batch_default_variant(bool row, int L) { return row ? 0 : (L >= 9 && L <= 12 ? 2 : 0); }
+
+const char *batch_variant_name(bool row, int variant)
+{
+    static const char *rn[kBatchRowVariants] = {"plain", "plain32"};
+    static const char *cn[kBatchColVariants] = {"plain", "narrow", "tma"};
+    if (row)
+        return variant >= 0 && variant < kBatchRowVariants ? rn[variant] : "";
+    return variant >= 0 && variant < kBatchColVariants ? cn[variant] : "";
+}
+
+cudaError_t launch_batch_pass(bool row, int L, BatchTable &t, int variant, int *err,
+                              cudaStream_t s)
 {
     switch (L) {
-    case 1: return batch_dispatch<1>(row, t, s);
-    case 2: return batch_dispatch<2>(row, t, s);
-    case 3: return batch_dispatch<3>(row, t, s);
-    case 4: return batch_dispatch<4>(row, t, s);
-    case 5: return batch_dispatch<5>(row, t, s);
-    case 6: return batch_dispatch<6>(row, t, s);
-    case 7: return batch_dispatch<7>(row, t, s);
-    case 8: return batch_dispatch<8>(row, t, s);
-    case 9: return batch_dispatch<9>(row, t, s);
-    case 10: return batch_dispatch<10>(row, t, s);
-    case 11: return batch_dispatch<11>(row, t, s);
-    case 12: return batch_dispatch<12>(row, t, s);
-    case 13: return batch_dispatch<13>(row, t, s);
-    case 14: return batch_dispatch<14>(row, t, s);
+    case 1: return batch_dispatch<1>(row, t, variant, err, s);
+    case 2: return batch_dispatch<2>(row, t, variant, err, s);
+    case 3: return batch_dispatch<3>(row, t, variant, err, s);
+    case 4: return batch_dispatch<4>(row, t, variant, err, s);
+    case 5: return batch_dispatch<5>(row, t, variant, err, s);
+    case 6: return batch_dispatch<6>(row, t, variant, err, s);
+    case 7: return batch_dispatch<7>(row, t, variant, err, s);
+    case 8: return batch_dispatch<8>(row, t, variant, err, s);
+    case 9: return batch_dispatch<9>(row, t, variant, err, s);
+    case 10: return batch_dispatch<10>(row, t, variant, err, s);
+    case 11: return batch_dispatch<11>(row, t, variant, err, s);
+    case 12: return batch_dispatch<12>(row, t, variant, err, s);
+    case 13: return batch_dispatch<13>(row, t, variant, err, s);
+    case 14: return batch_dispatch<14>(row, t, variant, err, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -278,6 +278,136 @@ void apply_tuned(fft2d_plan_s *p)
 
 }  // namespace
 
+namespace {
+
+// Grouped-launch variant for (pass, L): tuned winner (key pass + 2) or the
+// default.
+int batch_variant(int device, int pass, int L)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    load_tune_file_locked(device);
+    auto it = g_tuned.find(std::make_tuple(device, pass + 2, L, 0));
+    if (it != g_tuned.end())
+        return it->second;
+    return fft2d::batch_default_variant(pass == FFT2D_PASS_ROWS, L);
+}
+
+// Run the grouped passes of a batch.  With `timing` set, every (pass, L,
+// direction) group is launched once per variant and timed, and the fastest
+// variant per (pass, L) is recorded (the batch autotuner); otherwise each
+// group runs once with its chosen variant.
+fft2d_status batched_impl(int n, const fft2d_plan_t *plans, const void *const *in,
+                          void *const *out, cudaStream_t st, bool timing)
+{
+    static thread_local fft2d::BatchTable table;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (timing && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        return cuda_fail(cudaGetLastError(), "cudaEventCreate");
+    std::map<std::pair<int, int>, std::vector<float>> times;   // (pass, L) -> ms per variant
+    fft2d_status result = FFT2D_OK;
+    for (int pass = 0; pass < 2 && result == FFT2D_OK; pass++) {
+        const bool row = pass == FFT2D_PASS_ROWS;
+        for (int L = 1; L <= 14 && result == FFT2D_OK; L++) {
+            for (int dir = -1; dir <= 1 && result == FFT2D_OK; dir += 2) {
+                table.n = 0;
+                int *err = nullptr;
+                int first = -1;
+                for (int i = 0; i <= n; i++) {
+                    const bool flush = (i == n) || table.n == fft2d::kBatchTmaMaxJobs;
+                    if (flush && table.n > 0) {
+                        const int nv = row ? fft2d::kBatchRowVariants : fft2d::kBatchColVariants;
+                        if (!timing) {
+                            const int v = batch_variant(plans[first]->device, pass, L);
+                            cudaError_t e = fft2d::launch_batch_pass(row, L, table, v, err, st);
+                            if (e != cudaSuccess) {
+                                result = cuda_fail(e, "batched pass");
+                                break;
+                            }
+                        } else {
+                            auto &tv = times[std::make_pair(pass, L)];
+                            tv.resize(nv, 0.f);
+                            for (int v = 0; v < nv && result == FFT2D_OK; v++) {
+                                cudaError_t e = fft2d::launch_batch_pass(row, L, table, v, err, st);
+                                if (e == cudaSuccess)
+                                    e = cudaEventRecord(e0, st);
+                                for (int r = 0; r < 3 && e == cudaSuccess; r++)
+                                    e = fft2d::launch_batch_pass(row, L, table, v, err, st);
+                                if (e == cudaSuccess)
+                                    e = cudaEventRecord(e1, st);
+                                if (e == cudaSuccess)
+                                    e = cudaEventSynchronize(e1);
+                                float ms = 0.f;
+                                if (e == cudaSuccess)
+                                    e = cudaEventElapsedTime(&ms, e0, e1);
+                                if (e != cudaSuccess)
+                                    result = cuda_fail(e, "batched tuning");
+                                tv[v] += ms;
+                            }
+                        }
+                        table.n = 0;
+                    }
+                    if (i == n)
+                        break;
+                    const fft2d_plan_s *p = plans[i];
+                    if (p->Lr == 0 || p->Lc == 0 || (row ? p->Lc : p->Lr) != L || p->dir != dir)
+                        continue;
+                    if (first < 0) {
+                        first = i;
+                        err = p->dev_err;
+                    }
+                    fft2d::BatchJob &j = table.job[table.n++];
+                    j.in = static_cast<const float2 *>(row ? in[i] : out[i]);
+                    j.out = static_cast<float2 *>(out[i]);
+                    j.tw = row ? p->tw_rows : p->tw_cols;
+                    j.ld = p->cols;
+                    j.lines = row ? p->rows : p->cols;
+                    j.first_cta = 0;
+                    j.scale = (!row && p->dir == FFT2D_INVERSE)
+                                  ? (float)(1.0 / ((double)p->rows * (double)p->cols))
+                                  : 1.0f;
+                }
+            }
+        }
+    }
+    if (timing) {
+        if (result == FFT2D_OK && n > 0) {
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            load_tune_file_locked(plans[0]->device);
+            for (auto &kv : times) {
+                const auto &tv = kv.second;
+                int best = 0;
+                for (int v = 1; v < (int)tv.size(); v++)
+                    if (tv[v] < tv[best])
+                        best = v;
+                g_tuned[std::make_tuple(plans[0]->device, kv.first.first + 2, kv.first.second, 0)] =
+                    best;
+            }
+            save_tune_file_locked();
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    return result;
+}
+
+fft2d_status batched_check(int n, const fft2d_plan_t *plans, const void *const *in,
+                           void *const *out)
+{
+    if (n < 0 || (n > 0 && (!plans || !in || !out)))
+        return FFT2D_ERR_ARG;
+    for (int i = 0; i < n; i++)
+        if (!plans[i] || !in[i] || !out[i] || plans[i]->dtype != FFT2D_C64)
+            return FFT2D_ERR_ARG;
+    for (int i = 0; i < n; i++) {
+        fft2d_status s = check_device(plans[i]);
+        if (s != FFT2D_OK)
+            return s;
+    }
+    return FFT2D_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int fft2d_version(void) { return 100; }
@@ -749,58 +879,73 @@ fft2d_status fft2d_exec_host(fft2d_plan_t p, const void *in_host, void *out_host
 fft2d_status fft2d_exec_batched(int n, const fft2d_plan_t *plans, const void *const *in,
                                 void *const *out, void *stream)
 {
-    if (n < 0 || (n > 0 && (!plans || !in || !out)))
-        return FFT2D_ERR_ARG;
-    for (int i = 0; i < n; i++)
-        if (!plans[i] || !in[i] || !out[i] || plans[i]->dtype != FFT2D_C64)
-            return FFT2D_ERR_ARG;
-    for (int i = 0; i < n; i++) {
-        fft2d_status s = check_device(plans[i]);
-        if (s != FFT2D_OK)
-            return s;
-    }
+    fft2d_status s = batched_check(n, plans, in, out);
+    if (s != FFT2D_OK)
+        return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // images with a length-1 side take the single-image path
     for (int i = 0; i < n; i++) {
         if (plans[i]->Lr == 0 || plans[i]->Lc == 0) {
-            fft2d_status s = exec_impl(plans[i], in[i], out[i], -1, -1, st);
+            s = exec_impl(plans[i], in[i], out[i], -1, -1, st);
             if (s != FFT2D_OK)
                 return s;
         }
     }
-    // grouped row passes (in -> out), then grouped column passes (out, in place)
-    static thread_local fft2d::BatchTable table;
-    for (int pass = 0; pass < 2; pass++) {
-        const bool row = pass == 0;
-        for (int L = 1; L <= 14; L++) {
-            table.n = 0;
-            for (int i = 0; i <= n; i++) {
-                const bool flush = (i == n) || table.n == fft2d::kBatchMaxJobs;
-                if (flush && table.n > 0) {
-                    cudaError_t e = fft2d::launch_batch_pass(row, L, table, st);
-                    if (e != cudaSuccess)
-                        return cuda_fail(e, row ? "batched row pass" : "batched column pass");
-                    table.n = 0;
-                }
-                if (i == n)
-                    break;
-                const fft2d_plan_s *p = plans[i];
-                if (p->Lr == 0 || p->Lc == 0 || (row ? p->Lc : p->Lr) != L)
-                    continue;
-                fft2d::BatchJob &j = table.job[table.n++];
-                j.in = static_cast<const float2 *>(row ? in[i] : out[i]);
-                j.out = static_cast<float2 *>(out[i]);
-                j.tw = row ? p->tw_rows : p->tw_cols;
-                j.ld = p->cols;
-                j.lines = row ? p->rows : p->cols;
-                j.first_cta = 0;
-                j.scale = (!row && p->dir == FFT2D_INVERSE)
-                              ? (float)(1.0 / ((double)p->rows * (double)p->cols))
-                              : 1.0f;
-            }
-        }
-    }
+    return batched_impl(n, plans, in, out, st, false);
+}
+
+int fft2d_batch_variant_count(int pass)
+{
+    if (pass == FFT2D_PASS_ROWS)
+        return fft2d::kBatchRowVariants;
+    return pass == FFT2D_PASS_COLS ? fft2d::kBatchColVariants : 0;
+}
+
+const char *fft2d_batch_variant_name(int pass, int index)
+{
+    if (index < 0 || index >= fft2d_batch_variant_count(pass))
+        return "";
+    return fft2d::batch_variant_name(pass == FFT2D_PASS_ROWS, index);
+}
+
+int fft2d_batch_get_variant(int pass, int L)
+{
+    int dev = 0;
+    if (fft2d_batch_variant_count(pass) == 0 || L < 1 || L > 14 ||
+        cudaGetDevice(&dev) != cudaSuccess)
+        return -1;
+    return batch_variant(dev, pass, L);
+}
+
+fft2d_status fft2d_batch_set_variant(int pass, int L, int variant)
+{
+    const int n = fft2d_batch_variant_count(pass);
+    if (n == 0 || L < 1 || L > 14 || variant < -1 || variant >= n)
+        return FFT2D_ERR_ARG;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    load_tune_file_locked(dev);
+    const auto key = std::make_tuple(dev, pass + 2, L, 0);
+    if (variant < 0)
+        g_tuned.erase(key);
+    else
+        g_tuned[key] = variant;
     return FFT2D_OK;
+}
+
+fft2d_status fft2d_autotune_batched(int n, const fft2d_plan_t *plans, const void *const *in,
+                                    void *const *out, void *stream)
+{
+    fft2d_status s = batched_check(n, plans, in, out);
+    if (s != FFT2D_OK)
+        return s;
+    s = batched_impl(n, plans, in, out, static_cast<cudaStream_t>(stream), true);
+    for (int i = 0; i < n; i++)
+        cudaMemset(plans[i]->dev_err, 0, sizeof(int));
+    return s;
 }
 
 }  // extern "C"

@@ -57,6 +57,22 @@ int device_sm_count()
 
 int col_width(int L) { return 1 << col_kw(L); }
 
+bool encode_col_map(CUtensorMap *map, const float2 *base, int rows, int cols, long long ld, int W,
+                    int box_rows)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || (reinterpret_cast<uintptr_t>(base) & 15) || ((ld * 8) & 15))
+        return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 8};
+    cuuint32_t box[2] = {(cuuint32_t)W, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<float2 *>(base), dims, strides,
+               box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
 // One CTA waits, with the same bounded wait as the TMA pipeline, on an
 // mbarrier phase that nothing completes, then records the timeout.
 __global__ void selftest_timeout_kernel(int *err, unsigned long long limit_ns)
@@ -115,18 +131,8 @@ bool col_tma_usable(const PassArgs &a)
 template <class C>
 cudaError_t col_launch_tma(const PassArgs &a, cudaStream_t s)
 {
-    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     CUtensorMap map;
-    const int box_rows = C::N < 256 ? C::N : 256;
-    cuuint64_t dims[2] = {(cuuint64_t)a.cols, (cuuint64_t)a.rows};
-    cuuint64_t strides[1] = {(cuuint64_t)a.ld * 8};
-    cuuint32_t box[2] = {(cuuint32_t)C::W, (cuuint32_t)box_rows};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<float2 *>(a.in), dims,
-                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS)
+    if (!encode_col_map(&map, a.in, a.rows, a.cols, a.ld, C::W, C::N < 256 ? C::N : 256))
         return col_launch_any<LineCfg<C::L, C::KW, 0>>(a, s);
     auto k = col_tma2_kernel<C>;
     constexpr int SMEM = TmaSplit<C>::SMEM_BYTES;
@@ -169,9 +175,6 @@ cudaError_t col_launch_cluster(const PassArgs &a, cudaStream_t s)
 bool always(const PassArgs &) { return true; }
 bool whole_stages(const PassArgs &a) { return !a.partial; }
 
-// Values per thread of the TMA column kernel: 32 for tiles of 2^14 values
-// (512 threads of up to 128 registers), 16 below.
-constexpr int col_tma_ept(int L) { return L >= 10 ? 32 : 16; }
 
 template <int L>
 struct ColVariants {

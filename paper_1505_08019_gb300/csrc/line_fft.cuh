@@ -38,6 +38,7 @@
 #include <stdint.h>
 
 #include "async_copy.cuh"
+#include "passes.h"
 
 namespace fft2d {
 
@@ -509,15 +510,10 @@ __global__ void __launch_bounds__(C::T, C::MINB) col_pass_kernel(const IO io,
 }
 
 // ---------------------------------------------------------------------------
-// Persistent column pass fed by TMA.
-//
-// One CTA per SM walks over column tiles (W adjacent whole columns).  Each
-// tile arrives in shared memory by TMA tensor loads (boxes of W x 256 rows),
-// in natural order; group 0 gathers it in scrambled order straight from
-// there (the fused scramble), the tile is then reused as the exchange buffer,
-// and as soon as the last group has read its values into registers the TMA
-// load of the CTA's next tile is issued, so that transfer overlaps the last
-// stages and the stores of the current tile.
+// Pieces of the TMA-fed kernels: the tile arrives in shared memory in natural
+// order (TMA boxes or bulk copies), group 0 gathers it scrambled from there,
+// and the last group is split so the caller can recycle shared memory
+// between reading it and storing to global memory.
 
 // Group 0 from a natural-order tile in shared memory, slot
 // ((lb << L) | i) * W + w for element i of interleaved line w of line block
@@ -609,68 +605,6 @@ __device__ __forceinline__ void group_last_finish(float2 (&a)[C::EPT], float2 *o
             const float2 x = a[v * Gp::R + r];
             st_stream(dst + (long long)(r << Gp::S0) * ld, make_float2(x.x * scale, x.y * scale));
         }
-    }
-}
-
-// map: 2D tensor map over the column-pass input (inner dimension = columns,
-// 8-byte elements, box W x min(256, N)).  cols must be a multiple of W.
-// err: device status word; a lost TMA transfer sets kDevErrTmaTimeout.
-template <class C>
-__global__ void __launch_bounds__(C::T, C::T <= 512 ? 2 : 1) col_tma_kernel(const __grid_constant__ CUtensorMap map,
-                                                          float2 *out,
-                                                          const float2 *__restrict__ tw,
-                                                          int cols, long long ld, float scale,
-                                                          int *err)
-{
-    extern __shared__ __align__(1024) float2 sm[];
-    __shared__ __align__(8) uint64_t bar;
-    constexpr int BOX = C::N < 256 ? C::N : 256;
-    constexpr int NBOX = C::N / BOX;
-    constexpr uint32_t TILE_BYTES = (uint32_t)C::E * 8u;
-    const int ntiles = cols / C::W;
-    const int tid = threadIdx.x;
-    int tile = blockIdx.x;
-    if (tid == 0) {
-        mbar_init(&bar, 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    if (tid == 0 && tile < ntiles) {
-        mbar_arrive_expect_tx(&bar, TILE_BYTES);
-        for (int k = 0; k < NBOX; k++)
-            tma_load_2d(sm + k * BOX * C::W, &map, tile * C::W, k * BOX, &bar);
-    }
-    uint32_t parity = 0;
-    float2 a[C::EPT];
-    for (; tile < ntiles; tile += gridDim.x) {
-        const int lost = mbar_wait_bounded(&bar, parity) ? 0 : 1;
-        if (__syncthreads_or(lost)) {
-            if (tid == 0)
-                atomicExch(err, kDevErrTmaTimeout);
-            mbar_wait_bounded(&bar, parity);   // let a late transfer land before leaving
-            return;
-        }
-        parity ^= 1;
-        group_first_smem<C, false>(a, sm, tw, C::L);
-        __syncthreads();
-        if constexpr (C::NG >= 3) {
-            group_smem<C, 1, false>(a, sm, tw, C::L);
-            __syncthreads();
-        }
-        if constexpr (C::NG >= 4) {
-            group_smem<C, 2, false>(a, sm, tw, C::L);
-            __syncthreads();
-        }
-        group_last_read<C>(a, sm);
-        fence_proxy_async_smem();
-        __syncthreads();   // the tile buffer is free
-        const int next = tile + gridDim.x;
-        if (tid == 0 && next < ntiles) {
-            mbar_arrive_expect_tx(&bar, TILE_BYTES);
-            for (int k = 0; k < NBOX; k++)
-                tma_load_2d(sm + k * BOX * C::W, &map, next * C::W, k * BOX, &bar);
-        }
-        group_last_finish<C, false>(a, out + (long long)tile * C::W, tw, ld, scale, C::L);
     }
 }
 
@@ -787,24 +721,24 @@ struct TmaSplit {
 };
 
 template <class C>
-__device__ __forceinline__ void split_issue_early(float2 *sm, const CUtensorMap *map, int tile,
+__device__ __forceinline__ void split_issue_early(float2 *sm, const CUtensorMap *map, int c0,
                                                   uint64_t *bar)
 {
     using S = TmaSplit<C>;
     float2 *pref = sm + C::E;
     mbar_arrive_expect_tx(bar, S::EARLY_BYTES);
     for (int k = 0; k < S::NB; k++)
-        tma_load_2d(pref + k * S::BOX_VALS, map, tile * C::W, k * S::BOX, bar);
+        tma_load_2d(pref + k * S::BOX_VALS, map, c0, k * S::BOX, bar);
 }
 
 template <class C>
-__device__ __forceinline__ void split_issue_late(float2 *sm, const CUtensorMap *map, int tile,
+__device__ __forceinline__ void split_issue_late(float2 *sm, const CUtensorMap *map, int c0,
                                                  uint64_t *bar)
 {
     using S = TmaSplit<C>;
     mbar_arrive_expect_tx(bar, S::LATE_BYTES);
     for (int k = S::NB; k < S::NBOX; k++)
-        tma_load_2d(sm + (k - S::NB) * S::BOX_VALS, map, tile * C::W, k * S::BOX, bar);
+        tma_load_2d(sm + (k - S::NB) * S::BOX_VALS, map, c0, k * S::BOX, bar);
 }
 
 // Group 0 from the split tile (see above), ending with the swizzled exchange
@@ -852,16 +786,28 @@ __device__ __forceinline__ void group_first_split(float2 (&a)[C::EPT], float2 *s
     }
 }
 
-template <class C>
-__global__ void __launch_bounds__(C::T, 1) col_tma2_kernel(const __grid_constant__ CUtensorMap map,
-                                                           float2 *out,
-                                                           const float2 *__restrict__ tw,
-                                                           int cols, long long ld, float scale,
-                                                           int *err)
+// Where the persistent TMA column kernel finds tile t: the tensor map and
+// first column of its TMA boxes, the output pointer of its first column, the
+// image row pitch and the output scale.
+struct TilesOneImage {
+    const CUtensorMap *map;
+    float2 *out;
+    long long ld;
+    float scale;
+    int W;
+    __device__ const CUtensorMap *tmap(int) const { return map; }
+    __device__ int col(int t) const { return t * W; }
+    __device__ float2 *dst(int t) const { return out + (long long)t * W; }
+    __device__ long long pitch(int) const { return ld; }
+    __device__ float scl(int) const { return scale; }
+};
+
+template <class C, class Src>
+__device__ __forceinline__ void col_tma2_body(const Src &src, int ntiles,
+                                              const float2 *__restrict__ tw, int *err)
 {
     extern __shared__ __align__(1024) float2 sm[];
     __shared__ __align__(8) uint64_t bar_early, bar_late;
-    const int ntiles = cols / C::W;
     const int tid = threadIdx.x;
     int tile = blockIdx.x;
     if (tid == 0) {
@@ -871,8 +817,8 @@ __global__ void __launch_bounds__(C::T, 1) col_tma2_kernel(const __grid_constant
     }
     __syncthreads();
     if (tid == 0 && tile < ntiles) {
-        split_issue_early<C>(sm, &map, tile, &bar_early);
-        split_issue_late<C>(sm, &map, tile, &bar_late);
+        split_issue_early<C>(sm, src.tmap(tile), src.col(tile), &bar_early);
+        split_issue_late<C>(sm, src.tmap(tile), src.col(tile), &bar_late);
     }
     // the rotation factors stay in shared memory for the CTA's whole life
     float2 *stw = sm + TmaSplit<C>::TW_OFF;
@@ -895,7 +841,7 @@ __global__ void __launch_bounds__(C::T, 1) col_tma2_kernel(const __grid_constant
         parity ^= 1;
         group_first_split<C>(a, sm, stw, [&] {
             if (tid == 0 && next < ntiles)
-                split_issue_early<C>(sm, &map, next, &bar_early);
+                split_issue_early<C>(sm, src.tmap(next), src.col(next), &bar_early);
         });
         __syncthreads();
         if constexpr (C::NG >= 3) {
@@ -910,9 +856,59 @@ __global__ void __launch_bounds__(C::T, 1) col_tma2_kernel(const __grid_constant
         fence_proxy_async_smem();
         __syncthreads();   // the tile region is free
         if (tid == 0 && next < ntiles)
-            split_issue_late<C>(sm, &map, next, &bar_late);
-        group_last_finish<C, false, true>(a, out + (long long)tile * C::W, stw, ld, scale, C::L);
+            split_issue_late<C>(sm, src.tmap(next), src.col(next), &bar_late);
+        group_last_finish<C, false, true>(a, src.dst(tile), stw, src.pitch(tile), src.scl(tile),
+                                          C::L);
     }
+}
+
+template <class C>
+__global__ void __launch_bounds__(C::T, 1) col_tma2_kernel(const __grid_constant__ CUtensorMap map,
+                                                           float2 *out,
+                                                           const float2 *__restrict__ tw,
+                                                           int cols, long long ld, float scale,
+                                                           int *err)
+{
+    const TilesOneImage src{&map, out, ld, scale, C::W};
+    col_tma2_body<C>(src, cols / C::W, tw, err);
+}
+
+// The same kernel over the column tiles of many images of one column length
+// (a batch group): tile g belongs to the image whose first_tile range holds
+// it; each image brings its own tensor map, output, pitch and scale.
+struct TilesBatch {
+    const BatchTmaTable *t;
+    int W;
+    __device__ int job(int g) const
+    {
+        int lo = 0, hi = t->n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (t->first_tile[mid] <= g)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        return lo;
+    }
+    __device__ const CUtensorMap *tmap(int g) const { return &t->map[job(g)]; }
+    __device__ int col(int g) const { return (g - t->first_tile[job(g)]) * W; }
+    __device__ float2 *dst(int g) const
+    {
+        const int j = job(g);
+        return t->out[j] + (long long)(g - t->first_tile[j]) * W;
+    }
+    __device__ long long pitch(int g) const { return t->ld[job(g)]; }
+    __device__ float scl(int g) const { return t->scale[job(g)]; }
+};
+
+template <class C>
+__global__ void __launch_bounds__(C::T, 1) col_tma2_batch_kernel(const __grid_constant__ BatchTmaTable t,
+                                                                 const float2 *__restrict__ tw,
+                                                                 int *err)
+{
+    const TilesBatch src{&t, C::W};
+    col_tma2_body<C>(src, t.first_tile[t.n], tw, err);
 }
 
 // ---------------------------------------------------------------------------

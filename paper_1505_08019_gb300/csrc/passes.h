@@ -1,6 +1,7 @@
 // passes.h -- host-side entry points of the row and column pass kernels.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -44,6 +45,10 @@ constexpr int col_kw(int L)
 {
     return L >= 10 ? 14 - L : (13 - L < 4 ? 4 : (13 - L > 6 ? 6 : 13 - L));
 }
+
+// Values per thread of the TMA column kernel: 32 for tiles of 2^14 values
+// (512 threads of up to 128 registers), 16 below.
+constexpr int col_tma_ept(int L) { return L >= 10 ? 32 : 16; }
 
 // Lines per CTA of the row pass and interleaved columns per CTA of the
 // column pass for an axis of 2^L points.
@@ -89,8 +94,34 @@ struct BatchTable {
     int n;
     BatchJob job[kBatchMaxJobs];
 };
-// One launch for every job of `t` whose axis has 2^L points.
-cudaError_t launch_batch_pass(bool row, int L, BatchTable &t, cudaStream_t s);
+// Job table of the grouped TMA column kernel: one tensor map per image.
+constexpr int kBatchTmaMaxJobs = 96;
+struct alignas(64) BatchTmaTable {
+    CUtensorMap map[kBatchTmaMaxJobs];
+    float2 *out[kBatchTmaMaxJobs];
+    long long ld[kBatchTmaMaxJobs];
+    float scale[kBatchTmaMaxJobs];
+    int first_tile[kBatchTmaMaxJobs + 1];
+    int n;
+};
+
+// Grouped-launch variants: rows 0 plain, 1 plain32; columns 0 plain,
+// 1 narrow (half-width tiles), 2 tma (persistent, TMA-fed; 512..4096 rows).
+constexpr int kBatchRowVariants = 2;
+constexpr int kBatchColVariants = 3;
+int batch_default_variant(bool row, int L);
+const char *batch_variant_name(bool row, int variant);
+
+// One launch for every job of `t` whose axis has 2^L points (all jobs of one
+// direction: they share the rotation-factor table of job 0).  err: status
+// word for bounded waits.  A variant that cannot serve the jobs falls back
+// to the plain grouped kernel.
+cudaError_t launch_batch_pass(bool row, int L, BatchTable &t, int variant, int *err,
+                              cudaStream_t s);
+
+// 2D tensor map over a column-pass input (8-byte elements, box W x box_rows).
+bool encode_col_map(CUtensorMap *map, const float2 *base, int rows, int cols, long long ld, int W,
+                    int box_rows);
 
 cudaError_t launch_row_pass(int L, const PassArgs &a, cudaStream_t s);
 

@@ -62,6 +62,12 @@ _sigs = {
     "fft2d_stage_table": ([_I, _I, _P], _I),
     "fft2d_exec_noalloc": ([_I, _I, _I, _P, _P, _P], _I),
     "fft2d_autotune": ([_P, _P], _I),
+    "fft2d_batch_variant_count": ([_I], _I),
+    "fft2d_batch_variant_name": ([_I, _I], ctypes.c_char_p),
+    "fft2d_batch_get_variant": ([_I, _I], _I),
+    "fft2d_batch_set_variant": ([_I, _I, _I], _I),
+    "fft2d_autotune_batched": ([_I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
+                               _I),
     "fft2d_exec_h16": ([_P, _P, _P, _I, _P, _P, _P], _I),
     "fft2d_h16_pack": ([_I, _I, _P, _P, _P, _P], _I),
     "fft2d_h16_unpack": ([_I, _I, _P, _P, _I, _P, _P], _I),
@@ -237,6 +243,31 @@ def fft2d_h16_pack(rows: int, cols: int, inp, out, out_exp, stream=None) -> None
 def fft2d_h16_unpack(rows: int, cols: int, inp, exps, axis: int, out, stream=None) -> None:
     _check(lib.fft2d_h16_unpack(rows, cols, _dptr(inp), _dptr(exps), axis, _dptr(out),
                                 _stream(stream)), "fft2d_h16_unpack")
+
+
+def fft2d_batch_variant_count(pass_: int) -> int:
+    return lib.fft2d_batch_variant_count(pass_)
+
+
+def fft2d_batch_variant_name(pass_: int, index: int) -> str:
+    return lib.fft2d_batch_variant_name(pass_, index).decode()
+
+
+def fft2d_batch_get_variant(pass_: int, L: int) -> int:
+    return lib.fft2d_batch_get_variant(pass_, L)
+
+
+def fft2d_batch_set_variant(pass_: int, L: int, variant: int) -> None:
+    _check(lib.fft2d_batch_set_variant(pass_, L, variant), "fft2d_batch_set_variant")
+
+
+def fft2d_autotune_batched(plans, inps, outs, stream=None) -> None:
+    """Tune the grouped launches of this batch (buffers are overwritten)."""
+    n = len(plans)
+    arr = ctypes.c_void_p * max(n, 1)
+    _check(lib.fft2d_autotune_batched(n, arr(*plans), arr(*[_dptr(x) for x in inps]),
+                                      arr(*[_dptr(x) for x in outs]), _stream(stream)),
+           "fft2d_autotune_batched")
 
 
 def fft2d_autotune(plan: int, stream=None) -> None:

@@ -156,3 +156,94 @@ def test_batched_more_images_than_one_table(env):
     finally:
         for p in plans:
             fft.fft2d_destroy(p)
+
+
+def _batch_case(env, shapes, seed):
+    torch, fft, _ = env
+    imgs = synth.batch_images(shapes, seed=seed)
+    dirs = [fft.FFT2D_FORWARD if i % 2 else fft.FFT2D_INVERSE for i in range(len(shapes))]
+    solo = [run(env, im, d) for im, d in zip(imgs, dirs)]
+    plans = [fft.fft2d_plan(r, c, fft.FFT2D_C64, d) for (r, c), d in zip(shapes, dirs)]
+    return imgs, dirs, solo, plans
+
+
+def _run_batched(env, plans, imgs):
+    torch, fft, _ = env
+    ins = [torch.from_numpy(im).cuda() for im in imgs]
+    outs = [torch.empty_like(t) for t in ins]
+    fft.fft2d_exec_batched(plans, ins, outs)
+    torch.cuda.synchronize()
+    for p in plans[:1]:
+        fft.fft2d_sync_status(p)
+    return [o.cpu().numpy() for o in outs]
+
+
+BATCH_SHAPES = [(512, 1024), (1024, 512), (4096, 512), (512, 4096), (2048, 2048), (128, 256),
+                (256, 128), (1024, 1024), (64, 8192)]
+
+
+def test_batched_every_grouped_variant_is_bit_identical(env):
+    """Each grouped row kernel x each grouped column kernel (plain, narrow
+    tiles, persistent TMA-fed) gives every image its solo result bit for bit."""
+    torch, fft, _ = env
+    shapes = BATCH_SHAPES + synth.batch_shapes(12, seed=5)
+    imgs, dirs, solo, plans = _batch_case(env, shapes, seed=5)
+    R, C = fft.FFT2D_PASS_ROWS, fft.FFT2D_PASS_COLS
+    try:
+        assert fft.fft2d_batch_variant_count(R) >= 2
+        assert fft.fft2d_batch_variant_count(C) >= 3
+        for rv in range(fft.fft2d_batch_variant_count(R)):
+            for cv in range(fft.fft2d_batch_variant_count(C)):
+                for L in range(1, 15):
+                    fft.fft2d_batch_set_variant(R, L, rv)
+                    fft.fft2d_batch_set_variant(C, L, cv)
+                assert fft.fft2d_batch_get_variant(C, 12) == cv
+                got = _run_batched(env, plans, imgs)
+                names = (fft.fft2d_batch_variant_name(R, rv), fft.fft2d_batch_variant_name(C, cv))
+                for i, (g, w) in enumerate(zip(got, solo)):
+                    assert np.array_equal(g, w), f"variants {names}: image {i} {shapes[i]}"
+    finally:
+        for L in range(1, 15):
+            fft.fft2d_batch_set_variant(R, L, -1)
+            fft.fft2d_batch_set_variant(C, L, -1)
+        for p in plans:
+            fft.fft2d_destroy(p)
+
+
+def test_batch_variant_arguments(env):
+    torch, fft, _ = env
+    R, C = fft.FFT2D_PASS_ROWS, fft.FFT2D_PASS_COLS
+    assert fft.fft2d_batch_variant_name(C, 2) == "tma"
+    assert fft.fft2d_batch_variant_name(C, 99) == ""
+    assert fft.fft2d_batch_get_variant(C, 12) == 2      # default for 4096-point columns
+    assert fft.fft2d_batch_get_variant(R, 0) == -1
+    with pytest.raises(fft.FFT2DError):
+        fft.fft2d_batch_set_variant(C, 12, 3)
+    with pytest.raises(fft.FFT2DError):
+        fft.fft2d_batch_set_variant(R, 15, 0)
+
+
+def test_autotune_batched_then_batched_matches_solo(env):
+    torch, fft, _ = env
+    shapes = BATCH_SHAPES
+    imgs, dirs, solo, plans = _batch_case(env, shapes, seed=9)
+    R, C = fft.FFT2D_PASS_ROWS, fft.FFT2D_PASS_COLS
+    try:
+        ins = [torch.from_numpy(im).cuda() for im in imgs]
+        outs = [torch.empty_like(t) for t in ins]
+        fft.fft2d_autotune_batched(plans, ins, outs)
+        chosen = {L: (fft.fft2d_batch_get_variant(R, L), fft.fft2d_batch_get_variant(C, L))
+                  for L in (6, 7, 8, 9, 10, 11, 12, 13)}
+        print("[autotune_batched]", chosen)
+        for rv, cv in chosen.values():
+            assert 0 <= rv < fft.fft2d_batch_variant_count(R)
+            assert 0 <= cv < fft.fft2d_batch_variant_count(C)
+        got = _run_batched(env, plans, imgs)
+        for i, (g, w) in enumerate(zip(got, solo)):
+            assert np.array_equal(g, w), f"image {i} {shapes[i]}"
+    finally:
+        for L in range(1, 15):
+            fft.fft2d_batch_set_variant(R, L, -1)
+            fft.fft2d_batch_set_variant(C, L, -1)
+        for p in plans:
+            fft.fft2d_destroy(p)
