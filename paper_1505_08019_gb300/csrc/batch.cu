@@ -70,8 +70,9 @@ cudaError_t batch_launch(BatchTable &t, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// Grouped persistent TMA column pass: one tensor map per image; false when
-// some image cannot be described by one (alignment, partial tiles).
+// Grouped persistent TMA column pass: a load and a store tensor map per
+// image; not used when some image cannot be described by them (alignment,
+// partial tiles).
 template <class C>
 cudaError_t batch_launch_tma(const BatchTable &t, int *err, cudaStream_t s, bool *used)
 {
@@ -83,7 +84,10 @@ cudaError_t batch_launch_tma(const BatchTable &t, int *err, cudaStream_t s, bool
     for (int i = 0; i < t.n; i++) {
         const BatchJob &j = t.job[i];
         if (j.lines % C::W != 0 ||
-            !encode_col_map(&tt.map[i], j.in, C::N, j.lines, j.ld, C::W, C::N < 256 ? C::N : 256))
+            !encode_col_map(&tt.map[i], j.in, C::N, j.lines, j.ld, C::W, TmaSplit<C>::BOX,
+                            TmaSplit<C>::NB) ||
+            !encode_col_map(&tt.omap[i], j.out, C::N, j.lines, j.ld, C::W, tma_store_rows(C::L),
+                            TmaSplit<C>::NBOX))
             return cudaSuccess;
         tt.out[i] = j.out;
         tt.ld[i] = j.ld;
@@ -97,7 +101,7 @@ cudaError_t batch_launch_tma(const BatchTable &t, int *err, cudaStream_t s, bool
         *used = true;
         return cudaSuccess;
     }
-    auto k = col_tma2_batch_kernel<C>;
+    auto k = col_tma2_batch_kernel<C, tma_store_ok<C>()>;
     constexpr int SMEM = TmaSplit<C>::SMEM_BYTES;
     constexpr int kMaxDev = 64;
     static int occ[kMaxDev] = {};

@@ -58,16 +58,16 @@ int device_sm_count()
 int col_width(int L) { return 1 << col_kw(L); }
 
 bool encode_col_map(CUtensorMap *map, const float2 *base, int rows, int cols, long long ld, int W,
-                    int box_rows)
+                    int box_y, int box_z)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-    if (!enc || (reinterpret_cast<uintptr_t>(base) & 15) || ((ld * 8) & 15))
+    if (!enc || (reinterpret_cast<uintptr_t>(base) & 15) || ((ld * 8) & 15) || rows % 256 != 0)
         return false;
-    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)ld * 8};
-    cuuint32_t box[2] = {(cuuint32_t)W, (cuuint32_t)box_rows};
-    cuuint32_t estr[2] = {1, 1};
-    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<float2 *>(base), dims, strides,
+    cuuint64_t dims[3] = {(cuuint64_t)cols, 256, (cuuint64_t)(rows / 256)};
+    cuuint64_t strides[2] = {(cuuint64_t)ld * 8, (cuuint64_t)ld * 8 * 256};
+    cuuint32_t box[3] = {(cuuint32_t)W, (cuuint32_t)box_y, (cuuint32_t)box_z};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<float2 *>(base), dims, strides,
                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
            CUDA_SUCCESS;
@@ -123,18 +123,22 @@ template <class C>
 bool col_tma_usable(const PassArgs &a)
 {
     return !a.partial && a.err && tensor_map_encoder() &&
-           !(reinterpret_cast<uintptr_t>(a.in) & 15) && !((a.ld * 8) & 15) && a.cols % C::W == 0;
+           !(reinterpret_cast<uintptr_t>(a.in) & 15) && !(reinterpret_cast<uintptr_t>(a.out) & 15) &&
+           !((a.ld * 8) & 15) && a.cols % C::W == 0;
 }
 
-// Persistent TMA-fed column pass (col_tma2_kernel).  Falls back to the plain
-// kernel if the tile cannot be described by a tensor map.
-template <class C>
+// Persistent TMA-fed column pass (col_tma2_kernel), with TMA stores (TS) or
+// per-thread stores.  Falls back to the plain kernel if a tile cannot be
+// described by a tensor map.
+template <class C, bool TS>
 cudaError_t col_launch_tma(const PassArgs &a, cudaStream_t s)
 {
-    CUtensorMap map;
-    if (!encode_col_map(&map, a.in, a.rows, a.cols, a.ld, C::W, C::N < 256 ? C::N : 256))
+    CUtensorMap map, omap;
+    using S = TmaSplit<C>;
+    if (!encode_col_map(&map, a.in, a.rows, a.cols, a.ld, C::W, S::BOX, S::NB) ||
+        !encode_col_map(&omap, a.out, a.rows, a.cols, a.ld, C::W, tma_store_rows(C::L), S::NBOX))
         return col_launch_any<LineCfg<C::L, C::KW, 0>>(a, s);
-    auto k = col_tma2_kernel<C>;
+    auto k = col_tma2_kernel<C, TS>;
     constexpr int SMEM = TmaSplit<C>::SMEM_BYTES;
     static int occ[kMaxDev] = {};
     const int d = current_device();
@@ -153,7 +157,7 @@ cudaError_t col_launch_tma(const PassArgs &a, cudaStream_t s)
     int grid = sm_count() * occ[d];
     if (grid > ntiles)
         grid = ntiles;
-    k<<<grid, C::T, SMEM, s>>>(map, a.out, a.tw, a.cols, a.ld, a.scale, a.err);
+    k<<<grid, C::T, SMEM, s>>>(map, omap, a.out, a.tw, a.cols, a.ld, a.scale, a.err);
     return cudaGetLastError();
 }
 
@@ -184,6 +188,7 @@ struct ColVariants {
     using Tma16 = LineCfg<L, col_kw(L), 0, 16>;
     static constexpr int KWN = col_kw(L) - 1;                 // narrower tiles
     static constexpr bool HASNARROW = L >= 5 && KWN >= 2;
+
     using Narrow = LineCfg<L, (KWN >= 0 ? KWN : 0), 0>;
     // cluster shapes: W = 8 over 2 (2048 rows) or 4 (4096 rows) CTAs;
     // W = 4 over 2 or 4 CTAs for 8192 and 16384 rows
@@ -196,7 +201,7 @@ struct ColVariants {
     using Clu8 = ClusterColCfg<(L >= 13 ? L : 13), 3, (L >= 13 ? L - 11 : 2)>;
 
     struct Table {
-        Variant v[7];
+        Variant v[8];
         int n = 0;
     };
     static Table build()
@@ -204,10 +209,18 @@ struct ColVariants {
         Table t;
         t.v[t.n++] = {"plain", Plain::W, 16, always, col_launch_any<Plain>};
         if constexpr (HASTMA) {
+            // TMA loads with TMA stores where the tile shape allows them, the
+            // same engine with per-thread stores, and (lines of 1024..4096)
+            // 16 values per thread
+            constexpr bool TS32 = tma_store_ok<Tma32>();
             t.v[t.n++] = {Tma32::EPT == 32 ? "tma32" : "tma", Tma32::W, Tma32::EPT,
-                          col_tma_usable<Tma32>, col_launch_tma<Tma32>};
+                          col_tma_usable<Tma32>, col_launch_tma<Tma32, TS32>};
+            if constexpr (TS32)
+                t.v[t.n++] = {Tma32::EPT == 32 ? "tma32st" : "tmast", Tma32::W, Tma32::EPT,
+                              col_tma_usable<Tma32>, col_launch_tma<Tma32, false>};
             if constexpr (Tma32::EPT == 32)
-                t.v[t.n++] = {"tma16", Tma16::W, 16, col_tma_usable<Tma16>, col_launch_tma<Tma16>};
+                t.v[t.n++] = {"tma16", Tma16::W, 16, col_tma_usable<Tma16>,
+                              col_launch_tma<Tma16, tma_store_ok<Tma16>()>};
         }
         if constexpr (HASNARROW)
             t.v[t.n++] = {"narrow", Narrow::W, 16, whole_stages, col_launch_any<Narrow>};

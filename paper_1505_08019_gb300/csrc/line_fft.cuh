@@ -608,6 +608,75 @@ __device__ __forceinline__ void group_last_finish(float2 (&a)[C::EPT], float2 *o
     }
 }
 
+// ... or run its stages and hand the tile to TMA stores, half at a time,
+// through a staging buffer of E/2 values, so that the stores drain while the
+// CTA computes (the per-thread global stores of group_last_finish issue one
+// request per W-column row segment and stall the CTA until they leave).
+// The units split in two halves by their top index bit, which is bit S0-1 of
+// the row offset lo; half h is therefore rows (k << S0) | (h << (S0-1)) + q,
+// q < 2^(S0-1): one box of W x 2^(S0-1) x (N >> S0) of the 3D store map
+// (x = column, y = row within a 2^S0-row block, z = block) at y = h 2^(S0-1).
+// The staging slot of (k, q, w) is ((k << (S0-1)) | q) * W + w.  Before overwriting the buffer
+// with the second half, the issuing thread waits until the first half's
+// stores have read it; the second half is still being read when this
+// returns, so the caller waits (bulk_wait_read_all by thread 0, then a CTA
+// barrier) before it next writes the buffer.
+template <class C>
+constexpr bool tma_store_ok()
+{
+    using Gp = Grp<C, C::NG - 1>;
+    return C::NG >= 2 && C::LB == 1 && Gp::V >= 2 &&
+           ((C::T * (Gp::V / 2)) >> C::KW) == (1 << (Gp::S0 - 1)) &&
+           (1 << (Gp::S0 - 1)) == tma_store_rows(C::L);
+}
+
+template <class C, bool TWS = false>
+__device__ __forceinline__ void group_last_finish_tma(float2 (&a)[C::EPT], float2 *stage,
+                                                      const CUtensorMap *omap, int c0,
+                                                      const float2 *__restrict__ tw, float scale,
+                                                      int nst)
+{
+    using Gp = Grp<C, C::NG - 1>;
+    constexpr int S0 = Gp::S0;
+    constexpr int HALF = Gp::V / 2;
+    constexpr int QROWS = 1 << (S0 - 1);
+    static_assert(Gp::V >= 2 && C::LB == 1, "two halves of whole units, one line block");
+    static_assert((1 << S0) == 256, "store blocks are the 256-row blocks of the tensor maps");
+    static_assert(((C::T * HALF) >> C::KW) == QROWS, "the top unit bit is row bit S0-1");
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+#pragma unroll
+        for (int v = h * HALF; v < (h + 1) * HALF; v++) {
+            const int u = tid + v * C::T;
+            const int lo = (u >> C::KW) & ((1 << S0) - 1);
+            run_stages<C, C::NG - 1, false, TWS>(a, v, lo, tw, nst);
+        }
+        if (h == 1) {
+            if (tid == 0)
+                bulk_wait_read_all();
+            __syncthreads();
+        }
+#pragma unroll
+        for (int v = h * HALF; v < (h + 1) * HALF; v++) {
+            const int u = tid + v * C::T;
+            const int w = u & (C::W - 1);
+            const int q = (u >> C::KW) & (QROWS - 1);
+#pragma unroll
+            for (int r = 0; r < Gp::R; r++) {
+                const float2 x = a[v * Gp::R + r];
+                stage[((r * QROWS) | q) * C::W + w] = make_float2(x.x * scale, x.y * scale);
+            }
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tma_store_3d(omap, c0, h << (S0 - 1), 0, stage);   // box W x QROWS x NBX
+            bulk_commit();
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Persistent row pass fed by TMA bulk copies, double buffered: while a CTA
 // transforms its current block of LB rows in one shared-memory buffer, the
@@ -696,55 +765,52 @@ __global__ void __launch_bounds__(C::T, C::MINB) row_tma_kernel(const float2 *in
 
 // ---------------------------------------------------------------------------
 // Column pass with an early prefetch.  Shared memory holds the tile region
-// (the exchange buffer, one tile) and a prefetch region of NB boxes.  Boxes
-// 0..NB-1 of the NEXT tile land in the prefetch region as soon as group 0 has
-// gathered the current tile into registers -- while the remaining groups
-// still work -- and boxes NB.. land at the start of the tile region once the
-// last group has read it.  Group 0 of a tile finds box k in the prefetch
-// region (k < NB) or in the tile region (k >= NB); k depends only on the
-// register index, so the split costs no extra address arithmetic.
+// (the exchange buffer, one tile) and a prefetch region of half a tile.  The
+// tile is seen through a 3D tensor map (x = column, y = row within a block
+// of BOX = 256 rows, z = block), so each half moves with one TMA
+// instruction: blocks 0..NB-1 of the NEXT tile land in the prefetch region as
+// soon as group 0 has gathered the current tile into registers -- while the
+// remaining groups still work -- and blocks NB.. land at the start of the
+// tile region once the last group has read it.  Group 0 of a tile finds
+// block k in the prefetch region (k < NB) or in the tile region (k >= NB); k
+// depends only on the register index, so the split costs no extra address
+// arithmetic.
 template <class C>
 struct TmaSplit {
-    static constexpr int BOX = C::N < 256 ? C::N : 256;             // rows per box
+    static constexpr int BOX = C::N < 256 ? C::N : 256;             // rows per block
     static constexpr int NBOX = C::N / BOX;
     static constexpr int BOX_VALS = BOX * C::W;
-    static constexpr int PREF_LIMIT = 64 * 1024;                    // prefetch region
-    static constexpr int NB0 = PREF_LIMIT / (BOX_VALS * 8);
-    static constexpr int NB = NB0 < NBOX - 1 ? NB0 : NBOX - 1;       // early boxes
+    static constexpr int NB = NBOX / 2;                              // early blocks
     static constexpr int TW_VALS = C::N - 1;                         // twiddle table copy
     static constexpr int TW_OFF = C::E + NB * BOX_VALS;
     static constexpr int SMEM_BYTES = (TW_OFF + TW_VALS + 1) * 8;
     static constexpr uint32_t EARLY_BYTES = (uint32_t)NB * BOX_VALS * 8u;
     static constexpr uint32_t LATE_BYTES = (uint32_t)(NBOX - NB) * BOX_VALS * 8u;
-    static_assert(NB >= 1, "tile must span at least two boxes");
+    static_assert(NB >= 1 && 2 * NB == NBOX, "two equal halves of whole blocks");
     static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
 };
 
+// Load tensor map box of the split tile: W x BOX x NB (one half).
 template <class C>
 __device__ __forceinline__ void split_issue_early(float2 *sm, const CUtensorMap *map, int c0,
                                                   uint64_t *bar)
 {
-    using S = TmaSplit<C>;
-    float2 *pref = sm + C::E;
-    mbar_arrive_expect_tx(bar, S::EARLY_BYTES);
-    for (int k = 0; k < S::NB; k++)
-        tma_load_2d(pref + k * S::BOX_VALS, map, c0, k * S::BOX, bar);
+    mbar_arrive_expect_tx(bar, TmaSplit<C>::EARLY_BYTES);
+    tma_load_3d(sm + C::E, map, c0, 0, 0, bar);
 }
 
 template <class C>
 __device__ __forceinline__ void split_issue_late(float2 *sm, const CUtensorMap *map, int c0,
                                                  uint64_t *bar)
 {
-    using S = TmaSplit<C>;
-    mbar_arrive_expect_tx(bar, S::LATE_BYTES);
-    for (int k = S::NB; k < S::NBOX; k++)
-        tma_load_2d(sm + (k - S::NB) * S::BOX_VALS, map, c0, k * S::BOX, bar);
+    mbar_arrive_expect_tx(bar, TmaSplit<C>::LATE_BYTES);
+    tma_load_3d(sm, map, c0, 0, TmaSplit<C>::NB, bar);
 }
 
 // Group 0 from the split tile (see above), ending with the swizzled exchange
 // layout in the tile region.  `after_reads` runs once every thread has
 // gathered its values (the prefetch region is then free).
-template <class C, class F>
+template <class C, bool SYNC_AFTER, class F>
 __device__ __forceinline__ void group_first_split(float2 (&a)[C::EPT], float2 *sm,
                                                   const float2 *__restrict__ tw, F after_reads)
 {
@@ -774,6 +840,8 @@ __device__ __forceinline__ void group_first_split(float2 (&a)[C::EPT], float2 *s
     fence_proxy_async_smem();
     __syncthreads();   // every slot of both regions has been read
     after_reads();
+    if constexpr (SYNC_AFTER)
+        __syncthreads();   // what after_reads waited for holds for every thread
 #pragma unroll
     for (int v = 0; v < Gp::V; v++) {
         const int u = tid + v * C::T;
@@ -786,26 +854,37 @@ __device__ __forceinline__ void group_first_split(float2 (&a)[C::EPT], float2 *s
     }
 }
 
-// Where the persistent TMA column kernel finds tile t: the tensor map and
-// first column of its TMA boxes, the output pointer of its first column, the
-// image row pitch and the output scale.
+// Where the persistent TMA column kernel finds tile t: the tensor maps and
+// first column of its TMA boxes (load map over the input, store map over the
+// output), the output pointer of its first column, the image row pitch and
+// the output scale.
 struct TilesOneImage {
     const CUtensorMap *map;
+    const CUtensorMap *omap_;
     float2 *out;
     long long ld;
     float scale;
     int W;
     __device__ const CUtensorMap *tmap(int) const { return map; }
+    __device__ const CUtensorMap *omap(int) const { return omap_; }
     __device__ int col(int t) const { return t * W; }
     __device__ float2 *dst(int t) const { return out + (long long)t * W; }
     __device__ long long pitch(int) const { return ld; }
     __device__ float scl(int) const { return scale; }
 };
 
-template <class C, class Src>
+// Persistent column pass: CTA b takes tiles b, b + grid, ...  Shared memory:
+// the tile region (E values; the next tile's late boxes land in its lower
+// half), the prefetch region (the next tile's early boxes), the rotation
+// factors.  With TS (TMA stores) the upper half of the tile region is also
+// the staging buffer of the finished tile, drained while the next tile's
+// group 0 runs; otherwise each thread stores its results directly.
+template <class C, bool TS, class Src>
 __device__ __forceinline__ void col_tma2_body(const Src &src, int ntiles,
                                               const float2 *__restrict__ tw, int *err)
 {
+    static_assert(!TS || TmaSplit<C>::LATE_BYTES <= (uint32_t)C::E * 4u,
+                  "late boxes must leave the staging half free");
     extern __shared__ __align__(1024) float2 sm[];
     __shared__ __align__(8) uint64_t bar_early, bar_late;
     const int tid = threadIdx.x;
@@ -831,17 +910,24 @@ __device__ __forceinline__ void col_tma2_body(const Src &src, int ntiles,
         const int next = tile + gridDim.x;
         const bool ok = mbar_wait_bounded(&bar_early, parity) && mbar_wait_bounded(&bar_late, parity);
         if (__syncthreads_or(ok ? 0 : 1)) {
-            if (tid == 0)
+            if (tid == 0) {
                 atomicExch(err, kDevErrTmaTimeout);
+                if constexpr (TS)
+                    bulk_wait_all();
+            }
             // let late transfers land before the CTA leaves
             mbar_wait_bounded(&bar_early, parity);
             mbar_wait_bounded(&bar_late, parity);
             return;
         }
         parity ^= 1;
-        group_first_split<C>(a, sm, stw, [&] {
-            if (tid == 0 && next < ntiles)
-                split_issue_early<C>(sm, src.tmap(next), src.col(next), &bar_early);
+        group_first_split<C, TS>(a, sm, stw, [&] {
+            if (tid == 0) {
+                if (next < ntiles)
+                    split_issue_early<C>(sm, src.tmap(next), src.col(next), &bar_early);
+                if constexpr (TS)
+                    bulk_wait_read_all();   // the previous tile's staging half is free
+            }
         });
         __syncthreads();
         if constexpr (C::NG >= 3) {
@@ -857,25 +943,34 @@ __device__ __forceinline__ void col_tma2_body(const Src &src, int ntiles,
         __syncthreads();   // the tile region is free
         if (tid == 0 && next < ntiles)
             split_issue_late<C>(sm, src.tmap(next), src.col(next), &bar_late);
-        group_last_finish<C, false, true>(a, src.dst(tile), stw, src.pitch(tile), src.scl(tile),
-                                          C::L);
+        if constexpr (TS)
+            group_last_finish_tma<C, true>(a, sm + C::E / 2, src.omap(tile), src.col(tile), stw,
+                                           src.scl(tile), C::L);
+        else
+            group_last_finish<C, false, true>(a, src.dst(tile), stw, src.pitch(tile),
+                                              src.scl(tile), C::L);
+    }
+    if constexpr (TS) {
+        if (tid == 0)
+            bulk_wait_all();   // shared memory stays valid until the stores are done
     }
 }
 
-template <class C>
+template <class C, bool TS>
 __global__ void __launch_bounds__(C::T, 1) col_tma2_kernel(const __grid_constant__ CUtensorMap map,
+                                                           const __grid_constant__ CUtensorMap omap,
                                                            float2 *out,
                                                            const float2 *__restrict__ tw,
                                                            int cols, long long ld, float scale,
                                                            int *err)
 {
-    const TilesOneImage src{&map, out, ld, scale, C::W};
-    col_tma2_body<C>(src, cols / C::W, tw, err);
+    const TilesOneImage src{&map, &omap, out, ld, scale, C::W};
+    col_tma2_body<C, TS>(src, cols / C::W, tw, err);
 }
 
 // The same kernel over the column tiles of many images of one column length
 // (a batch group): tile g belongs to the image whose first_tile range holds
-// it; each image brings its own tensor map, output, pitch and scale.
+// it; each image brings its own tensor maps, output, pitch and scale.
 struct TilesBatch {
     const BatchTmaTable *t;
     int W;
@@ -892,6 +987,7 @@ struct TilesBatch {
         return lo;
     }
     __device__ const CUtensorMap *tmap(int g) const { return &t->map[job(g)]; }
+    __device__ const CUtensorMap *omap(int g) const { return &t->omap[job(g)]; }
     __device__ int col(int g) const { return (g - t->first_tile[job(g)]) * W; }
     __device__ float2 *dst(int g) const
     {
@@ -902,13 +998,13 @@ struct TilesBatch {
     __device__ float scl(int g) const { return t->scale[job(g)]; }
 };
 
-template <class C>
+template <class C, bool TS>
 __global__ void __launch_bounds__(C::T, 1) col_tma2_batch_kernel(const __grid_constant__ BatchTmaTable t,
                                                                  const float2 *__restrict__ tw,
                                                                  int *err)
 {
     const TilesBatch src{&t, C::W};
-    col_tma2_body<C>(src, t.first_tile[t.n], tw, err);
+    col_tma2_body<C, TS>(src, t.first_tile[t.n], tw, err);
 }
 
 // ---------------------------------------------------------------------------

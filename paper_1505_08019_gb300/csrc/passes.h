@@ -50,6 +50,10 @@ constexpr int col_kw(int L)
 // (512 threads of up to 128 registers), 16 below.
 constexpr int col_tma_ept(int L) { return L >= 10 ? 32 : 16; }
 
+// Rows of one TMA store box of the persistent column pass: half of the 2^8
+// rows that one unit of its last stage group spans (lines of 2^9..2^12).
+constexpr int tma_store_rows(int) { return 128; }
+
 // Lines per CTA of the row pass and interleaved columns per CTA of the
 // column pass for an axis of 2^L points.
 int row_lines_per_cta(int L);
@@ -94,10 +98,12 @@ struct BatchTable {
     int n;
     BatchJob job[kBatchMaxJobs];
 };
-// Job table of the grouped TMA column kernel: one tensor map per image.
-constexpr int kBatchTmaMaxJobs = 96;
-struct alignas(64) BatchTmaTable {
+// Job table of the grouped TMA column kernel: a load and a store tensor map
+// per image (a kernel parameter, well inside the 32 KB parameter limit).
+constexpr int kBatchTmaMaxJobs = 64;
+struct BatchTmaTable {   // 128-byte aligned through CUtensorMap
     CUtensorMap map[kBatchTmaMaxJobs];
+    CUtensorMap omap[kBatchTmaMaxJobs];
     float2 *out[kBatchTmaMaxJobs];
     long long ld[kBatchTmaMaxJobs];
     float scale[kBatchTmaMaxJobs];
@@ -119,9 +125,11 @@ const char *batch_variant_name(bool row, int variant);
 cudaError_t launch_batch_pass(bool row, int L, BatchTable &t, int variant, int *err,
                               cudaStream_t s);
 
-// 2D tensor map over a column-pass input (8-byte elements, box W x box_rows).
+// 3D tensor map over a column-pass image of 8-byte elements (rows a
+// multiple of 256): x = column, y = row within a block of 256 rows, z =
+// block; box W x box_y x box_z.
 bool encode_col_map(CUtensorMap *map, const float2 *base, int rows, int cols, long long ld, int W,
-                    int box_rows);
+                    int box_y, int box_z);
 
 cudaError_t launch_row_pass(int L, const PassArgs &a, cudaStream_t s);
 
