@@ -78,7 +78,7 @@ cudaError_t batch_launch_tma(const BatchTable &t, int *err, cudaStream_t s, bool
 {
     *used = false;
     static thread_local BatchTmaTable tt;
-    if (t.n > kBatchTmaMaxJobs || !err)
+    if (t.n > kBatchTmaMaxJobs || !err || (reinterpret_cast<uintptr_t>(t.job[0].tw) & 15))
         return cudaSuccess;
     int tiles = 0;
     for (int i = 0; i < t.n; i++) {

@@ -461,6 +461,9 @@ fft2d_status fft2d_plan(int rows, int cols, int dtype, int dir, fft2d_plan_t *ou
         return cuda_fail(e, "cudaGetDevice");
     }
     std::vector<float2> tr = stage_table(p->Lc, dir), tc = stage_table(p->Lr, dir);
+    // one padding entry: kernels may copy 2^L entries (a multiple of 16 bytes)
+    tr.push_back(make_float2(0.f, 0.f));
+    tc.push_back(make_float2(0.f, 0.f));
     e = cudaMalloc(&p->tw_rows, tr.size() * sizeof(float2));
     if (e == cudaSuccess)
         e = cudaMalloc(&p->tw_cols, tc.size() * sizeof(float2));

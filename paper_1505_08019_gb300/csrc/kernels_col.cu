@@ -124,7 +124,7 @@ bool col_tma_usable(const PassArgs &a)
 {
     return !a.partial && a.err && tensor_map_encoder() &&
            !(reinterpret_cast<uintptr_t>(a.in) & 15) && !(reinterpret_cast<uintptr_t>(a.out) & 15) &&
-           !((a.ld * 8) & 15) && a.cols % C::W == 0;
+           !(reinterpret_cast<uintptr_t>(a.tw) & 15) && !((a.ld * 8) & 15) && a.cols % C::W == 0;
 }
 
 // Persistent TMA-fed column pass (col_tma2_kernel), with TMA stores (TS) or

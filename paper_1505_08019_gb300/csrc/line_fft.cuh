@@ -784,6 +784,7 @@ struct TmaSplit {
     static constexpr int TW_VALS = C::N - 1;                         // twiddle table copy
     static constexpr int TW_OFF = C::E + NB * BOX_VALS;
     static constexpr int SMEM_BYTES = (TW_OFF + TW_VALS + 1) * 8;
+    static constexpr uint32_t TW_BYTES = (uint32_t)(TW_VALS + 1) * 8u;   // with padding
     static constexpr uint32_t EARLY_BYTES = (uint32_t)NB * BOX_VALS * 8u;
     static constexpr uint32_t LATE_BYTES = (uint32_t)(NBOX - NB) * BOX_VALS * 8u;
     static_assert(NB >= 1 && 2 * NB == NBOX, "two equal halves of whole blocks");
@@ -808,11 +809,13 @@ __device__ __forceinline__ void split_issue_late(float2 *sm, const CUtensorMap *
 }
 
 // Group 0 from the split tile (see above), ending with the swizzled exchange
-// layout in the tile region.  `after_reads` runs once every thread has
-// gathered its values (the prefetch region is then free).
-template <class C, bool SYNC_AFTER, class F>
+// layout in the tile region.  `before_barrier` runs just before the barrier
+// that follows the gather; `after_reads` runs once every thread has gathered
+// its values (the prefetch region is then free).
+template <class C, class F0, class F>
 __device__ __forceinline__ void group_first_split(float2 (&a)[C::EPT], float2 *sm,
-                                                  const float2 *__restrict__ tw, F after_reads)
+                                                  const float2 *__restrict__ tw, F0 before_barrier,
+                                                  F after_reads)
 {
     using Gp = Grp<C, 0>;
     using S = TmaSplit<C>;
@@ -838,10 +841,9 @@ __device__ __forceinline__ void group_first_split(float2 (&a)[C::EPT], float2 *s
     for (int v = 0; v < Gp::V; v++)
         run_stages<C, 0, false, true>(a, v, 0, tw, C::L);
     fence_proxy_async_smem();
+    before_barrier();  // what it waits for holds for every thread after the barrier
     __syncthreads();   // every slot of both regions has been read
     after_reads();
-    if constexpr (SYNC_AFTER)
-        __syncthreads();   // what after_reads waited for holds for every thread
 #pragma unroll
     for (int v = 0; v < Gp::V; v++) {
         const int u = tid + v * C::T;
@@ -895,15 +897,15 @@ __device__ __forceinline__ void col_tma2_body(const Src &src, int ntiles,
         fence_mbar_init();
     }
     __syncthreads();
+    // the rotation factors (N entries, the last one padding) stay in shared
+    // memory for the CTA's whole life; they arrive with the first tile
+    float2 *stw = sm + TmaSplit<C>::TW_OFF;
     if (tid == 0 && tile < ntiles) {
+        mbar_expect_tx(&bar_early, TmaSplit<C>::TW_BYTES);
+        bulk_load(stw, tw, TmaSplit<C>::TW_BYTES, &bar_early);
         split_issue_early<C>(sm, src.tmap(tile), src.col(tile), &bar_early);
         split_issue_late<C>(sm, src.tmap(tile), src.col(tile), &bar_late);
     }
-    // the rotation factors stay in shared memory for the CTA's whole life
-    float2 *stw = sm + TmaSplit<C>::TW_OFF;
-    for (int i = tid; i < TmaSplit<C>::TW_VALS; i += C::T)
-        stw[i] = __ldg(tw + i);
-    __syncthreads();
     uint32_t parity = 0;
     float2 a[C::EPT];
     for (; tile < ntiles; tile += gridDim.x) {
@@ -921,14 +923,18 @@ __device__ __forceinline__ void col_tma2_body(const Src &src, int ntiles,
             return;
         }
         parity ^= 1;
-        group_first_split<C, TS>(a, sm, stw, [&] {
-            if (tid == 0) {
-                if (next < ntiles)
+        group_first_split<C>(
+            a, sm, stw,
+            [&] {
+                if constexpr (TS) {
+                    if (tid == 0)
+                        bulk_wait_read_all();   // the previous tile's staging half is free
+                }
+            },
+            [&] {
+                if (tid == 0 && next < ntiles)
                     split_issue_early<C>(sm, src.tmap(next), src.col(next), &bar_early);
-                if constexpr (TS)
-                    bulk_wait_read_all();   // the previous tile's staging half is free
-            }
-        });
+            });
         __syncthreads();
         if constexpr (C::NG >= 3) {
             group_smem<C, 1, false, false, true>(a, sm, stw, C::L);

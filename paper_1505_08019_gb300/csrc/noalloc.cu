@@ -18,7 +18,10 @@
 namespace {
 
 constexpr int kMaxDevices = 64;
-constexpr int kTableVals = FFT2D_NOALLOC_MAX_SIDE - 1;   // entries per axis table
+// entries per axis table: 2^L - 1 rotation factors plus one padding entry
+// (the persistent column pass copies 2^L entries with one 16-byte-multiple
+// bulk copy, so every table starts on a 16-byte boundary)
+constexpr int kTableVals = FFT2D_NOALLOC_MAX_SIDE;
 
 // The shared scratch: both axes' rotation factors and the status word the
 // column kernel writes when a bounded wait gives up.  About 64 KB.

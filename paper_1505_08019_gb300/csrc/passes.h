@@ -11,7 +11,8 @@ namespace fft2d {
 struct PassArgs {
     const float2 *in;    // device, first pixel of the image
     float2 *out;         // device, may equal in
-    const float2 *tw;    // device, per-stage rotation factors of this axis
+    const float2 *tw;    // device, per-stage rotation factors of this axis: 2^L - 1
+                         // entries and one padding entry, 16-byte aligned
     int rows, cols;      // image shape
     long long ld;        // row pitch in pixels (== cols for a dense image)
     float scale;         // multiplies every stored value (1 or 1/(rows*cols))
@@ -135,6 +136,7 @@ cudaError_t launch_row_pass(int L, const PassArgs &a, cudaStream_t s);
 
 // Streaming multiprocessors of the current device (cached per device).
 int device_sm_count();
+
 int device_current();
 cudaError_t launch_selftest_timeout(int *err, cudaStream_t s);
 cudaError_t launch_col_pass(int L, const PassArgs &a, cudaStream_t s);
