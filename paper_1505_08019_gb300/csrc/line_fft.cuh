@@ -126,13 +126,19 @@ __device__ __forceinline__ float2 ld_tw(const float2 *p)
         return __ldg(p);
 }
 
-// W * b with one fixed rounding sequence (one product rounded, one fused
-// multiply-add), so that every kernel variant -- whatever the compiler would
-// otherwise contract -- produces the same bits.
-__device__ __forceinline__ float2 cmul_w(float2 w, float2 b)
+// One radix-2 butterfly (x0, x1) <- (x0 + W x1, x0 - W x1) with a fixed
+// rounding sequence, so that every kernel variant -- whatever the compiler
+// would otherwise contract -- produces the same bits.  Six fused
+// multiply-adds: the sum y = x0 + W x1 takes two per component (x0 + the
+// first partial product, then + the second), and the difference follows
+// from it as 2 x0 - y (exact doubling, one rounding), instead of forming W x1
+// and then both the sum and the difference (eight operations).
+__device__ __forceinline__ void butterfly_w(float2 &x0, float2 &x1, float2 w)
 {
-    return make_float2(__fmaf_rn(w.x, b.x, __fmul_rn(-w.y, b.y)),
-                       __fmaf_rn(w.x, b.y, __fmul_rn(w.y, b.x)));
+    const float2 y = make_float2(__fmaf_rn(-w.y, x1.y, __fmaf_rn(w.x, x1.x, x0.x)),
+                                 __fmaf_rn(w.y, x1.x, __fmaf_rn(w.x, x1.y, x0.y)));
+    x1 = make_float2(__fmaf_rn(2.0f, x0.x, -y.x), __fmaf_rn(2.0f, x0.y, -y.y));
+    x0 = y;
 }
 
 // Stages S0+1 .. S0+G on unit v of a[]: pairs (r, r + 2^t) at stage S0+1+t use
@@ -154,14 +160,13 @@ __device__ __forceinline__ void run_stages_g(float2 (&a)[NA], int v, int lo,
             const int jc = (r & ((1 << t) - 1)) << Gp::S0;
             float2 &x0 = a[v * Gp::R + r];
             float2 &x1 = a[v * Gp::R + (r | (1 << t))];
-            float2 m;
-            if (FIRST && jc == 0) {
-                m = x1;   // W = 1
+            if (FIRST && jc == 0) {   // W = 1
+                const float2 m = x1;
+                x1 = make_float2(__fsub_rn(x0.x, m.x), __fsub_rn(x0.y, m.y));
+                x0 = make_float2(__fadd_rn(x0.x, m.x), __fadd_rn(x0.y, m.y));
             } else {
-                m = cmul_w(ld_tw<TWS>(tws + lo + jc), x1);
+                butterfly_w(x0, x1, ld_tw<TWS>(tws + lo + jc));
             }
-            x1 = make_float2(__fsub_rn(x0.x, m.x), __fsub_rn(x0.y, m.y));
-            x0 = make_float2(__fadd_rn(x0.x, m.x), __fadd_rn(x0.y, m.y));
         }
     }
 }
