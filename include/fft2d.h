@@ -185,6 +185,21 @@ FFT2D_API fft2d_status fft2d_exec_host(fft2d_plan_t plan, const void *in_host, v
                              void *stream);
 
 /*
+ * fft2d_exec_host for n images at once, pipelined: while image i is
+ * transformed, image i+1 uploads and image i-1 downloads, on two internal
+ * copy streams and the caller's stream (three device image buffers per
+ * device, grown to the largest image and kept for the life of the process).
+ * Image i is transformed with plans[i] from in_host[i] to out_host[i];
+ * in_host[i] == out_host[i] is allowed, different images must not overlap.
+ * The copies start after the work already queued on `stream`.  complex64
+ * plans of one device only.  Synchronous: every copy has finished on return,
+ * after a failure too.  Pinned host memory gives the full copy bandwidth.
+ */
+FFT2D_API fft2d_status fft2d_exec_host_many(int n, const fft2d_plan_t *plans,
+                                            const void *const *in_host, void *const *out_host,
+                                            void *stream);
+
+/*
  * n independent transforms, possibly of different plans (sizes, directions),
  * issued on one stream: image i is transformed with plans[i] from in[i] to
  * out[i] (device pointers; in[i] == out[i] allowed; different images must not

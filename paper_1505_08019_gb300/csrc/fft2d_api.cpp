@@ -280,6 +280,69 @@ void apply_tuned(fft2d_plan_s *p)
 
 namespace {
 
+// Device buffers, streams and events of the pipelined host path, one set per
+// device, grown on demand and kept for the life of the process.  One call at
+// a time uses a device's set (the mutex).
+constexpr int kHostSlots = 3;      // images in flight: upload, transform, download
+constexpr int kHostMaxDev = 64;
+
+struct HostPipe {
+    std::mutex mu;
+    void *slot[kHostSlots] = {};
+    size_t slot_bytes = 0;
+    cudaStream_t up = nullptr, down = nullptr;
+    cudaEvent_t in_ready[kHostSlots] = {}, done[kHostSlots] = {}, freed[kHostSlots] = {};
+    cudaEvent_t start = nullptr;
+    bool ready = false;
+};
+
+HostPipe g_host_pipe[kHostMaxDev];
+
+cudaError_t host_pipe_prepare(HostPipe &hp, size_t bytes)
+{
+    cudaError_t e = cudaSuccess;
+    if (!hp.ready) {
+        e = cudaStreamCreateWithFlags(&hp.up, cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+            e = cudaStreamCreateWithFlags(&hp.down, cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&hp.start, cudaEventDisableTiming);
+        for (int k = 0; k < kHostSlots && e == cudaSuccess; k++) {
+            e = cudaEventCreateWithFlags(&hp.in_ready[k], cudaEventDisableTiming);
+            if (e == cudaSuccess)
+                e = cudaEventCreateWithFlags(&hp.done[k], cudaEventDisableTiming);
+            if (e == cudaSuccess)
+                e = cudaEventCreateWithFlags(&hp.freed[k], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess)
+            return e;
+        hp.ready = true;
+    }
+    if (bytes > hp.slot_bytes) {
+        for (int k = 0; k < kHostSlots; k++) {
+            cudaFree(hp.slot[k]);
+            hp.slot[k] = nullptr;
+        }
+        hp.slot_bytes = 0;
+        for (int k = 0; k < kHostSlots; k++) {
+            e = cudaMalloc(&hp.slot[k], bytes);
+            if (e != cudaSuccess) {
+                for (int j = 0; j < kHostSlots; j++) {
+                    cudaFree(hp.slot[j]);
+                    hp.slot[j] = nullptr;
+                }
+                return e;
+            }
+        }
+        hp.slot_bytes = bytes;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+namespace {
+
 // Grouped-launch variant for (pass, L): tuned winner (key pass + 2) or the
 // default.
 int batch_variant(int device, int pass, int L)
@@ -877,6 +940,85 @@ fft2d_status fft2d_exec_host(fft2d_plan_t p, const void *in_host, void *out_host
     if (e != cudaSuccess)
         return cuda_fail(e, "cudaStreamSynchronize");
     return FFT2D_OK;
+}
+
+fft2d_status fft2d_exec_host_many(int n, const fft2d_plan_t *plans, const void *const *in_host,
+                                  void *const *out_host, void *stream)
+{
+    if (n < 0 || (n > 0 && (!plans || !in_host || !out_host)))
+        return FFT2D_ERR_ARG;
+    size_t bytes = 0;
+    for (int i = 0; i < n; i++) {
+        if (!plans[i] || !in_host[i] || !out_host[i] || plans[i]->dtype != FFT2D_C64)
+            return FFT2D_ERR_ARG;
+        fft2d_status s = check_device(plans[i]);
+        if (s != FFT2D_OK)
+            return s;
+        const size_t b = (size_t)plans[i]->rows * plans[i]->cols * sizeof(float2);
+        bytes = b > bytes ? b : bytes;
+    }
+    if (n == 0)
+        return FFT2D_OK;
+    const int dev = plans[0]->device;
+    if (dev < 0 || dev >= kHostMaxDev)
+        return FFT2D_ERR_ARG;
+    HostPipe &hp = g_host_pipe[dev];
+    std::lock_guard<std::mutex> lock(hp.mu);
+    cudaError_t e = host_pipe_prepare(hp, bytes);
+    if (e != cudaSuccess)
+        return e == cudaErrorMemoryAllocation ? (cuda_fail(e, "cudaMalloc host pipeline"), FFT2D_ERR_OOM)
+                                              : cuda_fail(e, "host pipeline setup");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    fft2d_status result = FFT2D_OK;
+    // the copies start after the work already queued on the caller's stream
+    e = cudaEventRecord(hp.start, st);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(hp.up, hp.start, 0);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(hp.down, hp.start, 0);
+    if (e != cudaSuccess)
+        result = cuda_fail(e, "host pipeline ordering");
+    // image i uses slot i % kHostSlots: upload on `up`, transform on the
+    // caller's stream, download on `down`; the upload into a slot waits for
+    // the download of the image that used it before
+    for (int i = 0; i < n && result == FFT2D_OK; i++) {
+        const int k = i % kHostSlots;
+        const fft2d_plan_s *p = plans[i];
+        const size_t b = (size_t)p->rows * p->cols * sizeof(float2);
+        if (i >= kHostSlots)
+            e = cudaStreamWaitEvent(hp.up, hp.freed[k], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(hp.slot[k], in_host[i], b, cudaMemcpyHostToDevice, hp.up);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(hp.in_ready[k], hp.up);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(st, hp.in_ready[k], 0);
+        if (e != cudaSuccess) {
+            result = cuda_fail(e, "host pipeline upload");
+            break;
+        }
+        result = exec_impl(p, hp.slot[k], hp.slot[k], -1, -1, st);
+        if (result != FFT2D_OK)
+            break;
+        e = cudaEventRecord(hp.done[k], st);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(hp.down, hp.done[k], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(out_host[i], hp.slot[k], b, cudaMemcpyDeviceToHost, hp.down);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(hp.freed[k], hp.down);
+        if (e != cudaSuccess)
+            result = cuda_fail(e, "host pipeline download");
+    }
+    // synchronous: every queued copy and transform has finished on return,
+    // also after a failure (the slots may then be reused)
+    cudaError_t e1 = cudaStreamSynchronize(hp.up);
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    cudaError_t e3 = cudaStreamSynchronize(hp.down);
+    if (result == FFT2D_OK && (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess))
+        result = cuda_fail(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3),
+                           "cudaStreamSynchronize");
+    return result;
 }
 
 fft2d_status fft2d_exec_batched(int n, const fft2d_plan_t *plans, const void *const *in,

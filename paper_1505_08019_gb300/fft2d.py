@@ -66,6 +66,8 @@ _sigs = {
     "fft2d_batch_variant_name": ([_I, _I], ctypes.c_char_p),
     "fft2d_batch_get_variant": ([_I, _I], _I),
     "fft2d_batch_set_variant": ([_I, _I, _I], _I),
+    "fft2d_exec_host_many": ([_I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
+                             _I),
     "fft2d_autotune_batched": ([_I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
                                _I),
     "fft2d_exec_h16": ([_P, _P, _P, _I, _P, _P, _P], _I),
@@ -259,6 +261,17 @@ def fft2d_batch_get_variant(pass_: int, L: int) -> int:
 
 def fft2d_batch_set_variant(pass_: int, L: int, variant: int) -> None:
     _check(lib.fft2d_batch_set_variant(pass_, L, variant), "fft2d_batch_set_variant")
+
+
+def fft2d_exec_host_many(plans, inps, outs, stream=None) -> None:
+    """Pipelined fft2d_exec_host over many host images (synchronous)."""
+    n = len(plans)
+    if len(inps) != n or len(outs) != n:
+        raise ValueError("plans, inputs and outputs must have the same length")
+    arr = ctypes.c_void_p * max(n, 1)
+    _check(lib.fft2d_exec_host_many(n, arr(*plans), arr(*[_hptr(x) for x in inps]),
+                                    arr(*[_hptr(x) for x in outs]), _stream(stream)),
+           "fft2d_exec_host_many")
 
 
 def fft2d_autotune_batched(plans, inps, outs, stream=None) -> None:

@@ -63,6 +63,9 @@ def test_null_arguments(fft):
     assert fft.lib.fft2d_exec_pass(None, 0, None, None, None) == fft.FFT2D_ERR_ARG
     assert fft.lib.fft2d_destroy(None) == fft.FFT2D_OK
     assert fft.lib.fft2d_exec_batched(-1, None, None, None, None) == fft.FFT2D_ERR_ARG
+    assert fft.lib.fft2d_exec_host_many(-1, None, None, None, None) == fft.FFT2D_ERR_ARG
+    assert fft.lib.fft2d_exec_host_many(2, None, None, None, None) == fft.FFT2D_ERR_ARG
+    assert fft.lib.fft2d_exec_host_many(0, None, None, None, None) == fft.FFT2D_OK
     assert fft.lib.fft2d_stage_table(15, -1, None) == fft.FFT2D_ERR_ARG
 
 
