@@ -1,0 +1,251 @@
+// col_pair.cuh -- persistent column pass for columns of 2^(L+1) rows whose
+// 4-column tile is too large for one SM, split over a cluster of two CTAs.
+//
+// The DIT structure (Section 2 eqs. 2-3) splits the transform without any
+// extra pass over memory.  After the scramble, positions p < 2^L hold the
+// even rows and positions p >= 2^L the odd rows, each in the bit-reversed
+// order of a 2^L-point line, and stages 1..L never mix the two halves.  So
+// CTA b of the pair loads rows 2m + b of the tile by TMA (a tensor map with
+// twice the row pitch), runs stages 1..L on them with the same engine as the
+// single-CTA column pass (col_tma2_body: prefetch region, three stage
+// groups, rotation factors in shared memory) and ends with Y_b[k], k < 2^L,
+// in registers.  The last stage pairs Y_0[k] and Y_1[k]:
+//     X[k] = Y_0[k] + W^k Y_1[k],   X[k + 2^L] = Y_0[k] - W^k Y_1[k],
+// W = W_{2^(L+1)}.  Thread t holds the same indices k in both CTAs, so the
+// two twins exchange half of their values: CTA b keeps the k of its half
+// (top bit of k/2^(L-1) equal to b) and receives the partner's values of
+// them with posted remote stores into its shared memory, then writes rows k
+// and k + 2^L of its half with two TMA stores.
+//
+// Cluster barriers have no time limit, so both CTAs always execute the same
+// sequence of them: a CTA that lost a TMA transfer still reaches the next
+// cluster barrier, where the two exchange a "lost" flag and leave together.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "line_fft.cuh"
+
+namespace fft2d {
+
+__device__ __forceinline__ void cluster_arrive_release()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void cluster_wait_acquire()
+{
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Tile geometry of the pair kernel for a local engine C (2^L rows, W
+// columns, 512 threads x 32 values).
+template <class C>
+struct PairCol {
+    using S = TmaSplit<C>;
+    using Gl = Grp<C, C::NG - 1>;
+    static constexpr int L = C::L;                        // local stages
+    static constexpr int NL = C::N;                       // local rows
+    static constexpr int HALF_R = Gl::R / 2;              // register indices of one output half
+    static constexpr int RECV = Gl::V * HALF_R;           // values received per thread
+    static constexpr int OUT_BOX_Z = (NL / 2) / S::BOX;   // 256-row blocks of one output half
+    static_assert(C::EPT == 32 && C::NG == 3 && C::LB == 1, "512 threads x 32 values, 3 groups");
+    static_assert(Gl::S0 + Gl::G == L && (NL >> Gl::S0) == Gl::R,
+                  "the last group's register index is the top bits of k");
+    static_assert(RECV * C::T * 8 <= C::E * 4, "the receive buffer fits in half the tile region");
+    static_assert((NL / 2) % S::BOX == 0, "output halves are whole 256-row blocks");
+};
+
+// C: the local engine; CTA rank b of the cluster.  lmap: this CTA's load map
+// (rows b, b+2, ... of the image; box W x 256 x NB); omap: store map over the
+// output (box W x 256 x OUT_BOX_Z); twl: rotation factors of the local stages
+// (2^L entries, padding included); tw_last: W_{2^(L+1)}^k, k < 2^L.
+template <class C>
+__device__ __forceinline__ void col_pair_body(const CUtensorMap *lmap, const CUtensorMap *omap,
+                                              int ntiles, const float2 *__restrict__ twl,
+                                              const float2 *__restrict__ tw_last, float scale,
+                                              int *err)
+{
+    namespace cg = cooperative_groups;
+    using S = TmaSplit<C>;
+    using PC = PairCol<C>;
+    using Gl = Grp<C, C::NG - 1>;
+    extern __shared__ __align__(1024) float2 sm[];
+    __shared__ __align__(8) uint64_t bar_early, bar_late;
+    __shared__ int lost_flag[2];   // [0] this CTA, [1] written by the partner
+    cg::cluster_group cluster = cg::this_cluster();
+    const int b = (int)cluster.block_rank();
+    const int tid = threadIdx.x;
+    const int nclusters = (int)gridDim.x / 2;
+    float2 *stw = sm + S::TW_OFF;
+    float2 *recv = sm + C::E / 2;                       // upper half of the tile region
+    float2 *peer_recv = cluster.map_shared_rank(recv, b ^ 1);
+    int *peer_flag = cluster.map_shared_rank(lost_flag + 1, b ^ 1);   // its slot [1]
+    int tile = (int)blockIdx.x / 2;
+
+    if (tid == 0) {
+        mbar_init(&bar_early, 1);
+        mbar_init(&bar_late, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    // issued / waited phases of each mbarrier (thread 0 issues, all wait)
+    int n_early = 0, n_late = 0, w_early = 0, w_late = 0;
+    if (tile < ntiles) {
+        if (tid == 0) {
+            mbar_expect_tx(&bar_early, S::TW_BYTES);
+            bulk_load(stw, twl, S::TW_BYTES, &bar_early);
+            split_issue_early<C>(sm, lmap, tile * C::W, &bar_early);
+            split_issue_late<C>(sm, lmap, tile * C::W, &bar_late);
+        }
+        n_early = n_late = 1;
+    }
+    bool lost = false;
+    float2 a[C::EPT];
+    for (; tile < ntiles; tile += nclusters) {
+        const int next = tile + nclusters;
+        const bool ok = mbar_wait_bounded(&bar_early, (uint32_t)(w_early & 1)) &&
+                        mbar_wait_bounded(&bar_late, (uint32_t)(w_late & 1));
+        const int lost_here = __syncthreads_or(ok ? 0 : 1);
+        if (!lost_here) {
+            w_early++;
+            w_late++;
+            group_first_split<C>(
+                a, sm, stw,
+                [&] {
+                    if (tid == 0)
+                        bulk_wait_read_all();   // the previous tile's staging is free
+                },
+                [&] {
+                    if (tid == 0 && next < ntiles)
+                        split_issue_early<C>(sm, lmap, next * C::W, &bar_early);
+                });
+            if (next < ntiles)
+                n_early++;
+            __syncthreads();
+            group_smem<C, 1, false, false, true>(a, sm, stw, C::L);
+            __syncthreads();
+            group_last_read<C>(a, sm);
+            fence_proxy_async_smem();
+            __syncthreads();   // the tile region is free
+            if (tid == 0 && next < ntiles)
+                split_issue_late<C>(sm, lmap, next * C::W, &bar_late);
+            if (next < ntiles)
+                n_late++;
+#pragma unroll
+            for (int v = 0; v < Gl::V; v++) {
+                const int u = tid + v * C::T;
+                const int lo = (u >> C::KW) & ((1 << Gl::S0) - 1);
+                run_stages<C, C::NG - 1, false, true>(a, v, lo, stw, C::L);
+            }
+        }
+        // both CTAs are past their last read of this tile (the partner may
+        // now write into this CTA's receive buffer) and agree on "lost"
+        if (tid == 0) {
+            lost_flag[0] = lost_here;
+            *peer_flag = lost_here;
+        }
+        cluster_arrive_release();
+        cluster_wait_acquire();
+        if (lost_flag[0] | lost_flag[1]) {
+            lost = true;
+            break;
+        }
+
+        // send the partner the values of its half: register index r with
+        // top bit != b, slot (v * HALF_R + (r mod HALF_R)) * T + tid
+#pragma unroll
+        for (int v = 0; v < Gl::V; v++) {
+#pragma unroll
+            for (int i = 0; i < PC::HALF_R; i++) {
+                const float2 lo_half = a[v * Gl::R + i], hi_half = a[v * Gl::R + PC::HALF_R + i];
+                peer_recv[(v * PC::HALF_R + i) * C::T + tid] = b == 0 ? hi_half : lo_half;
+            }
+        }
+        float2 wk[PC::RECV];
+#pragma unroll
+        for (int v = 0; v < Gl::V; v++) {
+            const int u = tid + v * C::T;
+            const int lo = (u >> C::KW) & ((1 << Gl::S0) - 1);
+#pragma unroll
+            for (int i = 0; i < PC::HALF_R; i++) {
+                const int k = lo | ((b * PC::HALF_R + i) << Gl::S0);
+                wk[v * PC::HALF_R + i] = __ldg(tw_last + k);
+            }
+        }
+        cluster_arrive_release();
+        cluster_wait_acquire();
+
+        // the last stage on this CTA's half, then rows k and k + 2^L via two
+        // TMA stores from the staging buffer (the receive buffer, once read)
+        float2 o[2][PC::RECV];
+#pragma unroll
+        for (int v = 0; v < Gl::V; v++) {
+#pragma unroll
+            for (int i = 0; i < PC::HALF_R; i++) {
+                const int j = v * PC::HALF_R + i;
+                const float2 lo_half = a[v * Gl::R + i], hi_half = a[v * Gl::R + PC::HALF_R + i];
+                const float2 mine = b == 0 ? lo_half : hi_half;
+                const float2 theirs = recv[j * C::T + tid];
+                float2 x0 = b == 0 ? mine : theirs;
+                float2 x1 = b == 0 ? theirs : mine;
+                butterfly_w(x0, x1, wk[j]);
+                o[0][j] = make_float2(x0.x * scale, x0.y * scale);
+                o[1][j] = make_float2(x1.x * scale, x1.y * scale);
+            }
+        }
+        __syncthreads();   // the receive buffer has been read
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            if (h == 1) {
+                if (tid == 0)
+                    bulk_wait_read_all();
+                __syncthreads();
+            }
+#pragma unroll
+            for (int v = 0; v < Gl::V; v++) {
+                const int u = tid + v * C::T;
+                const int w = u & (C::W - 1);
+                const int lo = (u >> C::KW) & ((1 << Gl::S0) - 1);
+#pragma unroll
+                for (int i = 0; i < PC::HALF_R; i++)
+                    recv[((i << Gl::S0) | lo) * C::W + w] = o[h][v * PC::HALF_R + i];
+            }
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                // rows h 2^L + b 2^(L-1) + [0, 2^(L-1)): 256-row blocks from z
+                const int z = (h * PC::NL + b * (PC::NL / 2)) / S::BOX;
+                tma_store_3d(omap, tile * C::W, 0, z, recv);
+                bulk_commit();
+            }
+        }
+    }
+
+    if (lost) {
+        if (tid == 0)
+            atomicExch(err, kDevErrTmaTimeout);
+        // let transfers still in flight land before the CTA leaves
+        if (n_early > w_early)
+            mbar_wait_bounded(&bar_early, (uint32_t)(w_early & 1));
+        if (n_late > w_late)
+            mbar_wait_bounded(&bar_late, (uint32_t)(w_late & 1));
+    }
+    if (tid == 0)
+        bulk_wait_all();   // shared memory stays valid until the stores are done
+}
+
+template <class C>
+__global__ void __launch_bounds__(C::T, 1) col_pair_kernel(const __grid_constant__ CUtensorMap map0,
+                                                           const __grid_constant__ CUtensorMap map1,
+                                                           const __grid_constant__ CUtensorMap omap,
+                                                           const float2 *__restrict__ tw,
+                                                           int cols, float scale, int *err)
+{
+    const bool odd = (cooperative_groups::this_cluster().block_rank() & 1) != 0;
+    // the local stages use entries [0, 2^L) of the table, the last stage
+    // entries 2^L - 1 + k (stage L+1 starts at offset 2^L - 1)
+    col_pair_body<C>(odd ? &map1 : &map0, &omap, cols / C::W, tw, tw + (C::N - 1), scale, err);
+}
+
+}  // namespace fft2d

@@ -4,8 +4,11 @@
 // contiguous bytes of a row and the whole column stays on chip.
 #include <cudaTypedefs.h>
 
+#include <cstring>
 #include <mutex>
 
+#include "col_pair.cuh"
+#include "col_tmem.cuh"
 #include "line_fft.cuh"
 #include "passes.h"
 
@@ -161,6 +164,93 @@ cudaError_t col_launch_tma(const PassArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Persistent column pass with the next tile parked in TMEM (col_tmem_kernel):
+// TMA loads into a landing region, whole-tile TMA store.  Falls back to the
+// plain kernel if a tile cannot be described by a tensor map.
+template <class C>
+cudaError_t col_launch_tmem(const PassArgs &a, cudaStream_t s)
+{
+    CUtensorMap map, omap;
+    using S = TmaSplit<C>;
+    if (!encode_col_map(&map, a.in, a.rows, a.cols, a.ld, C::W, S::BOX, S::NB) ||
+        !encode_col_map(&omap, a.out, a.rows, a.cols, a.ld, C::W, S::BOX, S::NBOX))
+        return col_launch_any<LineCfg<C::L, C::KW, 0>>(a, s);
+    auto k = col_tmem_kernel<C>;
+    constexpr int SMEM = S::SMEM_BYTES;
+    static int occ[kMaxDev] = {};
+    const int d = current_device();
+    if (!occ[d]) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             SMEM);
+        if (e != cudaSuccess)
+            return e;
+        int o = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, C::T, SMEM);
+        if (e != cudaSuccess)
+            return e;
+        occ[d] = o > 0 ? o : 1;
+    }
+    const int ntiles = a.cols / C::W;
+    int grid = sm_count() * occ[d];
+    if (grid > ntiles)
+        grid = ntiles;
+    k<<<grid, C::T, SMEM, s>>>(map, omap, a.out, a.tw, a.cols, a.ld, a.scale, a.err);
+    return cudaGetLastError();
+}
+
+// Column pass over 2^(L+1)-row columns split over a CTA pair
+// (col_pair_kernel, local engine C of 2^L rows): one load map per CTA (rows
+// of one parity), one store map, a persistent grid of as many pairs as can
+// be resident at once.
+template <class C>
+bool col_pair_usable(const PassArgs &a)
+{
+    return col_tma_usable<C>(a) && a.rows == 2 * C::N;
+}
+
+template <class C>
+cudaError_t col_launch_pair(const PassArgs &a, cudaStream_t s)
+{
+    using S = TmaSplit<C>;
+    using PC = PairCol<C>;
+    CUtensorMap m0, m1, om;
+    if (!encode_col_map(&m0, a.in, a.rows / 2, a.cols, 2 * a.ld, C::W, S::BOX, S::NB) ||
+        !encode_col_map(&m1, a.in + a.ld, a.rows / 2, a.cols, 2 * a.ld, C::W, S::BOX, S::NB) ||
+        !encode_col_map(&om, a.out, a.rows, a.cols, a.ld, C::W, S::BOX, PC::OUT_BOX_Z))
+        return col_launch_any<LineCfg<C::L + 1, C::KW, 0>>(a, s);
+    auto k = col_pair_kernel<C>;
+    constexpr int SMEM = S::SMEM_BYTES;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(C::T);
+    cfg.dynamicSmemBytes = SMEM;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    static int pairs[kMaxDev] = {};
+    const int d = current_device();
+    if (!pairs[d]) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             SMEM);
+        if (e != cudaSuccess)
+            return e;
+        cfg.gridDim = dim3((unsigned)(2 * (sm_count() / 2)));
+        int n = 0;
+        e = cudaOccupancyMaxActiveClusters(&n, k, &cfg);
+        if (e != cudaSuccess)
+            return e;
+        pairs[d] = n > 0 ? n : 1;
+    }
+    const int ntiles = a.cols / C::W;
+    const int np = pairs[d] < ntiles ? pairs[d] : ntiles;
+    cfg.gridDim = dim3((unsigned)(2 * np));
+    return cudaLaunchKernelEx(&cfg, k, m0, m1, om, a.tw, a.cols, a.scale, a.err);
+}
+
 template <class CC>
 bool col_cluster_usable(const PassArgs &a)
 {
@@ -184,6 +274,8 @@ template <int L>
 struct ColVariants {
     using Plain = LineCfg<L, col_kw(L), 0>;
     static constexpr bool HASTMA = L >= 9 && L <= 12;
+    static constexpr bool HASTMEM = HASTMA && col_tma_ept(L) == 32;
+    using PairLocal = LineCfg<12, 2, 0, 32>;
     using Tma32 = LineCfg<L, col_kw(L), 0, col_tma_ept(L)>;
     using Tma16 = LineCfg<L, col_kw(L), 0, 16>;
     static constexpr int KWN = col_kw(L) - 1;                 // narrower tiles
@@ -229,6 +321,14 @@ struct ColVariants {
         if constexpr (HASCLUSTER8)
             t.v[t.n++] = {"cluster8", Clu8::W, 16, col_cluster_usable<Clu8>,
                           col_launch_cluster<Clu8>};
+        // the TMA engine with the next tile parked in TMEM (32 values a thread)
+        if constexpr (HASTMEM)
+            t.v[t.n++] = {"tmem", Tma32::W, 32, col_tma_usable<Tma32>, col_launch_tmem<Tma32>};
+        // 8192 rows: 4-column tiles over a CTA pair, the 4096-row engine on
+        // each half and the last stage through remote stores
+        if constexpr (L == 13)
+            t.v[t.n++] = {"pair", PairLocal::W, 32, col_pair_usable<PairLocal>,
+                          col_launch_pair<PairLocal>};
         return t;
     }
     static const Variant *table(int *n)
@@ -237,15 +337,24 @@ struct ColVariants {
         *n = t.n;
         return t.v;
     }
+    static int index_of(const char *name)
+    {
+        int n = 0;
+        const Variant *v = table(&n);
+        for (int i = 0; i < n; i++)
+            if (std::strcmp(v[i].name, name) == 0)
+                return i;
+        return 0;
+    }
     static int preferred()
     {
         if constexpr (HASTMA)
             return 1;   // measured fastest for 512..4096-row columns
-        else if constexpr (L >= 13) {
-            int n;
-            table(&n);
-            return n - 2;   // cluster of 4-column tiles: keeps 32-byte row segments
-        } else
+        else if constexpr (L == 13)
+            return index_of("pair");      // 4-column tiles over a CTA pair
+        else if constexpr (L == 14)
+            return index_of("cluster");   // 4-column tiles over 4 CTAs: 32-byte row segments
+        else
             return 0;
     }
 };
