@@ -38,6 +38,26 @@ __device__ __forceinline__ void cluster_wait_acquire()
     asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+// Bulk copy from this CTA's shared memory into another CTA's (dst and its
+// mbarrier are shared::cluster addresses); completes on that mbarrier.
+__device__ __forceinline__ void bulk_copy_to_peer(uint32_t dst, const void *src, uint32_t bytes,
+                                                  uint32_t peer_bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+        "[%3];" ::"r"(dst),
+        "r"(smem_addr(src)), "r"(bytes), "r"(peer_bar)
+        : "memory");
+}
+
 // Tile geometry of the pair kernel for a local engine C (2^L rows, W
 // columns, 512 threads x 32 values).
 template <class C>
@@ -49,6 +69,7 @@ struct PairCol {
     static constexpr int HALF_R = Gl::R / 2;              // register indices of one output half
     static constexpr int RECV = Gl::V * HALF_R;           // values received per thread
     static constexpr int OUT_BOX_Z = (NL / 2) / S::BOX;   // 256-row blocks of one output half
+    static constexpr uint32_t XBYTES = (uint32_t)RECV * C::T * 8u;   // values exchanged per CTA
     static_assert(C::EPT == 32 && C::NG == 3 && C::LB == 1, "512 threads x 32 values, 3 groups");
     static_assert(Gl::S0 + Gl::G == L && (NL >> Gl::S0) == Gl::R,
                   "the last group's register index is the top bits of k");
@@ -71,21 +92,28 @@ __device__ __forceinline__ void col_pair_body(const CUtensorMap *lmap, const CUt
     using PC = PairCol<C>;
     using Gl = Grp<C, C::NG - 1>;
     extern __shared__ __align__(1024) float2 sm[];
-    __shared__ __align__(8) uint64_t bar_early, bar_late;
+    __shared__ __align__(8) uint64_t bar_early, bar_late, bar_recv;
     __shared__ int lost_flag[2];   // [0] this CTA, [1] written by the partner
     cg::cluster_group cluster = cg::this_cluster();
     const int b = (int)cluster.block_rank();
     const int tid = threadIdx.x;
     const int nclusters = (int)gridDim.x / 2;
     float2 *stw = sm + S::TW_OFF;
-    float2 *recv = sm + C::E / 2;                       // upper half of the tile region
-    float2 *peer_recv = cluster.map_shared_rank(recv, b ^ 1);
+    // after the last read of a tile: the lower half of the tile region
+    // receives the partner's values, the upper half holds the values sent
+    // and then stages the output
+    float2 *recvb = sm;
+    float2 *sendb = sm + C::E / 2;
+    const uint32_t peer_recv = mapa_shared(smem_addr(recvb), (uint32_t)(b ^ 1));
+    const uint32_t peer_bar = mapa_shared(smem_addr(&bar_recv), (uint32_t)(b ^ 1));
     int *peer_flag = cluster.map_shared_rank(lost_flag + 1, b ^ 1);   // its slot [1]
+    int lost_recv = 0;
     int tile = (int)blockIdx.x / 2;
 
     if (tid == 0) {
         mbar_init(&bar_early, 1);
         mbar_init(&bar_late, 1);
+        mbar_init(&bar_recv, 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -101,12 +129,24 @@ __device__ __forceinline__ void col_pair_body(const CUtensorMap *lmap, const CUt
         n_early = n_late = 1;
     }
     bool lost = false;
+    int w_recv = 0;   // completed phases of bar_recv
     float2 a[C::EPT];
     for (; tile < ntiles; tile += nclusters) {
         const int next = tile + nclusters;
         const bool ok = mbar_wait_bounded(&bar_early, (uint32_t)(w_early & 1)) &&
                         mbar_wait_bounded(&bar_late, (uint32_t)(w_late & 1));
-        const int lost_here = __syncthreads_or(ok ? 0 : 1);
+        // a receive that timed out on the previous tile counts as lost too
+        const int lost_here = __syncthreads_or((ok ? 0 : 1) | lost_recv);
+        // the "lost" flags for cluster barrier X1 and the arming of the
+        // receive mbarrier, early so the remote flag store is long done
+        // when X1 is arrived at (the partner reads the flag after X1 and
+        // writes the next one only after X2)
+        if (tid == 0) {
+            if (!lost_recv)   // (a phase that timed out may still be open)
+                mbar_arrive_expect_tx(&bar_recv, PC::XBYTES);
+            lost_flag[0] = lost_here;
+            *peer_flag = lost_here;
+        }
         if (!lost_here) {
             w_early++;
             w_late++;
@@ -114,7 +154,7 @@ __device__ __forceinline__ void col_pair_body(const CUtensorMap *lmap, const CUt
                 a, sm, stw,
                 [&] {
                     if (tid == 0)
-                        bulk_wait_read_all();   // the previous tile's staging is free
+                        bulk_wait_read_all();   // the previous tile's stores have read T
                 },
                 [&] {
                     if (tid == 0 && next < ntiles)
@@ -126,43 +166,34 @@ __device__ __forceinline__ void col_pair_body(const CUtensorMap *lmap, const CUt
             group_smem<C, 1, false, false, true>(a, sm, stw, C::L);
             __syncthreads();
             group_last_read<C>(a, sm);
-            fence_proxy_async_smem();
             __syncthreads();   // the tile region is free
-            if (tid == 0 && next < ntiles)
-                split_issue_late<C>(sm, lmap, next * C::W, &bar_late);
-            if (next < ntiles)
-                n_late++;
+        }
+        // cluster barrier X1, arrive: this CTA's tile region is free and its
+        // receive mbarrier armed; the "lost" flags travel with it
+        cluster_arrive_release();
+        float2 wk[PC::RECV];
+        if (!lost_here) {
 #pragma unroll
             for (int v = 0; v < Gl::V; v++) {
                 const int u = tid + v * C::T;
                 const int lo = (u >> C::KW) & ((1 << Gl::S0) - 1);
                 run_stages<C, C::NG - 1, false, true>(a, v, lo, stw, C::L);
             }
-        }
-        // both CTAs are past their last read of this tile (the partner may
-        // now write into this CTA's receive buffer) and agree on "lost"
-        if (tid == 0) {
-            lost_flag[0] = lost_here;
-            *peer_flag = lost_here;
-        }
-        cluster_arrive_release();
-        cluster_wait_acquire();
-        if (lost_flag[0] | lost_flag[1]) {
-            lost = true;
-            break;
-        }
-
-        // send the partner the values of its half: register index r with
-        // top bit != b, slot (v * HALF_R + (r mod HALF_R)) * T + tid
+            // the partner's half -- register index r with top bit != b --
+            // into the send buffer, slot (v * HALF_R + (r mod HALF_R)) * T + tid
 #pragma unroll
-        for (int v = 0; v < Gl::V; v++) {
+            for (int v = 0; v < Gl::V; v++) {
 #pragma unroll
-            for (int i = 0; i < PC::HALF_R; i++) {
-                const float2 lo_half = a[v * Gl::R + i], hi_half = a[v * Gl::R + PC::HALF_R + i];
-                peer_recv[(v * PC::HALF_R + i) * C::T + tid] = b == 0 ? hi_half : lo_half;
+                for (int i = 0; i < PC::HALF_R; i++) {
+                    const float2 lo_half = a[v * Gl::R + i], hi_half = a[v * Gl::R + PC::HALF_R + i];
+                    sendb[(v * PC::HALF_R + i) * C::T + tid] = b == 0 ? hi_half : lo_half;
+                }
             }
+            fence_proxy_async_smem();
         }
-        float2 wk[PC::RECV];
+        __syncthreads();   // the send buffer is complete
+        // rotation factors of the last stage, W^k for this CTA's k (read from
+        // global memory; their latency hides behind the cluster barrier)
 #pragma unroll
         for (int v = 0; v < Gl::V; v++) {
             const int u = tid + v * C::T;
@@ -173,11 +204,22 @@ __device__ __forceinline__ void col_pair_body(const CUtensorMap *lmap, const CUt
                 wk[v * PC::HALF_R + i] = __ldg(tw_last + k);
             }
         }
-        cluster_arrive_release();
         cluster_wait_acquire();
+        if (lost_flag[0] | lost_flag[1]) {
+            lost = true;
+            break;
+        }
+        // the partner's tile region is free: one bulk copy of the send
+        // buffer into it, completing on the partner's receive mbarrier
+        if (tid == 0)
+            bulk_copy_to_peer(peer_recv, sendb, PC::XBYTES, peer_bar);
+        lost_recv = mbar_wait_bounded(&bar_recv, (uint32_t)(w_recv & 1)) ? 0 : 1;
+        if (!lost_recv)
+            w_recv++;
+        // cluster barrier X2, arrive: the partner's send buffer has been read
+        cluster_arrive_release();
 
-        // the last stage on this CTA's half, then rows k and k + 2^L via two
-        // TMA stores from the staging buffer (the receive buffer, once read)
+        // the last stage on this CTA's half
         float2 o[2][PC::RECV];
 #pragma unroll
         for (int v = 0; v < Gl::V; v++) {
@@ -186,7 +228,7 @@ __device__ __forceinline__ void col_pair_body(const CUtensorMap *lmap, const CUt
                 const int j = v * PC::HALF_R + i;
                 const float2 lo_half = a[v * Gl::R + i], hi_half = a[v * Gl::R + PC::HALF_R + i];
                 const float2 mine = b == 0 ? lo_half : hi_half;
-                const float2 theirs = recv[j * C::T + tid];
+                const float2 theirs = recvb[j * C::T + tid];
                 float2 x0 = b == 0 ? mine : theirs;
                 float2 x1 = b == 0 ? theirs : mine;
                 butterfly_w(x0, x1, wk[j]);
@@ -194,7 +236,17 @@ __device__ __forceinline__ void col_pair_body(const CUtensorMap *lmap, const CUt
                 o[1][j] = make_float2(x1.x * scale, x1.y * scale);
             }
         }
+        fence_proxy_async_smem();
         __syncthreads();   // the receive buffer has been read
+        if (tid == 0 && next < ntiles)
+            split_issue_late<C>(sm, lmap, next * C::W, &bar_late);
+        if (next < ntiles)
+            n_late++;
+        // X2, wait: this CTA's send buffer is free for staging
+        cluster_wait_acquire();
+
+        // rows k and k + 2^L of this half: two TMA stores from the staging
+        // buffer (the send buffer)
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             if (h == 1) {
@@ -209,20 +261,20 @@ __device__ __forceinline__ void col_pair_body(const CUtensorMap *lmap, const CUt
                 const int lo = (u >> C::KW) & ((1 << Gl::S0) - 1);
 #pragma unroll
                 for (int i = 0; i < PC::HALF_R; i++)
-                    recv[((i << Gl::S0) | lo) * C::W + w] = o[h][v * PC::HALF_R + i];
+                    sendb[((i << Gl::S0) | lo) * C::W + w] = o[h][v * PC::HALF_R + i];
             }
             fence_proxy_async_smem();
             __syncthreads();
             if (tid == 0) {
                 // rows h 2^L + b 2^(L-1) + [0, 2^(L-1)): 256-row blocks from z
                 const int z = (h * PC::NL + b * (PC::NL / 2)) / S::BOX;
-                tma_store_3d(omap, tile * C::W, 0, z, recv);
+                tma_store_3d(omap, tile * C::W, 0, z, sendb);
                 bulk_commit();
             }
         }
     }
 
-    if (lost) {
+    if (__syncthreads_or((lost || lost_recv) ? 1 : 0)) {
         if (tid == 0)
             atomicExch(err, kDevErrTmaTimeout);
         // let transfers still in flight land before the CTA leaves
@@ -230,6 +282,8 @@ __device__ __forceinline__ void col_pair_body(const CUtensorMap *lmap, const CUt
             mbar_wait_bounded(&bar_early, (uint32_t)(w_early & 1));
         if (n_late > w_late)
             mbar_wait_bounded(&bar_late, (uint32_t)(w_late & 1));
+        if (lost_recv)
+            mbar_wait_bounded(&bar_recv, (uint32_t)(w_recv & 1));
     }
     if (tid == 0)
         bulk_wait_all();   // shared memory stays valid until the stores are done
