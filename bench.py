@@ -50,6 +50,8 @@ def parse():
                          "fp16: half2 storage vs complex64 at 8192^2 and 16384^2; "
                          "serve: Poisson stream of mixed requests through fft2d_serve_*")
     ap.add_argument("--images", type=int, default=4, help="resident images per rank")
+    ap.add_argument("--fp16-sides", default="8192,16384",
+                    help="fp16 workload: comma-separated square sides")
     ap.add_argument("--side", type=int, default=SIDE)
     ap.add_argument("--e2e-steps", type=int, default=6)
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
@@ -542,7 +544,8 @@ def run_fp16(args):
     sptr = stream.cuda_stream
     peak, peak_src = measured_hbm_peak()
     results = {}
-    for side in (8192, 16384):
+    sides = [int(v) for v in args.fp16_sides.split(",") if v]
+    for side in sides:
         x = synth.uniform_complex(side, side, seed=side)
         dx = torch.from_numpy(x).cuda()
         y = torch.empty_like(dx)
@@ -604,13 +607,13 @@ def run_fp16(args):
             fft.fft2d_destroy(p)
         del dx, y, q, qo, xin, got16
         torch.cuda.empty_cache()
-    big = results["16384x16384"]
+    big = results[f"{max(sides)}x{max(sides)}"]
     line = {"metric": "2D FFT images/s, FP16 half2 storage vs complex64 (8192^2, 16384^2)",
             "value": big["fp16_images_per_s"], "unit": "images/s", "n_gpus": 1,
             "higher_is_better": True, "dtype": "f32 (half2 storage)",
             "data": "synthetic (seeded re, im ~ U[-1,1))",
-            "config": {"workload": "forward 2D FFT at 8192x8192 and 16384x16384; value = "
-                                   "16384^2 FP16 images/s"},
+            "config": {"workload": "forward 2D FFT at " + ", ".join(f"{v}x{v}" for v in sides)
+                                   + f"; value = {max(sides)}^2 FP16 images/s"},
             "roofline": {"bound": "hbm", "peak": peak, "unit": "GB/s", "peak_source": peak_src,
                          "algorithmic_bytes_per_px": {"fp16": 16, "fp32": 32}},
             "per_size": results}

@@ -71,10 +71,11 @@ def test_256_gray_forward(env):
         assert rel(gpu_fft(env, crop, -1), orc.dft2d(crop)) <= TOL
 
 
-@pytest.mark.parametrize("side", [1024, 4096])
+@pytest.mark.parametrize("side", [1024, 4096, 8192])
 def test_blob_forward_inverse(env, side):
-    """Forward + inverse on the Gaussian-blob image at the paper's size and at
-    4096x4096 (the benchmarked workload), whole outputs compared."""
+    """Forward + inverse on the Gaussian-blob image at the paper's size, at
+    4096x4096 (the benchmarked workload) and at 8192x8192 (columns on the
+    CTA-pair kernel), whole outputs compared."""
     _, _, orc = env
     x = synth.blob_image(side, side, seed=0)
     X = gpu_fft(env, x, -1)
