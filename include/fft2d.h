@@ -107,6 +107,26 @@ FFT2D_API fft2d_status fft2d_sync_status(fft2d_plan_t plan);
 FFT2D_API fft2d_status fft2d_selftest_timeout(fft2d_plan_t plan, void *stream);
 
 /*
+ * Self-test of the failure path of the persistent TMA-fed column kernels
+ * (the tile pipeline that brings each column tile of Section 2's second 1D
+ * transform into shared memory): runs the plan's column pass over `in` into
+ * `out` (device complex64 images of the plan's shape, row pitch = cols),
+ * except that CTA 0 never issues the second TMA load of its first tile.  That
+ * CTA's bounded wait gives up after about one second, the kernel records the
+ * timeout -- for the CTA-pair kernel of 8192-row columns both CTAs of the
+ * pair agree on it at their next cluster barrier and leave together -- lets
+ * the transfers in flight land, releases what it holds and returns; the
+ * next fft2d_sync_status reports FFT2D_ERR_TIMEOUT and `out` is incomplete.
+ * No GPU fault is involved and the context stays usable.
+ * Errors: FFT2D_ERR_ARG for a null plan or pointer, a half2 plan, a plan with
+ * one row, or when the column pass this plan would run (its variant, or the
+ * default for its size, after the alignment checks) is not a TMA-fed kernel.
+ * Asynchronous on `stream`.
+ */
+FFT2D_API fft2d_status fft2d_selftest_withheld_load(fft2d_plan_t plan, const void *in, void *out,
+                                                    void *stream);
+
+/*
  * Autotuner.  Times every kernel variant usable for this plan's shape on the
  * current device -- per pass: CTA tile shape (rows or adjacent columns per
  * CTA), values per thread, TMA-fed persistent or plain launches, and for

@@ -85,7 +85,7 @@ template <class C>
 __device__ __forceinline__ void col_pair_body(const CUtensorMap *lmap, const CUtensorMap *omap,
                                               int ntiles, const float2 *__restrict__ twl,
                                               const float2 *__restrict__ tw_last, float scale,
-                                              int *err)
+                                              int *err, int withhold)
 {
     namespace cg = cooperative_groups;
     using S = TmaSplit<C>;
@@ -124,7 +124,9 @@ __device__ __forceinline__ void col_pair_body(const CUtensorMap *lmap, const CUt
             mbar_expect_tx(&bar_early, S::TW_BYTES);
             bulk_load(stw, twl, S::TW_BYTES, &bar_early);
             split_issue_early<C>(sm, lmap, tile * C::W, &bar_early);
-            split_issue_late<C>(sm, lmap, tile * C::W, &bar_late);
+            // (self-test: CTA 0 withholds its first late boxes)
+            if (!(withhold && blockIdx.x == 0))
+                split_issue_late<C>(sm, lmap, tile * C::W, &bar_late);
         }
         n_early = n_late = 1;
     }
@@ -294,12 +296,14 @@ __global__ void __launch_bounds__(C::T, 1) col_pair_kernel(const __grid_constant
                                                            const __grid_constant__ CUtensorMap map1,
                                                            const __grid_constant__ CUtensorMap omap,
                                                            const float2 *__restrict__ tw,
-                                                           int cols, float scale, int *err)
+                                                           int cols, float scale, int *err,
+                                                           int withhold)
 {
     const bool odd = (cooperative_groups::this_cluster().block_rank() & 1) != 0;
     // the local stages use entries [0, 2^L) of the table, the last stage
     // entries 2^L - 1 + k (stage L+1 starts at offset 2^L - 1)
-    col_pair_body<C>(odd ? &map1 : &map0, &omap, cols / C::W, tw, tw + (C::N - 1), scale, err);
+    col_pair_body<C>(odd ? &map1 : &map0, &omap, cols / C::W, tw, tw + (C::N - 1), scale, err,
+                     withhold);
 }
 
 }  // namespace fft2d

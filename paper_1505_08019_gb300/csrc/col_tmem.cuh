@@ -114,9 +114,11 @@ __device__ __forceinline__ void tmem_issue_half(float2 *P, const CUtensorMap *ma
 // Persistent body: CTA b takes tiles b, b + grid, ...  Shared memory: tile
 // region T (E values), landing region P (E/2), rotation factors.  omap's box
 // is the whole tile (W x 256 x N/256), stored from T in natural row order.
+// withhold (self-test): CTA 0 does not issue its first tile's late half.
 template <class C, class Src>
 __device__ __forceinline__ void col_tmem_body(const Src &src, int ntiles,
-                                              const float2 *__restrict__ tw, int *err)
+                                              const float2 *__restrict__ tw, int *err,
+                                              int withhold)
 {
     using S = TmaSplit<C>;
     using TC = TmemCol<C>;
@@ -167,7 +169,7 @@ __device__ __forceinline__ void col_tmem_body(const Src &src, int ntiles,
         tmem_drain_half<C, 0>(P, taddr);
         fence_proxy_async_smem();
         __syncthreads();
-        if (tid == 0)
+        if (tid == 0 && !(withhold && blockIdx.x == 0))
             tmem_issue_half<C>(P, src.tmap(tile), src.col(tile), 1, &bar_late);
         lost = __syncthreads_or(mbar_wait_bounded(&bar_late, 0) ? 0 : 1);
         if (lost) {
@@ -296,10 +298,10 @@ __global__ void __launch_bounds__(C::T, 1) col_tmem_kernel(const __grid_constant
                                                            float2 *out,
                                                            const float2 *__restrict__ tw,
                                                            int cols, long long ld, float scale,
-                                                           int *err)
+                                                           int *err, int withhold)
 {
     const TilesOneImage src{&map, &omap, out, ld, scale, C::W};
-    col_tmem_body<C>(src, cols / C::W, tw, err);
+    col_tmem_body<C>(src, cols / C::W, tw, err, withhold);
 }
 
 }  // namespace fft2d

@@ -131,9 +131,10 @@ fft2d_status check_device(const fft2d_plan_s *p)
 
 // One pass over the image.  nst < 0: all stages of that axis.
 fft2d_status run_pass(const fft2d_plan_s *p, int pass, const void *in, void *out, int nst,
-                      bool allow_scale, cudaStream_t st)
+                      bool allow_scale, cudaStream_t st, int withhold = 0)
 {
     fft2d::PassArgs a;
+    a.withhold = withhold;
     a.in = static_cast<const float2 *>(in);
     a.out = static_cast<float2 *>(out);
     a.rows = p->rows;
@@ -167,6 +168,11 @@ fft2d_status run_pass(const fft2d_plan_s *p, int pass, const void *in, void *out
         a.tw = p->tw_cols;
         if (p->dir == FFT2D_INVERSE && allow_scale)
             a.scale = (float)(1.0 / ((double)p->rows * (double)p->cols));
+        if (withhold && !fft2d::col_pass_is_tma_fed(L, a)) {
+            std::snprintf(g_last_error, sizeof g_last_error,
+                          "the column pass of this plan does not run on a TMA-fed kernel");
+            return FFT2D_ERR_ARG;
+        }
         e = fft2d::launch_col_pass(L, a, st);
     }
     if (e != cudaSuccess)
@@ -884,6 +890,17 @@ fft2d_status fft2d_exec(fft2d_plan_t p, const void *in, void *out, void *stream)
     if (s != FFT2D_OK)
         return s;
     return exec_impl(p, in, out, -1, -1, static_cast<cudaStream_t>(stream));
+}
+
+fft2d_status fft2d_selftest_withheld_load(fft2d_plan_t p, const void *in, void *out,
+                                          void *stream)
+{
+    if (!p || !in || !out || p->dtype != FFT2D_C64 || p->Lr == 0)
+        return FFT2D_ERR_ARG;
+    fft2d_status s = check_device(p);
+    if (s != FFT2D_OK)
+        return s;
+    return run_pass(p, FFT2D_PASS_COLS, in, out, -1, true, static_cast<cudaStream_t>(stream), 1);
 }
 
 fft2d_status fft2d_exec_pass(fft2d_plan_t p, int pass, const void *in, void *out, void *stream)

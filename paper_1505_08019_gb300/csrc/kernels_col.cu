@@ -160,7 +160,8 @@ cudaError_t col_launch_tma(const PassArgs &a, cudaStream_t s)
     int grid = sm_count() * occ[d];
     if (grid > ntiles)
         grid = ntiles;
-    k<<<grid, C::T, SMEM, s>>>(map, omap, a.out, a.tw, a.cols, a.ld, a.scale, a.err);
+    k<<<grid, C::T, SMEM, s>>>(map, omap, a.out, a.tw, a.cols, a.ld, a.scale, a.err,
+                               a.withhold);
     return cudaGetLastError();
 }
 
@@ -194,7 +195,8 @@ cudaError_t col_launch_tmem(const PassArgs &a, cudaStream_t s)
     int grid = sm_count() * occ[d];
     if (grid > ntiles)
         grid = ntiles;
-    k<<<grid, C::T, SMEM, s>>>(map, omap, a.out, a.tw, a.cols, a.ld, a.scale, a.err);
+    k<<<grid, C::T, SMEM, s>>>(map, omap, a.out, a.tw, a.cols, a.ld, a.scale, a.err,
+                               a.withhold);
     return cudaGetLastError();
 }
 
@@ -248,7 +250,7 @@ cudaError_t col_launch_pair(const PassArgs &a, cudaStream_t s)
     const int ntiles = a.cols / C::W;
     const int np = pairs[d] < ntiles ? pairs[d] : ntiles;
     cfg.gridDim = dim3((unsigned)(2 * np));
-    return cudaLaunchKernelEx(&cfg, k, m0, m1, om, a.tw, a.cols, a.scale, a.err);
+    return cudaLaunchKernelEx(&cfg, k, m0, m1, om, a.tw, a.cols, a.scale, a.err, a.withhold);
 }
 
 template <class CC>
@@ -306,13 +308,13 @@ struct ColVariants {
             // 16 values per thread
             constexpr bool TS32 = tma_store_ok<Tma32>();
             t.v[t.n++] = {Tma32::EPT == 32 ? "tma32" : "tma", Tma32::W, Tma32::EPT,
-                          col_tma_usable<Tma32>, col_launch_tma<Tma32, TS32>};
+                          col_tma_usable<Tma32>, col_launch_tma<Tma32, TS32>, true};
             if constexpr (TS32)
                 t.v[t.n++] = {Tma32::EPT == 32 ? "tma32st" : "tmast", Tma32::W, Tma32::EPT,
-                              col_tma_usable<Tma32>, col_launch_tma<Tma32, false>};
+                              col_tma_usable<Tma32>, col_launch_tma<Tma32, false>, true};
             if constexpr (Tma32::EPT == 32)
                 t.v[t.n++] = {"tma16", Tma16::W, 16, col_tma_usable<Tma16>,
-                              col_launch_tma<Tma16, tma_store_ok<Tma16>()>};
+                              col_launch_tma<Tma16, tma_store_ok<Tma16>()>, true};
         }
         if constexpr (HASNARROW)
             t.v[t.n++] = {"narrow", Narrow::W, 16, whole_stages, col_launch_any<Narrow>};
@@ -323,12 +325,13 @@ struct ColVariants {
                           col_launch_cluster<Clu8>};
         // the TMA engine with the next tile parked in TMEM (32 values a thread)
         if constexpr (HASTMEM)
-            t.v[t.n++] = {"tmem", Tma32::W, 32, col_tma_usable<Tma32>, col_launch_tmem<Tma32>};
+            t.v[t.n++] = {"tmem", Tma32::W, 32, col_tma_usable<Tma32>, col_launch_tmem<Tma32>,
+                          true};
         // 8192 rows: 4-column tiles over a CTA pair, the 4096-row engine on
         // each half and the last stage through remote stores
         if constexpr (L == 13)
             t.v[t.n++] = {"pair", PairLocal::W, 32, col_pair_usable<PairLocal>,
-                          col_launch_pair<PairLocal>};
+                          col_launch_pair<PairLocal>, true};
         return t;
     }
     static const Variant *table(int *n)
@@ -395,16 +398,33 @@ int col_default_variant(int L)
     }
 }
 
-cudaError_t launch_col_pass(int L, const PassArgs &a, cudaStream_t s)
+namespace {
+
+// The variant launch_col_pass runs for these arguments (nullptr: none).
+const Variant *select_col_variant(int L, const PassArgs &a)
 {
     int n = 0;
     const Variant *v = col_variants(L, &n);
     if (!v || n == 0)
-        return cudaErrorInvalidValue;
+        return nullptr;
     int i = a.variant >= 0 && a.variant < n ? a.variant : col_default_variant(L);
     if (!v[i].usable(a))
         i = 0;   // the plain kernel serves every case
-    return v[i].launch(a, s);
+    return &v[i];
+}
+
+}  // namespace
+
+cudaError_t launch_col_pass(int L, const PassArgs &a, cudaStream_t s)
+{
+    const Variant *v = select_col_variant(L, a);
+    return v ? v->launch(a, s) : cudaErrorInvalidValue;
+}
+
+bool col_pass_is_tma_fed(int L, const PassArgs &a)
+{
+    const Variant *v = select_col_variant(L, a);
+    return v && v->tma_fed;
 }
 
 }  // namespace fft2d

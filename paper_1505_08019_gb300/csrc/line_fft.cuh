@@ -886,9 +886,12 @@ struct TilesOneImage {
 // factors.  With TS (TMA stores) the upper half of the tile region is also
 // the staging buffer of the finished tile, drained while the next tile's
 // group 0 runs; otherwise each thread stores its results directly.
+// withhold (self-test): CTA 0 does not issue its first tile's late boxes,
+// so its first wait runs out and the kernel takes its timeout path.
 template <class C, bool TS, class Src>
 __device__ __forceinline__ void col_tma2_body(const Src &src, int ntiles,
-                                              const float2 *__restrict__ tw, int *err)
+                                              const float2 *__restrict__ tw, int *err,
+                                              int withhold = 0)
 {
     static_assert(!TS || TmaSplit<C>::LATE_BYTES <= (uint32_t)C::E * 4u,
                   "late boxes must leave the staging half free");
@@ -909,7 +912,8 @@ __device__ __forceinline__ void col_tma2_body(const Src &src, int ntiles,
         mbar_expect_tx(&bar_early, TmaSplit<C>::TW_BYTES);
         bulk_load(stw, tw, TmaSplit<C>::TW_BYTES, &bar_early);
         split_issue_early<C>(sm, src.tmap(tile), src.col(tile), &bar_early);
-        split_issue_late<C>(sm, src.tmap(tile), src.col(tile), &bar_late);
+        if (!(withhold && blockIdx.x == 0))
+            split_issue_late<C>(sm, src.tmap(tile), src.col(tile), &bar_late);
     }
     uint32_t parity = 0;
     float2 a[C::EPT];
@@ -973,10 +977,10 @@ __global__ void __launch_bounds__(C::T, 1) col_tma2_kernel(const __grid_constant
                                                            float2 *out,
                                                            const float2 *__restrict__ tw,
                                                            int cols, long long ld, float scale,
-                                                           int *err)
+                                                           int *err, int withhold)
 {
     const TilesOneImage src{&map, &omap, out, ld, scale, C::W};
-    col_tma2_body<C, TS>(src, cols / C::W, tw, err);
+    col_tma2_body<C, TS>(src, cols / C::W, tw, err, withhold);
 }
 
 // The same kernel over the column tiles of many images of one column length

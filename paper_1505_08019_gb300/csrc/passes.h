@@ -20,6 +20,7 @@ struct PassArgs {
     bool partial;        // nst < log2(axis length)
     int *err;            // device status word (bounded-wait timeouts)
     int variant = -1;    // kernel variant index (-1: the default for this size)
+    int withhold = 0;    // self-test: CTA 0 does not issue its first tile's second TMA load
 };
 
 // One way to run a pass for one line length (see kernels_row.cu and
@@ -31,6 +32,7 @@ struct Variant {
     int ept;       // values per thread
     bool (*usable)(const PassArgs &);
     cudaError_t (*launch)(const PassArgs &, cudaStream_t);
+    bool tma_fed = false;   // persistent TMA-fed kernel: honours PassArgs::withhold
 };
 const Variant *row_variants(int L, int *n);
 const Variant *col_variants(int L, int *n);
@@ -140,5 +142,8 @@ int device_sm_count();
 int device_current();
 cudaError_t launch_selftest_timeout(int *err, cudaStream_t s);
 cudaError_t launch_col_pass(int L, const PassArgs &a, cudaStream_t s);
+// Whether the column-pass kernel that launch_col_pass would run for these
+// arguments is a TMA-fed one (the only kernels with the withhold self-test).
+bool col_pass_is_tma_fed(int L, const PassArgs &a);
 
 }  // namespace fft2d

@@ -51,6 +51,7 @@ _sigs = {
     "fft2d_destroy": ([_P], _I),
     "fft2d_sync_status": ([_P], _I),
     "fft2d_selftest_timeout": ([_P, _P], _I),
+    "fft2d_selftest_withheld_load": ([_P, _P, _P, _P], _I),
     "fft2d_plan_info": ([_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                          ctypes.POINTER(_I)], _I),
     "fft2d_exec": ([_P, _P, _P, _P], _I),
@@ -183,6 +184,11 @@ def fft2d_sync_status(plan: int) -> None:
 
 def fft2d_selftest_timeout(plan: int, stream=None) -> None:
     _check(lib.fft2d_selftest_timeout(plan, _stream(stream)), "fft2d_selftest_timeout")
+
+
+def fft2d_selftest_withheld_load(plan: int, inp, out, stream=None) -> None:
+    _check(lib.fft2d_selftest_withheld_load(plan, _dptr(inp), _dptr(out), _stream(stream)),
+           "fft2d_selftest_withheld_load")
 
 
 def fft2d_plan_info(plan: int) -> tuple[int, int, int, int]:

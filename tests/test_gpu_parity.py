@@ -269,6 +269,49 @@ def test_unaligned_buffers_take_the_plain_path(env):
         fft.fft2d_destroy(plan)
 
 
+@pytest.mark.parametrize("rows,variant", [(4096, "tma32"), (4096, "tmem"), (8192, "pair")])
+def test_withheld_tma_load_times_out_cleanly(env, rows, variant):
+    """Failure path of the persistent TMA-fed column kernels: CTA 0 never
+    issues one TMA load of its first tile, its bounded wait gives up, the
+    kernel (for the CTA pair: both CTAs, agreeing at their cluster barrier)
+    leaves cleanly, the host reads FFT2D_ERR_TIMEOUT, and the same plan then
+    transforms correctly."""
+    torch, fft, orc = env
+    cols = 256
+    plan = fft.fft2d_plan(rows, cols, fft.FFT2D_C64, fft.FFT2D_FORWARD)
+    try:
+        L = rows.bit_length() - 1
+        names = [fft.fft2d_variant_name(fft.FFT2D_PASS_COLS, L, v)
+                 for v in range(fft.fft2d_variant_count(fft.FFT2D_PASS_COLS, L))]
+        fft.fft2d_plan_set_variant(plan, fft.FFT2D_PASS_COLS, names.index(variant))
+        x = synth.uniform_complex(rows, cols, seed=rows)
+        dx = torch.from_numpy(x).cuda()
+        out = torch.empty_like(dx)
+        fft.fft2d_sync_status(plan)
+        fft.fft2d_selftest_withheld_load(plan, dx, out)
+        with pytest.raises(fft.FFT2DError) as ei:
+            fft.fft2d_sync_status(plan)
+        assert ei.value.status == fft.FFT2D_ERR_TIMEOUT
+        fft.fft2d_sync_status(plan)                      # cleared
+        fft.fft2d_exec(plan, dx, out)
+        fft.fft2d_sync_status(plan)
+        assert rel(out.cpu().numpy(), orc.fft2d(x, threads=16)) <= TOL
+    finally:
+        fft.fft2d_destroy(plan)
+
+
+def test_withheld_load_needs_a_tma_kernel(env):
+    torch, fft, _ = env
+    plan = fft.fft2d_plan(64, 64, fft.FFT2D_C64, fft.FFT2D_FORWARD)   # plain column kernel
+    try:
+        dx = torch.zeros((64, 64), dtype=torch.complex64, device="cuda")
+        with pytest.raises(fft.FFT2DError) as ei:
+            fft.fft2d_selftest_withheld_load(plan, dx, dx)
+        assert ei.value.status == fft.FFT2D_ERR_ARG
+    finally:
+        fft.fft2d_destroy(plan)
+
+
 def test_bounded_wait_reports_timeout_and_context_survives(env):
     """Failure path of the TMA pipeline: a wait on an mbarrier that nothing
     completes gives up (about 20 ms), the host reads FFT2D_ERR_TIMEOUT, the
