@@ -210,14 +210,36 @@ FFT2D_API fft2d_status fft2d_exec_host(fft2d_plan_t plan, const void *in_host, v
  * copy streams and the caller's stream (three device image buffers per
  * device, grown to the largest image and kept for the life of the process).
  * Image i is transformed with plans[i] from in_host[i] to out_host[i];
- * in_host[i] == out_host[i] is allowed, different images must not overlap.
- * The copies start after the work already queued on `stream`.  complex64
- * plans of one device only.  Synchronous: every copy has finished on return,
- * after a failure too.  Pinned host memory gives the full copy bandwidth.
+ * in_host[i] == out_host[i] is allowed.  An image may read the output of an
+ * earlier image of the same call (in_host[i] == out_host[j], j < i, the same
+ * pointer): its upload waits for that download, so a forward transform and
+ * its inverse can travel in one call.  Otherwise the host buffers of
+ * different images must not overlap.  The copies start after the work
+ * already queued on `stream`.  complex64 plans of one device only.
+ * Synchronous: every copy has finished on return, after a failure too.
+ * Pinned host memory gives the full copy bandwidth (the NVLink-C2C host link
+ * of a GB300 moved about 210 GB/s up, 190 GB/s down, 340 GB/s both at once).
  */
 FFT2D_API fft2d_status fft2d_exec_host_many(int n, const fft2d_plan_t *plans,
                                             const void *const *in_host, void *const *out_host,
                                             void *stream);
+
+/*
+ * fft2d_exec_host_many without the final wait: returns once everything is
+ * queued, with `stream` ordered after every copy and transform of the call,
+ * so calls issued back to back keep the host link busy across call
+ * boundaries and one synchronisation of `stream` (or an event recorded on
+ * it) covers them all.  The host buffers must stay valid, and must be
+ * neither written (inputs) nor read (outputs) by the host, until then.
+ * Dependencies are tracked within a call only: a later call may read a host
+ * buffer an earlier unfinished call writes only if that buffer is also
+ * written by the later call before it reads it (as when every call carries
+ * both a forward transform and its inverse).  On an error the call waits
+ * for what it queued and returns the status.
+ */
+FFT2D_API fft2d_status fft2d_exec_host_many_async(int n, const fft2d_plan_t *plans,
+                                                  const void *const *in_host,
+                                                  void *const *out_host, void *stream);
 
 /*
  * n independent transforms, possibly of different plans (sizes, directions),

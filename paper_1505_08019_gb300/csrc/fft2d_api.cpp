@@ -12,6 +12,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 #include <tuple>
 #include <vector>
 
@@ -298,7 +299,10 @@ struct HostPipe {
     size_t slot_bytes = 0;
     cudaStream_t up = nullptr, down = nullptr;
     cudaEvent_t in_ready[kHostSlots] = {}, done[kHostSlots] = {}, freed[kHostSlots] = {};
-    cudaEvent_t start = nullptr;
+    cudaEvent_t start = nullptr, join_up = nullptr, join_down = nullptr;
+    // download of the i-th image of a call: an upload of a later image of
+    // the same call that reads the same host buffer waits for it
+    std::vector<cudaEvent_t> image_out;
     bool ready = false;
 };
 
@@ -313,6 +317,10 @@ cudaError_t host_pipe_prepare(HostPipe &hp, size_t bytes)
             e = cudaStreamCreateWithFlags(&hp.down, cudaStreamNonBlocking);
         if (e == cudaSuccess)
             e = cudaEventCreateWithFlags(&hp.start, cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&hp.join_up, cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&hp.join_down, cudaEventDisableTiming);
         for (int k = 0; k < kHostSlots && e == cudaSuccess; k++) {
             e = cudaEventCreateWithFlags(&hp.in_ready[k], cudaEventDisableTiming);
             if (e == cudaSuccess)
@@ -959,33 +967,30 @@ fft2d_status fft2d_exec_host(fft2d_plan_t p, const void *in_host, void *out_host
     return FFT2D_OK;
 }
 
-fft2d_status fft2d_exec_host_many(int n, const fft2d_plan_t *plans, const void *const *in_host,
-                                  void *const *out_host, void *stream)
+namespace {
+
+// Queue the pipelined host transforms of fft2d_exec_host_many(_async) on the
+// device's host pipeline; the caller holds hp.mu.  On return (success or
+// not) `st` is ordered after every copy queued here.
+fft2d_status host_many_enqueue(HostPipe &hp, int n, const fft2d_plan_t *plans,
+                               const void *const *in_host, void *const *out_host, cudaStream_t st)
 {
-    if (n < 0 || (n > 0 && (!plans || !in_host || !out_host)))
-        return FFT2D_ERR_ARG;
     size_t bytes = 0;
     for (int i = 0; i < n; i++) {
-        if (!plans[i] || !in_host[i] || !out_host[i] || plans[i]->dtype != FFT2D_C64)
-            return FFT2D_ERR_ARG;
-        fft2d_status s = check_device(plans[i]);
-        if (s != FFT2D_OK)
-            return s;
         const size_t b = (size_t)plans[i]->rows * plans[i]->cols * sizeof(float2);
         bytes = b > bytes ? b : bytes;
     }
-    if (n == 0)
-        return FFT2D_OK;
-    const int dev = plans[0]->device;
-    if (dev < 0 || dev >= kHostMaxDev)
-        return FFT2D_ERR_ARG;
-    HostPipe &hp = g_host_pipe[dev];
-    std::lock_guard<std::mutex> lock(hp.mu);
     cudaError_t e = host_pipe_prepare(hp, bytes);
     if (e != cudaSuccess)
         return e == cudaErrorMemoryAllocation ? (cuda_fail(e, "cudaMalloc host pipeline"), FFT2D_ERR_OOM)
                                               : cuda_fail(e, "host pipeline setup");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    while ((int)hp.image_out.size() < n) {
+        cudaEvent_t ev = nullptr;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "host pipeline events");
+        hp.image_out.push_back(ev);
+    }
     fft2d_status result = FFT2D_OK;
     // the copies start after the work already queued on the caller's stream
     e = cudaEventRecord(hp.start, st);
@@ -996,14 +1001,20 @@ fft2d_status fft2d_exec_host_many(int n, const fft2d_plan_t *plans, const void *
     if (e != cudaSuccess)
         result = cuda_fail(e, "host pipeline ordering");
     // image i uses slot i % kHostSlots: upload on `up`, transform on the
-    // caller's stream, download on `down`; the upload into a slot waits for
-    // the download of the image that used it before
+    // caller's stream, download on `down`.  The upload into a slot waits for
+    // the last download from it (of this call or an earlier one), and for the
+    // download of an earlier image of this call whose output it reads.
     for (int i = 0; i < n && result == FFT2D_OK; i++) {
         const int k = i % kHostSlots;
         const fft2d_plan_s *p = plans[i];
         const size_t b = (size_t)p->rows * p->cols * sizeof(float2);
-        if (i >= kHostSlots)
-            e = cudaStreamWaitEvent(hp.up, hp.freed[k], 0);
+        e = cudaStreamWaitEvent(hp.up, hp.freed[k], 0);
+        for (int j = i - 1; j >= 0 && e == cudaSuccess; j--) {
+            if (out_host[j] == in_host[i]) {
+                e = cudaStreamWaitEvent(hp.up, hp.image_out[j], 0);
+                break;
+            }
+        }
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(hp.slot[k], in_host[i], b, cudaMemcpyHostToDevice, hp.up);
         if (e == cudaSuccess)
@@ -1024,17 +1035,89 @@ fft2d_status fft2d_exec_host_many(int n, const fft2d_plan_t *plans, const void *
             e = cudaMemcpyAsync(out_host[i], hp.slot[k], b, cudaMemcpyDeviceToHost, hp.down);
         if (e == cudaSuccess)
             e = cudaEventRecord(hp.freed[k], hp.down);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(hp.image_out[i], hp.down);
         if (e != cudaSuccess)
             result = cuda_fail(e, "host pipeline download");
     }
+    // join both copy streams into the caller's stream
+    e = cudaEventRecord(hp.join_up, hp.up);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(hp.join_down, hp.down);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(st, hp.join_up, 0);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(st, hp.join_down, 0);
+    if (e != cudaSuccess && result == FFT2D_OK)
+        result = cuda_fail(e, "host pipeline join");
+    return result;
+}
+
+fft2d_status host_many_check(int n, const fft2d_plan_t *plans, const void *const *in_host,
+                             void *const *out_host, HostPipe **hp)
+{
+    if (n < 0 || (n > 0 && (!plans || !in_host || !out_host)))
+        return FFT2D_ERR_ARG;
+    for (int i = 0; i < n; i++) {
+        if (!plans[i] || !in_host[i] || !out_host[i] || plans[i]->dtype != FFT2D_C64)
+            return FFT2D_ERR_ARG;
+        fft2d_status s = check_device(plans[i]);
+        if (s != FFT2D_OK)
+            return s;
+    }
+    if (n == 0)
+        return FFT2D_OK;
+    const int dev = plans[0]->device;
+    if (dev < 0 || dev >= kHostMaxDev)
+        return FFT2D_ERR_ARG;
+    *hp = &g_host_pipe[dev];
+    return FFT2D_OK;
+}
+
+// Wait for everything a failed enqueue may have left in flight.
+void host_many_drain(HostPipe &hp, cudaStream_t st)
+{
+    cudaStreamSynchronize(hp.up);
+    cudaStreamSynchronize(st);
+    cudaStreamSynchronize(hp.down);
+}
+
+}  // namespace
+
+fft2d_status fft2d_exec_host_many(int n, const fft2d_plan_t *plans, const void *const *in_host,
+                                  void *const *out_host, void *stream)
+{
+    HostPipe *hp = nullptr;
+    fft2d_status s = host_many_check(n, plans, in_host, out_host, &hp);
+    if (s != FFT2D_OK || n == 0)
+        return s;
+    std::lock_guard<std::mutex> lock(hp->mu);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    fft2d_status result = host_many_enqueue(*hp, n, plans, in_host, out_host, st);
     // synchronous: every queued copy and transform has finished on return,
     // also after a failure (the slots may then be reused)
-    cudaError_t e1 = cudaStreamSynchronize(hp.up);
+    cudaError_t e1 = cudaStreamSynchronize(hp->up);
     cudaError_t e2 = cudaStreamSynchronize(st);
-    cudaError_t e3 = cudaStreamSynchronize(hp.down);
+    cudaError_t e3 = cudaStreamSynchronize(hp->down);
     if (result == FFT2D_OK && (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess))
         result = cuda_fail(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3),
                            "cudaStreamSynchronize");
+    return result;
+}
+
+fft2d_status fft2d_exec_host_many_async(int n, const fft2d_plan_t *plans,
+                                        const void *const *in_host, void *const *out_host,
+                                        void *stream)
+{
+    HostPipe *hp = nullptr;
+    fft2d_status s = host_many_check(n, plans, in_host, out_host, &hp);
+    if (s != FFT2D_OK || n == 0)
+        return s;
+    std::lock_guard<std::mutex> lock(hp->mu);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    fft2d_status result = host_many_enqueue(*hp, n, plans, in_host, out_host, st);
+    if (result != FFT2D_OK)
+        host_many_drain(*hp, st);
     return result;
 }
 

@@ -69,6 +69,8 @@ _sigs = {
     "fft2d_batch_set_variant": ([_I, _I, _I], _I),
     "fft2d_exec_host_many": ([_I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
                              _I),
+    "fft2d_exec_host_many_async": (
+        [_I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _P], _I),
     "fft2d_autotune_batched": ([_I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
                                _I),
     "fft2d_exec_h16": ([_P, _P, _P, _I, _P, _P, _P], _I),
@@ -278,6 +280,18 @@ def fft2d_exec_host_many(plans, inps, outs, stream=None) -> None:
     _check(lib.fft2d_exec_host_many(n, arr(*plans), arr(*[_hptr(x) for x in inps]),
                                     arr(*[_hptr(x) for x in outs]), _stream(stream)),
            "fft2d_exec_host_many")
+
+
+def fft2d_exec_host_many_async(plans, inps, outs, stream=None) -> None:
+    """fft2d_exec_host_many without the final wait: the stream is ordered
+    after every copy; keep the host buffers alive until it is synchronised."""
+    n = len(plans)
+    if len(inps) != n or len(outs) != n:
+        raise ValueError("plans, inputs and outputs must have the same length")
+    arr = ctypes.c_void_p * max(n, 1)
+    _check(lib.fft2d_exec_host_many_async(n, arr(*plans), arr(*[_hptr(x) for x in inps]),
+                                          arr(*[_hptr(x) for x in outs]), _stream(stream)),
+           "fft2d_exec_host_many_async")
 
 
 def fft2d_autotune_batched(plans, inps, outs, stream=None) -> None:

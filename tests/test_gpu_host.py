@@ -74,3 +74,66 @@ def test_many_host_pageable_and_repeat(env):
             assert rel(o, orc.fft2d(im, threads=8)) <= TOL
     finally:
         fft.fft2d_destroy(plan)
+
+
+def test_forward_and_inverse_in_one_call(env):
+    """An image may read an earlier image's output in the same call: the
+    inverse of each forward transform travels in the same call (its upload
+    waits for the forward's download) and gives the same bits as two
+    separate calls."""
+    torch, fft, orc = env
+    shapes = [(1024, 1024), (512, 2048), (2048, 512), (256, 256)]
+    imgs = synth.batch_images(shapes, seed=21)
+    fwd = [fft.fft2d_plan(r, c, fft.FFT2D_C64, fft.FFT2D_FORWARD) for r, c in shapes]
+    inv = [fft.fft2d_plan(r, c, fft.FFT2D_C64, fft.FFT2D_INVERSE) for r, c in shapes]
+    try:
+        hin = [torch.from_numpy(im).pin_memory() for im in imgs]
+        mid = [torch.empty_like(h).pin_memory() for h in hin]
+        fft.fft2d_exec_host_many(fwd, hin, mid)
+        want_fwd = [m.numpy().copy() for m in mid]
+        back = [torch.empty_like(h).pin_memory() for h in hin]
+        fft.fft2d_exec_host_many(inv, mid, back)
+        want_rt = [b.numpy().copy() for b in back]
+
+        mid2 = [torch.empty_like(h).pin_memory() for h in hin]
+        back2 = [torch.empty_like(h).pin_memory() for h in hin]
+        fft.fft2d_exec_host_many(fwd + inv, hin + mid2, mid2 + back2)
+        for i in range(len(shapes)):
+            assert np.array_equal(mid2[i].numpy(), want_fwd[i]), f"forward {shapes[i]}"
+            assert np.array_equal(back2[i].numpy(), want_rt[i]), f"round trip {shapes[i]}"
+            assert rel(back2[i].numpy(), imgs[i]) <= TOL
+        # in place on the host: forward into the buffer, inverse back in it
+        work = [torch.empty_like(h).pin_memory() for h in hin]
+        fft.fft2d_exec_host_many(fwd + inv, hin + work, work + work)
+        for i in range(len(shapes)):
+            assert np.array_equal(work[i].numpy(), want_rt[i]), f"in place {shapes[i]}"
+    finally:
+        for p in fwd + inv:
+            fft.fft2d_destroy(p)
+
+
+def test_async_calls_back_to_back(env):
+    """Several asynchronous calls queued back to back, one synchronisation:
+    the same bits as synchronous calls, the host buffers reused across calls
+    the way a repeated forward + inverse step reuses them."""
+    torch, fft, _ = env
+    shapes = [(2048, 2048)] * 3
+    imgs = synth.batch_images(shapes, seed=5)
+    pf = fft.fft2d_plan(2048, 2048, fft.FFT2D_C64, fft.FFT2D_FORWARD)
+    pi = fft.fft2d_plan(2048, 2048, fft.FFT2D_C64, fft.FFT2D_INVERSE)
+    try:
+        hin = [torch.from_numpy(im).pin_memory() for im in imgs]
+        ref = [torch.empty_like(h).pin_memory() for h in hin]
+        fft.fft2d_exec_host_many([pf] * 3 + [pi] * 3, hin + ref, ref + ref)
+        want = [r.numpy().copy() for r in ref]
+        out = [torch.empty_like(h).pin_memory() for h in hin]
+        stream = torch.cuda.current_stream()
+        for _ in range(4):
+            fft.fft2d_exec_host_many_async([pf] * 3 + [pi] * 3, hin + out, out + out,
+                                           stream.cuda_stream)
+        stream.synchronize()
+        for i in range(3):
+            assert np.array_equal(out[i].numpy(), want[i])
+    finally:
+        fft.fft2d_destroy(pf)
+        fft.fft2d_destroy(pi)
