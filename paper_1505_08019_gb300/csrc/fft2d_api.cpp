@@ -369,13 +369,89 @@ int batch_variant(int device, int pass, int L)
     return fft2d::batch_default_variant(pass == FFT2D_PASS_ROWS, L);
 }
 
+// Internal streams of the grouped executor, one set per (device, caller
+// stream) so that batches issued on different streams still overlap: the
+// groups of one pass are independent, so they run on kBatchLanes streams at
+// once (the tail of one launch overlaps the start of the next); the column
+// pass starts after every row group, and the caller's stream waits for
+// everything.
+constexpr int kBatchLanes = 4;
+struct BatchLanes {
+    std::mutex mu;
+    cudaStream_t s[kBatchLanes] = {};
+    cudaEvent_t fork = nullptr, ev[kBatchLanes] = {};
+    bool ready = false;
+};
+std::mutex g_batch_lanes_mu;
+std::map<std::pair<int, cudaStream_t>, BatchLanes *> g_batch_lanes;   // kept for the process
+
+BatchLanes *batch_lanes(int dev, cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lock(g_batch_lanes_mu);
+    BatchLanes *&bl = g_batch_lanes[std::make_pair(dev, st)];
+    if (!bl)
+        bl = new (std::nothrow) BatchLanes();
+    return bl;
+}
+
+cudaError_t batch_lanes_prepare(BatchLanes &bl)
+{
+    if (bl.ready)
+        return cudaSuccess;
+    cudaError_t e = cudaEventCreateWithFlags(&bl.fork, cudaEventDisableTiming);
+    for (int k = 0; k < kBatchLanes && e == cudaSuccess; k++) {
+        e = cudaStreamCreateWithFlags(&bl.s[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&bl.ev[k], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess)
+        bl.ready = true;
+    return e;
+}
+
+// Every lane waits for `from` (one stream) ...
+cudaError_t lanes_wait_stream(BatchLanes &bl, cudaStream_t from)
+{
+    cudaError_t e = cudaEventRecord(bl.fork, from);
+    for (int k = 0; k < kBatchLanes && e == cudaSuccess; k++)
+        e = cudaStreamWaitEvent(bl.s[k], bl.fork, 0);
+    return e;
+}
+
+// ... and `to` waits for every lane.
+cudaError_t stream_wait_lanes(BatchLanes &bl, cudaStream_t to)
+{
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < kBatchLanes && e == cudaSuccess; k++) {
+        e = cudaEventRecord(bl.ev[k], bl.s[k]);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(to, bl.ev[k], 0);
+    }
+    return e;
+}
+
 // Run the grouped passes of a batch.  With `timing` set, every (pass, L,
-// direction) group is launched once per variant and timed, and the fastest
-// variant per (pass, L) is recorded (the batch autotuner); otherwise each
-// group runs once with its chosen variant.
+// direction) group is launched once per variant and timed on `st`, and the
+// fastest variant per (pass, L) is recorded (the batch autotuner);
+// otherwise each group runs once with its chosen variant, the groups of a
+// pass spread over the device's internal lanes.
 fft2d_status batched_impl(int n, const fft2d_plan_t *plans, const void *const *in,
                           void *const *out, cudaStream_t st, bool timing)
 {
+    BatchLanes *bl = nullptr;
+    std::unique_lock<std::mutex> lanes_lock;
+    if (!timing && n > 0) {
+        bl = batch_lanes(plans[0]->device, st);
+        if (!bl)
+            return FFT2D_ERR_OOM;
+        lanes_lock = std::unique_lock<std::mutex>(bl->mu);
+        cudaError_t e = batch_lanes_prepare(*bl);
+        if (e == cudaSuccess)
+            e = lanes_wait_stream(*bl, st);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "batch lanes");
+    }
+    int group = 0;
     static thread_local fft2d::BatchTable table;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (timing && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
@@ -384,6 +460,16 @@ fft2d_status batched_impl(int n, const fft2d_plan_t *plans, const void *const *i
     fft2d_status result = FFT2D_OK;
     for (int pass = 0; pass < 2 && result == FFT2D_OK; pass++) {
         const bool row = pass == FFT2D_PASS_ROWS;
+        if (bl && !row) {
+            // the column pass starts once every row group has finished
+            cudaError_t e = stream_wait_lanes(*bl, bl->s[0]);
+            if (e == cudaSuccess)
+                e = lanes_wait_stream(*bl, bl->s[0]);
+            if (e != cudaSuccess) {
+                result = cuda_fail(e, "batch lanes");
+                break;
+            }
+        }
         for (int L = 1; L <= 14 && result == FFT2D_OK; L++) {
             for (int dir = -1; dir <= 1 && result == FFT2D_OK; dir += 2) {
                 table.n = 0;
@@ -395,7 +481,8 @@ fft2d_status batched_impl(int n, const fft2d_plan_t *plans, const void *const *i
                         const int nv = row ? fft2d::kBatchRowVariants : fft2d::kBatchColVariants;
                         if (!timing) {
                             const int v = batch_variant(plans[first]->device, pass, L);
-                            cudaError_t e = fft2d::launch_batch_pass(row, L, table, v, err, st);
+                            cudaStream_t ls = bl->s[group++ % kBatchLanes];
+                            cudaError_t e = fft2d::launch_batch_pass(row, L, table, v, err, ls);
                             if (e != cudaSuccess) {
                                 result = cuda_fail(e, "batched pass");
                                 break;
@@ -445,6 +532,11 @@ fft2d_status batched_impl(int n, const fft2d_plan_t *plans, const void *const *i
                 }
             }
         }
+    }
+    if (bl) {
+        cudaError_t e = stream_wait_lanes(*bl, st);
+        if (e != cudaSuccess && result == FFT2D_OK)
+            result = cuda_fail(e, "batch lanes");
     }
     if (timing) {
         if (result == FFT2D_OK && n > 0) {
