@@ -50,6 +50,8 @@ def parse():
                          "fp16: half2 storage vs complex64 at 8192^2 and 16384^2; "
                          "serve: Poisson stream of mixed requests through fft2d_serve_*")
     ap.add_argument("--images", type=int, default=4, help="resident images per rank")
+    ap.add_argument("--streams", type=int, default=0,
+                    help="CUDA streams the resident images are spread over (0: one per image)")
     ap.add_argument("--fp16-sides", default="8192,16384",
                     help="fp16 workload: comma-separated square sides")
     ap.add_argument("--side", type=int, default=SIDE)
@@ -233,15 +235,28 @@ def run_ours(args):
     ROWS, COLS = fft.FFT2D_PASS_ROWS, fft.FFT2D_PASS_COLS
     exec_pass = fft.fft2d_exec_pass
 
+    # the resident images are independent: each runs on its own stream,
+    # forked from and joined back into the timing stream, so one image's
+    # launch tails overlap another's
+    nstreams = min(args.streams if args.streams > 0 else B, B)
+    lanes = [stream] if nstreams == 1 else [torch.cuda.Stream(dev) for _ in range(nstreams)]
+    fork = torch.cuda.Event()
+    joins = [torch.cuda.Event() for _ in lanes]
+
     def step(evs=None):
         # forward then inverse of every resident image; with `evs`, an event
         # brackets every kernel launch (rows fwd, cols fwd, rows inv, cols inv)
-        for x, X in zip(xs, Xs):
+        if evs is None and nstreams > 1:
+            fork.record(stream)
+            for ln in lanes:
+                ln.wait_event(fork)
+        for i, (x, X) in enumerate(zip(xs, Xs)):
             if evs is None:
-                exec_pass(pf, ROWS, x, X, sptr)
-                exec_pass(pf, COLS, X, X, sptr)
-                exec_pass(pi, ROWS, X, X, sptr)
-                exec_pass(pi, COLS, X, X, sptr)
+                lp = lanes[i % nstreams].cuda_stream
+                exec_pass(pf, ROWS, x, X, lp)
+                exec_pass(pf, COLS, X, X, lp)
+                exec_pass(pi, ROWS, X, X, lp)
+                exec_pass(pi, COLS, X, X, lp)
             else:
                 e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
                 e[0].record(stream)
@@ -254,6 +269,10 @@ def run_ours(args):
                 exec_pass(pi, COLS, X, X, sptr)
                 e[4].record(stream)
                 evs.append(e)
+        if evs is None and nstreams > 1:
+            for ln, j in zip(lanes, joins):
+                j.record(ln)
+                stream.wait_event(j)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -370,6 +389,7 @@ def run_ours(args):
             "config": {"workload": f"{side}x{side} complex64 2D FFT, forward+inverse of "
                                    f"{B} resident images per GPU per step",
                        "side": side, "images_per_gpu": B, "parallelism": f"replicas x{ws}",
+                       "streams": nstreams,
                        "l2": f"inputs larger than L2 ({B} images x 2 buffers x "
                              f"{img_bytes >> 20} MiB rotated)",
                        "transform_counting": "forward and inverse each count as one image"},
