@@ -13,9 +13,11 @@
 //     X[k] = Y_0[k] + W^k Y_1[k],   X[k + 2^L] = Y_0[k] - W^k Y_1[k],
 // W = W_{2^(L+1)}.  Thread t holds the same indices k in both CTAs, so the
 // two twins exchange half of their values: CTA b keeps the k of its half
-// (top bit of k/2^(L-1) equal to b) and receives the partner's values of
-// them with posted remote stores into its shared memory, then writes rows k
-// and k + 2^L of its half with two TMA stores.
+// (top bit of k/2^(L-1) equal to b).  Each thread writes the partner's half
+// into a send buffer, one thread moves the whole buffer into the partner's
+// shared memory with a single bulk copy that completes on the partner's
+// mbarrier, and each CTA then runs the last stage on its half and writes
+// rows k and k + 2^L of it with two TMA stores.
 //
 // Cluster barriers have no time limit, so both CTAs always execute the same
 // sequence of them: a CTA that lost a TMA transfer still reaches the next
