@@ -134,6 +134,7 @@ fft2d_status check_device(const fft2d_plan_s *p)
 fft2d_status run_pass(const fft2d_plan_s *p, int pass, const void *in, void *out, int nst,
                       bool allow_scale, cudaStream_t st, int withhold = 0)
 {
+    fft2d::NvtxRange range(pass == FFT2D_PASS_ROWS ? "fft2d row pass" : "fft2d column pass");
     fft2d::PassArgs a;
     a.withhold = withhold;
     a.in = static_cast<const float2 *>(in);
@@ -438,6 +439,7 @@ cudaError_t stream_wait_lanes(BatchLanes &bl, cudaStream_t to)
 fft2d_status batched_impl(int n, const fft2d_plan_t *plans, const void *const *in,
                           void *const *out, cudaStream_t st, bool timing)
 {
+    fft2d::NvtxRange range(timing ? "fft2d batched autotune" : "fft2d batched");
     BatchLanes *bl = nullptr;
     std::unique_lock<std::mutex> lanes_lock;
     if (!timing && n > 0) {
@@ -1067,6 +1069,7 @@ namespace {
 fft2d_status host_many_enqueue(HostPipe &hp, int n, const fft2d_plan_t *plans,
                                const void *const *in_host, void *const *out_host, cudaStream_t st)
 {
+    fft2d::NvtxRange range("fft2d host pipeline");
     size_t bytes = 0;
     for (int i = 0; i < n; i++) {
         const size_t b = (size_t)plans[i]->rows * plans[i]->cols * sizeof(float2);

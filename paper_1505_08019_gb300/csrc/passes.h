@@ -4,8 +4,19 @@
 #include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 namespace fft2d {
+
+// An NVTX range for the host-side span of one library call or pass launch
+// (shown by Nsight Systems / Nsight Compute when attached; a no-op stub
+// otherwise).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Arguments common to both passes (complex64 storage, FP32 arithmetic).
 struct PassArgs {

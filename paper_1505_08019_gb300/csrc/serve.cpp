@@ -200,6 +200,7 @@ struct fft2d_server_s {
     // ------------------------------------------------------------- launch
     fft2d_status launch(Batch &b)
     {
+        fft2d::NvtxRange range("fft2d serve batch");
         cudaStream_t st = streams[b.stream];
         for (Req *q : b.reqs) {
             const size_t bytes = (size_t)q->r.rows * q->r.cols * 8;
