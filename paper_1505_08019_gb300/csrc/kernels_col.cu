@@ -130,10 +130,10 @@ bool col_tma_usable(const PassArgs &a)
            !(reinterpret_cast<uintptr_t>(a.tw) & 15) && !((a.ld * 8) & 15) && a.cols % C::W == 0;
 }
 
-// Persistent TMA-fed column pass (col_tma2_kernel), with TMA stores (TS) or
-// per-thread stores.  Falls back to the plain kernel if a tile cannot be
-// described by a tensor map.
-template <class C, bool TS>
+// Persistent TMA-fed column pass (col_tma2_kernel), with TMA stores (TS),
+// per-thread stores, or half of each (TS and HYB).  Falls back to the plain
+// kernel if a tile cannot be described by a tensor map.
+template <class C, bool TS, bool HYB = false>
 cudaError_t col_launch_tma(const PassArgs &a, cudaStream_t s)
 {
     CUtensorMap map, omap;
@@ -141,7 +141,7 @@ cudaError_t col_launch_tma(const PassArgs &a, cudaStream_t s)
     if (!encode_col_map(&map, a.in, a.rows, a.cols, a.ld, C::W, S::BOX, S::NB) ||
         !encode_col_map(&omap, a.out, a.rows, a.cols, a.ld, C::W, tma_store_rows(C::L), S::NBOX))
         return col_launch_any<LineCfg<C::L, C::KW, 0>>(a, s);
-    auto k = col_tma2_kernel<C, TS>;
+    auto k = col_tma2_kernel<C, TS, HYB>;
     constexpr int SMEM = TmaSplit<C>::SMEM_BYTES;
     static int occ[kMaxDev] = {};
     const int d = current_device();
@@ -295,7 +295,7 @@ struct ColVariants {
     using Clu8 = ClusterColCfg<(L >= 13 ? L : 13), 3, (L >= 13 ? L - 11 : 2)>;
 
     struct Table {
-        Variant v[8];
+        Variant v[10];
         int n = 0;
     };
     static Table build()
@@ -327,6 +327,10 @@ struct ColVariants {
         if constexpr (HASTMEM)
             t.v[t.n++] = {"tmem", Tma32::W, 32, col_tma_usable<Tma32>, col_launch_tmem<Tma32>,
                           true};
+        // half of each tile through TMA stores, half through per-thread stores
+        if constexpr (HASTMEM && tma_store_ok<Tma32>())
+            t.v[t.n++] = {"tma32h", Tma32::W, 32, col_tma_usable<Tma32>,
+                          col_launch_tma<Tma32, true, true>, true};
         // 8192 rows: 4-column tiles over a CTA pair, the 4096-row engine on
         // each half and the last stage through remote stores
         if constexpr (L == 13)
@@ -349,10 +353,18 @@ struct ColVariants {
                 return i;
         return 0;
     }
+    // The default per column length, from timings of every variant on a
+    // GB300 (512..4096 rows, square and 1:4 images): narrow tiles for 512 and
+    // 1024 rows, the TMA pass with per-thread stores for 2048, and the TMA
+    // pass with half TMA / half per-thread stores for 4096.
     static int preferred()
     {
-        if constexpr (HASTMA)
-            return 1;   // measured fastest for 512..4096-row columns
+        if constexpr (L == 9 || L == 10)
+            return index_of("narrow");
+        else if constexpr (L == 11)
+            return index_of("tma32st");
+        else if constexpr (L == 12)
+            return index_of("tma32h");
         else if constexpr (L == 13)
             return index_of("pair");      // 4-column tiles over a CTA pair
         else if constexpr (L == 14)

@@ -682,6 +682,70 @@ __device__ __forceinline__ void group_last_finish_tma(float2 (&a)[C::EPT], float
     }
 }
 
+// ... or split the store work between the two store paths of the SM: the
+// first half of the units goes out through the staging buffer and one TMA
+// store (as above), the second half straight from registers with
+// per-thread stores, so neither the TMA unit nor the load/store unit carries
+// all 2^L row segments of the tile and nothing waits for the staging buffer
+// in the middle of the group.
+template <class C, bool TWS = false>
+__device__ __forceinline__ void group_last_finish_hybrid(float2 (&a)[C::EPT], float2 *stage,
+                                                         const CUtensorMap *omap, int c0,
+                                                         float2 *out, long long ld,
+                                                         const float2 *__restrict__ tw,
+                                                         float scale, int nst)
+{
+    using Gp = Grp<C, C::NG - 1>;
+    constexpr int S0 = Gp::S0;
+    constexpr int HALF = Gp::V / 2;
+    constexpr int QROWS = 1 << (S0 - 1);
+    static_assert(Gp::V >= 2 && C::LB == 1, "two halves of whole units, one line block");
+    static_assert((1 << S0) == 256, "store blocks are the 256-row blocks of the tensor maps");
+    static_assert(((C::T * HALF) >> C::KW) == QROWS, "the top unit bit is row bit S0-1");
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int v = 0; v < HALF; v++) {
+        const int u = tid + v * C::T;
+        const int lo = (u >> C::KW) & ((1 << S0) - 1);
+        run_stages<C, C::NG - 1, false, TWS>(a, v, lo, tw, nst);
+    }
+#pragma unroll
+    for (int v = 0; v < HALF; v++) {
+        const int u = tid + v * C::T;
+        const int w = u & (C::W - 1);
+        const int q = (u >> C::KW) & (QROWS - 1);
+#pragma unroll
+        for (int r = 0; r < Gp::R; r++) {
+            const float2 x = a[v * Gp::R + r];
+            stage[((r * QROWS) | q) * C::W + w] = make_float2(x.x * scale, x.y * scale);
+        }
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+        tma_store_3d(omap, c0, 0, 0, stage);   // box W x QROWS x NBX
+        bulk_commit();
+    }
+#pragma unroll
+    for (int v = HALF; v < Gp::V; v++) {
+        const int u = tid + v * C::T;
+        const int lo = (u >> C::KW) & ((1 << S0) - 1);
+        run_stages<C, C::NG - 1, false, TWS>(a, v, lo, tw, nst);
+    }
+#pragma unroll
+    for (int v = HALF; v < Gp::V; v++) {
+        const int u = tid + v * C::T;
+        const int w = u & (C::W - 1);
+        const int lo = (u >> C::KW) & ((1 << S0) - 1);
+        float2 *dst = out + (long long)lo * ld + w;
+#pragma unroll
+        for (int r = 0; r < Gp::R; r++) {
+            const float2 x = a[v * Gp::R + r];
+            st_stream(dst + (long long)(r << S0) * ld, make_float2(x.x * scale, x.y * scale));
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Persistent row pass fed by TMA bulk copies, double buffered: while a CTA
 // transforms its current block of LB rows in one shared-memory buffer, the
@@ -888,7 +952,9 @@ struct TilesOneImage {
 // group 0 runs; otherwise each thread stores its results directly.
 // withhold (self-test): CTA 0 does not issue its first tile's late boxes,
 // so its first wait runs out and the kernel takes its timeout path.
-template <class C, bool TS, class Src>
+// HYB (with TS): the last group stores half the tile through TMA and half
+// with per-thread stores (group_last_finish_hybrid).
+template <class C, bool TS, class Src, bool HYB = false>
 __device__ __forceinline__ void col_tma2_body(const Src &src, int ntiles,
                                               const float2 *__restrict__ tw, int *err,
                                               int withhold = 0)
@@ -958,7 +1024,11 @@ __device__ __forceinline__ void col_tma2_body(const Src &src, int ntiles,
         __syncthreads();   // the tile region is free
         if (tid == 0 && next < ntiles)
             split_issue_late<C>(sm, src.tmap(next), src.col(next), &bar_late);
-        if constexpr (TS)
+        if constexpr (TS && HYB)
+            group_last_finish_hybrid<C, true>(a, sm + C::E / 2, src.omap(tile), src.col(tile),
+                                              src.dst(tile), src.pitch(tile), stw, src.scl(tile),
+                                              C::L);
+        else if constexpr (TS)
             group_last_finish_tma<C, true>(a, sm + C::E / 2, src.omap(tile), src.col(tile), stw,
                                            src.scl(tile), C::L);
         else
@@ -971,7 +1041,7 @@ __device__ __forceinline__ void col_tma2_body(const Src &src, int ntiles,
     }
 }
 
-template <class C, bool TS>
+template <class C, bool TS, bool HYB = false>
 __global__ void __launch_bounds__(C::T, 1) col_tma2_kernel(const __grid_constant__ CUtensorMap map,
                                                            const __grid_constant__ CUtensorMap omap,
                                                            float2 *out,
@@ -980,7 +1050,7 @@ __global__ void __launch_bounds__(C::T, 1) col_tma2_kernel(const __grid_constant
                                                            int *err, int withhold)
 {
     const TilesOneImage src{&map, &omap, out, ld, scale, C::W};
-    col_tma2_body<C, TS>(src, cols / C::W, tw, err, withhold);
+    col_tma2_body<C, TS, TilesOneImage, HYB>(src, cols / C::W, tw, err, withhold);
 }
 
 // The same kernel over the column tiles of many images of one column length
