@@ -394,7 +394,8 @@ FFT2D_API fft2d_status fft2d_exec_noalloc(int rows, int cols, int dir, const voi
  * Batch autotuner: for every group of fft2d_exec_batched's grouped launches
  * in this batch (pass, axis length, direction), time each grouped-kernel
  * variant (rows: plain, 32 values per thread; columns: plain, half-width
- * tiles, persistent TMA-fed) and keep the fastest per (pass, axis length) in
+ * tiles, persistent TMA-fed with TMA stores, with per-thread stores, or with
+ * half of each) and keep the fastest per (pass, axis length) in
  * the process-wide tuning table (and FFT2D_TUNE_CACHE).  Later
  * fft2d_exec_batched calls use the winners.  The buffers are overwritten
  * with intermediate results (the passes run several times).  Synchronous.

@@ -72,8 +72,9 @@ cudaError_t batch_launch(BatchTable &t, cudaStream_t s)
 
 // Grouped persistent TMA column pass: a load and a store tensor map per
 // image; not used when some image cannot be described by them (alignment,
-// partial tiles).
-template <class C>
+// partial tiles).  Store mode: 0 TMA stores, 1 per-thread stores, 2 half of
+// each (TMA stores need tma_store_ok; otherwise per-thread stores).
+template <class C, int MODE>
 cudaError_t batch_launch_tma(const BatchTable &t, int *err, cudaStream_t s, bool *used)
 {
     *used = false;
@@ -101,7 +102,8 @@ cudaError_t batch_launch_tma(const BatchTable &t, int *err, cudaStream_t s, bool
         *used = true;
         return cudaSuccess;
     }
-    auto k = col_tma2_batch_kernel<C, tma_store_ok<C>()>;
+    constexpr bool TS = MODE != 1 && tma_store_ok<C>();
+    auto k = col_tma2_batch_kernel<C, TS, TS && MODE == 2>;
     constexpr int SMEM = TmaSplit<C>::SMEM_BYTES;
     constexpr int kMaxDev = 64;
     static int occ[kMaxDev] = {};
@@ -133,10 +135,12 @@ cudaError_t batch_dispatch(bool row, BatchTable &t, int variant, int *err, cudaS
         return batch_launch<LineCfg<L, 0, row_kb(L)>, true>(t, s);
     }
     if constexpr (L >= 9 && L <= 12) {
-        if (variant == 2) {
+        if (variant >= 2 && variant <= 4) {
+            using C = LineCfg<L, col_kw(L), 0, col_tma_ept(L)>;
             bool used = false;
-            cudaError_t e =
-                batch_launch_tma<LineCfg<L, col_kw(L), 0, col_tma_ept(L)>>(t, err, s, &used);
+            cudaError_t e = variant == 2   ? batch_launch_tma<C, 0>(t, err, s, &used)
+                            : variant == 3 ? batch_launch_tma<C, 1>(t, err, s, &used)
+                                           : batch_launch_tma<C, 2>(t, err, s, &used);
             if (e != cudaSuccess || used)
                 return e;
         }
@@ -150,12 +154,23 @@ cudaError_t batch_dispatch(bool row, BatchTable &t, int variant, int *err, cudaS
 
 }  // namespace
 
-int batch_default_variant(bool row, int L) { return row ? 0 : (L >= 9 && L <= 12 ? 2 : 0); }
+// Defaults, from timings on a GB300 (the batch autotuner can override them):
+// per-thread stores for 1024- and 2048-row columns, half of each for 4096.
+int batch_default_variant(bool row, int L)
+{
+    if (row)
+        return 0;
+    if (L == 10 || L == 11)
+        return 3;
+    if (L == 12)
+        return 4;
+    return L == 9 ? 2 : 0;
+}
 
 const char *batch_variant_name(bool row, int variant)
 {
     static const char *rn[kBatchRowVariants] = {"plain", "plain32"};
-    static const char *cn[kBatchColVariants] = {"plain", "narrow", "tma"};
+    static const char *cn[kBatchColVariants] = {"plain", "narrow", "tma", "tmast", "tmah"};
     if (row)
         return variant >= 0 && variant < kBatchRowVariants ? rn[variant] : "";
     return variant >= 0 && variant < kBatchColVariants ? cn[variant] : "";

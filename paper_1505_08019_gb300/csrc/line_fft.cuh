@@ -1083,13 +1083,13 @@ struct TilesBatch {
     __device__ float scl(int g) const { return t->scale[job(g)]; }
 };
 
-template <class C, bool TS>
+template <class C, bool TS, bool HYB = false>
 __global__ void __launch_bounds__(C::T, 1) col_tma2_batch_kernel(const __grid_constant__ BatchTmaTable t,
                                                                  const float2 *__restrict__ tw,
                                                                  int *err)
 {
     const TilesBatch src{&t, C::W};
-    col_tma2_body<C, TS>(src, t.first_tile[t.n], tw, err);
+    col_tma2_body<C, TS, TilesBatch, HYB>(src, t.first_tile[t.n], tw, err);
 }
 
 // ---------------------------------------------------------------------------

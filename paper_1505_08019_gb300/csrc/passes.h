@@ -126,9 +126,11 @@ struct BatchTmaTable {   // 128-byte aligned through CUtensorMap
 };
 
 // Grouped-launch variants: rows 0 plain, 1 plain32; columns 0 plain,
-// 1 narrow (half-width tiles), 2 tma (persistent, TMA-fed; 512..4096 rows).
+// 1 narrow (half-width tiles), 2 tma (persistent, TMA-fed, TMA stores;
+// 512..4096 rows), 3 tmast (the same with per-thread stores), 4 tmah (half
+// of each tile through TMA stores, half through per-thread stores).
 constexpr int kBatchRowVariants = 2;
-constexpr int kBatchColVariants = 3;
+constexpr int kBatchColVariants = 5;
 int batch_default_variant(bool row, int L);
 const char *batch_variant_name(bool row, int variant);
 

@@ -213,12 +213,13 @@ def test_batched_every_grouped_variant_is_bit_identical(env):
 def test_batch_variant_arguments(env):
     torch, fft, _ = env
     R, C = fft.FFT2D_PASS_ROWS, fft.FFT2D_PASS_COLS
-    assert fft.fft2d_batch_variant_name(C, 2) == "tma"
+    assert [fft.fft2d_batch_variant_name(C, v) for v in range(fft.fft2d_batch_variant_count(C))] \
+        == ["plain", "narrow", "tma", "tmast", "tmah"]
     assert fft.fft2d_batch_variant_name(C, 99) == ""
-    assert fft.fft2d_batch_get_variant(C, 12) == 2      # default for 4096-point columns
+    assert fft.fft2d_batch_get_variant(C, 12) == 4      # default for 4096-point columns: tmah
     assert fft.fft2d_batch_get_variant(R, 0) == -1
     with pytest.raises(fft.FFT2DError):
-        fft.fft2d_batch_set_variant(C, 12, 3)
+        fft.fft2d_batch_set_variant(C, 12, fft.fft2d_batch_variant_count(C))
     with pytest.raises(fft.FFT2DError):
         fft.fft2d_batch_set_variant(R, 15, 0)
 
