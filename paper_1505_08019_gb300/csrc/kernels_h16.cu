@@ -33,7 +33,8 @@ template <int L>
 cudaError_t h16_dispatch(bool row, const H16PassArgs &a, cudaStream_t s)
 {
     if (row) {
-        using C = LineCfg<L, 0, row_kb(L)>;
+        // 8192-point rows: 32 values per thread (256 threads), as for complex64
+        using C = LineCfg<L, 0, row_kb(L), L == 13 ? 32 : 16>;
         return a.rows % C::LB ? h16_launch<C, true, true>(a, s) : h16_launch<C, true, false>(a, s);
     }
     using C = LineCfg<L, col_kw(L), 0>;
