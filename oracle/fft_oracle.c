@@ -349,3 +349,113 @@ int oracle_dft2d(const double *x, double *X, long rows, long cols, int sign)
     }
     return ORACLE_OK;
 }
+
+/*
+ * The discrete cosine transform, one of the "similar transforms" Section 5
+ * says the method extends to (the paper gives no algorithm for it; the
+ * oracle evaluates the definitions directly, with no FFT):
+ *
+ *   forward (DCT-II):  X[k] = sum_{j<n} x[j] cos(pi k (2j+1) / (2n)),
+ *   inverse (DCT-III): x[j] = (1/n) (X[0] + 2 sum_{1<=k<n} X[k] cos(pi k (2j+1) / (2n))),
+ *
+ * so that the inverse undoes the forward.  Real data, doubles.  The cosine
+ * of pi*m/(2n) is taken from a table over m < 4n; the integer phase
+ * k*(2j+1) is reduced modulo 4n first, and the quarter turns are exact.
+ */
+static double *oracle_cos_table(long n)
+{
+    double *c = (double *)malloc(sizeof(double) * 4 * (size_t)n);
+    if (!c)
+        return NULL;
+    for (long m = 0; m < 4 * n; m++) {
+        if (m == 0)
+            c[m] = 1.0;
+        else if (m == n || m == 3 * n)
+            c[m] = 0.0;
+        else if (m == 2 * n)
+            c[m] = -1.0;
+        else
+            c[m] = cos(ORACLE_PI * (double)m / (2.0 * (double)n));
+    }
+    return c;
+}
+
+static void oracle_dct_line_tab(const double *x, long in_stride, double *X, long out_stride,
+                                long n, int inverse, const double *ctab)
+{
+    for (long a = 0; a < n; a++) {
+        double s = 0.0;
+        for (long b = 0; b < n; b++) {
+            /* forward: output k = a, input j = b; inverse: output j = a, input k = b */
+            long k = inverse ? b : a, j = inverse ? a : b;
+            double c = ctab[(k * (2 * j + 1)) % (4 * n)];
+            double w = inverse ? (b == 0 ? 1.0 : 2.0) : 1.0;
+            s += w * x[b * in_stride] * c;
+        }
+        X[a * out_stride] = inverse ? s / (double)n : s;
+    }
+}
+
+int oracle_dct_line(const double *x, long in_stride, double *X, long out_stride, long n,
+                    int inverse)
+{
+    if (n < 1)
+        return ORACLE_ERR_ARG;
+    double *ctab = oracle_cos_table(n);
+    if (!ctab)
+        return ORACLE_ERR_OOM;
+    oracle_dct_line_tab(x, in_stride, X, out_stride, n, inverse, ctab);
+    free(ctab);
+    return ORACLE_OK;
+}
+
+/*
+ * 2D transform of a rows x cols real image z (row-major), in place: every
+ * row, then every column, each by the definition above.  Any sizes >= 1.
+ */
+int oracle_dct2d(double *z, long rows, long cols, int inverse)
+{
+    if (rows < 1 || cols < 1)
+        return ORACLE_ERR_ARG;
+    long nmax = rows > cols ? rows : cols;
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)nmax);
+    double *crow = oracle_cos_table(cols), *ccol = oracle_cos_table(rows);
+    if (!tmp || !crow || !ccol) {
+        free(tmp);
+        free(crow);
+        free(ccol);
+        return ORACLE_ERR_OOM;
+    }
+    for (long r = 0; r < rows; r++) {
+        oracle_dct_line_tab(z + r * cols, 1, tmp, 1, cols, inverse, crow);
+        memcpy(z + r * cols, tmp, sizeof(double) * (size_t)cols);
+    }
+    for (long c = 0; c < cols; c++) {
+        oracle_dct_line_tab(z + c, cols, tmp, 1, rows, inverse, ccol);
+        for (long r = 0; r < rows; r++)
+            z[r * cols + c] = tmp[r];
+    }
+    free(tmp);
+    free(crow);
+    free(ccol);
+    return ORACLE_OK;
+}
+
+/*
+ * One output of the forward 2D DCT as the double sum of its definition (no
+ * separation): X[k][l] = sum_m sum_n x[m][n] cos(pi k (2m+1)/(2 rows))
+ * cos(pi l (2n+1)/(2 cols)).  O(rows*cols) per output.
+ */
+double oracle_dct2d_at(const double *x, long rows, long cols, long k, long l)
+{
+    double s = 0.0;
+    for (long m = 0; m < rows; m++) {
+        long pm = (k * (2 * m + 1)) % (4 * rows);
+        double cm = cos(ORACLE_PI * (double)pm / (2.0 * (double)rows));
+        for (long n = 0; n < cols; n++) {
+            long pn = (l * (2 * n + 1)) % (4 * cols);
+            s += x[m * cols + n] * cm * cos(ORACLE_PI * (double)pn / (2.0 * (double)cols));
+        }
+    }
+    return s;
+}

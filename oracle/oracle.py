@@ -10,7 +10,10 @@ code with the CUDA path.  Every function works on numpy ``complex128`` data
                  (Section 2 eqs. 2-3, Section 3.1 eq. 4);
 * ``fft2d``   -- rows, then columns (Section 2, separability), inverse scaled
                  by 1/(rows*cols);
-* ``dft1d`` / ``dft2d`` -- eq. 1 evaluated directly (brute force).
+* ``dft1d`` / ``dft2d`` -- eq. 1 evaluated directly (brute force);
+* ``dct1d`` / ``dct2d`` / ``dct2d_at`` -- the discrete cosine transform (one
+                 of the "similar transforms" of Section 5) from its definition,
+                 real data.
 
 ``fft2d(..., threads=k)`` splits the lines of each axis over k POSIX threads
 inside the C code; the arithmetic per line is the same single-threaded code.
@@ -78,6 +81,12 @@ class Oracle:
         lib.oracle_dft2d.restype = I
         lib.oracle_gaussian_lowpass.argtypes = [P, L, L, ctypes.c_double, ctypes.c_double]
         lib.oracle_gaussian_lowpass.restype = None
+        lib.oracle_dct_line.argtypes = [P, L, P, L, L, I]
+        lib.oracle_dct_line.restype = I
+        lib.oracle_dct2d.argtypes = [P, L, L, I]
+        lib.oracle_dct2d.restype = I
+        lib.oracle_dct2d_at.argtypes = [P, L, L, L, L]
+        lib.oracle_dct2d_at.restype = ctypes.c_double
         self.lib = lib
 
     # -- Section 3.2 ---------------------------------------------------------
@@ -152,6 +161,30 @@ class Oracle:
         X = self.fft2d(x, threads=threads)
         X = self.lowpass(X, R / 8.0, C / 8.0)
         return self.fft2d(X, inverse=True, threads=threads)
+
+    # -- discrete cosine transform (Section 5's "similar transforms"),
+    #    real data, evaluated from its definition (no FFT)
+    def dct1d(self, x, inverse: bool = False) -> np.ndarray:
+        """DCT-II of a real line, or (inverse) the scaled DCT-III that undoes it."""
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+        X = np.empty_like(x)
+        rc = self.lib.oracle_dct_line(_ptr(x), 1, _ptr(X), 1, x.shape[0], int(inverse))
+        if rc != 0:
+            raise ValueError(f"oracle_dct_line failed ({rc})")
+        return X
+
+    def dct2d(self, x, inverse: bool = False) -> np.ndarray:
+        """2D DCT-II (rows, then columns) of a real image, or its inverse (copy)."""
+        z = np.array(x, dtype=np.float64, copy=True, order="C")
+        rc = self.lib.oracle_dct2d(_ptr(z), z.shape[0], z.shape[1], int(inverse))
+        if rc != 0:
+            raise ValueError(f"oracle_dct2d failed ({rc})")
+        return z
+
+    def dct2d_at(self, x, k: int, l: int) -> float:
+        """One forward 2D DCT output X[k][l] as the direct double sum."""
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+        return float(self.lib.oracle_dct2d_at(_ptr(x), x.shape[0], x.shape[1], k, l))
 
 
 _default: Oracle | None = None

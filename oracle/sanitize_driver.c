@@ -25,6 +25,10 @@ void oracle_gaussian_lowpass(double *z, long rows, long cols, double sr, double 
 int oracle_dft_line(const double *x, long in_stride, double *X, long out_stride, long n,
                     int sign);
 int oracle_dft2d(const double *x, double *X, long rows, long cols, int sign);
+int oracle_dct_line(const double *x, long in_stride, double *X, long out_stride, long n,
+                    int inverse);
+int oracle_dct2d(double *z, long rows, long cols, int inverse);
+double oracle_dct2d_at(const double *x, long rows, long cols, long k, long l);
 
 static int failures = 0;
 
@@ -139,6 +143,36 @@ int main(void)
         oracle_scale(z, n, 0.5);
         oracle_gaussian_lowpass(z, rows, cols, rows / 8.0, cols / 8.0);
         free(z);
+    }
+
+    /* discrete cosine transform: round trip, and single outputs against the
+     * separated 2D transform, sides 1 .. 16 */
+    for (long rows = 1; rows <= 16; rows *= 2) {
+        for (long cols = 1; cols <= 16; cols *= 2) {
+            const long n = rows * cols;
+            double *x = malloc((size_t)n * sizeof(double));
+            double *z = malloc((size_t)n * sizeof(double));
+            for (long i = 0; i < n; i++)
+                x[i] = next_value();
+            memcpy(z, x, (size_t)n * sizeof(double));
+            check(oracle_dct2d(z, rows, cols, 0) == 0, "dct2d status", rows, cols);
+            for (long k = 0; k < rows; k++)
+                for (long l = 0; l < cols; l++) {
+                    const double a = oracle_dct2d_at(x, rows, cols, k, l);
+                    check(fabs(a - z[k * cols + l]) <= 1e-12 * (1.0 + fabs(a)), "dct2d_at", k, l);
+                }
+            check(oracle_dct2d(z, rows, cols, 1) == 0, "idct2d status", rows, cols);
+            double err = 0.0;
+            for (long i = 0; i < n; i++)
+                err = fmax(err, fabs(z[i] - x[i]));
+            check(err <= 1e-12, "dct round trip", rows, cols);
+            double line[16], out[16];
+            check(oracle_dct_line(x, 1, out, 1, cols, 0) == 0 &&
+                      oracle_dct_line(out, 1, line, 1, cols, 1) == 0,
+                  "dct_line status", cols, 0);
+            free(x);
+            free(z);
+        }
     }
 
     /* argument errors are reported, not acted on */

@@ -222,7 +222,60 @@ def pin_lowpass(orc):
     assert abs(y.mean() - x.mean()) < 1e-12
 
 
-ALL_PINS = [pin_lowpass, pin_bitrev, pin_fft1d_brute, pin_dft1d_brute, pin_fft1d_library,
+def pin_dct_library(orc, shapes=((1, 1), (1, 8), (2, 2), (4, 8), (8, 4), (16, 32), (32, 16),
+                                  (64, 64), (5, 3), (6, 10))):
+    """The 2D DCT-II against an independent library: scipy's unnormalised type-2
+    transform is twice this definition on every axis."""
+    import scipy.fft as sf
+    g = np.random.default_rng(11)
+    for R, C in shapes:
+        x = g.uniform(-1, 1, (R, C))
+        want = sf.dctn(x, type=2, norm=None) / 4.0
+        assert rel(orc.dct2d(x), want) <= 1e-13, (R, C)
+        line = g.uniform(-1, 1, C)
+        assert rel(orc.dct1d(line), sf.dct(line, type=2, norm=None) / 2.0) <= 1e-13, C
+
+
+def pin_dct_brute(orc):
+    """Every output of small 2D DCTs equals the unseparated double sum."""
+    g = np.random.default_rng(12)
+    for R, C in ((1, 1), (2, 4), (4, 4), (8, 2), (3, 5)):
+        x = g.uniform(-1, 1, (R, C))
+        X = orc.dct2d(x)
+        for k in range(R):
+            for l in range(C):
+                assert abs(X[k, l] - orc.dct2d_at(x, k, l)) <= 1e-12 * max(1.0, abs(X[k, l])), (R, C, k, l)
+
+
+def pin_dct_closed_forms(orc):
+    """A constant lands only at [0][0] (c R C); the cosine basis image of
+    (k0, l0) lands only there, with weight (R / (2 - [k0 == 0])) (C / (2 - [l0 == 0]))."""
+    R, C = 8, 16
+    X = orc.dct2d(np.full((R, C), 0.75))
+    assert abs(X[0, 0] - 0.75 * R * C) <= 1e-12
+    X[0, 0] = 0.0
+    assert np.abs(X).max() <= 1e-12
+    m = np.arange(R)[:, None]
+    n = np.arange(C)[None, :]
+    for k0, l0 in ((0, 0), (0, 5), (3, 0), (1, 1), (7, 15), (4, 8)):
+        x = np.cos(np.pi * k0 * (2 * m + 1) / (2 * R)) * np.cos(np.pi * l0 * (2 * n + 1) / (2 * C))
+        X = orc.dct2d(x)
+        want = (R if k0 == 0 else R / 2) * (C if l0 == 0 else C / 2)
+        assert abs(X[k0, l0] - want) <= 1e-11, (k0, l0)
+        X[k0, l0] = 0.0
+        assert np.abs(X).max() <= 1e-11, (k0, l0)
+
+
+def pin_dct_round_trip(orc):
+    """The inverse undoes the forward, square and non-square."""
+    g = np.random.default_rng(13)
+    for R, C in ((1, 1), (4, 4), (16, 8), (2, 64), (32, 32)):
+        x = g.uniform(-1, 1, (R, C))
+        assert np.abs(orc.dct2d(orc.dct2d(x), inverse=True) - x).max() <= 1e-12, (R, C)
+
+
+ALL_PINS = [pin_dct_library, pin_dct_brute, pin_dct_closed_forms, pin_dct_round_trip,
+            pin_lowpass, pin_bitrev, pin_fft1d_brute, pin_dft1d_brute, pin_fft1d_library,
             pin_fft2d_library, pin_dft2d, pin_crops_brute, pin_closed_forms,
             pin_invariants, pin_partial_stages]
 

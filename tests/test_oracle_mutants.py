@@ -47,6 +47,23 @@ MUTANTS = {
     # quarter-turn value wrong
     "quarter_turn": ("static const double sq[4] = {0.0, 1.0, 0.0, -1.0};",
                      "static const double sq[4] = {0.0, -1.0, 0.0, 1.0};"),
+    # DCT: half-sample shift dropped from the cosine phase (2j instead of 2j+1)
+    "dct_phase": ("double c = ctab[(k * (2 * j + 1)) % (4 * n)];",
+                  "double c = ctab[(k * (2 * j)) % (4 * n)];"),
+    # DCT inverse: the k = 0 term weighted like the others
+    "dct_inverse_weight": ("double w = inverse ? (b == 0 ? 1.0 : 2.0) : 1.0;",
+                           "double w = inverse ? 2.0 : 1.0;"),
+    # DCT inverse: 1/n missing
+    "dct_inverse_scale": ("X[a * out_stride] = inverse ? s / (double)n : s;",
+                          "X[a * out_stride] = s;"),
+    # DCT: cosine table wrong at the half turn
+    "dct_half_turn": ("            c[m] = -1.0;", "            c[m] = 1.0;"),
+    # DCT: columns walked with row strides
+    "dct_column_strides": ("oracle_dct_line_tab(z + c, cols, tmp, 1, rows, inverse, ccol);",
+                           "oracle_dct_line_tab(z + c * rows, 1, tmp, 1, rows, inverse, ccol);"),
+    # DCT single output: phase of the row factor off by one
+    "dct_at_phase": ("long pm = (k * (2 * m + 1)) % (4 * rows);",
+                     "long pm = (k * (2 * m + 2)) % (4 * rows);"),
 }
 
 
