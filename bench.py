@@ -43,17 +43,20 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--requests", type=int, default=20000, help="serving workload: requests")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving workload: mean req/s")
-    ap.add_argument("--workload", choices=["fft4096", "batched", "fp16", "serve"],
+    ap.add_argument("--workload", choices=["fft4096", "batched", "fp16", "serve", "dct"],
                     default="fft4096",
                     help="fft4096: the 4096x4096 forward+inverse benchmark (default); "
                          "batched: 64 uneven images through the grouped executor; "
                          "fp16: half2 storage vs complex64 at 8192^2 and 16384^2; "
-                         "serve: Poisson stream of mixed requests through fft2d_serve_*")
+                         "serve: Poisson stream of mixed requests through fft2d_serve_*; "
+                         "dct: real 2D DCT-II at 4096^2 and 8192^2 beside the complex FFT")
     ap.add_argument("--images", type=int, default=4, help="resident images per rank")
     ap.add_argument("--streams", type=int, default=0,
                     help="CUDA streams the resident images are spread over (0: one per image)")
     ap.add_argument("--fp16-sides", default="8192,16384",
                     help="fp16 workload: comma-separated square sides")
+    ap.add_argument("--dct-sides", default="4096,8192",
+                    help="dct workload: comma-separated square sides")
     ap.add_argument("--side", type=int, default=SIDE)
     ap.add_argument("--e2e-steps", type=int, default=6)
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
@@ -778,6 +781,102 @@ def run_serve(args):
     }
     print(json.dumps(line), flush=True)
 
+# ------------------------------------------------------------- DCT workload
+def run_dct(args):
+    """Unnormalised 2D DCT-II of real gray images (U[0,1), one float per
+    pixel) through plans of dtype FFT2D_R32_DCT2, beside the forward complex64
+    FFT of the same side.  Four input/output pairs are used in turn, so that
+    consecutive launches do not find their image in L2.  Sampled outputs are
+    checked against the oracle's direct double sum."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1505_08019_gb300 as fft
+    import synth
+    from oracle import oracle
+    orc = oracle.get()
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    peak, peak_src = measured_hbm_peak()
+    nbuf = 4
+    results = {}
+    sides = [int(v) for v in args.dct_sides.split(",") if v]
+
+    def t(fn, n):
+        for i in range(3):
+            fn(i)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for i in range(n):
+            fn(i)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    for side in sides:
+        x = synth.gray_real(side, side, seed=side)
+        xs = [torch.from_numpy(x).cuda() for _ in range(nbuf)]
+        ys = [torch.empty_like(xs[0]) for _ in range(nbuf)]
+        pd = fft.fft2d_plan(side, side, fft.FFT2D_R32_DCT2, fft.FFT2D_FORWARD)
+        reps = 40 if side <= 4096 else 16
+        ms = t(lambda i: fft.fft2d_exec(pd, xs[i % nbuf], ys[i % nbuf], sptr), reps)
+        ms_rows = t(lambda i: fft.fft2d_exec_pass(pd, fft.FFT2D_PASS_ROWS, xs[i % nbuf],
+                                                  ys[i % nbuf], sptr), reps)
+        ms_cols = t(lambda i: fft.fft2d_exec_pass(pd, fft.FFT2D_PASS_COLS, xs[i % nbuf],
+                                                  ys[i % nbuf], sptr), reps)
+        fft.fft2d_exec(pd, xs[0], ys[0], sptr)
+        torch.cuda.synchronize()
+        got = ys[0].cpu().numpy()
+        del xs, ys
+        torch.cuda.empty_cache()
+        # the complex64 forward FFT of the same side, for comparison
+        zc = [torch.zeros((side, side), dtype=torch.complex64, device="cuda") for _ in range(2)]
+        pc = fft.fft2d_plan(side, side, fft.FFT2D_C64, fft.FFT2D_FORWARD)
+        ms_fft = t(lambda i: fft.fft2d_exec(pc, zc[i % 2], zc[(i + 1) % 2], sptr), reps)
+        fft.fft2d_destroy(pc)
+        del zc
+        torch.cuda.empty_cache()
+        # sampled outputs against the direct double sum
+        g = np.random.default_rng(side)
+        idx = [(0, 0), (side // 2, side // 2), (side - 1, side - 1)] + \
+              [(int(a), int(b)) for a, b in zip(g.integers(0, side, 5), g.integers(0, side, 5))]
+        rms = float(np.linalg.norm(x.astype(np.float64))) / 2.0
+        worst = 0.0
+        for k, l in idx:
+            want = orc.dct2d_at(x, k, l)
+            worst = max(worst, abs(float(got[k, l]) - want) / (4.0 * rms + abs(want)))
+        px = side * side
+        results[f"{side}x{side}"] = {
+            "dct_ms": ms, "dct_row_pass_ms": ms_rows, "dct_col_pass_ms": ms_cols,
+            "dct_images_per_s": 1e3 / ms,
+            "dct_hbm_frac": (16.0 * px / (ms * 1e-3) / 1e9) / peak,
+            "dct_row_pass_hbm_frac": (8.0 * px / (ms_rows * 1e-3) / 1e9) / peak,
+            "dct_col_pass_hbm_frac": (8.0 * px / (ms_cols * 1e-3) / 1e9) / peak,
+            "complex64_fft_forward_ms": ms_fft,
+            "dct_speedup_vs_complex_fft": ms_fft / ms,
+            "sampled_outputs_checked": len(idx),
+            "worst_sample_err_over_bound_scale": worst, "tolerance": 1e-5,
+            "kernels": fft.fft2d_plan_describe(pd)}
+        fft.fft2d_destroy(pd)
+    head = results[f"{sides[0]}x{sides[0]}"]
+    line = {"metric": "2D DCT-II images/s (real FP32 images)",
+            "value": head["dct_images_per_s"], "unit": "images/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic (seeded gray images, U[0,1))",
+            "config": {"workload": "forward unnormalised 2D DCT-II at "
+                                   + ", ".join(f"{v}x{v}" for v in sides)
+                                   + f"; value = {sides[0]}^2 images/s; {nbuf} input/output "
+                                     "pairs used in turn (L2 not reused between launches)"},
+            "roofline": {"bound": "hbm", "peak": peak, "unit": "GB/s", "peak_source": peak_src,
+                         "algorithmic_bytes_per_px": 16,
+                         "achieved": 16.0 * sides[0] ** 2 / (head["dct_ms"] * 1e-3) / 1e9,
+                         "frac": head["dct_hbm_frac"]},
+            "per_size": results}
+    print(json.dumps(line), flush=True)
+
 
 def main():
     args = parse()
@@ -789,6 +888,8 @@ def main():
         run_fp16(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "dct":
+        run_dct(args)
     else:
         run_ours(args)
 

@@ -55,6 +55,7 @@ typedef struct fft2d_plan_s *fft2d_plan_t;
 /* Storage types (dtype argument). */
 #define FFT2D_C64 0  /* complex64: float2 per pixel, FP32 arithmetic */
 #define FFT2D_C32H 1 /* half2 per pixel + a power-of-two exponent per line, FP32 arithmetic */
+#define FFT2D_R32_DCT2 2 /* real float per pixel: the 2D DCT-II (see fft2d_plan), FP32 arithmetic */
 
 /* Directions (dir argument). */
 #define FFT2D_FORWARD (-1)
@@ -87,6 +88,26 @@ typedef enum {
  * to the current device.  *out receives the plan; on error it is set to NULL.
  */
 FFT2D_API fft2d_status fft2d_plan(int rows, int cols, int dtype, int dir, fft2d_plan_t *out);
+
+/*
+ * Plans of dtype FFT2D_R32_DCT2: the 2D discrete cosine transform, which
+ * Section 5 names as a transform the method carries over to.  The image is
+ * real, one float per pixel, row-major (pitch = cols); fft2d_exec and
+ * fft2d_exec_pass (rows: in -> out, columns: in -> out; in may equal out)
+ * compute the unnormalised DCT-II
+ *   X[k][l] = sum_{m<rows} sum_{n<cols} x[m][n] cos(pi k (2m+1) / (2 rows))
+ *                                               cos(pi l (2n+1) / (2 cols))
+ * as one pass along the rows, then one along the columns, each on the
+ * radix-2 engine: a length-N DCT-II is one length-N complex DFT of the
+ * reordered line (even samples ascending, odd samples descending) followed
+ * by a rotation by exp(-i pi k / (2N)) (Makhoul, 1980), and two real lines
+ * share one complex line.  The plan also holds the (cos, sin)(pi k / (2N))
+ * tables, built in FP64 and rounded to FP32.
+ * Errors: FFT2D_ERR_UNSUPPORTED for a side of 1 or dir = FFT2D_INVERSE (the
+ * inverse, DCT-III, is not provided).  The other entry points reject these
+ * plans with FFT2D_ERR_ARG, except fft2d_exec_host, fft2d_plan_info,
+ * fft2d_plan_describe, fft2d_sync_status and fft2d_destroy.
+ */
 
 /*
  * Wait for all work on the device, then report device-side failures of this

@@ -29,6 +29,8 @@ struct fft2d_plan_s {
     int row_variant;   // kernel variant of each pass (-1: per-size default)
     int col_variant;
     int *exp_rows;     // half2 plans: exponents of the row pass output, one per row
+    float2 *post_rows; // DCT plans: (cos, sin)(pi k / (2 cols)), k = 0 .. cols/2
+    float2 *post_cols; // DCT plans: (cos, sin)(pi k / (2 rows)), k = 0 .. rows/2
 };
 
 namespace {
@@ -107,6 +109,28 @@ std::vector<float2> stage_table(int L, int dir)
     return t;
 }
 
+// Post-rotation table of the DCT-II along an axis of N = 2^L points:
+// (cos, sin)(pi k / (2N)) for k = 0 .. N/2, i.e. angles 2 pi k / (4N) up to
+// pi/4, from the same octant-reduced FP64 evaluation as the stage tables
+// (k = 0 is exactly (1, 0)).
+std::vector<float2> dct_post_table(int L)
+{
+    const long long N = 1LL << L;
+    std::vector<float2> t((size_t)(N / 2 + 1));
+    for (long long k = 0; k <= N / 2; k++) {
+        double c, sn;
+        twiddle_fp64(k, 4 * N, &c, &sn);
+        t[(size_t)k] = make_float2((float)c, (float)sn);
+    }
+    return t;
+}
+
+// Bytes of one image of the plan's storage type (C64 and DCT plans).
+size_t image_bytes(const fft2d_plan_s *p)
+{
+    return (size_t)p->rows * p->cols * (p->dtype == FFT2D_R32_DCT2 ? sizeof(float) : sizeof(float2));
+}
+
 fft2d_status check_shape(int rows, int cols)
 {
     if (rows < 1 || cols < 1 || (rows & (rows - 1)) || (cols & (cols - 1)))
@@ -182,9 +206,31 @@ fft2d_status run_pass(const fft2d_plan_s *p, int pass, const void *in, void *out
     return FFT2D_OK;
 }
 
+// One DCT-II pass of a DCT plan (rows: lines of cols points; columns: lines
+// of rows points).
+fft2d_status run_dct_pass(const fft2d_plan_s *p, int pass, const void *in, void *out,
+                          cudaStream_t st)
+{
+    fft2d::NvtxRange range(pass == FFT2D_PASS_ROWS ? "fft2d dct rows" : "fft2d dct cols");
+    const bool row = pass == FFT2D_PASS_ROWS;
+    cudaError_t e = fft2d::launch_dct_pass(row, row ? p->Lc : p->Lr, static_cast<const float *>(in),
+                                           static_cast<float *>(out), p->rows, p->cols,
+                                           row ? p->tw_rows : p->tw_cols,
+                                           row ? p->post_rows : p->post_cols, 1.0f, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, row ? "DCT row pass launch" : "DCT column pass launch");
+    return FFT2D_OK;
+}
+
 fft2d_status exec_impl(const fft2d_plan_s *p, const void *in, void *out, int rs, int cs,
                        cudaStream_t st)
 {
+    if (p->dtype == FFT2D_R32_DCT2) {
+        fft2d_status s = run_dct_pass(p, FFT2D_PASS_ROWS, in, out, st);
+        if (s != FFT2D_OK)
+            return s;
+        return run_dct_pass(p, FFT2D_PASS_COLS, out, out, st);
+    }
     const bool full = (rs < 0 || rs == p->Lc) && (cs < 0 || cs == p->Lr);
     fft2d_status s = run_pass(p, FFT2D_PASS_ROWS, in, out, rs, full, st);
     if (s != FFT2D_OK)
@@ -611,9 +657,11 @@ fft2d_status fft2d_plan(int rows, int cols, int dtype, int dir, fft2d_plan_t *ou
         return st;
     if (dir != FFT2D_FORWARD && dir != FFT2D_INVERSE)
         return FFT2D_ERR_ARG;
-    if (dtype != FFT2D_C64 && dtype != FFT2D_C32H)
+    if (dtype != FFT2D_C64 && dtype != FFT2D_C32H && dtype != FFT2D_R32_DCT2)
         return FFT2D_ERR_ARG;
-    if (dtype == FFT2D_C32H && (rows < 2 || cols < 2))
+    if ((dtype == FFT2D_C32H || dtype == FFT2D_R32_DCT2) && (rows < 2 || cols < 2))
+        return FFT2D_ERR_UNSUPPORTED;
+    if (dtype == FFT2D_R32_DCT2 && dir != FFT2D_FORWARD)
         return FFT2D_ERR_UNSUPPORTED;
     fft2d_plan_s *p = new (std::nothrow) fft2d_plan_s();
     if (!p)
@@ -675,6 +723,24 @@ fft2d_status fft2d_plan(int rows, int cols, int dtype, int dir, fft2d_plan_t *ou
             return FFT2D_ERR_OOM;
         }
     }
+    if (dtype == FFT2D_R32_DCT2) {
+        const std::vector<float2> pr = dct_post_table(p->Lc), pc = dct_post_table(p->Lr);
+        e = cudaMalloc(&p->post_rows, pr.size() * sizeof(float2));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&p->post_cols, pc.size() * sizeof(float2));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p->post_rows, pr.data(), pr.size() * sizeof(float2),
+                           cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p->post_cols, pc.data(), pc.size() * sizeof(float2),
+                           cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            fft2d_destroy(p);
+            return cuda_fail(e, "DCT post-rotation tables");
+        }
+        *out = p;
+        return FFT2D_OK;
+    }
     apply_tuned(p);
     *out = p;
     return FFT2D_OK;
@@ -682,7 +748,7 @@ fft2d_status fft2d_plan(int rows, int cols, int dtype, int dir, fft2d_plan_t *ou
 
 fft2d_status fft2d_autotune(fft2d_plan_t p, void *stream)
 {
-    if (!p)
+    if (!p || p->dtype == FFT2D_R32_DCT2)
         return FFT2D_ERR_ARG;
     fft2d_status s = check_device(p);
     if (s != FFT2D_OK)
@@ -868,7 +934,8 @@ const char *fft2d_variant_name(int pass, int L, int index)
 
 fft2d_status fft2d_plan_set_variant(fft2d_plan_t p, int pass, int variant)
 {
-    if (!p || (pass != FFT2D_PASS_ROWS && pass != FFT2D_PASS_COLS))
+    if (!p || (pass != FFT2D_PASS_ROWS && pass != FFT2D_PASS_COLS) ||
+        p->dtype == FFT2D_R32_DCT2)
         return FFT2D_ERR_ARG;
     const int L = pass == FFT2D_PASS_ROWS ? p->Lc : p->Lr;
     if (variant < -1 || variant >= fft2d_variant_count(pass, L) + (L == 0 ? 1 : 0))
@@ -884,6 +951,11 @@ fft2d_status fft2d_plan_describe(fft2d_plan_t p, char *buf, int len)
 {
     if (!p || !buf || len <= 0)
         return FFT2D_ERR_ARG;
+    if (p->dtype == FFT2D_R32_DCT2) {
+        std::snprintf(buf, (size_t)len, "rows:dct2(lines=%d,points=%d) cols:dct2(lines=%d,points=%d)",
+                      p->rows / 2, p->cols, p->cols / 2, p->rows);
+        return FFT2D_OK;
+    }
     std::string out;
     for (int pass = 0; pass < 2; pass++) {
         const int L = pass == FFT2D_PASS_ROWS ? p->Lc : p->Lr;
@@ -918,6 +990,8 @@ fft2d_status fft2d_destroy(fft2d_plan_t p)
     cudaFree(p->dev_err);
     if (p->exp_rows)
         cudaFree(p->exp_rows);
+    cudaFree(p->post_rows);
+    cudaFree(p->post_cols);
     if (p->staging)
         cudaFree(p->staging);
     delete p;
@@ -986,7 +1060,7 @@ fft2d_status fft2d_plan_info(fft2d_plan_t p, int *rows, int *cols, int *dtype, i
 
 fft2d_status fft2d_exec(fft2d_plan_t p, const void *in, void *out, void *stream)
 {
-    if (!p || !in || !out || p->dtype != FFT2D_C64)
+    if (!p || !in || !out || (p->dtype != FFT2D_C64 && p->dtype != FFT2D_R32_DCT2))
         return FFT2D_ERR_ARG;
     fft2d_status s = check_device(p);
     if (s != FFT2D_OK)
@@ -1008,11 +1082,13 @@ fft2d_status fft2d_selftest_withheld_load(fft2d_plan_t p, const void *in, void *
 fft2d_status fft2d_exec_pass(fft2d_plan_t p, int pass, const void *in, void *out, void *stream)
 {
     if (!p || !in || !out || (pass != FFT2D_PASS_ROWS && pass != FFT2D_PASS_COLS) ||
-        p->dtype != FFT2D_C64)
+        (p->dtype != FFT2D_C64 && p->dtype != FFT2D_R32_DCT2))
         return FFT2D_ERR_ARG;
     fft2d_status s = check_device(p);
     if (s != FFT2D_OK)
         return s;
+    if (p->dtype == FFT2D_R32_DCT2)
+        return run_dct_pass(p, pass, in, out, static_cast<cudaStream_t>(stream));
     return run_pass(p, pass, in, out, -1, true, static_cast<cudaStream_t>(stream));
 }
 
@@ -1031,12 +1107,12 @@ fft2d_status fft2d_exec_stages(fft2d_plan_t p, const void *in, void *out, int ro
 
 fft2d_status fft2d_exec_host(fft2d_plan_t p, const void *in_host, void *out_host, void *stream)
 {
-    if (!p || !in_host || !out_host || p->dtype != FFT2D_C64)
+    if (!p || !in_host || !out_host || (p->dtype != FFT2D_C64 && p->dtype != FFT2D_R32_DCT2))
         return FFT2D_ERR_ARG;
     fft2d_status s = check_device(p);
     if (s != FFT2D_OK)
         return s;
-    const size_t bytes = (size_t)p->rows * p->cols * sizeof(float2);
+    const size_t bytes = image_bytes(p);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (!p->staging) {
         cudaError_t e = cudaMalloc(&p->staging, bytes);

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libfft2d.so")
 
 FFT2D_C64 = 0
 FFT2D_C32H = 1
+FFT2D_R32_DCT2 = 2
 FFT2D_FORWARD = -1
 FFT2D_INVERSE = 1
 FFT2D_PASS_ROWS = 0

@@ -27,6 +27,12 @@ def uniform_real(rows: int, cols: int, seed: int = 0) -> np.ndarray:
     return out
 
 
+def gray_real(rows: int, cols: int, seed: int = 0) -> np.ndarray:
+    """Real gray image (one float32 per pixel) ~ U[0, 1): the input of the
+    discrete cosine transform; the same draws as ``uniform_real``'s real part."""
+    return rng(seed).random((rows, cols), dtype=np.float32)
+
+
 def blob_image(rows: int, cols: int, seed: int = 0, nblobs: int = 8) -> np.ndarray:
     """Smooth background of Gaussian blobs plus U[0, 1) noise, imaginary 0.
 
