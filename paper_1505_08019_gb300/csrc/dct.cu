@@ -23,6 +23,8 @@
 //
 // Definition computed (unnormalised, the oracle's):
 //   X[k][l] = sum_m sum_n x[m][n] cos(pi k (2m+1) / (2R)) cos(pi l (2n+1) / (2C)).
+#include <cmath>
+
 #include "line_fft.cuh"
 #include "passes.h"
 
@@ -224,6 +226,510 @@ __global__ void __launch_bounds__(C::T, C::MINB) line_dct_kernel(const DctIO d,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Persistent TMA-fed column pass of the DCT (columns of 2^11 and 2^12 points,
+// tiles of W complex columns = 2W real columns).
+//
+// The reorder needs no gather table: two tensor maps see the image's even
+// rows and its odd rows (row stride 2 ld), so one TMA load brings
+// x[0], x[2], .., x[N-2] = v[0 .. N/2) in order (the "even region") and
+// another x[1], x[3], .., x[N-1] = v[N-1], v[N-2], .., v[N/2] (the "odd
+// region", reversed).  Group 0 then gathers v[i] scrambled from the even
+// region (i < N/2) or from odd-region slot N-1-i; which one is fixed by the
+// register index.  As in the complex column pass, the next tile's even rows
+// land in a prefetch region while the current tile is worked on and its odd
+// rows in the lower half of the tile region once the last group has read it.
+//
+// The last group holds rows lo + r 2^S0 of a unit.  Output k pairs with
+// N - k, i.e. unit lo with unit 2^S0 - lo (reversed r), so the units are
+// dealt out such that each thread owns both members of its pairs
+// (dct_unit_lo);
+// the pairing and rotation then run in registers.  Units with lo < 2^(S0-1)
+// leave through a staging buffer and one TMA store, the others with
+// per-thread stores.
+template <class C>
+struct DctCol {
+    using Gl = Grp<C, C::NG - 1>;
+    static constexpr int HALF = C::N / 2;                  // rows of one parity
+    static constexpr int BY = HALF < 256 ? HALF : 256;     // rows per block of a parity map
+    static constexpr int NZ = HALF / BY;
+    static constexpr int HVALS = HALF * C::W;              // values of one parity region
+    static constexpr int TW_OFF = C::E + HVALS;
+    static constexpr int SMEM_BYTES = (TW_OFF + C::N) * 8;
+    static constexpr uint32_t HBYTES = (uint32_t)HVALS * 8u;
+    static constexpr uint32_t TW_BYTES = (uint32_t)C::N * 8u;   // N-1 entries + padding
+    static constexpr int M = 1 << Gl::S0;                  // rows of one store block
+    static constexpr int QROWS = M / 2;
+    static_assert(C::LB == 1 && C::NG >= 2, "one line block, two stage groups at least");
+    static_assert(M == 256, "store blocks are the 256-row blocks of the store map");
+    static_assert(((C::T * (Gl::V / 2)) >> C::KW) == QROWS, "threads cover half the row offsets");
+    static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
+};
+
+// The last stage group of a line: unit lo (0 <= lo < M = 2^S0) holds rows
+// lo + M r, r < R.  Output k pairs with N - k, i.e. row lo + M r of unit lo
+// with row (M - lo) + M (R-1-r) of unit M - lo (unit 0 pairs with itself,
+// r with R - r).  The M units of a line are dealt out V to a thread so that
+// every pair stays inside one thread: with Q = 2M/V, thread j (0 <= j < M/V)
+// takes, for t < V/2, the offsets t Q + j (register unit 2t) and t Q + Q - j
+// (unit 2t+1) -- unit 2t pairs with unit 2(V/2-1-t)+1 -- and thread 0 the
+// offsets t Q and t Q + Q/2, which pair among themselves.
+template <class C>
+__device__ __forceinline__ int dct_unit_lo(int v, int j)
+{
+    using Gl = Grp<C, C::NG - 1>;
+    constexpr int Q = 2 * (1 << Gl::S0) / Gl::V;
+    const int t = v >> 1;
+    if (j != 0)
+        return t * Q + ((v & 1) ? Q - j : j);
+    return t * Q + ((v & 1) ? Q / 2 : 0);
+}
+
+// Whether unit v of every thread holds rows with offset below M/2.
+template <class C>
+__host__ __device__ constexpr bool dct_unit_low(int v)
+{
+    using Gl = Grp<C, C::NG - 1>;
+    return Gl::V == 2 ? v == 0 : (v >> 1) < Gl::V / 4;
+}
+
+// The rotations (cos, sin)(pi q / 32), q < 16, passed by value to the
+// paired kernels (they sit in the constant bank).  Row lo + M r of a line of
+// N = M R points needs (cos, sin)(pi (lo + M r) / (2N)), the table entry of
+// lo rotated by pi r / (2R) = pi q / 32 with q = r 16 / R: one complex
+// product instead of a table load per output pair.  Both factors are FP32
+// roundings of FP64 values, so the product is within a few units in the last
+// place of the exact rotation.
+struct DctRot {
+    float2 r[16];
+};
+
+__device__ __forceinline__ float2 rot_mul(float2 b, float2 t)
+{
+    return make_float2(b.x * t.x - b.y * t.y, b.y * t.x + b.x * t.y);
+}
+
+// Rows p of za and N - p of zb, cs = (cos, sin)(pi p / (2N)): the outputs at
+// both, from the one below N/2 (cos and sin swap between p and N - p).
+__device__ __forceinline__ void dct_pair_rows(float2 &za, float2 &zb, float2 cs, bool a_low,
+                                              float scale)
+{
+    float2 xk, xp;
+    if (a_low) {
+        dct_pair(za, zb, cs, scale, xk, xp);
+        za = xk;
+        zb = xp;
+    } else {
+        dct_pair(zb, za, make_float2(cs.y, cs.x), scale, xk, xp);
+        zb = xk;
+        za = xp;
+    }
+}
+
+// Units UA and UB (UA may equal UB) whose rows r and R-1-r pair, UA at an
+// offset whose rotation is `base`; rows r < RMAX of UA.
+template <class C, int UA, int UB, int RMAX>
+__device__ __forceinline__ void dct_pair_units(float2 (&a)[C::EPT], float2 base,
+                                               const DctRot &rot, float scale)
+{
+    using Gl = Grp<C, C::NG - 1>;
+    constexpr int R = Gl::R;
+#pragma unroll
+    for (int r = 0; r < RMAX; r++)
+        dct_pair_rows(a[UA * R + r], a[UB * R + R - 1 - r], rot_mul(base, rot.r[r * (16 / R)]),
+                      r < R / 2, scale);
+}
+
+// Unit U of offset 0: rows M r, pairs (r, R - r); rows 0 and N/2 pair with
+// themselves.
+template <class C, int U>
+__device__ __forceinline__ void dct_pair_unit0(float2 (&a)[C::EPT], const DctRot &rot,
+                                               float scale)
+{
+    using Gl = Grp<C, C::NG - 1>;
+    constexpr int R = Gl::R;
+    float2 xk, xp;
+    dct_pair(a[U * R], a[U * R], make_float2(1.f, 0.f), scale, xk, xp);
+    a[U * R] = xk;
+    dct_pair(a[U * R + R / 2], a[U * R + R / 2], rot.r[8], scale, xk, xp);
+    a[U * R + R / 2] = xk;
+#pragma unroll
+    for (int r = 1; r < R / 2; r++) {
+        dct_pair(a[U * R + r], a[U * R + R - r], rot.r[r * (16 / R)], scale, xk, xp);
+        a[U * R + r] = xk;
+        a[U * R + R - r] = xp;
+    }
+}
+
+template <class C, int T0>
+__device__ __forceinline__ void dct_pairs_j_side0(float2 (&a)[C::EPT], int j,
+                                                  const float2 *__restrict__ post,
+                                                  const DctRot &rot, float scale)
+{
+    using Gl = Grp<C, C::NG - 1>;
+    constexpr int V = Gl::V, Q = 2 * (1 << Gl::S0) / V, R = Gl::R;
+    if constexpr (T0 < V / 2) {
+        dct_pair_units<C, 2 * T0, 2 * (V / 2 - 1 - T0) + 1, R>(a, __ldg(post + T0 * Q + j), rot,
+                                                               scale);
+        dct_pairs_j_side0<C, T0 + 1>(a, j, post, rot, scale);
+    }
+}
+
+// Thread 0's units: side 0 (offsets t Q) pair t <-> V/2 - t, side 1
+// (offsets t Q + Q/2) pair t <-> V/2 - 1 - t.
+template <class C, int T0>
+__device__ __forceinline__ void dct_pairs_0(float2 (&a)[C::EPT], const float2 *__restrict__ post,
+                                            const DctRot &rot, float scale)
+{
+    using Gl = Grp<C, C::NG - 1>;
+    constexpr int V = Gl::V, Q = 2 * (1 << Gl::S0) / V, R = Gl::R;
+    if constexpr (T0 < V / 2) {
+        constexpr int P0 = V / 2 - T0, P1 = V / 2 - 1 - T0;
+        if constexpr (T0 == 0)
+            dct_pair_unit0<C, 0>(a, rot, scale);
+        else if constexpr (T0 < P0)
+            dct_pair_units<C, 2 * T0, 2 * P0, R>(a, __ldg(post + T0 * Q), rot, scale);
+        else if constexpr (T0 == P0)
+            dct_pair_units<C, 2 * T0, 2 * T0, R / 2>(a, __ldg(post + T0 * Q), rot, scale);
+        if constexpr (T0 < P1)
+            dct_pair_units<C, 2 * T0 + 1, 2 * P1 + 1, R>(a, __ldg(post + T0 * Q + Q / 2), rot,
+                                                         scale);
+        else if constexpr (T0 == P1)
+            dct_pair_units<C, 2 * T0 + 1, 2 * T0 + 1, R / 2>(a, __ldg(post + T0 * Q + Q / 2), rot,
+                                                             scale);
+        dct_pairs_0<C, T0 + 1>(a, post, rot, scale);
+    }
+}
+
+// Pair and rotate every output of the thread's last-group units (natural
+// order spectrum Z in, DCT outputs X out, same registers).  post: the
+// axis's table, read at the units' offsets only.
+template <class C>
+__device__ __forceinline__ void dct_pairs(float2 (&a)[C::EPT], int j,
+                                          const float2 *__restrict__ post, const DctRot &rot,
+                                          float scale)
+{
+    if (j != 0)
+        dct_pairs_j_side0<C, 0>(a, j, post, rot, scale);
+    else
+        dct_pairs_0<C, 0>(a, post, rot, scale);
+}
+
+// The table of (cos, sin)(pi q / 32), built once in FP64.
+const DctRot &dct_rot_table()
+{
+    static const DctRot t = [] {
+        DctRot r{};
+        for (int q = 0; q < 16; q++) {
+            const double ang = 3.14159265358979323846264338327950288 * q / 32.0;
+            r.r[q] = make_float2(q == 0 ? 1.f : (float)std::cos(ang), q == 0 ? 0.f : (float)std::sin(ang));
+        }
+        return r;
+    }();
+    return t;
+}
+
+// ---------------------------------------------------------------------------
+// Row pass with vector loads and the pairing in registers (rows of 2^10 ..
+// 2^14 points, 32 values per thread).  One 8-byte load at x[2i] of a real
+// row brings v[i] and v[N-1-i].  In group 0 a thread therefore takes the
+// units hib and 2^HB - 1 - hib of one line: position i = top + hib of the
+// first pairs with N-1-i of the second (register r <-> r ^ (R-1)), and
+// the loads of the two real rows of the complex line fill both units.  The
+// last group is dealt out as in the column pass (dct_unit_lo), so each
+// thread rotates its pairs (k, N-k) in registers and stores the two real
+// rows' outputs directly.
+template <class C>
+__global__ void __launch_bounds__(C::T, C::MINB) row_dct_kernel(const DctIO d,
+                                                                const float2 *__restrict__ tw,
+                                                                const float2 *__restrict__ post,
+                                                                const DctRot rot,
+                                                                long long nlines, float scale)
+{
+    using G0 = Grp<C, 0>;
+    using Gl = Grp<C, C::NG - 1>;
+    static_assert(C::KW == 0 && C::NG >= 2 && G0::V == 2, "rows, two stage groups, 2 units");
+    constexpr int HH = 1 << (G0::HB - 1);           // group-0 threads per line
+    constexpr int P = (1 << Gl::S0) / Gl::V;        // last-group threads per line
+    static_assert(HH * C::LB == C::T && P * C::LB == C::T, "threads cover the line blocks");
+    extern __shared__ float2 sm[];
+    const int tid = threadIdx.x;
+    const long long line0 = (long long)blockIdx.x * C::LB;
+    const long long nvalid = nlines - line0;
+    float2 a[C::EPT];
+    {
+        const int lb = tid / HH;
+        const int h = tid & (HH - 1);
+        const int h1 = 2 * HH - 1 - h;
+        const bool ok = lb < nvalid;
+        const float *ra = d.in + 2 * (line0 + lb) * d.cols;
+        const float *rb = ra + d.cols;
+#pragma unroll
+        for (int r = 0; r < G0::R; r += 2) {   // top(r) < N/2 exactly for even r
+            const int top = brev_c(r, G0::G) << G0::HB;
+            const int rc = r ^ (G0::R - 1);
+            float2 fa = make_float2(0.f, 0.f), fb = fa, ga = fa, gb = fa;
+            if (ok) {
+                fa = __ldg(reinterpret_cast<const float2 *>(ra + 2 * (top + h)));
+                fb = __ldg(reinterpret_cast<const float2 *>(rb + 2 * (top + h)));
+                ga = __ldg(reinterpret_cast<const float2 *>(ra + 2 * (top + h1)));
+                gb = __ldg(reinterpret_cast<const float2 *>(rb + 2 * (top + h1)));
+            }
+            a[r] = make_float2(fa.x, fb.x);                  // unit 0, position top + h
+            a[G0::R + rc] = make_float2(fa.y, fb.y);         // unit 1, N-1-(top + h)
+            a[G0::R + r] = make_float2(ga.x, gb.x);          // unit 1, position top + h1
+            a[rc] = make_float2(ga.y, gb.y);                 // unit 0, N-1-(top + h1)
+        }
+#pragma unroll
+        for (int v = 0; v < 2; v++)
+            run_stages<C, 0, false>(a, v, 0, tw, C::L);
+#pragma unroll
+        for (int v = 0; v < 2; v++) {
+            const int hi = brev_rt(v ? h1 : h, G0::HB);
+#pragma unroll
+            for (int r = 0; r < G0::R; r++)
+                sm[sidx<C>(lb, r | (hi << G0::G), 0)] = a[v * G0::R + r];
+        }
+    }
+    __syncthreads();
+    if constexpr (C::NG >= 3) {
+        group_smem<C, 1, false>(a, sm, tw, C::L);
+        __syncthreads();
+    }
+    if constexpr (C::NG >= 4) {
+        group_smem<C, 2, false>(a, sm, tw, C::L);
+        __syncthreads();
+    }
+    const int lb = tid / P;
+    const int j = tid % P;
+#pragma unroll
+    for (int v = 0; v < Gl::V; v++) {
+        const int lo = dct_unit_lo<C>(v, j);
+#pragma unroll
+        for (int r = 0; r < Gl::R; r++)
+            a[v * Gl::R + r] = sm[sidx<C>(lb, lo | (r << Gl::S0), 0)];
+    }
+#pragma unroll
+    for (int v = 0; v < Gl::V; v++)
+        run_stages<C, C::NG - 1, false>(a, v, dct_unit_lo<C>(v, j), tw, C::L);
+    dct_pairs<C>(a, j, post, rot, scale);
+    if (lb >= nvalid)
+        return;
+    float *oa = d.out + 2 * (line0 + lb) * d.cols;
+    float *ob = oa + d.cols;
+#pragma unroll
+    for (int v = 0; v < Gl::V; v++) {
+        const int lo = dct_unit_lo<C>(v, j);
+#pragma unroll
+        for (int r = 0; r < Gl::R; r++) {
+            const int p = lo + (r << Gl::S0);
+            oa[p] = a[v * Gl::R + r].x;
+            ob[p] = a[v * Gl::R + r].y;
+        }
+    }
+}
+
+template <class C>
+cudaError_t row_dct_launch(const DctIO &d, const float2 *tw, const float2 *post, long long nlines,
+                           float scale, cudaStream_t s)
+{
+    auto k = row_dct_kernel<C>;
+    constexpr int bytes = C::SMEM_BYTES;
+    if (bytes > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess)
+            return e;
+    }
+    const unsigned grid = (unsigned)((nlines + C::LB - 1) / C::LB);
+    k<<<grid, C::T, bytes, s>>>(d, tw, post, dct_rot_table(), nlines, scale);
+    return cudaGetLastError();
+}
+
+// maps: even rows (me), odd rows (mo), each x = complex column, y = row
+// pair within a block of BY, z = block, box W x BY x NZ; omap: the output as
+// complex columns, x, row within a 256-row block, block, box W x 128 x N/256.
+template <class C>
+__global__ void __launch_bounds__(C::T, 1) col_dct_tma_kernel(
+    const __grid_constant__ CUtensorMap me, const __grid_constant__ CUtensorMap mo,
+    const __grid_constant__ CUtensorMap omap, float2 *out, long long ld, int ntiles,
+    const float2 *__restrict__ tw, const float2 *__restrict__ post, const DctRot rot, float scale,
+    int *err)
+{
+    using D = DctCol<C>;
+    using G0 = Grp<C, 0>;
+    using Gl = Grp<C, C::NG - 1>;
+    extern __shared__ __align__(1024) float2 sm[];
+    __shared__ __align__(8) uint64_t bar_even, bar_odd;
+    const int tid = threadIdx.x;
+    int tile = blockIdx.x;
+    float2 *pref = sm + C::E;          // even region
+    float2 *stw = sm + D::TW_OFF;      // rotation factors, loaded once
+    float2 *stage = sm + C::E / 2;     // staging half of the tile region
+    if (tid == 0) {
+        mbar_init(&bar_even, 1);
+        mbar_init(&bar_odd, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0 && tile < ntiles) {
+        mbar_expect_tx(&bar_even, D::TW_BYTES);
+        bulk_load(stw, tw, D::TW_BYTES, &bar_even);
+        mbar_arrive_expect_tx(&bar_even, D::HBYTES);
+        tma_load_3d(pref, &me, tile * C::W, 0, 0, &bar_even);
+        mbar_arrive_expect_tx(&bar_odd, D::HBYTES);
+        tma_load_3d(sm, &mo, tile * C::W, 0, 0, &bar_odd);
+    }
+    uint32_t parity = 0;
+    const int j = tid >> C::KW;
+    float2 a[C::EPT];
+    for (; tile < ntiles; tile += gridDim.x) {
+        const int next = tile + gridDim.x;
+        const bool ok = mbar_wait_bounded(&bar_even, parity) && mbar_wait_bounded(&bar_odd, parity);
+        if (__syncthreads_or(ok ? 0 : 1)) {
+            if (tid == 0) {
+                atomicExch(err, kDevErrTmaTimeout);
+                bulk_wait_all();
+            }
+            mbar_wait_bounded(&bar_even, parity);
+            mbar_wait_bounded(&bar_odd, parity);
+            return;
+        }
+        parity ^= 1;
+        // group 0: v[i] from the even region (i < N/2) or odd-region slot N-1-i
+#pragma unroll
+        for (int v = 0; v < G0::V; v++) {
+            const int u = tid + v * C::T;
+            const int w = u & (C::W - 1);
+            const int hib = (u >> C::KW) & ((1 << G0::HB) - 1);
+#pragma unroll
+            for (int r = 0; r < G0::R; r++) {
+                const int i = (brev_c(r, G0::G) << G0::HB) | hib;
+                a[v * G0::R + r] = (brev_c(r, G0::G) << G0::HB) < D::HALF
+                                       ? pref[i * C::W + w]
+                                       : sm[(C::N - 1 - i) * C::W + w];
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < G0::V; v++)
+            run_stages<C, 0, false, true>(a, v, 0, stw, C::L);
+        fence_proxy_async_smem();
+        if (tid == 0)
+            bulk_wait_read_all();   // the previous tile's staging half is free
+        __syncthreads();            // both regions have been read
+        if (tid == 0 && next < ntiles) {
+            mbar_arrive_expect_tx(&bar_even, D::HBYTES);
+            tma_load_3d(pref, &me, next * C::W, 0, 0, &bar_even);
+        }
+#pragma unroll
+        for (int v = 0; v < G0::V; v++) {
+            const int u = tid + v * C::T;
+            const int w = u & (C::W - 1);
+            const int hib = (u >> C::KW) & ((1 << G0::HB) - 1);
+            const int hi = brev_rt(hib, G0::HB);
+#pragma unroll
+            for (int r = 0; r < G0::R; r++)
+                sm[sidx<C>(0, r | (hi << G0::G), w)] = a[v * G0::R + r];
+        }
+        __syncthreads();
+        if constexpr (C::NG >= 3) {
+            group_smem<C, 1, false, false, true>(a, sm, stw, C::L);
+            __syncthreads();
+        }
+        if constexpr (C::NG >= 4) {
+            group_smem<C, 2, false, false, true>(a, sm, stw, C::L);
+            __syncthreads();
+        }
+        // last group: units dealt out in pairs
+        const int w = tid & (C::W - 1);
+#pragma unroll
+        for (int v = 0; v < Gl::V; v++) {
+            const int lo = dct_unit_lo<C>(v, j);
+#pragma unroll
+            for (int r = 0; r < Gl::R; r++)
+                a[v * Gl::R + r] = sm[sidx<C>(0, lo | (r << Gl::S0), w)];
+        }
+        fence_proxy_async_smem();
+        __syncthreads();   // the tile region is free
+        if (tid == 0 && next < ntiles) {
+            mbar_arrive_expect_tx(&bar_odd, D::HBYTES);
+            tma_load_3d(sm, &mo, next * C::W, 0, 0, &bar_odd);
+        }
+#pragma unroll
+        for (int v = 0; v < Gl::V; v++)
+            run_stages<C, C::NG - 1, false, true>(a, v, dct_unit_lo<C>(v, j), stw, C::L);
+        dct_pairs<C>(a, j, post, rot, scale);
+        // units with row offsets below M/2: staging + one TMA store
+#pragma unroll
+        for (int v = 0; v < Gl::V; v++) {
+            if (!dct_unit_low<C>(v))
+                continue;
+            const int q = dct_unit_lo<C>(v, j) & (D::QROWS - 1);
+#pragma unroll
+            for (int r = 0; r < Gl::R; r++)
+                stage[((r * D::QROWS) | q) * C::W + w] = a[v * Gl::R + r];
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tma_store_3d(&omap, tile * C::W, 0, 0, stage);
+            bulk_commit();
+        }
+        // the others: per-thread stores
+#pragma unroll
+        for (int v = 0; v < Gl::V; v++) {
+            if (dct_unit_low<C>(v))
+                continue;
+            float2 *dst = out + (long long)dct_unit_lo<C>(v, j) * ld + (long long)tile * C::W + w;
+#pragma unroll
+            for (int r = 0; r < Gl::R; r++)
+                st_stream(dst + (long long)(r << Gl::S0) * ld, a[v * Gl::R + r]);
+        }
+    }
+    if (tid == 0)
+        bulk_wait_all();   // shared memory stays valid until the stores are done
+}
+
+// The TMA-fed DCT column pass when the image allows it: complex width a
+// multiple of W, 16-byte aligned buffers and table, a status word; returns
+// cudaErrorNotSupported otherwise (the caller then runs the plain kernel).
+template <class C>
+cudaError_t dct_col_tma_launch(const DctIO &d, const float2 *tw, const float2 *post, float scale,
+                               int *err, cudaStream_t s)
+{
+    using D = DctCol<C>;
+    const long long cc = d.cols / 2;   // complex columns
+    if (!err || cc % C::W != 0 || (reinterpret_cast<uintptr_t>(d.in) & 15) ||
+        (reinterpret_cast<uintptr_t>(d.out) & 15) || (reinterpret_cast<uintptr_t>(tw) & 15) ||
+        (cc * 8) % 16 != 0 || !tensor_maps_available())
+        return cudaErrorNotSupported;
+    const float2 *in = reinterpret_cast<const float2 *>(d.in);
+    float2 *out = reinterpret_cast<float2 *>(d.out);
+    CUtensorMap me, mo, omap;
+    if (!encode_map_xyz(&me, in, cc, D::BY, D::NZ, 2 * cc, 2 * cc * D::BY, C::W, D::BY, D::NZ) ||
+        !encode_map_xyz(&mo, in + cc, cc, D::BY, D::NZ, 2 * cc, 2 * cc * D::BY, C::W, D::BY,
+                        D::NZ) ||
+        !encode_map_xyz(&omap, out, cc, 256, C::N / 256, cc, cc * 256, C::W, D::QROWS,
+                        C::N / 256))
+        return cudaErrorNotSupported;
+    auto k = col_dct_tma_kernel<C>;
+    constexpr int SMEM = D::SMEM_BYTES;
+    static bool attr_set[64] = {};
+    const int dev = device_current();
+    if (!attr_set[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (e != cudaSuccess)
+            return e;
+        attr_set[dev] = true;
+    }
+    const int ntiles = (int)(cc / C::W);
+    int grid = device_sm_count();
+    if (grid > ntiles)
+        grid = ntiles;
+    k<<<grid, C::T, SMEM, s>>>(me, mo, omap, out, cc, ntiles, tw, post, dct_rot_table(), scale,
+                               err);
+    return cudaGetLastError();
+}
+
 template <class C, bool ROW>
 cudaError_t dct_launch(const DctIO &d, const float2 *tw, const float2 *post, long long nlines,
                        float scale, cudaStream_t s)
@@ -243,34 +749,44 @@ cudaError_t dct_launch(const DctIO &d, const float2 *tw, const float2 *post, lon
 
 template <int L>
 cudaError_t dct_dispatch(bool row, const DctIO &d, const float2 *tw, const float2 *post,
-                         float scale, cudaStream_t s)
+                         float scale, int *err, cudaStream_t s)
 {
-    if (row)
+    if (row) {
+        if constexpr (L >= 10)
+            return row_dct_launch<LineCfg<L, 0, row_kb(L), 32>>(d, tw, post, d.rows / 2, scale, s);
         return dct_launch<LineCfg<L, 0, row_kb(L)>, true>(d, tw, post, d.rows / 2, scale, s);
+    }
+    if constexpr (L == 11 || L == 12) {
+        const cudaError_t e =
+            dct_col_tma_launch<LineCfg<L, col_kw(L), 0, 32>>(d, tw, post, scale, err, s);
+        if (e != cudaErrorNotSupported)
+            return e;
+    }
     return dct_launch<LineCfg<L, col_kw(L), 0>, false>(d, tw, post, d.cols / 2, scale, s);
 }
 
 }  // namespace
 
 cudaError_t launch_dct_pass(bool row, int L, const float *in, float *out, int rows, int cols,
-                            const float2 *tw, const float2 *post, float scale, cudaStream_t s)
+                            const float2 *tw, const float2 *post, float scale, int *err,
+                            cudaStream_t s)
 {
     const DctIO d{in, out, rows, cols};
     switch (L) {
-    case 1: return dct_dispatch<1>(row, d, tw, post, scale, s);
-    case 2: return dct_dispatch<2>(row, d, tw, post, scale, s);
-    case 3: return dct_dispatch<3>(row, d, tw, post, scale, s);
-    case 4: return dct_dispatch<4>(row, d, tw, post, scale, s);
-    case 5: return dct_dispatch<5>(row, d, tw, post, scale, s);
-    case 6: return dct_dispatch<6>(row, d, tw, post, scale, s);
-    case 7: return dct_dispatch<7>(row, d, tw, post, scale, s);
-    case 8: return dct_dispatch<8>(row, d, tw, post, scale, s);
-    case 9: return dct_dispatch<9>(row, d, tw, post, scale, s);
-    case 10: return dct_dispatch<10>(row, d, tw, post, scale, s);
-    case 11: return dct_dispatch<11>(row, d, tw, post, scale, s);
-    case 12: return dct_dispatch<12>(row, d, tw, post, scale, s);
-    case 13: return dct_dispatch<13>(row, d, tw, post, scale, s);
-    case 14: return dct_dispatch<14>(row, d, tw, post, scale, s);
+    case 1: return dct_dispatch<1>(row, d, tw, post, scale, err, s);
+    case 2: return dct_dispatch<2>(row, d, tw, post, scale, err, s);
+    case 3: return dct_dispatch<3>(row, d, tw, post, scale, err, s);
+    case 4: return dct_dispatch<4>(row, d, tw, post, scale, err, s);
+    case 5: return dct_dispatch<5>(row, d, tw, post, scale, err, s);
+    case 6: return dct_dispatch<6>(row, d, tw, post, scale, err, s);
+    case 7: return dct_dispatch<7>(row, d, tw, post, scale, err, s);
+    case 8: return dct_dispatch<8>(row, d, tw, post, scale, err, s);
+    case 9: return dct_dispatch<9>(row, d, tw, post, scale, err, s);
+    case 10: return dct_dispatch<10>(row, d, tw, post, scale, err, s);
+    case 11: return dct_dispatch<11>(row, d, tw, post, scale, err, s);
+    case 12: return dct_dispatch<12>(row, d, tw, post, scale, err, s);
+    case 13: return dct_dispatch<13>(row, d, tw, post, scale, err, s);
+    case 14: return dct_dispatch<14>(row, d, tw, post, scale, err, s);
     default: return cudaErrorInvalidValue;
     }
 }

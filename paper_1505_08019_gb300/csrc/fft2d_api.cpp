@@ -216,7 +216,8 @@ fft2d_status run_dct_pass(const fft2d_plan_s *p, int pass, const void *in, void 
     cudaError_t e = fft2d::launch_dct_pass(row, row ? p->Lc : p->Lr, static_cast<const float *>(in),
                                            static_cast<float *>(out), p->rows, p->cols,
                                            row ? p->tw_rows : p->tw_cols,
-                                           row ? p->post_rows : p->post_cols, 1.0f, st);
+                                           row ? p->post_rows : p->post_cols, 1.0f,
+                                           p->dev_err, st);
     if (e != cudaSuccess)
         return cuda_fail(e, row ? "DCT row pass launch" : "DCT column pass launch");
     return FFT2D_OK;

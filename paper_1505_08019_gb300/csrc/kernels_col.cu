@@ -76,6 +76,25 @@ bool encode_col_map(CUtensorMap *map, const float2 *base, int rows, int cols, lo
            CUDA_SUCCESS;
 }
 
+bool encode_map_xyz(CUtensorMap *map, const void *base, long long xdim, int ydim, int zdim,
+                    long long ystride, long long zstride, int box_x, int box_y, int box_z)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || (reinterpret_cast<uintptr_t>(base) & 15) || ((ystride * 8) & 15) ||
+        ((zstride * 8) & 15))
+        return false;
+    cuuint64_t dims[3] = {(cuuint64_t)xdim, (cuuint64_t)ydim, (cuuint64_t)zdim};
+    cuuint64_t strides[2] = {(cuuint64_t)ystride * 8, (cuuint64_t)zstride * 8};
+    cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, (cuuint32_t)box_z};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<void *>(base), dims, strides,
+               box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+bool tensor_maps_available() { return tensor_map_encoder() != nullptr; }
+
 // One CTA waits, with the same bounded wait as the TMA pipeline, on an
 // mbarrier phase that nothing completes, then records the timeout.
 __global__ void selftest_timeout_kernel(int *err, unsigned long long limit_ns)

@@ -152,9 +152,20 @@ bool encode_col_map(CUtensorMap *map, const float2 *base, int rows, int cols, lo
 // (lines of rows = 2^L points).  Two real lines share one complex line of
 // the radix-2 engine.  tw: this axis's forward per-stage table; post: the
 // axis's (cos, sin)(pi k / (2N)), k = 0..N/2.  rows, cols >= 2; in may equal
-// out.
+// out.  err: the plan's device status word (bounded waits of the TMA-fed
+// column kernel).
 cudaError_t launch_dct_pass(bool row, int L, const float *in, float *out, int rows, int cols,
-                            const float2 *tw, const float2 *post, float scale, cudaStream_t s);
+                            const float2 *tw, const float2 *post, float scale, int *err,
+                            cudaStream_t s);
+
+// 3D tensor map over 8-byte elements: x = element within a row (xdim), y
+// (ydim rows, ystride elements apart), z (zdim blocks, zstride elements
+// apart); box box_x x box_y x box_z.  False if the driver's encoder is
+// missing or rejects the description (base 16-byte aligned, strides
+// multiples of 16 bytes).
+bool encode_map_xyz(CUtensorMap *map, const void *base, long long xdim, int ydim, int zdim,
+                    long long ystride, long long zstride, int box_x, int box_y, int box_z);
+bool tensor_maps_available();
 
 cudaError_t launch_row_pass(int L, const PassArgs &a, cudaStream_t s);
 

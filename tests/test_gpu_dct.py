@@ -82,10 +82,14 @@ def test_dct_small_shapes(env, rows, cols):
 
 
 @pytest.mark.parametrize("rows,cols", [(64, 256), (256, 64), (2, 1024), (1024, 2),
-                                       (512, 512), (128, 2048), (1024, 1024)])
+                                       (512, 512), (128, 2048), (1024, 1024),
+                                       (2048, 64), (4096, 32), (2048, 8), (4096, 4)])
 def test_dct_whole_outputs(env, rows, cols):
     """Non-square and wide/tall images spanning several CTAs and a partly
-    filled last CTA (2 rows: one complex line), whole outputs compared."""
+    filled last CTA (2 rows: one complex line), whole outputs compared.
+    Columns of 2048 and 4096 rows run on the TMA-fed column kernel when the
+    image is at least two tiles wide (64 and 32 columns here) and on the
+    plain kernel otherwise (8 and 4 columns)."""
     _, _, orc = env
     x = synth.gray_real(rows, cols, seed=7)
     err = rel(gpu_dct(env, x), orc.dct2d(x))
@@ -101,12 +105,13 @@ def test_dct_blob_in_place(env):
     assert err <= TOL, err
 
 
-def test_dct_single_passes(env):
+@pytest.mark.parametrize("rows,cols", [(64, 128), (16, 2048), (2048, 16), (8, 4096)])
+def test_dct_single_passes(env, rows, cols):
     """fft2d_exec_pass: the row pass alone is the 1D DCT-II of every row, the
     column pass alone that of every column; rows then columns is the 2D
     transform."""
     _, fft, orc = env
-    x = synth.gray_real(64, 128, seed=11)
+    x = synth.gray_real(rows, cols, seed=11)
     rows_only = np.stack([orc.dct1d(r) for r in x.astype(np.float64)])
     cols_only = np.stack([orc.dct1d(c) for c in x.astype(np.float64).T]).T
     assert rel(gpu_dct(env, x, passes=[fft.FFT2D_PASS_ROWS]), rows_only) <= TOL
@@ -141,6 +146,25 @@ def test_dct_large_sampled(env, side, nsamp):
         want = orc.dct2d_at(zm, k, l)
         assert abs(float(got[k, l]) - want) <= TOL * (4.0 * rms + abs(want)), \
             ("zero-mean", k, l, float(got[k, l]), want)
+
+
+@pytest.mark.parametrize("rows,cols", [(4096, 4096), (2048, 16384), (8192, 8192),
+                                       (16384, 512), (4096, 64)])
+def test_dct_separable_full(env, rows, cols):
+    """A separable image x[m][n] = f[m] g[n] (small integers: the products
+    are exact in FP32) has X[k][l] = F[k] G[l] with F, G the 1D transforms
+    of f and g, which the oracle computes cheaply: every output of a dense
+    full-size image is checked, in every column tile of every CTA."""
+    _, _, orc = env
+    g = np.random.default_rng(rows + cols)
+    f = g.integers(0, 16, rows).astype(np.float64)
+    h = g.integers(-8, 8, cols).astype(np.float64)
+    x = np.outer(f, h).astype(np.float32)
+    got = gpu_dct(env, x)
+    want = np.outer(orc.dct1d(f), orc.dct1d(h))
+    err = rel(got, want)
+    print(f"[dct] separable {rows}x{cols}: rel_l2={err:.3e}")
+    assert err <= TOL, err
 
 
 @pytest.mark.parametrize("rows,cols,k0,l0", [(4096, 4096, 37, 1900), (4096, 4096, 2048, 0),
