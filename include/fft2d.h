@@ -94,19 +94,23 @@ FFT2D_API fft2d_status fft2d_plan(int rows, int cols, int dtype, int dir, fft2d_
  * Section 5 names as a transform the method carries over to.  The image is
  * real, one float per pixel, row-major (pitch = cols); fft2d_exec and
  * fft2d_exec_pass (rows: in -> out, columns: in -> out; in may equal out)
- * compute the unnormalised DCT-II
+ * compute, with dir = FFT2D_FORWARD, the unnormalised DCT-II
  *   X[k][l] = sum_{m<rows} sum_{n<cols} x[m][n] cos(pi k (2m+1) / (2 rows))
  *                                               cos(pi l (2n+1) / (2 cols))
- * as one pass along the rows, then one along the columns, each on the
- * radix-2 engine: a length-N DCT-II is one length-N complex DFT of the
- * reordered line (even samples ascending, odd samples descending) followed
- * by a rotation by exp(-i pi k / (2N)) (Makhoul, 1980), and two real lines
- * share one complex line.  The plan also holds the (cos, sin)(pi k / (2N))
- * tables, built in FP64 and rounded to FP32.
- * Errors: FFT2D_ERR_UNSUPPORTED for a side of 1 or dir = FFT2D_INVERSE (the
- * inverse, DCT-III, is not provided).  The other entry points reject these
- * plans with FFT2D_ERR_ARG, except fft2d_exec_host, fft2d_plan_info,
- * fft2d_plan_describe, fft2d_sync_status and fft2d_destroy.
+ * and with dir = FFT2D_INVERSE its exact inverse, the DCT-III
+ *   x[m][n] = 1/(rows cols) sum_k sum_l e_k e_l X[k][l] cos(..) cos(..),
+ *   e_0 = 1, e_k = 2 (k > 0),
+ * as one pass along the rows, then one along the columns (whose pass
+ * carries the whole 1/(rows cols), as for the FFT), each on the radix-2
+ * engine: a length-N DCT-II is one length-N complex DFT of the reordered
+ * line (even samples ascending, odd samples descending) followed by a
+ * rotation by exp(-i pi k / (2N)) (Makhoul, 1980); the inverse rotates
+ * first, then runs the inverse DFT and undoes the reordering.  Two real
+ * lines share one complex line.  The plan also holds the
+ * (cos, sin)(pi k / (2N)) tables, built in FP64 and rounded to FP32.
+ * Errors: FFT2D_ERR_UNSUPPORTED for a side of 1.  The other entry points
+ * reject these plans with FFT2D_ERR_ARG, except fft2d_exec_host,
+ * fft2d_plan_info, fft2d_plan_describe, fft2d_sync_status and fft2d_destroy.
  */
 
 /*

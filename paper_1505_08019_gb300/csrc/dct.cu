@@ -266,6 +266,190 @@ struct DctCol {
     static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
 };
 
+// ---------------------------------------------------------------------------
+// Inverse (DCT-III, the oracle's x[n] = (1/N)(X[0] + 2 sum_k X[k]
+// cos(pi k (2n+1) / (2N)))) through one inverse DFT:
+//   V[k] = exp(i pi k / (2N)) (X[k] - i X[N-k])   (X[N] = 0),
+//   v = IDFT(V),  x[2n] = v[n],  x[2n+1] = v[N-1-n].
+// Two real lines a, b share the complex line z = X_a + i X_b; since the
+// IDFT is linear, Z[k] = V_a[k] + i V_b[k] gives v_a + i v_b:
+//   Z[k]   = (c + i s) ((X_a[k] + X_b[N-k]) + i (X_b[k] - X_a[N-k])),
+//   Z[N-k] = (s + i c) ((X_a[N-k] + X_b[k]) + i (X_b[N-k] - X_a[k])),
+// (c, s) = (cos, sin)(pi k / (2N)); Z[0] = z[0].
+__device__ __forceinline__ void idct_pre(float2 za, float2 zb, float2 cs, float2 &yk, float2 &yp)
+{
+    const float ux = za.x + zb.y, uy = za.y - zb.x;
+    const float vx = zb.x + za.y, vy = zb.y - za.x;
+    yk = make_float2(cs.x * ux - cs.y * uy, cs.y * ux + cs.x * uy);
+    yp = make_float2(cs.y * vx - cs.x * vy, cs.x * vx + cs.y * vy);
+}
+
+// The un-reordering store of v[n] and v[N-1-n] (n < N/2) of complex line lb
+// (rows: real rows 2(line0+lb), +1; columns: complex column line0 + w).
+template <bool ROW>
+__device__ __forceinline__ void idct_store(const DctIO &d, long long line0, int lb, int w, int n,
+                                           float2 zn, float2 zm, float scale)
+{
+    if constexpr (ROW) {
+        const long long ra = 2 * (line0 + lb);
+        reinterpret_cast<float2 *>(d.out + ra * d.cols)[n] = make_float2(zn.x * scale, zm.x * scale);
+        reinterpret_cast<float2 *>(d.out + (ra + 1) * d.cols)[n] =
+            make_float2(zn.y * scale, zm.y * scale);
+    } else {
+        float2 *o = reinterpret_cast<float2 *>(d.out) + line0 + w;
+        o[(long long)(2 * n) * (d.cols / 2)] = make_float2(zn.x * scale, zn.y * scale);
+        o[(long long)(2 * n + 1) * (d.cols / 2)] = make_float2(zm.x * scale, zm.y * scale);
+    }
+}
+
+// The inverse pass for any line length: the spectrum lines land in shared
+// memory in natural order, are pre-rotated in place (pairs k, N-k), run
+// through the radix-2 stages from there (conjugate rotation factors), come
+// back in natural order and leave un-reordered.
+template <class C, bool ROW>
+__global__ void __launch_bounds__(C::T, C::MINB) line_idct_kernel(const DctIO d,
+                                                                  const float2 *__restrict__ tw,
+                                                                  const float2 *__restrict__ post,
+                                                                  long long nlines, float scale)
+{
+    extern __shared__ float2 sm[];
+    constexpr int HALF = C::N / 2;
+    const int tid = threadIdx.x;
+    const long long line0 = (long long)blockIdx.x * (ROW ? C::LB : C::W);
+    const long long nvalid = nlines - line0;
+    for (int e = tid; e < C::E; e += C::T) {
+        const int w = e & (C::W - 1);
+        const int k = (e >> C::KW) & (C::N - 1);
+        const int lb = e >> (C::L + C::KW);
+        float2 z = make_float2(0.f, 0.f);
+        if (ROW ? lb < nvalid : w < nvalid) {
+            if constexpr (ROW) {
+                const long long ra = 2 * (line0 + lb);
+                z = make_float2(__ldg(d.in + ra * d.cols + k), __ldg(d.in + (ra + 1) * d.cols + k));
+            } else {
+                z = __ldg(reinterpret_cast<const float2 *>(d.in) + (long long)k * (d.cols / 2) +
+                          line0 + w);
+            }
+        }
+        sm[e] = z;
+    }
+    __syncthreads();
+    // pre-rotation: item q -> line block / column and k in [0, N/2); k = 0
+    // also handles k = N/2
+#pragma unroll
+    for (int t = 0; t < C::EPT / 2; t++) {
+        const int q = tid + t * C::T;
+        const int w = ROW ? 0 : q & (C::W - 1);
+        const int rest = ROW ? q : q >> C::KW;
+        const int lb = ROW ? rest / HALF : 0;
+        const int k = rest % HALF;
+        float2 *line = sm + ((long long)lb << (C::L + C::KW)) + w;
+        float2 yk, yp;
+        if (k == 0) {
+            const float2 zh = line[HALF << C::KW];
+            idct_pre(zh, zh, __ldg(post + HALF), yk, yp);
+            line[HALF << C::KW] = yk;
+        } else {
+            idct_pre(line[k << C::KW], line[(C::N - k) << C::KW], __ldg(post + k), yk, yp);
+            line[k << C::KW] = yk;
+            line[(C::N - k) << C::KW] = yp;
+        }
+    }
+    __syncthreads();
+    float2 a[C::EPT];
+    if constexpr (C::NG == 1) {
+        using G0 = Grp<C, 0>;
+#pragma unroll
+        for (int v = 0; v < G0::V; v++) {
+            const int u = tid + v * C::T;
+            const int w = u & (C::W - 1);
+            const int lb = u >> C::KW;
+#pragma unroll
+            for (int r = 0; r < G0::R; r++)
+                a[v * G0::R + r] = sm[(((lb << C::L) | brev_c(r, G0::G)) << C::KW) | w];
+            run_stages<C, 0, false>(a, v, 0, tw, C::L);
+            if (ROW ? lb >= nvalid : w >= nvalid)
+                continue;
+#pragma unroll
+            for (int n = 0; n < HALF; n++)
+                idct_store<ROW>(d, line0, lb, w, n, a[v * G0::R + n], a[v * G0::R + C::N - 1 - n],
+                                scale);
+        }
+    } else {
+        group_first_smem<C, false>(a, sm, tw, C::L);
+        __syncthreads();
+        if constexpr (C::NG >= 3) {
+            group_smem<C, 1, false>(a, sm, tw, C::L);
+            __syncthreads();
+        }
+        if constexpr (C::NG >= 4) {
+            group_smem<C, 2, false>(a, sm, tw, C::L);
+            __syncthreads();
+        }
+        using Gl = Grp<C, C::NG - 1>;
+#pragma unroll
+        for (int v = 0; v < Gl::V; v++) {
+            const int u = tid + v * C::T;
+            const int w = u & (C::W - 1);
+            const int u2 = u >> C::KW;
+            const int lo = u2 & ((1 << Gl::S0) - 1);
+            const int lb = u2 >> Gl::S0;
+#pragma unroll
+            for (int r = 0; r < Gl::R; r++)
+                a[v * Gl::R + r] = sm[sidx<C>(lb, lo | (r << Gl::S0), w)];
+        }
+#pragma unroll
+        for (int v = 0; v < Gl::V; v++) {
+            const int u = tid + v * C::T;
+            const int lo = (u >> C::KW) & ((1 << Gl::S0) - 1);
+            run_stages<C, C::NG - 1, false>(a, v, lo, tw, C::L);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int v = 0; v < Gl::V; v++) {
+            const int u = tid + v * C::T;
+            const int w = u & (C::W - 1);
+            const int u2 = u >> C::KW;
+            const int lo = u2 & ((1 << Gl::S0) - 1);
+            const int lb = u2 >> Gl::S0;
+#pragma unroll
+            for (int r = 0; r < Gl::R; r++)
+                sm[((((lb << C::L) | lo | (r << Gl::S0))) << C::KW) | w] = a[v * Gl::R + r];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < C::EPT / 2; t++) {
+            const int q = tid + t * C::T;
+            const int w = ROW ? 0 : q & (C::W - 1);
+            const int rest = ROW ? q : q >> C::KW;
+            const int lb = ROW ? rest / HALF : 0;
+            const int n = rest % HALF;
+            if (ROW ? lb >= nvalid : w >= nvalid)
+                continue;
+            const float2 *line = sm + ((long long)lb << (C::L + C::KW)) + w;
+            idct_store<ROW>(d, line0, lb, w, n, line[n << C::KW], line[(C::N - 1 - n) << C::KW],
+                            scale);
+        }
+    }
+}
+
+template <class C, bool ROW>
+cudaError_t idct_launch(const DctIO &d, const float2 *tw, const float2 *post, long long nlines,
+                        float scale, cudaStream_t s)
+{
+    auto k = line_idct_kernel<C, ROW>;
+    constexpr int bytes = C::E * 8;
+    if (bytes > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess)
+            return e;
+    }
+    const long long per = ROW ? C::LB : C::W;
+    const unsigned grid = (unsigned)((nlines + per - 1) / per);
+    k<<<grid, C::T, bytes, s>>>(d, tw, post, nlines, scale);
+    return cudaGetLastError();
+}
+
 // The last stage group of a line: unit lo (0 <= lo < M = 2^S0) holds rows
 // lo + M r, r < R.  Output k pairs with N - k, i.e. row lo + M r of unit lo
 // with row (M - lo) + M (R-1-r) of unit M - lo (unit 0 pairs with itself,
@@ -748,9 +932,14 @@ cudaError_t dct_launch(const DctIO &d, const float2 *tw, const float2 *post, lon
 }
 
 template <int L>
-cudaError_t dct_dispatch(bool row, const DctIO &d, const float2 *tw, const float2 *post,
-                         float scale, int *err, cudaStream_t s)
+cudaError_t dct_dispatch(bool row, bool inverse, const DctIO &d, const float2 *tw,
+                         const float2 *post, float scale, int *err, cudaStream_t s)
 {
+    if (inverse) {
+        if (row)
+            return idct_launch<LineCfg<L, 0, row_kb(L)>, true>(d, tw, post, d.rows / 2, scale, s);
+        return idct_launch<LineCfg<L, col_kw(L), 0>, false>(d, tw, post, d.cols / 2, scale, s);
+    }
     if (row) {
         if constexpr (L >= 10)
             return row_dct_launch<LineCfg<L, 0, row_kb(L), 32>>(d, tw, post, d.rows / 2, scale, s);
@@ -767,26 +956,26 @@ cudaError_t dct_dispatch(bool row, const DctIO &d, const float2 *tw, const float
 
 }  // namespace
 
-cudaError_t launch_dct_pass(bool row, int L, const float *in, float *out, int rows, int cols,
-                            const float2 *tw, const float2 *post, float scale, int *err,
+cudaError_t launch_dct_pass(bool row, bool inverse, int L, const float *in, float *out, int rows,
+                            int cols, const float2 *tw, const float2 *post, float scale, int *err,
                             cudaStream_t s)
 {
     const DctIO d{in, out, rows, cols};
     switch (L) {
-    case 1: return dct_dispatch<1>(row, d, tw, post, scale, err, s);
-    case 2: return dct_dispatch<2>(row, d, tw, post, scale, err, s);
-    case 3: return dct_dispatch<3>(row, d, tw, post, scale, err, s);
-    case 4: return dct_dispatch<4>(row, d, tw, post, scale, err, s);
-    case 5: return dct_dispatch<5>(row, d, tw, post, scale, err, s);
-    case 6: return dct_dispatch<6>(row, d, tw, post, scale, err, s);
-    case 7: return dct_dispatch<7>(row, d, tw, post, scale, err, s);
-    case 8: return dct_dispatch<8>(row, d, tw, post, scale, err, s);
-    case 9: return dct_dispatch<9>(row, d, tw, post, scale, err, s);
-    case 10: return dct_dispatch<10>(row, d, tw, post, scale, err, s);
-    case 11: return dct_dispatch<11>(row, d, tw, post, scale, err, s);
-    case 12: return dct_dispatch<12>(row, d, tw, post, scale, err, s);
-    case 13: return dct_dispatch<13>(row, d, tw, post, scale, err, s);
-    case 14: return dct_dispatch<14>(row, d, tw, post, scale, err, s);
+    case 1: return dct_dispatch<1>(row, inverse, d, tw, post, scale, err, s);
+    case 2: return dct_dispatch<2>(row, inverse, d, tw, post, scale, err, s);
+    case 3: return dct_dispatch<3>(row, inverse, d, tw, post, scale, err, s);
+    case 4: return dct_dispatch<4>(row, inverse, d, tw, post, scale, err, s);
+    case 5: return dct_dispatch<5>(row, inverse, d, tw, post, scale, err, s);
+    case 6: return dct_dispatch<6>(row, inverse, d, tw, post, scale, err, s);
+    case 7: return dct_dispatch<7>(row, inverse, d, tw, post, scale, err, s);
+    case 8: return dct_dispatch<8>(row, inverse, d, tw, post, scale, err, s);
+    case 9: return dct_dispatch<9>(row, inverse, d, tw, post, scale, err, s);
+    case 10: return dct_dispatch<10>(row, inverse, d, tw, post, scale, err, s);
+    case 11: return dct_dispatch<11>(row, inverse, d, tw, post, scale, err, s);
+    case 12: return dct_dispatch<12>(row, inverse, d, tw, post, scale, err, s);
+    case 13: return dct_dispatch<13>(row, inverse, d, tw, post, scale, err, s);
+    case 14: return dct_dispatch<14>(row, inverse, d, tw, post, scale, err, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -213,10 +213,14 @@ fft2d_status run_dct_pass(const fft2d_plan_s *p, int pass, const void *in, void 
 {
     fft2d::NvtxRange range(pass == FFT2D_PASS_ROWS ? "fft2d dct rows" : "fft2d dct cols");
     const bool row = pass == FFT2D_PASS_ROWS;
-    cudaError_t e = fft2d::launch_dct_pass(row, row ? p->Lc : p->Lr, static_cast<const float *>(in),
+    const bool inverse = p->dir == FFT2D_INVERSE;
+    // the inverse's 1/(rows cols) rides on the column pass, as for the FFT
+    const float scale = (inverse && !row) ? (float)(1.0 / ((double)p->rows * p->cols)) : 1.0f;
+    cudaError_t e = fft2d::launch_dct_pass(row, inverse, row ? p->Lc : p->Lr,
+                                           static_cast<const float *>(in),
                                            static_cast<float *>(out), p->rows, p->cols,
                                            row ? p->tw_rows : p->tw_cols,
-                                           row ? p->post_rows : p->post_cols, 1.0f,
+                                           row ? p->post_rows : p->post_cols, scale,
                                            p->dev_err, st);
     if (e != cudaSuccess)
         return cuda_fail(e, row ? "DCT row pass launch" : "DCT column pass launch");
@@ -661,8 +665,6 @@ fft2d_status fft2d_plan(int rows, int cols, int dtype, int dir, fft2d_plan_t *ou
     if (dtype != FFT2D_C64 && dtype != FFT2D_C32H && dtype != FFT2D_R32_DCT2)
         return FFT2D_ERR_ARG;
     if ((dtype == FFT2D_C32H || dtype == FFT2D_R32_DCT2) && (rows < 2 || cols < 2))
-        return FFT2D_ERR_UNSUPPORTED;
-    if (dtype == FFT2D_R32_DCT2 && dir != FFT2D_FORWARD)
         return FFT2D_ERR_UNSUPPORTED;
     fft2d_plan_s *p = new (std::nothrow) fft2d_plan_s();
     if (!p)

@@ -147,15 +147,16 @@ cudaError_t launch_batch_pass(bool row, int L, BatchTable &t, int variant, int *
 bool encode_col_map(CUtensorMap *map, const float2 *base, int rows, int cols, long long ld, int W,
                     int box_y, int box_z);
 
-// 2D DCT-II of a real FP32 image (dct.cu): one pass along the rows
-// (row = true: lines of cols = 2^L points, in -> out) or along the columns
-// (lines of rows = 2^L points).  Two real lines share one complex line of
-// the radix-2 engine.  tw: this axis's forward per-stage table; post: the
-// axis's (cos, sin)(pi k / (2N)), k = 0..N/2.  rows, cols >= 2; in may equal
-// out.  err: the plan's device status word (bounded waits of the TMA-fed
-// column kernel).
-cudaError_t launch_dct_pass(bool row, int L, const float *in, float *out, int rows, int cols,
-                            const float2 *tw, const float2 *post, float scale, int *err,
+// 2D DCT of a real FP32 image (dct.cu): one pass along the rows (row =
+// true: lines of cols = 2^L points, in -> out) or along the columns (lines
+// of rows = 2^L points), DCT-II forward or its inverse (DCT-III, unscaled:
+// the caller passes the 1/N factors in `scale`).  Two real lines share one
+// complex line of the radix-2 engine.  tw: this axis's per-stage table of
+// the direction (conjugated for the inverse); post: the axis's
+// (cos, sin)(pi k / (2N)), k = 0..N/2.  rows, cols >= 2; in may equal out.
+// err: the plan's device status word (bounded waits of the TMA-fed kernels).
+cudaError_t launch_dct_pass(bool row, bool inverse, int L, const float *in, float *out, int rows,
+                            int cols, const float2 *tw, const float2 *post, float scale, int *err,
                             cudaStream_t s);
 
 // 3D tensor map over 8-byte elements: x = element within a row (xdim), y

@@ -50,10 +50,11 @@ def rel(a, b):
     return float(np.linalg.norm((a - b).ravel()) / (d if d > 0 else 1.0))
 
 
-def gpu_dct(env, x, inplace=False, passes=None):
+def gpu_dct(env, x, inplace=False, passes=None, inverse=False):
     torch, fft, _ = env
     R, C = x.shape
-    plan = fft.fft2d_plan(R, C, fft.FFT2D_R32_DCT2, fft.FFT2D_FORWARD)
+    plan = fft.fft2d_plan(R, C, fft.FFT2D_R32_DCT2,
+                          fft.FFT2D_INVERSE if inverse else fft.FFT2D_FORWARD)
     try:
         dx = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
         out = dx if inplace else torch.empty_like(dx)
@@ -185,13 +186,11 @@ def test_dct_basis_image(env, rows, cols, k0, l0):
 
 
 def test_dct_plan_rules(env):
-    """DCT plans: inverse and sides of 1 are not provided; the complex-only
-    entry points refuse the plan; describe names the DCT passes."""
+    """DCT plans: sides of 1 are not provided; the complex-only entry points
+    refuse the plan; describe names the DCT passes."""
     torch, fft, _ = env
     import ctypes
     h = ctypes.c_void_p()
-    assert fft.lib.fft2d_plan(8, 8, fft.FFT2D_R32_DCT2, fft.FFT2D_INVERSE,
-                              ctypes.byref(h)) == fft.FFT2D_ERR_UNSUPPORTED
     assert fft.lib.fft2d_plan(1, 8, fft.FFT2D_R32_DCT2, fft.FFT2D_FORWARD,
                               ctypes.byref(h)) == fft.FFT2D_ERR_UNSUPPORTED
     plan = fft.fft2d_plan(16, 32, fft.FFT2D_R32_DCT2, fft.FFT2D_FORWARD)
@@ -218,3 +217,64 @@ def test_dct_host_buffers(env):
     finally:
         fft.fft2d_destroy(plan)
     assert rel(out, orc.dct2d(x)) <= TOL
+
+
+# ------------------------------------------------------------------ inverse
+@pytest.mark.parametrize("rows", [2, 4, 8, 16, 32])
+@pytest.mark.parametrize("cols", [2, 8, 32])
+def test_idct_small_shapes(env, rows, cols):
+    """DCT-III (the oracle's scaled inverse) of small spectra."""
+    _, _, orc = env
+    X = synth.gray_real(rows, cols, seed=rows * 31 + cols) - np.float32(0.5)
+    err = rel(gpu_dct(env, X, inverse=True), orc.dct2d(X, inverse=True))
+    assert err <= TOL, err
+
+
+@pytest.mark.parametrize("rows,cols", [(64, 256), (256, 64), (2, 1024), (1024, 2),
+                                       (512, 512), (2048, 64), (4096, 32), (128, 2048)])
+def test_idct_whole_outputs(env, rows, cols):
+    _, _, orc = env
+    X = synth.gray_real(rows, cols, seed=9) - np.float32(0.5)
+    err = rel(gpu_dct(env, X, inverse=True), orc.dct2d(X, inverse=True))
+    print(f"[idct] {rows}x{cols}: rel_l2={err:.3e}")
+    assert err <= TOL, err
+
+
+def test_idct_in_place_and_passes(env):
+    """In place; the row pass alone is the unscaled DCT-III of every row
+    (cols times the oracle's inverse), the column pass alone carries the
+    whole 1/(rows cols)."""
+    _, fft, orc = env
+    R, C = 64, 128
+    X = synth.gray_real(R, C, seed=4) - np.float32(0.5)
+    assert rel(gpu_dct(env, X, inplace=True, inverse=True), orc.dct2d(X, inverse=True)) <= TOL
+    X64 = X.astype(np.float64)
+    rows_only = np.stack([orc.dct1d(r, inverse=True) for r in X64]) * C
+    cols_only = np.stack([orc.dct1d(c, inverse=True) for c in X64.T]).T / C
+    assert rel(gpu_dct(env, X, passes=[fft.FFT2D_PASS_ROWS], inverse=True), rows_only) <= TOL
+    assert rel(gpu_dct(env, X, passes=[fft.FFT2D_PASS_COLS], inverse=True), cols_only) <= TOL
+
+
+@pytest.mark.parametrize("rows,cols", [(4096, 4096), (2048, 16384), (8192, 8192), (16384, 512)])
+def test_idct_separable_full(env, rows, cols):
+    """Separable spectrum F[k] G[l] (small integers): the inverse is the outer
+    product of the 1D inverses, every output checked."""
+    _, _, orc = env
+    g = np.random.default_rng(rows * 3 + cols)
+    f = g.integers(-8, 8, rows).astype(np.float64)
+    h = g.integers(-8, 8, cols).astype(np.float64)
+    X = np.outer(f, h).astype(np.float32)
+    got = gpu_dct(env, X, inverse=True)
+    want = np.outer(orc.dct1d(f, inverse=True), orc.dct1d(h, inverse=True))
+    err = rel(got, want)
+    print(f"[idct] separable {rows}x{cols}: rel_l2={err:.3e}")
+    assert err <= TOL, err
+
+
+@pytest.mark.parametrize("rows,cols", [(4096, 4096), (8192, 1024), (256, 16384)])
+def test_dct_round_trip(env, rows, cols):
+    """Forward then inverse on the GPU gives the image back."""
+    x = synth.gray_real(rows, cols, seed=12)
+    err = rel(gpu_dct(env, gpu_dct(env, x), inverse=True), x)
+    print(f"[dct] round trip {rows}x{cols}: rel_l2={err:.3e}")
+    assert err <= TOL, err
