@@ -931,13 +931,365 @@ cudaError_t dct_launch(const DctIO &d, const float2 *tw, const float2 *post, lon
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Fast inverse passes (rows of 2^10 .. 2^14 points; TMA-fed columns of 2^11
+// and 2^12 points).  The pre-rotation pairs spectrum entries k and N - k of
+// a line.  In the first stage group, position i = top(r) + hib (top(r) =
+// brev(r) 2^HB) pairs with N - i = top(r ^ (R-1)) + (2^HB - hib), so a
+// thread takes the units hib = h and 2^HB - h (h < 2^(HB-1)); thread 0 the
+// units 0 and 2^(HB-1), each paired with itself.  The rotation of position
+// top(r) + h is that of h turned by pi brev(r) / (2R) (a DctRot entry).
+template <class C>
+__device__ __forceinline__ void idct_pre_units(float2 (&a)[C::EPT], int h,
+                                               const float2 *__restrict__ post, const DctRot &rot)
+{
+    using G0 = Grp<C, 0>;
+    constexpr int R = G0::R, G = G0::G, HH = 1 << (G0::HB - 1), QS = 16 / R;
+    float2 yk, yp;
+    if (h != 0) {
+        const float2 b0 = __ldg(post + h), b1 = __ldg(post + (2 * HH - h));
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int rc = r ^ (R - 1);
+            if (brev_c(r, G) < R / 2) {
+                idct_pre(a[r], a[R + rc], rot_mul(b0, rot.r[brev_c(r, G) * QS]), yk, yp);
+                a[r] = yk;
+                a[R + rc] = yp;
+            } else {
+                idct_pre(a[R + rc], a[r], rot_mul(b1, rot.r[brev_c(rc, G) * QS]), yk, yp);
+                a[R + rc] = yk;
+                a[r] = yp;
+            }
+        }
+    } else {
+        // unit 0: positions brev(r) 2^HB; b <-> R - b, k = 0 left alone,
+        // k = N/2 (b = R/2) paired with itself
+#pragma unroll
+        for (int b = 1; b < R / 2; b++) {
+            const int r = brev_c(b, G), r2 = brev_c(R - b, G);
+            idct_pre(a[r], a[r2], rot.r[b * QS], yk, yp);
+            a[r] = yk;
+            a[r2] = yp;
+        }
+        idct_pre(a[brev_c(R / 2, G)], a[brev_c(R / 2, G)], rot.r[8], yk, yp);
+        a[brev_c(R / 2, G)] = yk;
+        // unit 1: positions top(r) + 2^(HB-1), pairs (r, r ^ (R-1))
+        const float2 bh = __ldg(post + HH);
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            if (brev_c(r, G) >= R / 2)
+                continue;
+            const int rc = r ^ (R - 1);
+            idct_pre(a[R + r], a[R + rc], rot_mul(bh, rot.r[brev_c(r, G) * QS]), yk, yp);
+            a[R + r] = yk;
+            a[R + rc] = yp;
+        }
+    }
+}
+
+// Inverse row pass: scalar loads of the two spectrum rows, pre-rotation in
+// registers, the stages, and a last group dealt out in complementary units
+// (offsets t Q + j and t Q + Q - 1 - j, Q = 2M/V): position n pairs with
+// N - 1 - n, so each thread writes x[2n] = v[n], x[2n+1] = v[N-1-n] of both
+// real rows with 8-byte stores.
+template <class C>
+__global__ void __launch_bounds__(C::T, C::MINB) row_idct_kernel(const DctIO d,
+                                                                 const float2 *__restrict__ tw,
+                                                                 const float2 *__restrict__ post,
+                                                                 const DctRot rot,
+                                                                 long long nlines, float scale)
+{
+    using G0 = Grp<C, 0>;
+    using Gl = Grp<C, C::NG - 1>;
+    static_assert(C::KW == 0 && C::NG >= 2 && G0::V == 2, "rows, two stage groups, 2 units");
+    constexpr int HH = 1 << (G0::HB - 1);
+    constexpr int M = 1 << Gl::S0, V = Gl::V, R = Gl::R, Q = 2 * M / V, P = M / V;
+    static_assert(HH * C::LB == C::T && P * C::LB == C::T, "threads cover the line blocks");
+    extern __shared__ float2 sm[];
+    const int tid = threadIdx.x;
+    const long long line0 = (long long)blockIdx.x * C::LB;
+    const long long nvalid = nlines - line0;
+    float2 a[C::EPT];
+    {
+        const int lb = tid / HH;
+        const int h = tid & (HH - 1);
+        const int h1 = h == 0 ? HH : 2 * HH - h;
+        const bool ok = lb < nvalid;
+        const float *ra = d.in + 2 * (line0 + lb) * d.cols;
+        const float *rb = ra + d.cols;
+#pragma unroll
+        for (int r = 0; r < G0::R; r++) {
+            const int top = brev_c(r, G0::G) << G0::HB;
+            a[r] = ok ? make_float2(__ldg(ra + top + h), __ldg(rb + top + h)) : make_float2(0.f, 0.f);
+            a[G0::R + r] = ok ? make_float2(__ldg(ra + top + h1), __ldg(rb + top + h1))
+                              : make_float2(0.f, 0.f);
+        }
+        idct_pre_units<C>(a, h, post, rot);
+#pragma unroll
+        for (int v = 0; v < 2; v++)
+            run_stages<C, 0, false>(a, v, 0, tw, C::L);
+#pragma unroll
+        for (int v = 0; v < 2; v++) {
+            const int hi = brev_rt(v ? h1 : h, G0::HB);
+#pragma unroll
+            for (int r = 0; r < G0::R; r++)
+                sm[sidx<C>(lb, r | (hi << G0::G), 0)] = a[v * G0::R + r];
+        }
+    }
+    __syncthreads();
+    if constexpr (C::NG >= 3) {
+        group_smem<C, 1, false>(a, sm, tw, C::L);
+        __syncthreads();
+    }
+    if constexpr (C::NG >= 4) {
+        group_smem<C, 2, false>(a, sm, tw, C::L);
+        __syncthreads();
+    }
+    const int lb = tid / P;
+    const int j = tid % P;
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+        const int lo = (v >> 1) * Q + ((v & 1) ? Q - 1 - j : j);
+#pragma unroll
+        for (int r = 0; r < R; r++)
+            a[v * R + r] = sm[sidx<C>(lb, lo | (r << Gl::S0), 0)];
+        run_stages<C, C::NG - 1, false>(a, v, lo, tw, C::L);
+    }
+    if (lb >= nvalid)
+        return;
+    float2 *oa = reinterpret_cast<float2 *>(d.out + 2 * (line0 + lb) * d.cols);
+    float2 *ob = reinterpret_cast<float2 *>(d.out + (2 * (line0 + lb) + 1) * d.cols);
+#pragma unroll
+    for (int t = 0; t < V / 2; t++) {
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const float2 za = a[(2 * t) * R + r];                       // n = t Q + j + M r
+            const float2 zb = a[(2 * (V / 2 - 1 - t) + 1) * R + R - 1 - r];   // N - 1 - n
+            if (r < R / 2) {
+                const int n = t * Q + j + M * r;
+                oa[n] = make_float2(za.x * scale, zb.x * scale);
+                ob[n] = make_float2(za.y * scale, zb.y * scale);
+            } else {
+                const int n = C::N - 1 - (t * Q + j + M * r);
+                oa[n] = make_float2(zb.x * scale, za.x * scale);
+                ob[n] = make_float2(zb.y * scale, za.y * scale);
+            }
+        }
+    }
+}
+
+template <class C>
+cudaError_t row_idct_launch(const DctIO &d, const float2 *tw, const float2 *post,
+                            long long nlines, float scale, cudaStream_t s)
+{
+    auto k = row_idct_kernel<C>;
+    constexpr int bytes = C::SMEM_BYTES;
+    if (bytes > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess)
+            return e;
+    }
+    const unsigned grid = (unsigned)((nlines + C::LB - 1) / C::LB);
+    k<<<grid, C::T, bytes, s>>>(d, tw, post, dct_rot_table(), nlines, scale);
+    return cudaGetLastError();
+}
+
+// Inverse column pass, persistent and TMA-fed like the complex column pass
+// (natural-order tiles, the next tile's first half prefetched).  Group 0
+// gathers the units of idct_pre_units from the tile and pre-rotates them;
+// the last group keeps the natural units.  Output row 2n takes v[n] and row
+// 2n+1 takes v[N-1-n]: the rows below N/2 of the transformed tile go
+// through a staging buffer and one TMA store over the even output rows
+// (row stride 2 ld), the others with per-thread stores to the odd rows.
+// maps: map (the input, 256-row blocks, box W x 256 x NB), oe (the even
+// output rows, box W x BY x NZ as DctCol).
+template <class C>
+__global__ void __launch_bounds__(C::T, 1) col_idct_tma_kernel(
+    const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap oe, float2 *out,
+    long long ld, int ntiles, const float2 *__restrict__ tw, const float2 *__restrict__ post,
+    const DctRot rot, float scale, int *err)
+{
+    using S = TmaSplit<C>;
+    using G0 = Grp<C, 0>;
+    using Gl = Grp<C, C::NG - 1>;
+    constexpr int HH = 1 << (G0::HB - 1);
+    static_assert(C::LB == 1 && C::NG >= 2 && G0::V == 2, "one line block, 2 group-0 units");
+    static_assert((C::T >> C::KW) == HH, "threads cover half the group-0 units");
+    static_assert((1 << G0::HB) <= S::BOX, "box index must depend on the register only");
+    static_assert(S::LATE_BYTES <= (uint32_t)C::E * 4u, "late boxes leave the staging half free");
+    extern __shared__ __align__(1024) float2 sm[];
+    __shared__ __align__(8) uint64_t bar_early, bar_late;
+    const int tid = threadIdx.x;
+    int tile = blockIdx.x;
+    const float2 *pref = sm + C::E;
+    float2 *stw = sm + S::TW_OFF;
+    float2 *stage = sm + C::E / 2;
+    if (tid == 0) {
+        mbar_init(&bar_early, 1);
+        mbar_init(&bar_late, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0 && tile < ntiles) {
+        mbar_expect_tx(&bar_early, S::TW_BYTES);
+        bulk_load(stw, tw, S::TW_BYTES, &bar_early);
+        split_issue_early<C>(sm, &map, tile * C::W, &bar_early);
+        split_issue_late<C>(sm, &map, tile * C::W, &bar_late);
+    }
+    uint32_t parity = 0;
+    const int w = tid & (C::W - 1);
+    const int h = tid >> C::KW;
+    const int h1 = h == 0 ? HH : 2 * HH - h;
+    float2 a[C::EPT];
+    for (; tile < ntiles; tile += gridDim.x) {
+        const int next = tile + gridDim.x;
+        const bool ok = mbar_wait_bounded(&bar_early, parity) && mbar_wait_bounded(&bar_late, parity);
+        if (__syncthreads_or(ok ? 0 : 1)) {
+            if (tid == 0) {
+                atomicExch(err, kDevErrTmaTimeout);
+                bulk_wait_all();
+            }
+            mbar_wait_bounded(&bar_early, parity);
+            mbar_wait_bounded(&bar_late, parity);
+            return;
+        }
+        parity ^= 1;
+#pragma unroll
+        for (int v = 0; v < 2; v++) {
+            const int hib = v ? h1 : h;
+#pragma unroll
+            for (int r = 0; r < G0::R; r++) {
+                const int top = brev_c(r, G0::G) << G0::HB;   // compile-time
+                const int k = top / S::BOX;
+                const float2 *bx = k < S::NB ? pref + k * S::BOX_VALS : sm + (k - S::NB) * S::BOX_VALS;
+                a[v * G0::R + r] = bx[((top % S::BOX) | hib) * C::W + w];
+            }
+        }
+        idct_pre_units<C>(a, h, post, rot);
+#pragma unroll
+        for (int v = 0; v < 2; v++)
+            run_stages<C, 0, false, true>(a, v, 0, stw, C::L);
+        fence_proxy_async_smem();
+        if (tid == 0)
+            bulk_wait_read_all();   // the previous tile's staging half is free
+        __syncthreads();            // both regions have been read
+        if (tid == 0 && next < ntiles)
+            split_issue_early<C>(sm, &map, next * C::W, &bar_early);
+#pragma unroll
+        for (int v = 0; v < 2; v++) {
+            const int hi = brev_rt(v ? h1 : h, G0::HB);
+#pragma unroll
+            for (int r = 0; r < G0::R; r++)
+                sm[sidx<C>(0, r | (hi << G0::G), w)] = a[v * G0::R + r];
+        }
+        __syncthreads();
+        if constexpr (C::NG >= 3) {
+            group_smem<C, 1, false, false, true>(a, sm, stw, C::L);
+            __syncthreads();
+        }
+        if constexpr (C::NG >= 4) {
+            group_smem<C, 2, false, false, true>(a, sm, stw, C::L);
+            __syncthreads();
+        }
+        group_last_read<C>(a, sm);
+        fence_proxy_async_smem();
+        __syncthreads();   // the tile region is free
+        if (tid == 0 && next < ntiles)
+            split_issue_late<C>(sm, &map, next * C::W, &bar_late);
+#pragma unroll
+        for (int v = 0; v < Gl::V; v++) {
+            const int u = tid + v * C::T;
+            const int lo = (u >> C::KW) & ((1 << Gl::S0) - 1);
+            run_stages<C, C::NG - 1, false, true>(a, v, lo, stw, C::L);
+        }
+        // positions below N/2 (r < R/2): staging slot p W + w, one TMA store
+#pragma unroll
+        for (int v = 0; v < Gl::V; v++) {
+            const int u = tid + v * C::T;
+            const int lo = (u >> C::KW) & ((1 << Gl::S0) - 1);
+#pragma unroll
+            for (int r = 0; r < Gl::R / 2; r++) {
+                const float2 x = a[v * Gl::R + r];
+                stage[(lo + (r << Gl::S0)) * C::W + w] = make_float2(x.x * scale, x.y * scale);
+            }
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tma_store_3d(&oe, tile * C::W, 0, 0, stage);
+            bulk_commit();
+        }
+        // the others: odd output rows 2 (N-1-p) + 1
+#pragma unroll
+        for (int v = 0; v < Gl::V; v++) {
+            const int u = tid + v * C::T;
+            const int lo = (u >> C::KW) & ((1 << Gl::S0) - 1);
+            float2 *dst = out + (long long)tile * C::W + w;
+#pragma unroll
+            for (int r = Gl::R / 2; r < Gl::R; r++) {
+                const int p = lo + (r << Gl::S0);
+                const float2 x = a[v * Gl::R + r];
+                st_stream(dst + (long long)(2 * (C::N - 1 - p) + 1) * ld,
+                          make_float2(x.x * scale, x.y * scale));
+            }
+        }
+    }
+    if (tid == 0)
+        bulk_wait_all();
+}
+
+template <class C>
+cudaError_t idct_col_tma_launch(const DctIO &d, const float2 *tw, const float2 *post, float scale,
+                                int *err, cudaStream_t s)
+{
+    using S = TmaSplit<C>;
+    using D = DctCol<C>;
+    const long long cc = d.cols / 2;
+    if (!err || cc % C::W != 0 || (reinterpret_cast<uintptr_t>(d.in) & 15) ||
+        (reinterpret_cast<uintptr_t>(d.out) & 15) || (reinterpret_cast<uintptr_t>(tw) & 15) ||
+        (cc * 8) % 16 != 0 || !tensor_maps_available())
+        return cudaErrorNotSupported;
+    const float2 *in = reinterpret_cast<const float2 *>(d.in);
+    float2 *out = reinterpret_cast<float2 *>(d.out);
+    CUtensorMap map, oe;
+    if (!encode_map_xyz(&map, in, cc, 256, C::N / 256, cc, cc * 256, C::W, S::BOX, S::NB) ||
+        !encode_map_xyz(&oe, out, cc, D::BY, D::NZ, 2 * cc, 2 * cc * D::BY, C::W, D::BY, D::NZ))
+        return cudaErrorNotSupported;
+    auto k = col_idct_tma_kernel<C>;
+    constexpr int SMEM = S::SMEM_BYTES;
+    static bool attr_set[64] = {};
+    const int dev = device_current();
+    if (!attr_set[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (e != cudaSuccess)
+            return e;
+        attr_set[dev] = true;
+    }
+    const int ntiles = (int)(cc / C::W);
+    int grid = device_sm_count();
+    if (grid > ntiles)
+        grid = ntiles;
+    k<<<grid, C::T, SMEM, s>>>(map, oe, out, cc, ntiles, tw, post, dct_rot_table(), scale, err);
+    return cudaGetLastError();
+}
+
 template <int L>
 cudaError_t dct_dispatch(bool row, bool inverse, const DctIO &d, const float2 *tw,
                          const float2 *post, float scale, int *err, cudaStream_t s)
 {
     if (inverse) {
-        if (row)
+        if (row) {
+            if constexpr (L >= 10)
+                return row_idct_launch<LineCfg<L, 0, row_kb(L), 32>>(d, tw, post, d.rows / 2,
+                                                                     scale, s);
             return idct_launch<LineCfg<L, 0, row_kb(L)>, true>(d, tw, post, d.rows / 2, scale, s);
+        }
+        if constexpr (L == 11 || L == 12) {
+            const cudaError_t e =
+                idct_col_tma_launch<LineCfg<L, col_kw(L), 0, 32>>(d, tw, post, scale, err, s);
+            if (e != cudaErrorNotSupported)
+                return e;
+        }
         return idct_launch<LineCfg<L, col_kw(L), 0>, false>(d, tw, post, d.cols / 2, scale, s);
     }
     if (row) {
