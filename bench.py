@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--fp16-sides", default="8192,16384",
                     help="fp16 workload: comma-separated square sides")
     ap.add_argument("--dct-sides", default="4096,8192",
-                    help="dct workload: comma-separated square sides")
+                    help="dct workload: comma-separated sides (S or RxC)")
     ap.add_argument("--side", type=int, default=SIDE)
     ap.add_argument("--e2e-steps", type=int, default=6)
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
@@ -785,7 +785,7 @@ def run_serve(args):
 def run_dct(args):
     """Unnormalised 2D DCT-II of real gray images (U[0,1), one float per
     pixel) through plans of dtype FFT2D_R32_DCT2, beside the forward complex64
-    FFT of the same side.  Four input/output pairs are used in turn, so that
+    FFT of the same shape.  Four input/output pairs are used in turn, so that
     consecutive launches do not find their image in L2.  Sampled outputs are
     checked against the oracle's direct double sum."""
     import torch
@@ -801,7 +801,11 @@ def run_dct(args):
     peak, peak_src = measured_hbm_peak()
     nbuf = 4
     results = {}
-    sides = [int(v) for v in args.dct_sides.split(",") if v]
+    shapes = []
+    for v in args.dct_sides.split(","):
+        if v:
+            r, _, c = v.partition("x")
+            shapes.append((int(r), int(c or r)))
 
     def t(fn, n):
         for i in range(3):
@@ -816,18 +820,18 @@ def run_dct(args):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / n
 
-    for side in sides:
-        x = synth.gray_real(side, side, seed=side)
+    for R, C in shapes:
+        x = synth.gray_real(R, C, seed=R + C)
         xs = [torch.from_numpy(x).cuda() for _ in range(nbuf)]
         ys = [torch.empty_like(xs[0]) for _ in range(nbuf)]
-        pd = fft.fft2d_plan(side, side, fft.FFT2D_R32_DCT2, fft.FFT2D_FORWARD)
-        reps = 40 if side <= 4096 else 16
+        pd = fft.fft2d_plan(R, C, fft.FFT2D_R32_DCT2, fft.FFT2D_FORWARD)
+        reps = 40 if R * C <= 4096 * 4096 else 16
         ms = t(lambda i: fft.fft2d_exec(pd, xs[i % nbuf], ys[i % nbuf], sptr), reps)
         ms_rows = t(lambda i: fft.fft2d_exec_pass(pd, fft.FFT2D_PASS_ROWS, xs[i % nbuf],
                                                   ys[i % nbuf], sptr), reps)
         ms_cols = t(lambda i: fft.fft2d_exec_pass(pd, fft.FFT2D_PASS_COLS, xs[i % nbuf],
                                                   ys[i % nbuf], sptr), reps)
-        pinv = fft.fft2d_plan(side, side, fft.FFT2D_R32_DCT2, fft.FFT2D_INVERSE)
+        pinv = fft.fft2d_plan(R, C, fft.FFT2D_R32_DCT2, fft.FFT2D_INVERSE)
         ims = t(lambda i: fft.fft2d_exec(pinv, xs[i % nbuf], ys[i % nbuf], sptr), reps)
         ims_rows = t(lambda i: fft.fft2d_exec_pass(pinv, fft.FFT2D_PASS_ROWS, xs[i % nbuf],
                                                    ys[i % nbuf], sptr), reps)
@@ -842,27 +846,27 @@ def run_dct(args):
         fft.fft2d_destroy(pinv)
         del xs, ys
         torch.cuda.empty_cache()
-        # the complex64 forward FFT of the same side, for comparison
-        zc = [torch.zeros((side, side), dtype=torch.complex64, device="cuda") for _ in range(2)]
-        pc = fft.fft2d_plan(side, side, fft.FFT2D_C64, fft.FFT2D_FORWARD)
+        # the complex64 forward FFT of the same shape, for comparison
+        zc = [torch.zeros((R, C), dtype=torch.complex64, device="cuda") for _ in range(2)]
+        pc = fft.fft2d_plan(R, C, fft.FFT2D_C64, fft.FFT2D_FORWARD)
         ms_fft = t(lambda i: fft.fft2d_exec(pc, zc[i % 2], zc[(i + 1) % 2], sptr), reps)
         fft.fft2d_destroy(pc)
         del zc
         torch.cuda.empty_cache()
         # sampled outputs against the direct double sum
-        g = np.random.default_rng(side)
-        idx = [(0, 0), (side // 2, side // 2), (side - 1, side - 1)] + \
-              [(int(a), int(b)) for a, b in zip(g.integers(0, side, 5), g.integers(0, side, 5))]
+        g = np.random.default_rng(R + C)
+        idx = [(0, 0), (R // 2, C // 2), (R - 1, C - 1)] + \
+              [(int(a), int(b)) for a, b in zip(g.integers(0, R, 5), g.integers(0, C, 5))]
         # the FP32 error bound of a radix-2 transform: u log2(n) ||X||_2, with
         # ||X||_2 <= sqrt(R C) ||x||_2 for the unnormalised DCT-II
-        bound = 2.0 ** -24 * np.log2(side * side) * side * float(
+        bound = 2.0 ** -24 * np.log2(R * C) * np.sqrt(R * C) * float(
             np.linalg.norm(x.astype(np.float64)))
         worst = 0.0
         for k, l in idx:
             want = orc.dct2d_at(x, k, l)
             worst = max(worst, abs(float(got[k, l]) - want) / bound)
-        px = side * side
-        results[f"{side}x{side}"] = {
+        px = R * C
+        results[f"{R}x{C}"] = {
             "dct_ms": ms, "dct_row_pass_ms": ms_rows, "dct_col_pass_ms": ms_cols,
             "dct_images_per_s": 1e3 / ms,
             "dct_hbm_frac": (16.0 * px / (ms * 1e-3) / 1e9) / peak,
@@ -877,18 +881,19 @@ def run_dct(args):
             "worst_sample_err_over_fp32_bound": worst,
             "kernels": fft.fft2d_plan_describe(pd)}
         fft.fft2d_destroy(pd)
-    head = results[f"{sides[0]}x{sides[0]}"]
+    R0, C0 = shapes[0]
+    head = results[f"{R0}x{C0}"]
     line = {"metric": "2D DCT-II images/s (real FP32 images)",
             "value": head["dct_images_per_s"], "unit": "images/s", "n_gpus": 1,
             "higher_is_better": True, "dtype": "f32",
             "data": "synthetic (seeded gray images, U[0,1))",
             "config": {"workload": "forward unnormalised 2D DCT-II at "
-                                   + ", ".join(f"{v}x{v}" for v in sides)
-                                   + f"; value = {sides[0]}^2 images/s; {nbuf} input/output "
+                                   + ", ".join(f"{r}x{c}" for r, c in shapes)
+                                   + f"; value = {R0}x{C0} images/s; {nbuf} input/output "
                                      "pairs used in turn (L2 not reused between launches)"},
             "roofline": {"bound": "hbm", "peak": peak, "unit": "GB/s", "peak_source": peak_src,
                          "algorithmic_bytes_per_px": 16,
-                         "achieved": 16.0 * sides[0] ** 2 / (head["dct_ms"] * 1e-3) / 1e9,
+                         "achieved": 16.0 * R0 * C0 / (head["dct_ms"] * 1e-3) / 1e9,
                          "frac": head["dct_hbm_frac"]},
             "per_size": results}
     print(json.dumps(line), flush=True)

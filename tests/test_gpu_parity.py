@@ -333,3 +333,32 @@ def test_bounded_wait_reports_timeout_and_context_survives(env):
         assert rel(out.cpu().numpy(), orc.fft2d(x)) <= TOL
     finally:
         fft.fft2d_destroy(plan)
+
+
+def table1_rows():
+    """Sizes and printed maximum errors of Table 1 (tests/golden/table1.txt)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "table1.txt")
+    rows = []
+    with open(path) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                side, _, _, err = line.split()
+                rows.append((int(side), float(err)))
+    return rows
+
+
+@pytest.mark.parametrize("side,paper_err", table1_rows())
+def test_table1_sizes_max_error(env, side, paper_err):
+    """At the sizes of Table 1, gray images in [0, 1): the largest error of
+    the image recovered by forward + inverse (the reading of the paper's
+    undefined "GPU maximum error" as an error in gray levels) stays far below
+    the printed 0.007, and the forward spectrum matches the oracle."""
+    _, _, orc = env
+    x = synth.uniform_real(side, side, seed=side)
+    X = gpu_fft(env, x, -1)
+    assert rel(X, orc.fft2d(x)) <= TOL
+    back = gpu_fft(env, X, 1)
+    max_err = float(np.abs(back.astype(np.complex128) - x.astype(np.complex128)).max())
+    print(f"[table1] {side}^2: max |ifft(fft(x)) - x| = {max_err:.2e} (paper: {paper_err})")
+    assert max_err <= paper_err / 100
