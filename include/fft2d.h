@@ -135,8 +135,10 @@ FFT2D_API fft2d_status fft2d_selftest_timeout(fft2d_plan_t plan, void *stream);
  * Self-test of the failure path of the persistent TMA-fed column kernels
  * (the tile pipeline that brings each column tile of Section 2's second 1D
  * transform into shared memory): runs the plan's column pass over `in` into
- * `out` (device complex64 images of the plan's shape, row pitch = cols),
- * except that CTA 0 never issues the second TMA load of its first tile.  That
+ * `out` (device images of the plan's shape and dtype, row pitch = cols;
+ * for FFT2D_R32_DCT2 plans the DCT column pass of the plan's direction,
+ * which is TMA-fed for columns of 2048 and 4096 points), except that CTA 0
+ * never issues the second TMA load of its first tile.  That
  * CTA's bounded wait gives up after about one second, the kernel records the
  * timeout -- for the CTA-pair kernel of 8192-row columns both CTAs of the
  * pair agree on it at their next cluster barrier and leave together -- lets
@@ -145,7 +147,9 @@ FFT2D_API fft2d_status fft2d_selftest_timeout(fft2d_plan_t plan, void *stream);
  * No GPU fault is involved and the context stays usable.
  * Errors: FFT2D_ERR_ARG for a null plan or pointer, a half2 plan, a plan with
  * one row, or when the column pass this plan would run (its variant, or the
- * default for its size, after the alignment checks) is not a TMA-fed kernel.
+ * default for its size, after the alignment checks) is not a TMA-fed kernel
+ * (for a DCT plan: columns of other lengths, or a width that is not a whole
+ * number of tiles).
  * Asynchronous on `stream`.
  */
 FFT2D_API fft2d_status fft2d_selftest_withheld_load(fft2d_plan_t plan, const void *in, void *out,

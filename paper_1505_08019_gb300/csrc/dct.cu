@@ -1,6 +1,7 @@
-// dct.cu -- the 2D discrete cosine transform (DCT-II) of real images on the
-// radix-2 passes: Section 5 names the DCT among the transforms the method
-// extends to, without giving an algorithm.  This file uses the well-known
+// dct.cu -- the 2D discrete cosine transform of real images on the radix-2
+// passes: the DCT-II forward and its inverse, the DCT-III (further down).
+// Section 5 names the DCT among the transforms the method extends to,
+// without giving an algorithm.  This file uses the well-known
 // reduction of a length-N DCT-II to one length-N complex DFT (Makhoul, IEEE
 // Trans. ASSP 1980), on the same scramble + butterfly engine as the FFT:
 //
@@ -23,6 +24,14 @@
 //
 // Definition computed (unnormalised, the oracle's):
 //   X[k][l] = sum_m sum_n x[m][n] cos(pi k (2m+1) / (2R)) cos(pi l (2n+1) / (2C)).
+//
+// Kernels, forward / inverse:
+//  * line_dct_kernel / line_idct_kernel: any line length, row or column
+//    pass; the pairing of outputs (k, N-k) goes through shared memory;
+//  * row_dct_kernel / row_idct_kernel: rows of 2^10 .. 2^14 points, 32
+//    values per thread, loads, pairing and stores in registers;
+//  * col_dct_tma_kernel / col_idct_tma_kernel: persistent TMA-fed column
+//    passes for columns of 2^11 and 2^12 points.
 #include <cmath>
 
 #include "line_fft.cuh"
@@ -737,7 +746,7 @@ __global__ void __launch_bounds__(C::T, 1) col_dct_tma_kernel(
     const __grid_constant__ CUtensorMap me, const __grid_constant__ CUtensorMap mo,
     const __grid_constant__ CUtensorMap omap, float2 *out, long long ld, int ntiles,
     const float2 *__restrict__ tw, const float2 *__restrict__ post, const DctRot rot, float scale,
-    int *err)
+    int *err, int withhold)
 {
     using D = DctCol<C>;
     using G0 = Grp<C, 0>;
@@ -760,8 +769,10 @@ __global__ void __launch_bounds__(C::T, 1) col_dct_tma_kernel(
         bulk_load(stw, tw, D::TW_BYTES, &bar_even);
         mbar_arrive_expect_tx(&bar_even, D::HBYTES);
         tma_load_3d(pref, &me, tile * C::W, 0, 0, &bar_even);
-        mbar_arrive_expect_tx(&bar_odd, D::HBYTES);
-        tma_load_3d(sm, &mo, tile * C::W, 0, 0, &bar_odd);
+        if (!(withhold && blockIdx.x == 0)) {   // self-test: the first odd rows never come
+            mbar_arrive_expect_tx(&bar_odd, D::HBYTES);
+            tma_load_3d(sm, &mo, tile * C::W, 0, 0, &bar_odd);
+        }
     }
     uint32_t parity = 0;
     const int j = tid >> C::KW;
@@ -878,7 +889,7 @@ __global__ void __launch_bounds__(C::T, 1) col_dct_tma_kernel(
 // cudaErrorNotSupported otherwise (the caller then runs the plain kernel).
 template <class C>
 cudaError_t dct_col_tma_launch(const DctIO &d, const float2 *tw, const float2 *post, float scale,
-                               int *err, cudaStream_t s)
+                               int *err, int withhold, cudaStream_t s)
 {
     using D = DctCol<C>;
     const long long cc = d.cols / 2;   // complex columns
@@ -910,7 +921,7 @@ cudaError_t dct_col_tma_launch(const DctIO &d, const float2 *tw, const float2 *p
     if (grid > ntiles)
         grid = ntiles;
     k<<<grid, C::T, SMEM, s>>>(me, mo, omap, out, cc, ntiles, tw, post, dct_rot_table(), scale,
-                               err);
+                               err, withhold);
     return cudaGetLastError();
 }
 
@@ -1107,7 +1118,7 @@ template <class C>
 __global__ void __launch_bounds__(C::T, 1) col_idct_tma_kernel(
     const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap oe, float2 *out,
     long long ld, int ntiles, const float2 *__restrict__ tw, const float2 *__restrict__ post,
-    const DctRot rot, float scale, int *err)
+    const DctRot rot, float scale, int *err, int withhold)
 {
     using S = TmaSplit<C>;
     using G0 = Grp<C, 0>;
@@ -1134,7 +1145,8 @@ __global__ void __launch_bounds__(C::T, 1) col_idct_tma_kernel(
         mbar_expect_tx(&bar_early, S::TW_BYTES);
         bulk_load(stw, tw, S::TW_BYTES, &bar_early);
         split_issue_early<C>(sm, &map, tile * C::W, &bar_early);
-        split_issue_late<C>(sm, &map, tile * C::W, &bar_late);
+        if (!(withhold && blockIdx.x == 0))   // self-test: the first late half never comes
+            split_issue_late<C>(sm, &map, tile * C::W, &bar_late);
     }
     uint32_t parity = 0;
     const int w = tid & (C::W - 1);
@@ -1240,7 +1252,7 @@ __global__ void __launch_bounds__(C::T, 1) col_idct_tma_kernel(
 
 template <class C>
 cudaError_t idct_col_tma_launch(const DctIO &d, const float2 *tw, const float2 *post, float scale,
-                                int *err, cudaStream_t s)
+                                int *err, int withhold, cudaStream_t s)
 {
     using S = TmaSplit<C>;
     using D = DctCol<C>;
@@ -1269,14 +1281,25 @@ cudaError_t idct_col_tma_launch(const DctIO &d, const float2 *tw, const float2 *
     int grid = device_sm_count();
     if (grid > ntiles)
         grid = ntiles;
-    k<<<grid, C::T, SMEM, s>>>(map, oe, out, cc, ntiles, tw, post, dct_rot_table(), scale, err);
+    k<<<grid, C::T, SMEM, s>>>(map, oe, out, cc, ntiles, tw, post, dct_rot_table(), scale, err,
+                               withhold);
     return cudaGetLastError();
 }
 
 template <int L>
 cudaError_t dct_dispatch(bool row, bool inverse, const DctIO &d, const float2 *tw,
-                         const float2 *post, float scale, int *err, cudaStream_t s)
+                         const float2 *post, float scale, int *err, int withhold, cudaStream_t s)
 {
+    if (withhold) {   // the self-test runs on the TMA-fed column kernels only
+        if (row)
+            return cudaErrorNotSupported;
+        if constexpr (L == 11 || L == 12)
+            return inverse ? idct_col_tma_launch<LineCfg<L, col_kw(L), 0, 32>>(d, tw, post, scale,
+                                                                                err, 1, s)
+                           : dct_col_tma_launch<LineCfg<L, col_kw(L), 0, 32>>(d, tw, post, scale,
+                                                                               err, 1, s);
+        return cudaErrorNotSupported;
+    }
     if (inverse) {
         if (row) {
             if constexpr (L >= 10)
@@ -1286,7 +1309,7 @@ cudaError_t dct_dispatch(bool row, bool inverse, const DctIO &d, const float2 *t
         }
         if constexpr (L == 11 || L == 12) {
             const cudaError_t e =
-                idct_col_tma_launch<LineCfg<L, col_kw(L), 0, 32>>(d, tw, post, scale, err, s);
+                idct_col_tma_launch<LineCfg<L, col_kw(L), 0, 32>>(d, tw, post, scale, err, 0, s);
             if (e != cudaErrorNotSupported)
                 return e;
         }
@@ -1299,7 +1322,7 @@ cudaError_t dct_dispatch(bool row, bool inverse, const DctIO &d, const float2 *t
     }
     if constexpr (L == 11 || L == 12) {
         const cudaError_t e =
-            dct_col_tma_launch<LineCfg<L, col_kw(L), 0, 32>>(d, tw, post, scale, err, s);
+            dct_col_tma_launch<LineCfg<L, col_kw(L), 0, 32>>(d, tw, post, scale, err, 0, s);
         if (e != cudaErrorNotSupported)
             return e;
     }
@@ -1310,24 +1333,24 @@ cudaError_t dct_dispatch(bool row, bool inverse, const DctIO &d, const float2 *t
 
 cudaError_t launch_dct_pass(bool row, bool inverse, int L, const float *in, float *out, int rows,
                             int cols, const float2 *tw, const float2 *post, float scale, int *err,
-                            cudaStream_t s)
+                            cudaStream_t s, int withhold)
 {
     const DctIO d{in, out, rows, cols};
     switch (L) {
-    case 1: return dct_dispatch<1>(row, inverse, d, tw, post, scale, err, s);
-    case 2: return dct_dispatch<2>(row, inverse, d, tw, post, scale, err, s);
-    case 3: return dct_dispatch<3>(row, inverse, d, tw, post, scale, err, s);
-    case 4: return dct_dispatch<4>(row, inverse, d, tw, post, scale, err, s);
-    case 5: return dct_dispatch<5>(row, inverse, d, tw, post, scale, err, s);
-    case 6: return dct_dispatch<6>(row, inverse, d, tw, post, scale, err, s);
-    case 7: return dct_dispatch<7>(row, inverse, d, tw, post, scale, err, s);
-    case 8: return dct_dispatch<8>(row, inverse, d, tw, post, scale, err, s);
-    case 9: return dct_dispatch<9>(row, inverse, d, tw, post, scale, err, s);
-    case 10: return dct_dispatch<10>(row, inverse, d, tw, post, scale, err, s);
-    case 11: return dct_dispatch<11>(row, inverse, d, tw, post, scale, err, s);
-    case 12: return dct_dispatch<12>(row, inverse, d, tw, post, scale, err, s);
-    case 13: return dct_dispatch<13>(row, inverse, d, tw, post, scale, err, s);
-    case 14: return dct_dispatch<14>(row, inverse, d, tw, post, scale, err, s);
+    case 1: return dct_dispatch<1>(row, inverse, d, tw, post, scale, err, withhold, s);
+    case 2: return dct_dispatch<2>(row, inverse, d, tw, post, scale, err, withhold, s);
+    case 3: return dct_dispatch<3>(row, inverse, d, tw, post, scale, err, withhold, s);
+    case 4: return dct_dispatch<4>(row, inverse, d, tw, post, scale, err, withhold, s);
+    case 5: return dct_dispatch<5>(row, inverse, d, tw, post, scale, err, withhold, s);
+    case 6: return dct_dispatch<6>(row, inverse, d, tw, post, scale, err, withhold, s);
+    case 7: return dct_dispatch<7>(row, inverse, d, tw, post, scale, err, withhold, s);
+    case 8: return dct_dispatch<8>(row, inverse, d, tw, post, scale, err, withhold, s);
+    case 9: return dct_dispatch<9>(row, inverse, d, tw, post, scale, err, withhold, s);
+    case 10: return dct_dispatch<10>(row, inverse, d, tw, post, scale, err, withhold, s);
+    case 11: return dct_dispatch<11>(row, inverse, d, tw, post, scale, err, withhold, s);
+    case 12: return dct_dispatch<12>(row, inverse, d, tw, post, scale, err, withhold, s);
+    case 13: return dct_dispatch<13>(row, inverse, d, tw, post, scale, err, withhold, s);
+    case 14: return dct_dispatch<14>(row, inverse, d, tw, post, scale, err, withhold, s);
     default: return cudaErrorInvalidValue;
     }
 }

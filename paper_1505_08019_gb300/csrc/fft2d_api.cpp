@@ -1074,11 +1074,27 @@ fft2d_status fft2d_exec(fft2d_plan_t p, const void *in, void *out, void *stream)
 fft2d_status fft2d_selftest_withheld_load(fft2d_plan_t p, const void *in, void *out,
                                           void *stream)
 {
-    if (!p || !in || !out || p->dtype != FFT2D_C64 || p->Lr == 0)
+    if (!p || !in || !out || (p->dtype != FFT2D_C64 && p->dtype != FFT2D_R32_DCT2) || p->Lr == 0)
         return FFT2D_ERR_ARG;
     fft2d_status s = check_device(p);
     if (s != FFT2D_OK)
         return s;
+    if (p->dtype == FFT2D_R32_DCT2) {
+        const bool inverse = p->dir == FFT2D_INVERSE;
+        const float scale = inverse ? (float)(1.0 / ((double)p->rows * p->cols)) : 1.0f;
+        cudaError_t e = fft2d::launch_dct_pass(false, inverse, p->Lr, static_cast<const float *>(in),
+                                               static_cast<float *>(out), p->rows, p->cols,
+                                               p->tw_cols, p->post_cols, scale, p->dev_err,
+                                               static_cast<cudaStream_t>(stream), 1);
+        if (e == cudaErrorNotSupported) {
+            std::snprintf(g_last_error, sizeof g_last_error,
+                          "the column pass of this plan does not run on a TMA-fed kernel");
+            return FFT2D_ERR_ARG;
+        }
+        if (e != cudaSuccess)
+            return cuda_fail(e, "DCT column pass launch");
+        return FFT2D_OK;
+    }
     return run_pass(p, FFT2D_PASS_COLS, in, out, -1, true, static_cast<cudaStream_t>(stream), 1);
 }
 

@@ -155,9 +155,12 @@ bool encode_col_map(CUtensorMap *map, const float2 *base, int rows, int cols, lo
 // the direction (conjugated for the inverse); post: the axis's
 // (cos, sin)(pi k / (2N)), k = 0..N/2.  rows, cols >= 2; in may equal out.
 // err: the plan's device status word (bounded waits of the TMA-fed kernels).
+// withhold (self-test, column pass only): run the TMA-fed column kernel with
+// CTA 0's first second-half load never issued; cudaErrorNotSupported when
+// this pass does not run on such a kernel.
 cudaError_t launch_dct_pass(bool row, bool inverse, int L, const float *in, float *out, int rows,
                             int cols, const float2 *tw, const float2 *post, float scale, int *err,
-                            cudaStream_t s);
+                            cudaStream_t s, int withhold = 0);
 
 // 3D tensor map over 8-byte elements: x = element within a row (xdim), y
 // (ydim rows, ystride elements apart), z (zdim blocks, zstride elements

@@ -278,3 +278,42 @@ def test_dct_round_trip(env, rows, cols):
     err = rel(gpu_dct(env, gpu_dct(env, x), inverse=True), x)
     print(f"[dct] round trip {rows}x{cols}: rel_l2={err:.3e}")
     assert err <= TOL, err
+
+
+@pytest.mark.parametrize("rows,inverse", [(4096, False), (2048, True)])
+def test_dct_withheld_load_times_out_cleanly(env, rows, inverse):
+    """Failure path of the TMA-fed DCT column kernels: CTA 0 never issues the
+    second load of its first tile, its bounded wait gives up, the host reads
+    FFT2D_ERR_TIMEOUT, and the same plan then transforms correctly."""
+    torch, fft, orc = env
+    cols = 64
+    plan = fft.fft2d_plan(rows, cols, fft.FFT2D_R32_DCT2,
+                          fft.FFT2D_INVERSE if inverse else fft.FFT2D_FORWARD)
+    try:
+        x = synth.gray_real(rows, cols, seed=rows) - np.float32(0.5)
+        dx = torch.from_numpy(x).cuda()
+        out = torch.empty_like(dx)
+        fft.fft2d_sync_status(plan)
+        fft.fft2d_selftest_withheld_load(plan, dx, out)
+        with pytest.raises(fft.FFT2DError) as ei:
+            fft.fft2d_sync_status(plan)
+        assert ei.value.status == fft.FFT2D_ERR_TIMEOUT
+        fft.fft2d_sync_status(plan)                      # cleared
+        fft.fft2d_exec(plan, dx, out)
+        fft.fft2d_sync_status(plan)
+        assert rel(out.cpu().numpy(), orc.dct2d(x, inverse=inverse)) <= TOL
+    finally:
+        fft.fft2d_destroy(plan)
+
+
+def test_dct_withheld_load_needs_a_tma_kernel(env):
+    """Columns of 1024 points (plain kernel): the self-test is refused."""
+    torch, fft, _ = env
+    plan = fft.fft2d_plan(1024, 64, fft.FFT2D_R32_DCT2, fft.FFT2D_FORWARD)
+    try:
+        dx = torch.zeros((1024, 64), device="cuda")
+        with pytest.raises(fft.FFT2DError) as ei:
+            fft.fft2d_selftest_withheld_load(plan, dx, dx)
+        assert ei.value.status == fft.FFT2D_ERR_ARG
+    finally:
+        fft.fft2d_destroy(plan)
