@@ -110,6 +110,7 @@ FFT2D_API fft2d_status fft2d_plan(int rows, int cols, int dtype, int dir, fft2d_
  * (cos, sin)(pi k / (2N)) tables, built in FP64 and rounded to FP32.
  * Errors: FFT2D_ERR_UNSUPPORTED for a side of 1.  The other entry points
  * reject these plans with FFT2D_ERR_ARG, except fft2d_exec_host,
+ * fft2d_exec_host_many(_async), fft2d_selftest_withheld_load,
  * fft2d_plan_info, fft2d_plan_describe, fft2d_sync_status and fft2d_destroy.
  */
 
@@ -244,7 +245,8 @@ FFT2D_API fft2d_status fft2d_exec_host(fft2d_plan_t plan, const void *in_host, v
  * pointer): its upload waits for that download, so a forward transform and
  * its inverse can travel in one call.  Otherwise the host buffers of
  * different images must not overlap.  The copies start after the work
- * already queued on `stream`.  complex64 plans of one device only.
+ * already queued on `stream`.  complex64 and DCT plans (FFT2D_R32_DCT2,
+ * 4-byte pixels) of one device only; both kinds may be mixed in one call.
  * Synchronous: every copy has finished on return, after a failure too.
  * Pinned host memory gives the full copy bandwidth (the NVLink-C2C host link
  * of a GB300 moved about 210 GB/s up, 190 GB/s down, 340 GB/s both at once).

@@ -1167,7 +1167,7 @@ fft2d_status host_many_enqueue(HostPipe &hp, int n, const fft2d_plan_t *plans,
     fft2d::NvtxRange range("fft2d host pipeline");
     size_t bytes = 0;
     for (int i = 0; i < n; i++) {
-        const size_t b = (size_t)plans[i]->rows * plans[i]->cols * sizeof(float2);
+        const size_t b = image_bytes(plans[i]);
         bytes = b > bytes ? b : bytes;
     }
     cudaError_t e = host_pipe_prepare(hp, bytes);
@@ -1197,7 +1197,7 @@ fft2d_status host_many_enqueue(HostPipe &hp, int n, const fft2d_plan_t *plans,
     for (int i = 0; i < n && result == FFT2D_OK; i++) {
         const int k = i % kHostSlots;
         const fft2d_plan_s *p = plans[i];
-        const size_t b = (size_t)p->rows * p->cols * sizeof(float2);
+        const size_t b = image_bytes(p);
         e = cudaStreamWaitEvent(hp.up, hp.freed[k], 0);
         for (int j = i - 1; j >= 0 && e == cudaSuccess; j--) {
             if (out_host[j] == in_host[i]) {
@@ -1249,7 +1249,8 @@ fft2d_status host_many_check(int n, const fft2d_plan_t *plans, const void *const
     if (n < 0 || (n > 0 && (!plans || !in_host || !out_host)))
         return FFT2D_ERR_ARG;
     for (int i = 0; i < n; i++) {
-        if (!plans[i] || !in_host[i] || !out_host[i] || plans[i]->dtype != FFT2D_C64)
+        if (!plans[i] || !in_host[i] || !out_host[i] ||
+            (plans[i]->dtype != FFT2D_C64 && plans[i]->dtype != FFT2D_R32_DCT2))
             return FFT2D_ERR_ARG;
         fft2d_status s = check_device(plans[i]);
         if (s != FFT2D_OK)

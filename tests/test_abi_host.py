@@ -49,6 +49,10 @@ def test_version_and_strerror(fft):
     (4, 1 << 15, 0, 1, 3),
     (8, 8, 0, 0, 1),             # bad direction
     (8, 8, 7, -1, 1),            # bad dtype
+    (1, 8, 2, -1, 8),            # DCT plan with a side of 1: not provided
+    (8, 1, 2, 1, 8),
+    (1, 8, 1, -1, 8),            # half2 plan with a side of 1: not provided
+    (6, 8, 2, -1, 2),            # DCT plan, side not a power of two
 ])
 def test_plan_argument_errors(fft, rows, cols, dtype, dir_, want):
     import ctypes

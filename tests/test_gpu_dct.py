@@ -317,3 +317,29 @@ def test_dct_withheld_load_needs_a_tma_kernel(env):
         assert ei.value.status == fft.FFT2D_ERR_ARG
     finally:
         fft.fft2d_destroy(plan)
+
+
+def test_dct_host_pipeline_mixed(env):
+    """fft2d_exec_host_many with DCT plans (forward, then the inverse of the
+    same buffer in one call) mixed with a complex64 FFT plan."""
+    torch, fft, orc = env
+    x = synth.gray_real(256, 512, seed=21)
+    z = synth.uniform_complex(128, 128, seed=22)
+    pf = fft.fft2d_plan(256, 512, fft.FFT2D_R32_DCT2, fft.FFT2D_FORWARD)
+    pi = fft.fft2d_plan(256, 512, fft.FFT2D_R32_DCT2, fft.FFT2D_INVERSE)
+    pc = fft.fft2d_plan(128, 128, fft.FFT2D_C64, fft.FFT2D_FORWARD)
+    try:
+        hx = torch.from_numpy(x).pin_memory()
+        hX = torch.empty_like(hx).pin_memory()
+        hback = torch.empty_like(hx).pin_memory()
+        hz = torch.from_numpy(z).pin_memory()
+        hZ = torch.empty_like(hz).pin_memory()
+        fft.fft2d_exec_host_many([pf, pc, pi], [hx, hz, hX], [hX, hZ, hback])
+        assert rel(hX.numpy(), orc.dct2d(x)) <= TOL
+        assert rel(hback.numpy(), x) <= TOL
+        zc = np.asarray(hZ.numpy(), np.complex128)
+        want = orc.fft2d(z)
+        assert float(np.linalg.norm(zc - want) / np.linalg.norm(want)) <= TOL
+    finally:
+        for p in (pf, pi, pc):
+            fft.fft2d_destroy(p)
