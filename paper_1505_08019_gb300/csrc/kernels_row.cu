@@ -8,6 +8,8 @@
 //   2  plain2x : twice the rows per CTA (two line blocks in flight)
 //   3  tma     : persistent, double-buffered TMA bulk loads (16-byte aligned,
 //                dense whole blocks only)
+//   4  split   : persistent, one row per CTA at a time with the next row's
+//                first half prefetched (rows of 4096..16384 points)
 #include "line_fft.cuh"
 #include "passes.h"
 
@@ -73,6 +75,141 @@ cudaError_t row_launch_tma(const PassArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Persistent row pass for long rows, one row (LB = 1) per CTA at a time.
+// Shared memory holds the row region (the exchange buffer) and a prefetch
+// region of half a row.  A row arrives as two bulk copies: its first half
+// into the prefetch region as soon as group 0 has gathered the previous row,
+// its second half into the lower half of the row region once the last group
+// has read the previous row from there.  Group 0 finds position i in the
+// prefetch region (i < N/2) or in the row region (i >= N/2); which one is
+// fixed by the register index.  Rotation factors come from global memory
+// (a 16384-point table is 128 KB).
+template <class C>
+struct RowSplit {
+    static constexpr int HALF = C::E / 2;
+    static constexpr int SMEM_BYTES = (C::E + HALF) * 8;
+    static constexpr uint32_t HALF_BYTES = (uint32_t)HALF * 8u;
+    static_assert(C::LB == 1 && C::KW == 0 && C::NG >= 2, "one row per CTA, two stage groups");
+    static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
+};
+
+template <class C>
+__device__ __forceinline__ void row_split_issue(float2 *dst, const float2 *src, uint64_t *bar)
+{
+    mbar_arrive_expect_tx(bar, RowSplit<C>::HALF_BYTES);
+    bulk_load(dst, src, RowSplit<C>::HALF_BYTES, bar);
+}
+
+template <class C>
+__global__ void __launch_bounds__(C::T, 1) row_split_kernel(const float2 *in, float2 *out,
+                                                            const float2 *__restrict__ tw,
+                                                            int rows, long long ld, float scale,
+                                                            int *err)
+{
+    using S = RowSplit<C>;
+    using G0 = Grp<C, 0>;
+    extern __shared__ __align__(128) float2 sm[];
+    __shared__ __align__(8) uint64_t bar_early, bar_late;
+    float2 *pref = sm + C::E;
+    const int tid = threadIdx.x;
+    int row = blockIdx.x;
+    if (tid == 0) {
+        mbar_init(&bar_early, 1);
+        mbar_init(&bar_late, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0 && row < rows) {
+        row_split_issue<C>(pref, in + (long long)row * ld, &bar_early);
+        row_split_issue<C>(sm, in + (long long)row * ld + S::HALF, &bar_late);
+    }
+    uint32_t parity = 0;
+    float2 a[C::EPT];
+    for (; row < rows; row += gridDim.x) {
+        const int next = row + gridDim.x;
+        const bool ok = mbar_wait_bounded(&bar_early, parity) && mbar_wait_bounded(&bar_late, parity);
+        if (__syncthreads_or(ok ? 0 : 1)) {
+            if (tid == 0)
+                atomicExch(err, kDevErrTmaTimeout);
+            mbar_wait_bounded(&bar_early, parity);
+            mbar_wait_bounded(&bar_late, parity);
+            return;
+        }
+        parity ^= 1;
+#pragma unroll
+        for (int v = 0; v < G0::V; v++) {
+            const int hib = (tid + v * C::T) & ((1 << G0::HB) - 1);
+#pragma unroll
+            for (int r = 0; r < G0::R; r++) {
+                const int top = brev_c(r, G0::G) << G0::HB;   // compile-time
+                a[v * G0::R + r] = top < S::HALF ? pref[top | hib] : sm[(top - S::HALF) | hib];
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < G0::V; v++)
+            run_stages<C, 0, false>(a, v, 0, tw, C::L);
+        fence_proxy_async_smem();
+        __syncthreads();   // both regions have been read
+        if (tid == 0 && next < rows)
+            row_split_issue<C>(pref, in + (long long)next * ld, &bar_early);
+#pragma unroll
+        for (int v = 0; v < G0::V; v++) {
+            const int hib = (tid + v * C::T) & ((1 << G0::HB) - 1);
+            const int hi = brev_rt(hib, G0::HB);
+#pragma unroll
+            for (int r = 0; r < G0::R; r++)
+                sm[sidx<C>(0, r | (hi << G0::G), 0)] = a[v * G0::R + r];
+        }
+        __syncthreads();
+        if constexpr (C::NG >= 3) {
+            group_smem<C, 1, false>(a, sm, tw, C::L);
+            __syncthreads();
+        }
+        if constexpr (C::NG >= 4) {
+            group_smem<C, 2, false>(a, sm, tw, C::L);
+            __syncthreads();
+        }
+        group_last_read<C>(a, sm);
+        fence_proxy_async_smem();
+        __syncthreads();   // the row region is free
+        if (tid == 0 && next < rows)
+            row_split_issue<C>(sm, in + (long long)next * ld + S::HALF, &bar_late);
+        group_last_finish<C, false>(a, out + (long long)row * ld, tw, 1, scale, C::L);
+    }
+}
+
+template <class C>
+bool row_split_usable(const PassArgs &a)
+{
+    return !a.partial && a.err && !(reinterpret_cast<uintptr_t>(a.in) & 15) &&
+           !((a.ld * 8) & 15);
+}
+
+template <class C>
+cudaError_t row_launch_split(const PassArgs &a, cudaStream_t s)
+{
+    constexpr int SMEM = RowSplit<C>::SMEM_BYTES;
+    auto k = row_split_kernel<C>;
+    constexpr int kMaxDev = 64;
+    static int occ[kMaxDev] = {};
+    const int d = device_current();
+    if (!occ[d]) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (e != cudaSuccess)
+            return e;
+        int o = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, C::T, SMEM);
+        if (e != cudaSuccess)
+            return e;
+        occ[d] = o > 0 ? o : 1;
+    }
+    int grid = device_sm_count() * occ[d];
+    if (grid > a.rows)
+        grid = a.rows;
+    k<<<grid, C::T, SMEM, s>>>(a.in, a.out, a.tw, a.rows, a.ld, a.scale, a.err);
+    return cudaGetLastError();
+}
+
 bool always(const PassArgs &) { return true; }
 bool whole_stages(const PassArgs &a) { return !a.partial; }
 
@@ -85,9 +222,10 @@ struct RowVariants {
     static constexpr bool HAS32 = L >= 5 && Plain32::E >= 32;
     static constexpr bool HAS2X = L >= 5 && L <= 13 && Plain2x::E * 8 <= 128 * 1024;
     static constexpr bool HASTMA = L >= 5 && L <= 13;
+    static constexpr bool HASSPLIT = L >= 12;
 
     struct Table {
-        Variant v[4];
+        Variant v[5];
         int n = 0;
     };
     static Table build()
@@ -100,6 +238,8 @@ struct RowVariants {
             t.v[t.n++] = {"plain2x", 1 << KB2, 16, whole_stages, row_launch_any<Plain2x>};
         if constexpr (HASTMA)
             t.v[t.n++] = {"tma", 1 << row_kb(L), 16, row_tma_usable<Plain>, row_launch_tma<Plain>};
+        if constexpr (HASSPLIT)
+            t.v[t.n++] = {"split", 1, 16, row_split_usable<Plain>, row_launch_split<Plain>};
         return t;
     }
     static const Variant *table(int *n)

@@ -53,7 +53,7 @@ def run(env, x, direction, row_variant=-1, col_variant=-1):
 
 
 SHAPES = [(64, 32), (512, 512), (1024, 2048), (2048, 4096), (4096, 4096), (8192, 256),
-          (256, 8192), (16384, 64), (64, 16384)]
+          (256, 8192), (16384, 64), (64, 16384), (1024, 8192), (512, 16384)]
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"{s[0]}x{s[1]}")
