@@ -243,7 +243,11 @@ FFT2D_API fft2d_status fft2d_exec_host(fft2d_plan_t plan, const void *in_host, v
  * in_host[i] == out_host[i] is allowed.  An image may read the output of an
  * earlier image of the same call (in_host[i] == out_host[j], j < i, the same
  * pointer): its upload waits for that download, so a forward transform and
- * its inverse can travel in one call.  Otherwise the host buffers of
+ * its inverse can travel in one call.  When that earlier image is the one
+ * just before (in_host[i] == out_host[i-1], images of the same byte size),
+ * image i is transformed straight from the device copy of that output and
+ * nothing is uploaded for it; its result is downloaded as usual.
+ * Otherwise the host buffers of
  * different images must not overlap.  The copies start after the work
  * already queued on `stream`.  complex64 and DCT plans (FFT2D_R32_DCT2,
  * 4-byte pixels) of one device only; both kinds may be mixed in one call.

@@ -1198,24 +1198,33 @@ fft2d_status host_many_enqueue(HostPipe &hp, int n, const fft2d_plan_t *plans,
         const int k = i % kHostSlots;
         const fft2d_plan_s *p = plans[i];
         const size_t b = image_bytes(p);
-        e = cudaStreamWaitEvent(hp.up, hp.freed[k], 0);
-        for (int j = i - 1; j >= 0 && e == cudaSuccess; j--) {
-            if (out_host[j] == in_host[i]) {
-                e = cudaStreamWaitEvent(hp.up, hp.image_out[j], 0);
-                break;
+        // an image whose input is the previous image's output (a forward
+        // transform followed by its inverse) starts from the device copy of
+        // that output, still in the previous slot: no upload
+        const bool chained = i > 0 && in_host[i] == out_host[i - 1] && b == image_bytes(plans[i - 1]);
+        const int kp = (i + kHostSlots - 1) % kHostSlots;
+        if (chained) {
+            e = cudaStreamWaitEvent(st, hp.freed[k], 0);
+        } else {
+            e = cudaStreamWaitEvent(hp.up, hp.freed[k], 0);
+            for (int j = i - 1; j >= 0 && e == cudaSuccess; j--) {
+                if (out_host[j] == in_host[i]) {
+                    e = cudaStreamWaitEvent(hp.up, hp.image_out[j], 0);
+                    break;
+                }
             }
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(hp.slot[k], in_host[i], b, cudaMemcpyHostToDevice, hp.up);
+            if (e == cudaSuccess)
+                e = cudaEventRecord(hp.in_ready[k], hp.up);
+            if (e == cudaSuccess)
+                e = cudaStreamWaitEvent(st, hp.in_ready[k], 0);
         }
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(hp.slot[k], in_host[i], b, cudaMemcpyHostToDevice, hp.up);
-        if (e == cudaSuccess)
-            e = cudaEventRecord(hp.in_ready[k], hp.up);
-        if (e == cudaSuccess)
-            e = cudaStreamWaitEvent(st, hp.in_ready[k], 0);
         if (e != cudaSuccess) {
             result = cuda_fail(e, "host pipeline upload");
             break;
         }
-        result = exec_impl(p, hp.slot[k], hp.slot[k], -1, -1, st);
+        result = exec_impl(p, chained ? hp.slot[kp] : hp.slot[k], hp.slot[k], -1, -1, st);
         if (result != FFT2D_OK)
             break;
         e = cudaEventRecord(hp.done[k], st);
@@ -1225,6 +1234,10 @@ fft2d_status host_many_enqueue(HostPipe &hp, int n, const fft2d_plan_t *plans,
             e = cudaMemcpyAsync(out_host[i], hp.slot[k], b, cudaMemcpyDeviceToHost, hp.down);
         if (e == cudaSuccess)
             e = cudaEventRecord(hp.freed[k], hp.down);
+        // the previous slot was read by this transform: it is free once this
+        // download (which follows the transform) is done
+        if (e == cudaSuccess && chained)
+            e = cudaEventRecord(hp.freed[kp], hp.down);
         if (e == cudaSuccess)
             e = cudaEventRecord(hp.image_out[i], hp.down);
         if (e != cudaSuccess)

@@ -149,9 +149,11 @@ def test_dct_large_sampled(env, side, nsamp):
             ("zero-mean", k, l, float(got[k, l]), want)
 
 
-@pytest.mark.parametrize("rows,cols", [(4096, 4096), (2048, 16384), (8192, 8192),
-                                       (16384, 512), (4096, 64)])
-def test_dct_separable_full(env, rows, cols):
+@pytest.mark.parametrize("rows,cols,inplace", [(4096, 4096, False), (2048, 16384, False),
+                                               (8192, 8192, False), (16384, 512, False),
+                                               (4096, 64, False), (2048, 1024, True),
+                                               (4096, 8192, True)])
+def test_dct_separable_full(env, rows, cols, inplace):
     """A separable image x[m][n] = f[m] g[n] (small integers: the products
     are exact in FP32) has X[k][l] = F[k] G[l] with F, G the 1D transforms
     of f and g, which the oracle computes cheaply: every output of a dense
@@ -161,7 +163,7 @@ def test_dct_separable_full(env, rows, cols):
     f = g.integers(0, 16, rows).astype(np.float64)
     h = g.integers(-8, 8, cols).astype(np.float64)
     x = np.outer(f, h).astype(np.float32)
-    got = gpu_dct(env, x)
+    got = gpu_dct(env, x, inplace=inplace)
     want = np.outer(orc.dct1d(f), orc.dct1d(h))
     err = rel(got, want)
     print(f"[dct] separable {rows}x{cols}: rel_l2={err:.3e}")
@@ -255,8 +257,10 @@ def test_idct_in_place_and_passes(env):
     assert rel(gpu_dct(env, X, passes=[fft.FFT2D_PASS_COLS], inverse=True), cols_only) <= TOL
 
 
-@pytest.mark.parametrize("rows,cols", [(4096, 4096), (2048, 16384), (8192, 8192), (16384, 512)])
-def test_idct_separable_full(env, rows, cols):
+@pytest.mark.parametrize("rows,cols,inplace", [(4096, 4096, False), (2048, 16384, False),
+                                               (8192, 8192, False), (16384, 512, False),
+                                               (2048, 1024, True), (4096, 8192, True)])
+def test_idct_separable_full(env, rows, cols, inplace):
     """Separable spectrum F[k] G[l] (small integers): the inverse is the outer
     product of the 1D inverses, every output checked."""
     _, _, orc = env
@@ -264,7 +268,7 @@ def test_idct_separable_full(env, rows, cols):
     f = g.integers(-8, 8, rows).astype(np.float64)
     h = g.integers(-8, 8, cols).astype(np.float64)
     X = np.outer(f, h).astype(np.float32)
-    got = gpu_dct(env, X, inverse=True)
+    got = gpu_dct(env, X, inverse=True, inplace=inplace)
     want = np.outer(orc.dct1d(f, inverse=True), orc.dct1d(h, inverse=True))
     err = rel(got, want)
     print(f"[idct] separable {rows}x{cols}: rel_l2={err:.3e}")

@@ -137,3 +137,56 @@ def test_async_calls_back_to_back(env):
     finally:
         fft.fft2d_destroy(pf)
         fft.fft2d_destroy(pi)
+
+
+def test_chained_images_skip_the_upload(env):
+    """An image whose input is the previous image's output is transformed
+    from the device copy of that output: the interleaved order (forward,
+    its inverse, next forward, ...) and a chain of three give the same bits
+    as separate calls, synchronous and asynchronous, with shapes that
+    change along the call."""
+    torch, fft, _ = env
+    shapes = [(1024, 1024), (512, 2048), (2048, 512), (256, 256), (1024, 1024)]
+    imgs = synth.batch_images(shapes, seed=33)
+    fwd = [fft.fft2d_plan(r, c, fft.FFT2D_C64, fft.FFT2D_FORWARD) for r, c in shapes]
+    inv = [fft.fft2d_plan(r, c, fft.FFT2D_C64, fft.FFT2D_INVERSE) for r, c in shapes]
+    try:
+        hin = [torch.from_numpy(im).pin_memory() for im in imgs]
+        mid = [torch.empty_like(h).pin_memory() for h in hin]
+        back = [torch.empty_like(h).pin_memory() for h in hin]
+        fft.fft2d_exec_host_many(fwd, hin, mid)
+        fft.fft2d_exec_host_many(inv, mid, back)
+        want_fwd = [m.numpy().copy() for m in mid]
+        want_rt = [b.numpy().copy() for b in back]
+        again = [torch.empty_like(h).pin_memory() for h in hin]
+        fft.fft2d_exec_host_many(fwd, back, again)
+        want_again = [a.numpy().copy() for a in again]
+
+        plans, ins, outs = [], [], []
+        mid2 = [torch.empty_like(h).pin_memory() for h in hin]
+        back2 = [torch.empty_like(h).pin_memory() for h in hin]
+        for i in range(len(shapes)):
+            plans += [fwd[i], inv[i]]
+            ins += [hin[i], mid2[i]]
+            outs += [mid2[i], back2[i]]
+        fft.fft2d_exec_host_many(plans, ins, outs)
+        for i in range(len(shapes)):
+            assert np.array_equal(mid2[i].numpy(), want_fwd[i]), f"forward {shapes[i]}"
+            assert np.array_equal(back2[i].numpy(), want_rt[i]), f"inverse {shapes[i]}"
+
+        # in place on the host, chains of three, several asynchronous calls
+        work = [torch.empty_like(h).pin_memory() for h in hin]
+        plans, ins, outs = [], [], []
+        for i in range(len(shapes)):
+            plans += [fwd[i], inv[i], fwd[i]]
+            ins += [hin[i], work[i], work[i]]
+            outs += [work[i], work[i], work[i]]
+        stream = torch.cuda.current_stream()
+        for _ in range(3):
+            fft.fft2d_exec_host_many_async(plans, ins, outs, stream.cuda_stream)
+        stream.synchronize()
+        for i in range(len(shapes)):
+            assert np.array_equal(work[i].numpy(), want_again[i]), f"chain of three {shapes[i]}"
+    finally:
+        for p in fwd + inv:
+            fft.fft2d_destroy(p)
