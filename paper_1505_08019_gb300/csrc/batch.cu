@@ -106,9 +106,9 @@ cudaError_t batch_launch_tma(const BatchTable &t, int *err, cudaStream_t s, bool
     auto k = col_tma2_batch_kernel<C, TS, TS && MODE == 2>;
     constexpr int SMEM = TmaSplit<C>::SMEM_BYTES;
     constexpr int kMaxDev = 64;
-    static int occ[kMaxDev] = {};
+    static DeviceCache occ;
     const int d = device_current();
-    if (!occ[d]) {
+    if (!occ.get(d)) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
         if (e != cudaSuccess)
             return e;
@@ -116,9 +116,9 @@ cudaError_t batch_launch_tma(const BatchTable &t, int *err, cudaStream_t s, bool
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, C::T, SMEM);
         if (e != cudaSuccess)
             return e;
-        occ[d] = o > 0 ? o : 1;
+        occ.set(d, o > 0 ? o : 1);
     }
-    int grid = device_sm_count() * occ[d];
+    int grid = device_sm_count() * occ.get(d);
     if (grid > tiles)
         grid = tiles;
     k<<<grid, C::T, SMEM, s>>>(tt, t.job[0].tw, err);

@@ -908,13 +908,13 @@ cudaError_t dct_col_tma_launch(const DctIO &d, const float2 *tw, const float2 *p
         return cudaErrorNotSupported;
     auto k = col_dct_tma_kernel<C>;
     constexpr int SMEM = D::SMEM_BYTES;
-    static bool attr_set[64] = {};
+    static DeviceCache attr_set;
     const int dev = device_current();
-    if (!attr_set[dev]) {
+    if (!attr_set.get(dev)) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
         if (e != cudaSuccess)
             return e;
-        attr_set[dev] = true;
+        attr_set.set(dev, 1);
     }
     const int ntiles = (int)(cc / C::W);
     int grid = device_sm_count();
@@ -1269,13 +1269,13 @@ cudaError_t idct_col_tma_launch(const DctIO &d, const float2 *tw, const float2 *
         return cudaErrorNotSupported;
     auto k = col_idct_tma_kernel<C>;
     constexpr int SMEM = S::SMEM_BYTES;
-    static bool attr_set[64] = {};
+    static DeviceCache attr_set;
     const int dev = device_current();
-    if (!attr_set[dev]) {
+    if (!attr_set.get(dev)) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
         if (e != cudaSuccess)
             return e;
-        attr_set[dev] = true;
+        attr_set.set(dev, 1);
     }
     const int ntiles = (int)(cc / C::W);
     int grid = device_sm_count();

@@ -47,14 +47,14 @@ int device_current()
 
 int device_sm_count()
 {
-    static int cache[kMaxDev] = {};
+    static DeviceCache cache;
     const int d = device_current();
-    if (!cache[d]) {
+    if (!cache.get(d)) {
         int n = 0;
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d);
-        cache[d] = n > 0 ? n : 1;
+        cache.set(d, n > 0 ? n : 1);
     }
-    return cache[d];
+    return cache.get(d);
 }
 
 
@@ -162,9 +162,9 @@ cudaError_t col_launch_tma(const PassArgs &a, cudaStream_t s)
         return col_launch_any<LineCfg<C::L, C::KW, 0>>(a, s);
     auto k = col_tma2_kernel<C, TS, HYB>;
     constexpr int SMEM = TmaSplit<C>::SMEM_BYTES;
-    static int occ[kMaxDev] = {};
+    static DeviceCache occ;
     const int d = current_device();
-    if (!occ[d]) {
+    if (!occ.get(d)) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              SMEM);
         if (e != cudaSuccess)
@@ -173,10 +173,10 @@ cudaError_t col_launch_tma(const PassArgs &a, cudaStream_t s)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, C::T, SMEM);
         if (e != cudaSuccess)
             return e;
-        occ[d] = o > 0 ? o : 1;
+        occ.set(d, o > 0 ? o : 1);
     }
     const int ntiles = a.cols / C::W;
-    int grid = sm_count() * occ[d];
+    int grid = sm_count() * occ.get(d);
     if (grid > ntiles)
         grid = ntiles;
     k<<<grid, C::T, SMEM, s>>>(map, omap, a.out, a.tw, a.cols, a.ld, a.scale, a.err,
@@ -197,9 +197,9 @@ cudaError_t col_launch_tmem(const PassArgs &a, cudaStream_t s)
         return col_launch_any<LineCfg<C::L, C::KW, 0>>(a, s);
     auto k = col_tmem_kernel<C>;
     constexpr int SMEM = S::SMEM_BYTES;
-    static int occ[kMaxDev] = {};
+    static DeviceCache occ;
     const int d = current_device();
-    if (!occ[d]) {
+    if (!occ.get(d)) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              SMEM);
         if (e != cudaSuccess)
@@ -208,10 +208,10 @@ cudaError_t col_launch_tmem(const PassArgs &a, cudaStream_t s)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, C::T, SMEM);
         if (e != cudaSuccess)
             return e;
-        occ[d] = o > 0 ? o : 1;
+        occ.set(d, o > 0 ? o : 1);
     }
     const int ntiles = a.cols / C::W;
-    int grid = sm_count() * occ[d];
+    int grid = sm_count() * occ.get(d);
     if (grid > ntiles)
         grid = ntiles;
     k<<<grid, C::T, SMEM, s>>>(map, omap, a.out, a.tw, a.cols, a.ld, a.scale, a.err,
@@ -252,9 +252,9 @@ cudaError_t col_launch_pair(const PassArgs &a, cudaStream_t s)
     cfg.stream = s;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    static int pairs[kMaxDev] = {};
+    static DeviceCache pairs;
     const int d = current_device();
-    if (!pairs[d]) {
+    if (!pairs.get(d)) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              SMEM);
         if (e != cudaSuccess)
@@ -264,10 +264,10 @@ cudaError_t col_launch_pair(const PassArgs &a, cudaStream_t s)
         e = cudaOccupancyMaxActiveClusters(&n, k, &cfg);
         if (e != cudaSuccess)
             return e;
-        pairs[d] = n > 0 ? n : 1;
+        pairs.set(d, n > 0 ? n : 1);
     }
     const int ntiles = a.cols / C::W;
-    const int np = pairs[d] < ntiles ? pairs[d] : ntiles;
+    const int np = pairs.get(d) < ntiles ? pairs.get(d) : ntiles;
     cfg.gridDim = dim3((unsigned)(2 * np));
     return cudaLaunchKernelEx(&cfg, k, m0, m1, om, a.tw, a.cols, a.scale, a.err, a.withhold);
 }

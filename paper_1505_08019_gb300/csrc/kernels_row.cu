@@ -55,9 +55,9 @@ cudaError_t row_launch_tma(const PassArgs &a, cudaStream_t s)
     constexpr int SMEM = RowTma<C>::SMEM_BYTES;
     auto k = row_tma_kernel<C>;
     constexpr int kMaxDev = 64;
-    static int occ[kMaxDev] = {};
+    static DeviceCache occ;
     const int d = device_current();
-    if (!occ[d]) {
+    if (!occ.get(d)) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
         if (e != cudaSuccess)
             return e;
@@ -65,10 +65,10 @@ cudaError_t row_launch_tma(const PassArgs &a, cudaStream_t s)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, C::T, SMEM);
         if (e != cudaSuccess)
             return e;
-        occ[d] = o > 0 ? o : 1;
+        occ.set(d, o > 0 ? o : 1);
     }
     const int ntiles = a.rows / C::LB;
-    int grid = device_sm_count() * occ[d];
+    int grid = device_sm_count() * occ.get(d);
     if (grid > ntiles)
         grid = ntiles;
     k<<<grid, C::T, SMEM, s>>>(a.in, a.out, a.tw, a.rows, a.ld, a.scale, a.err);
@@ -191,9 +191,9 @@ cudaError_t row_launch_split(const PassArgs &a, cudaStream_t s)
     constexpr int SMEM = RowSplit<C>::SMEM_BYTES;
     auto k = row_split_kernel<C>;
     constexpr int kMaxDev = 64;
-    static int occ[kMaxDev] = {};
+    static DeviceCache occ;
     const int d = device_current();
-    if (!occ[d]) {
+    if (!occ.get(d)) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
         if (e != cudaSuccess)
             return e;
@@ -201,9 +201,9 @@ cudaError_t row_launch_split(const PassArgs &a, cudaStream_t s)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, C::T, SMEM);
         if (e != cudaSuccess)
             return e;
-        occ[d] = o > 0 ? o : 1;
+        occ.set(d, o > 0 ? o : 1);
     }
-    int grid = device_sm_count() * occ[d];
+    int grid = device_sm_count() * occ.get(d);
     if (grid > a.rows)
         grid = a.rows;
     k<<<grid, C::T, SMEM, s>>>(a.in, a.out, a.tw, a.rows, a.ld, a.scale, a.err);

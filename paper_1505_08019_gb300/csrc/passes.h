@@ -1,6 +1,8 @@
 // passes.h -- host-side entry points of the row and column pass kernels.
 #pragma once
 
+#include <atomic>
+
 #include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -16,6 +18,15 @@ struct NvtxRange {
     ~NvtxRange() { nvtxRangePop(); }
     NvtxRange(const NvtxRange &) = delete;
     NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
+// One int per device (index from device_current(), below 64), computed on
+// first use by the launching thread; threads that race on the first use
+// compute and store the same value.
+struct DeviceCache {
+    std::atomic<int> v[64];
+    int get(int d) const { return v[d].load(std::memory_order_relaxed); }
+    void set(int d, int x) { v[d].store(x, std::memory_order_relaxed); }
 };
 
 // Arguments common to both passes (complex64 storage, FP32 arithmetic).
