@@ -47,3 +47,24 @@ def test_rejects_bad_sizes(orc):
         orc.fft2d(np.zeros((3, 4), np.complex128))
     with pytest.raises(ValueError):
         orc.fft1d(np.zeros(8), nstages=4)
+
+
+def test_table1_fixture_and_oracle_round_trip(orc):
+    """tests/golden/table1.txt holds Table 1 as printed: five gray-image
+    sides 128..2048 with a maximum error of 0.007.  At the three smallest
+    sides the FP64 oracle's forward + inverse recovers a [0, 1) gray image
+    to far better than that (the GPU test holds the FP32 path to 1 %)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "table1.txt")
+    rows = []
+    with open(path) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                side, _, _, err = line.split()
+                rows.append((int(side), float(err)))
+    assert [r[0] for r in rows] == [128, 256, 512, 1024, 2048]
+    assert all(e == 0.007 for _, e in rows)
+    for side, err in rows[:3]:
+        x = uniform_real(side, side, seed=side).astype(np.complex128)
+        back = orc.fft2d(orc.fft2d(x), inverse=True)
+        assert float(np.abs(back - x).max()) <= err * 1e-9
