@@ -236,46 +236,6 @@ __global__ void __launch_bounds__(C::T, C::MINB) line_dct_kernel(const DctIO d,
 }
 
 // ---------------------------------------------------------------------------
-// Persistent TMA-fed column pass of the DCT (columns of 2^11 and 2^12 points,
-// tiles of W complex columns = 2W real columns).
-//
-// The reorder needs no gather table: two tensor maps see the image's even
-// rows and its odd rows (row stride 2 ld), so one TMA load brings
-// x[0], x[2], .., x[N-2] = v[0 .. N/2) in order (the "even region") and
-// another x[1], x[3], .., x[N-1] = v[N-1], v[N-2], .., v[N/2] (the "odd
-// region", reversed).  Group 0 then gathers v[i] scrambled from the even
-// region (i < N/2) or from odd-region slot N-1-i; which one is fixed by the
-// register index.  As in the complex column pass, the next tile's even rows
-// land in a prefetch region while the current tile is worked on and its odd
-// rows in the lower half of the tile region once the last group has read it.
-//
-// The last group holds rows lo + r 2^S0 of a unit.  Output k pairs with
-// N - k, i.e. unit lo with unit 2^S0 - lo (reversed r), so the units are
-// dealt out such that each thread owns both members of its pairs
-// (dct_unit_lo);
-// the pairing and rotation then run in registers.  Units with lo < 2^(S0-1)
-// leave through a staging buffer and one TMA store, the others with
-// per-thread stores.
-template <class C>
-struct DctCol {
-    using Gl = Grp<C, C::NG - 1>;
-    static constexpr int HALF = C::N / 2;                  // rows of one parity
-    static constexpr int BY = HALF < 256 ? HALF : 256;     // rows per block of a parity map
-    static constexpr int NZ = HALF / BY;
-    static constexpr int HVALS = HALF * C::W;              // values of one parity region
-    static constexpr int TW_OFF = C::E + HVALS;
-    static constexpr int SMEM_BYTES = (TW_OFF + C::N) * 8;
-    static constexpr uint32_t HBYTES = (uint32_t)HVALS * 8u;
-    static constexpr uint32_t TW_BYTES = (uint32_t)C::N * 8u;   // N-1 entries + padding
-    static constexpr int M = 1 << Gl::S0;                  // rows of one store block
-    static constexpr int QROWS = M / 2;
-    static_assert(C::LB == 1 && C::NG >= 2, "one line block, two stage groups at least");
-    static_assert(M == 256, "store blocks are the 256-row blocks of the store map");
-    static_assert(((C::T * (Gl::V / 2)) >> C::KW) == QROWS, "threads cover half the row offsets");
-    static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
-};
-
-// ---------------------------------------------------------------------------
 // Inverse (DCT-III, the oracle's x[n] = (1/N)(X[0] + 2 sum_k X[k]
 // cos(pi k (2n+1) / (2N)))) through one inverse DFT:
 //   V[k] = exp(i pi k / (2N)) (X[k] - i X[N-k])   (X[N] = 0),
@@ -737,6 +697,45 @@ cudaError_t row_dct_launch(const DctIO &d, const float2 *tw, const float2 *post,
     k<<<grid, C::T, bytes, s>>>(d, tw, post, dct_rot_table(), nlines, scale);
     return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// Persistent TMA-fed column pass of the DCT (columns of 2^11 and 2^12 points,
+// tiles of W complex columns = 2W real columns).
+//
+// The reorder needs no gather table: two tensor maps see the image's even
+// rows and its odd rows (row stride 2 ld), so one TMA load brings
+// x[0], x[2], .., x[N-2] = v[0 .. N/2) in order (the "even region") and
+// another x[1], x[3], .., x[N-1] = v[N-1], v[N-2], .., v[N/2] (the "odd
+// region", reversed).  Group 0 then gathers v[i] scrambled from the even
+// region (i < N/2) or from odd-region slot N-1-i; which one is fixed by the
+// register index.  As in the complex column pass, the next tile's even rows
+// land in a prefetch region while the current tile is worked on and its odd
+// rows in the lower half of the tile region once the last group has read it.
+//
+// The last group holds rows lo + r 2^S0 of a unit.  Output k pairs with
+// N - k, i.e. unit lo with unit 2^S0 - lo (reversed r), so the units are
+// dealt out such that each thread owns both members of its pairs
+// (dct_unit_lo); the pairing and rotation then run in registers.  Units
+// with lo < 2^(S0-1) leave through a staging buffer and one TMA store, the
+// others with per-thread stores.
+template <class C>
+struct DctCol {
+    using Gl = Grp<C, C::NG - 1>;
+    static constexpr int HALF = C::N / 2;                  // rows of one parity
+    static constexpr int BY = HALF < 256 ? HALF : 256;     // rows per block of a parity map
+    static constexpr int NZ = HALF / BY;
+    static constexpr int HVALS = HALF * C::W;              // values of one parity region
+    static constexpr int TW_OFF = C::E + HVALS;
+    static constexpr int SMEM_BYTES = (TW_OFF + C::N) * 8;
+    static constexpr uint32_t HBYTES = (uint32_t)HVALS * 8u;
+    static constexpr uint32_t TW_BYTES = (uint32_t)C::N * 8u;   // N-1 entries + padding
+    static constexpr int M = 1 << Gl::S0;                  // rows of one store block
+    static constexpr int QROWS = M / 2;
+    static_assert(C::LB == 1 && C::NG >= 2, "one line block, two stage groups at least");
+    static_assert(M == 256, "store blocks are the 256-row blocks of the store map");
+    static_assert(((C::T * (Gl::V / 2)) >> C::KW) == QROWS, "threads cover half the row offsets");
+    static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
+};
 
 // maps: even rows (me), odd rows (mo), each x = complex column, y = row
 // pair within a block of BY, z = block, box W x BY x NZ; omap: the output as
