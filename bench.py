@@ -43,13 +43,14 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--requests", type=int, default=20000, help="serving workload: requests")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving workload: mean req/s")
-    ap.add_argument("--workload", choices=["fft4096", "batched", "fp16", "serve", "dct"],
+    ap.add_argument("--workload", choices=["fft4096", "batched", "fp16", "serve", "dct", "sizes"],
                     default="fft4096",
                     help="fft4096: the 4096x4096 forward+inverse benchmark (default); "
                          "batched: 64 uneven images through the grouped executor; "
                          "fp16: half2 storage vs complex64 at 8192^2 and 16384^2; "
                          "serve: Poisson stream of mixed requests through fft2d_serve_*; "
-                         "dct: real 2D DCT-II at 4096^2 and 8192^2 beside the complex FFT")
+                         "dct: real 2D DCT-II at 4096^2 and 8192^2 beside the complex FFT; "
+                         "sizes: forward+inverse at the paper's Table 1 image sizes")
     ap.add_argument("--images", type=int, default=4, help="resident images per rank")
     ap.add_argument("--streams", type=int, default=0,
                     help="CUDA streams the resident images are spread over (0: one per image)")
@@ -933,6 +934,101 @@ def run_dct(args):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------- Table 1 image sizes
+def run_sizes(args):
+    """Forward + inverse complex64 transforms at the paper's Table 1 gray
+    image sizes (128^2 .. 2048^2) and at 4096^2, one image at a time on one
+    stream (the paper's setting), with enough images in rotation that the
+    working set exceeds L2, captured in a CUDA graph and replayed (and, for
+    context, the same calls from a Python loop).  Reports microseconds per
+    transform, the
+    fraction of measured HBM bandwidth at 32 B/px, and the error of the
+    round trip against the input."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1505_08019_gb300 as fft
+    import synth
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    peak, peak_src = measured_hbm_peak()
+    results = {}
+    for side in (128, 256, 512, 1024, 2048, 4096):
+        img_bytes = side * side * 8
+        nimg = max(2, int(2 * 129e6 // img_bytes) + 1)   # rotation larger than twice L2
+        x = synth.uniform_real(side, side, seed=side)
+        xs = [torch.from_numpy(x).cuda() for _ in range(nimg)]
+        ys = [torch.empty_like(xs[0]) for _ in range(nimg)]
+        pf = fft.fft2d_plan(side, side, fft.FFT2D_C64, fft.FFT2D_FORWARD)
+        pi = fft.fft2d_plan(side, side, fft.FFT2D_C64, fft.FFT2D_INVERSE)
+        reps = max(40, nimg * 4)
+
+        def step(i):
+            fft.fft2d_exec(pf, xs[i % nimg], ys[i % nimg], sptr)
+            fft.fft2d_exec(pi, ys[i % nimg], ys[i % nimg], sptr)
+
+        for i in range(5):
+            step(i)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for i in range(reps):
+            step(i)
+        b.record(stream)
+        torch.cuda.synchronize()
+        us_eager = a.elapsed_time(b) * 1e3 / (2 * reps)
+        # the same steps captured once in a CUDA graph and replayed: the
+        # device time without the host's per-call launch cost
+        per_graph = min(nimg, 256)
+        gs = torch.cuda.Stream()
+        gs.wait_stream(stream)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=gs):
+            for i in range(per_graph):
+                fft.fft2d_exec(pf, xs[i % nimg], ys[i % nimg], gs.cuda_stream)
+                fft.fft2d_exec(pi, ys[i % nimg], ys[i % nimg], gs.cuda_stream)
+        replays = max(3, reps // per_graph)
+        graph.replay()
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(replays):
+            graph.replay()
+        b.record(stream)
+        torch.cuda.synchronize()
+        us = a.elapsed_time(b) * 1e3 / (2 * per_graph * replays)
+        del graph
+        fft.fft2d_exec(pf, xs[0], ys[0], sptr)
+        fft.fft2d_exec(pi, ys[0], ys[0], sptr)
+        torch.cuda.synchronize()
+        back = ys[0].cpu().numpy()
+        max_err = float(np.abs(back.astype(np.complex128) - x.astype(np.complex128)).max())
+        results[f"{side}x{side}"] = {
+            "us_per_transform": us, "transforms_per_s": 1e6 / us,
+            "us_per_transform_eager_python_loop": us_eager,
+            "hbm_frac": (32.0 * side * side / (us * 1e-6) / 1e9) / peak,
+            "round_trip_max_abs_err": max_err, "images_in_rotation": nimg}
+        fft.fft2d_destroy(pf)
+        fft.fft2d_destroy(pi)
+        del xs, ys
+        torch.cuda.empty_cache()
+    line = {"metric": "2D FFT transforms/s at the paper's Table 1 sizes (one stream)",
+            "value": results["2048x2048"]["transforms_per_s"], "unit": "transforms/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic (seeded U[0,1) gray images)",
+            "config": {"workload": "forward and inverse complex64 FFT, one image at a time on "
+                                   "one stream, 128^2 .. 4096^2, CUDA-graph replay; value = "
+                                   "2048^2 transforms/s",
+                       "l2": "images rotated so the working set exceeds L2"},
+            "roofline": {"bound": "hbm", "peak": peak, "unit": "GB/s", "peak_source": peak_src,
+                         "algorithmic_bytes_per_px": 32},
+            "paper_table1_gpu_ms": {"128x128": 16, "256x256": 16, "512x512": 28,
+                                    "1024x1024": 62, "2048x2048": 250},
+            "per_size": results}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -945,6 +1041,8 @@ def main():
         run_serve(args)
     elif args.workload == "dct":
         run_dct(args)
+    elif args.workload == "sizes":
+        run_sizes(args)
     else:
         run_ours(args)
 
