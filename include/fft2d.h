@@ -200,6 +200,9 @@ FFT2D_API fft2d_status fft2d_plan_info(fft2d_plan_t plan, int *rows, int *cols, 
  * fused, all log2(rows) stages, inverse scale fused into the store).
  * in and out are device pointers to rows*cols pixels; in == out is allowed
  * (in place).  Partial overlap of in and out is not allowed.  Two launches.
+ * Once the plan has run on its device (the first launch of each kernel sets
+ * its shared-memory limit), the call allocates nothing and may be captured
+ * in a CUDA graph on `stream`.
  */
 FFT2D_API fft2d_status fft2d_exec(fft2d_plan_t plan, const void *in, void *out, void *stream);
 
