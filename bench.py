@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--dct-sides", default="4096,8192",
                     help="dct workload: comma-separated sides (S or RxC)")
     ap.add_argument("--side", type=int, default=SIDE)
-    ap.add_argument("--e2e-steps", type=int, default=6)
+    ap.add_argument("--e2e-steps", type=int, default=12)
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="bound on the CPU-baseline sample (wall seconds)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
