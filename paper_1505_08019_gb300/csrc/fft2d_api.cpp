@@ -955,8 +955,9 @@ fft2d_status fft2d_plan_describe(fft2d_plan_t p, char *buf, int len)
     if (!p || !buf || len <= 0)
         return FFT2D_ERR_ARG;
     if (p->dtype == FFT2D_R32_DCT2) {
-        std::snprintf(buf, (size_t)len, "rows:dct2(lines=%d,points=%d) cols:dct2(lines=%d,points=%d)",
-                      p->rows / 2, p->cols, p->cols / 2, p->rows);
+        const char *kind = p->dir == FFT2D_INVERSE ? "dct3" : "dct2";
+        std::snprintf(buf, (size_t)len, "rows:%s(lines=%d,points=%d) cols:%s(lines=%d,points=%d)",
+                      kind, p->rows / 2, p->cols, kind, p->cols / 2, p->rows);
         return FFT2D_OK;
     }
     std::string out;

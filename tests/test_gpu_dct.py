@@ -242,6 +242,16 @@ def test_idct_whole_outputs(env, rows, cols):
     assert err <= TOL, err
 
 
+def test_idct_plan_describe(env):
+    _, fft, _ = env
+    plan = fft.fft2d_plan(32, 64, fft.FFT2D_R32_DCT2, fft.FFT2D_INVERSE)
+    try:
+        assert fft.fft2d_plan_describe(plan) == \
+            "rows:dct3(lines=16,points=64) cols:dct3(lines=32,points=32)"
+    finally:
+        fft.fft2d_destroy(plan)
+
+
 def test_idct_in_place_and_passes(env):
     """In place; the row pass alone is the unscaled DCT-III of every row
     (cols times the oracle's inverse), the column pass alone carries the
