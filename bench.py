@@ -51,7 +51,7 @@ def parse():
                          "serve: Poisson stream of mixed requests through fft2d_serve_*; "
                          "dct: real 2D DCT-II at 4096^2 and 8192^2 beside the complex FFT; "
                          "sizes: forward+inverse at the paper's Table 1 image sizes")
-    ap.add_argument("--images", type=int, default=4, help="resident images per rank")
+    ap.add_argument("--images", type=int, default=8, help="resident images per rank")
     ap.add_argument("--streams", type=int, default=0,
                     help="CUDA streams the resident images are spread over (0: one per image)")
     ap.add_argument("--fp16-sides", default="8192,16384",
