@@ -329,8 +329,8 @@ def run_ours(args):
     hout = [torch.empty_like(h).pin_memory() for h in hin]
     # one call per step: for every image its forward transform (hin -> hout)
     # and then its inverse (hout -> hout); the inverse starts from the device
-    # copy of the forward result, so each step uploads the B inputs and
-    # downloads both results of every image
+    # copy of the forward result and overwrites it on the host, so each step
+    # uploads the B inputs and downloads the B round-trip results
     step_plans, step_in, step_out = [], [], []
     for b_ in range(B):
         step_plans += [pf, pi]
@@ -349,11 +349,12 @@ def run_ours(args):
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
     img_bytes = side * side * 8
     e2e = {"value": 2 * B * args.e2e_steps * ws / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": B * img_bytes, "d2h_bytes_per_step": 2 * B * img_bytes,
+           "h2d_bytes_per_step": B * img_bytes, "d2h_bytes_per_step": B * img_bytes,
            "steps": args.e2e_steps,
-           "call": "fft2d_exec_host_many_async, one call per step (each image's forward "
-                   "transform, then its inverse from the device copy of the forward result), "
-                   "stream synchronised after the last (pinned host buffers; uploads, "
+           "call": "fft2d_exec_host_many_async, one call per step: each image's forward "
+                   "transform, then its inverse from the device copy of the forward result "
+                   "into the same host buffer (the overwritten forward result is not copied "
+                   "back); stream synchronised after the last (pinned host buffers; uploads, "
                    "transforms and downloads of consecutive images overlap)"}
     # the same transforms one synchronous fft2d_exec_host call at a time
     t0 = time.perf_counter()
@@ -865,10 +866,10 @@ def run_dct(args):
             img_bytes = R * C * 4
             e2e = {"value": 2 * nbuf * args.e2e_steps / dt, "unit": "images/s",
                    "h2d_bytes_per_step": nbuf * img_bytes,
-                   "d2h_bytes_per_step": 2 * nbuf * img_bytes, "steps": args.e2e_steps,
+                   "d2h_bytes_per_step": nbuf * img_bytes, "steps": args.e2e_steps,
                    "call": "fft2d_exec_host_many_async, one call per step: each image's "
                            "forward transform, then its inverse from the device copy of the "
-                           "forward result (pinned host buffers)"}
+                           "forward result into the same host buffer (pinned host buffers)"}
             del hin, hout
         fft.fft2d_exec(pd, xs[0], ys[0], sptr)
         fft.fft2d_exec(pinv, ys[0], xs[1], sptr)

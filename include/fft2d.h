@@ -249,7 +249,10 @@ FFT2D_API fft2d_status fft2d_exec_host(fft2d_plan_t plan, const void *in_host, v
  * its inverse can travel in one call.  When that earlier image is the one
  * just before (in_host[i] == out_host[i-1], images of the same byte size),
  * image i is transformed straight from the device copy of that output and
- * nothing is uploaded for it; its result is downloaded as usual.
+ * nothing is uploaded for it.  If image i also writes the same host buffer
+ * (out_host[i] == out_host[i-1], e.g. a forward transform and its inverse in
+ * place), the earlier result could never be observed on the host and is not
+ * copied back; every other result is.
  * Otherwise the host buffers of
  * different images must not overlap.  The copies start after the work
  * already queued on `stream`.  complex64 and DCT plans (FFT2D_R32_DCT2,

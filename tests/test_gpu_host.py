@@ -174,6 +174,18 @@ def test_chained_images_skip_the_upload(env):
             assert np.array_equal(mid2[i].numpy(), want_fwd[i]), f"forward {shapes[i]}"
             assert np.array_equal(back2[i].numpy(), want_rt[i]), f"inverse {shapes[i]}"
 
+        # forward and inverse into one host buffer: the overwritten forward
+        # result is not copied back, the final content is the round trip
+        one = [torch.empty_like(h).pin_memory() for h in hin]
+        plans, ins, outs = [], [], []
+        for i in range(len(shapes)):
+            plans += [fwd[i], inv[i]]
+            ins += [hin[i], one[i]]
+            outs += [one[i], one[i]]
+        fft.fft2d_exec_host_many(plans, ins, outs)
+        for i in range(len(shapes)):
+            assert np.array_equal(one[i].numpy(), want_rt[i]), f"same buffer {shapes[i]}"
+
         # in place on the host, chains of three, several asynchronous calls
         work = [torch.empty_like(h).pin_memory() for h in hin]
         plans, ins, outs = [], [], []
