@@ -240,7 +240,7 @@ FFT2D_API fft2d_status fft2d_exec_host(fft2d_plan_t plan, const void *in_host, v
 /*
  * fft2d_exec_host for n images at once, pipelined: while image i is
  * transformed, image i+1 uploads and image i-1 downloads, on two internal
- * copy streams and the caller's stream (three device image buffers per
+ * copy streams and the caller's stream (six device image buffers per
  * device, grown to the largest image and kept for the life of the process).
  * Image i is transformed with plans[i] from in_host[i] to out_host[i];
  * in_host[i] == out_host[i] is allowed.  An image may read the output of an

@@ -342,7 +342,10 @@ namespace {
 // Device buffers, streams and events of the pipelined host path, one set per
 // device, grown on demand and kept for the life of the process.  One call at
 // a time uses a device's set (the mutex).
-constexpr int kHostSlots = 3;      // images in flight: upload, transform, download
+// Device image buffers of the host pipeline: images in flight between
+// upload, transform and download.  A forward transform and its chained
+// inverse hold two at once, so three pairs stay in flight with six.
+constexpr int kHostSlots = 6;
 constexpr int kHostMaxDev = 64;
 
 struct HostPipe {
