@@ -68,3 +68,12 @@ def test_table1_fixture_and_oracle_round_trip(orc):
         x = uniform_real(side, side, seed=side).astype(np.complex128)
         back = orc.fft2d(orc.fft2d(x), inverse=True)
         assert float(np.abs(back - x).max()) <= err * 1e-9
+
+
+def test_gray_real_is_uniform_real_real_part():
+    """The DCT's gray images are the same draws as the FFT's gray images."""
+    from synth import gray_real
+    for shape, seed in (((4, 8), 0), ((64, 32), 7)):
+        g = gray_real(*shape, seed=seed)
+        assert g.dtype == np.float32 and g.flags.c_contiguous
+        assert np.array_equal(g, uniform_real(*shape, seed=seed).real)
