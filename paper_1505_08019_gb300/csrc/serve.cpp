@@ -106,10 +106,12 @@ struct fft2d_server_s {
     // ------------------------------------------------------------- memory
     // Take a buffer of at least `need` bytes from the pool, or allocate one if
     // the budget allows.  Returns nullptr (without waiting) when it cannot.
-    void *acquire(size_t need)
+    // With `exact`, a pooled buffer is taken only if it has exactly `need`
+    // bytes.
+    void *acquire(size_t need, bool exact = false)
     {
         auto it = pool.lower_bound(need);
-        if (it != pool.end() && it->first <= 2 * need) {
+        if (it != pool.end() && (exact ? it->first == need : it->first <= 2 * need)) {
             void *p = it->second;
             pooled -= it->first;
             used += it->first;
@@ -154,15 +156,15 @@ struct fft2d_server_s {
         pool.emplace(n, p);
     }
 
-    bool admit(Req *q)
+    bool try_admit(Req *q, bool exact)
     {
         const size_t px = (size_t)q->r.rows * q->r.cols;
-        q->buf_c64 = acquire(px * 8);
+        q->buf_c64 = acquire(px * 8, exact);
         if (!q->buf_c64)
             return false;
         if (q->r.dtype == FFT2D_C32H) {
-            q->buf_h16 = acquire(px * 4);
-            q->exps = static_cast<int *>(acquire((size_t)(q->r.rows + q->r.cols) * 4));
+            q->buf_h16 = acquire(px * 4, exact);
+            q->exps = static_cast<int *>(acquire((size_t)(q->r.rows + q->r.cols) * 4, exact));
             if (!q->buf_h16 || !q->exps) {
                 release(q->buf_c64);
                 release(q->buf_h16);
@@ -173,6 +175,34 @@ struct fft2d_server_s {
             }
         }
         return true;
+    }
+
+    void free_pool()
+    {
+        for (auto &kv : pool) {
+            if (simulate)
+                std::free(kv.second);
+            else
+                cudaFree(kv.second);
+        }
+        pool.clear();
+        pooled = 0;
+    }
+
+    // Admit q if its buffers fit the budget now.  A pooled buffer taken for
+    // one of q's buffers may be up to twice as large as asked; when nothing
+    // is in use (no request in flight), that surplus could be all that keeps
+    // q's other buffers out, and no completion would ever change it.  In that
+    // case the pool is released and q gets buffers of exactly its sizes,
+    // which fit because submission refuses requests larger than the budget.
+    bool admit(Req *q)
+    {
+        if (try_admit(q, false))
+            return true;
+        if (used != 0)
+            return false;   // wait for in-flight work to return memory
+        free_pool();
+        return try_admit(q, true);
     }
 
     void free_req(Req *q)
@@ -447,7 +477,7 @@ fft2d_status fft2d_serve_submit(fft2d_server_t s, const fft2d_request *req,
     q->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        // two buffers of a request may round up to 2x in the pool
+        // a request larger than the whole budget could never be admitted
         if (q->bytes > s->budget) {
             s->rejected++;
             delete q;
@@ -536,12 +566,7 @@ fft2d_status fft2d_serve_destroy(fft2d_server_t s)
         s->worker.join();
     for (auto &kv : s->all)
         delete kv.second;
-    for (auto &kv : s->pool) {
-        if (s->simulate)
-            std::free(kv.second);
-        else
-            cudaFree(kv.second);
-    }
+    s->free_pool();
     for (auto &kv : s->plans)
         fft2d_destroy(kv.second);
     if (!s->simulate)

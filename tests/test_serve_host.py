@@ -133,3 +133,23 @@ def test_wait_timeout_and_unknown_ticket(fft):
             fft.fft2d_serve_wait(srv, t, 1)        # each ticket is waited for once
     finally:
         fft.fft2d_serve_destroy(srv)
+
+
+def test_oversized_pooled_buffer_does_not_stall_admission(fft):
+    """A 128x128 complex64 request leaves a 128 KiB buffer in the pool.  The
+    next request, a 64x128 half2 one, takes it for its 64 KiB complex64
+    buffer (pooled buffers up to twice the size are reused) and would then
+    find no room for its half2 buffer under a 140 000-byte budget, with
+    nothing in flight to free memory.  The server must fall back to exact
+    sizes instead of waiting for ever."""
+    srv = make(fft, 140000, streams=1)
+    buf = np.zeros(8, np.complex64)
+    try:
+        t = fft.fft2d_serve_submit(srv, 0, 128, 128, fft.FFT2D_C64, buf, buf)
+        fft.fft2d_serve_wait(srv, t, 10000)
+        t = fft.fft2d_serve_submit(srv, 1, 64, 128, fft.FFT2D_C32H, buf, buf)
+        fft.fft2d_serve_wait(srv, t, 10000)
+        st = fft.fft2d_serve_stats_get(srv)
+        assert st["completed"] == 2 and st["peak_device_bytes"] <= 140000
+    finally:
+        fft.fft2d_serve_destroy(srv)
