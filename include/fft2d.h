@@ -407,10 +407,13 @@ FFT2D_API fft2d_status fft2d_stage_table(int L, int dir, float *out);
 
 /*
  * The whole 2D transform (as fft2d_exec) without any device allocation, for
- * callers that cannot allocate: code running while a CUDA graph is being
- * captured, code that must not go through a process's caching allocator, or
- * hosts that manage every byte of the device themselves.  The paper has no
- * counterpart; this is a deployment convenience.
+ * callers that cannot allocate: a plug-in inside a host application that
+ * manages every byte of the device itself (a cudaMalloc behind its back
+ * breaks its accounting or fails because it reserved the whole device), code
+ * in a process whose caching allocator already holds the free memory, and
+ * latency-bound paths where cudaMalloc's implicit device synchronisation is
+ * not allowed.  The paper has no counterpart; this is a deployment
+ * convenience.
  *
  * rows, cols: powers of two, 1 <= side <= FFT2D_NOALLOC_MAX_SIDE (4096);
  * larger sides return FFT2D_ERR_TOO_LARGE (use a plan for them).  dir is

@@ -1,13 +1,16 @@
 // noalloc.cu -- the 2D transform for callers that cannot allocate device memory.
 //
 // fft2d_exec needs a plan, and a plan allocates device memory (its rotation
-// factor tables and its status word).  Some callers cannot allocate: code
-// running while a CUDA graph is being captured, code that must not touch a
-// process's caching allocator, or embedded hosts that own every byte of the
-// device themselves.  fft2d_exec_noalloc serves them: the same row and column
-// pass kernels run with their tables and status word taken from one
-// file-scope device array that exists from the moment the library is loaded
-// on a device until the process exits.
+// factor tables and its status word).  Some callers cannot allocate: a
+// plug-in inside a host application that owns every byte of the device
+// through its own memory manager (a cudaMalloc behind its back breaks its
+// accounting, or fails because it has reserved the whole device), code in a
+// process whose caching allocator already holds the free memory, and
+// latency-bound paths where cudaMalloc's implicit device synchronisation is
+// not allowed.  fft2d_exec_noalloc serves them: the same row and column pass
+// kernels run with their tables and status word taken from one file-scope
+// device array that exists from the moment the library is loaded on a device
+// until the process exits.
 #include <cuda_runtime.h>
 
 #include <mutex>

@@ -1,7 +1,9 @@
 """fft2d_exec_noalloc -- the plan-free entry point for callers that cannot
-allocate device memory (graph capture, foreign allocators) -- must give the
-same results as fft2d_exec, within the FP32 tolerance of the other GPU tests,
-call after call on its shared static scratch.  Collected last on purpose."""
+allocate device memory (a plug-in in a host application that owns the whole
+device, a process whose caching allocator holds the free memory, paths where
+cudaMalloc's implicit synchronisation is not allowed) -- must give the same
+results as fft2d_exec, within the FP32 tolerance of the other GPU tests, call
+after call on its shared static scratch.  Collected last on purpose."""
 import ctypes
 
 import numpy as np
@@ -77,3 +79,22 @@ def test_noalloc_in_place_and_limits(env):
     st = fft.lib.fft2d_exec_noalloc(12, 8, fft.FFT2D_FORWARD, ctypes.c_void_p(big.data_ptr()),
                                     ctypes.c_void_p(big.data_ptr()), None)
     assert st == fft.FFT2D_ERR_NOT_POW2
+
+
+@pytest.mark.parametrize("shape", [(1, 1024), (1024, 1), (1, 1)], ids=lambda s: f"{s[0]}x{s[1]}")
+def test_noalloc_single_line_shapes(env, shape):
+    """The entry point's own branches: a single row (the inverse scale rides
+    on the row pass), a single column (the row pass is a copy, or nothing in
+    place), both directions, in place and out of place."""
+    torch, fft = env
+    R, C = shape
+    for direction in (fft.FFT2D_FORWARD, fft.FFT2D_INVERSE):
+        x = synth.uniform_complex(R, C, seed=R + 2 * C + direction)
+        want = via_plan(torch, fft, x, direction)
+        dx = torch.from_numpy(x).cuda()
+        out = torch.empty_like(dx)
+        fft.fft2d_exec_noalloc(R, C, direction, dx, out)
+        fft.fft2d_exec_noalloc(R, C, direction, dx, dx)
+        torch.cuda.synchronize()
+        assert rel(out.cpu().numpy(), want) <= TOL
+        assert rel(dx.cpu().numpy(), want) <= TOL
