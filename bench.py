@@ -51,7 +51,10 @@ def parse():
                          "serve: Poisson stream of mixed requests through fft2d_serve_*; "
                          "dct: real 2D DCT-II at 4096^2 and 8192^2 beside the complex FFT; "
                          "sizes: forward+inverse at the paper's Table 1 image sizes")
-    ap.add_argument("--images", type=int, default=8, help="resident images per rank")
+    ap.add_argument("--images", type=int, default=256,
+                    help="resident images per rank (one step = forward + inverse of each)")
+    ap.add_argument("--distinct", type=int, default=8,
+                    help="distinct seeded images the resident images are copies of")
     ap.add_argument("--streams", type=int, default=0,
                     help="CUDA streams the resident images are spread over (0: one per image)")
     ap.add_argument("--fp16-sides", default="8192,16384",
@@ -60,8 +63,12 @@ def parse():
                     help="dct workload: comma-separated sides (S or RxC)")
     ap.add_argument("--side", type=int, default=SIDE)
     ap.add_argument("--e2e-steps", type=int, default=12)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0,
-                    help="bound on the CPU-baseline sample (wall seconds)")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="bound on each CPU-baseline sample (wall seconds)")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="default workload: leave out the serve / fp16 / batched sub-results")
+    ap.add_argument("--serve-sample", type=int, default=4000,
+                    help="default workload: requests of the serving sub-result")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
     return ap.parse_args()
@@ -215,6 +222,221 @@ def host_cores():
         return os.cpu_count() or 1
 
 
+def cpu_model() -> str:
+    """The host CPU's model name as lscpu reports it (else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def cpu_baseline(side, seconds):
+    """The oracle on all host cores and on one thread, same workload."""
+    th = host_cores()
+    v, n, dt = cpu_oracle_sample(side, seconds, th)
+    v1, n1, dt1 = cpu_oracle_sample(side, seconds, 1)
+    return {"value": v, "unit": UNIT, "cores": th, "kind": "oracle",
+            "cpu_model": cpu_model(),
+            "sample": f"{n} transforms ({n // 2} forward+inverse pairs) of one "
+                      f"{side}x{side} blob image, FP64 C oracle on {th} threads, {dt:.1f} s",
+            "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                              "sample": f"{n1} transforms ({n1 // 2} pairs), one thread, "
+                                        f"{dt1:.1f} s"}}
+
+
+def rel_l2(a, b, chunk=1 << 24):
+    """||a - b|| / ||b|| in float64 (b the reference), in chunks."""
+    a = np.asarray(a).reshape(-1)
+    b = np.asarray(b).reshape(-1)
+    num = den = 0.0
+    for i in range(0, b.size, chunk):
+        bb = b[i:i + chunk].astype(np.complex128)
+        d = a[i:i + chunk].astype(np.complex128) - bb
+        num += float(np.vdot(d, d).real)
+        den += float(np.vdot(bb, bb).real)
+    return float(np.sqrt(num / den)) if den > 0 else float(np.sqrt(num))
+
+
+# ------------------------------------------------- half2 storage, in numpy
+def h16_quantise_rows(x):
+    """complex64 image -> (half2 [R, C, 2], per-row exponents) by the storage
+    format's definition: e = k - 14 for a row whose largest |component| is
+    f 2^k (f in [0.5, 1)), q = x 2^-e rounded to half precision."""
+    m = np.maximum(np.abs(x.real), np.abs(x.imag)).max(axis=1).astype(np.float64)
+    _, k = np.frexp(m)
+    e = np.where(m > 0, k - 14, 0).astype(np.int32)
+    f = np.ldexp(np.float32(1.0), -e).astype(np.float32)[:, None]
+    q = np.empty(x.shape + (2,), np.float16)
+    q[..., 0] = (x.real * f).astype(np.float16)
+    q[..., 1] = (x.imag * f).astype(np.float16)
+    return q, e
+
+
+def h16_dequantise(q, e, axis):
+    """half2 [R, C, 2] with exponents per row (axis 0) or column (1) ->
+    complex128 q * 2^e."""
+    sc = np.ldexp(1.0, e.astype(np.int64))
+    sc = sc[:, None] if axis == 0 else sc[None, :]
+    return q[..., 0].astype(np.float64) * sc + 1j * (q[..., 1].astype(np.float64) * sc)
+
+
+def cuda_timer(torch, stream):
+    """fn, n -> mean ms per call over n calls after 3 warm-up calls, timed
+    with CUDA events on `stream`."""
+    def t(fn, n):
+        for i in range(3):
+            fn(i)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for i in range(n):
+            fn(i)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+    return t
+
+
+def measure_fp16(fft, torch, orc, side, reps):
+    """Forward 2D FFT of a side x side image (re, im ~ U[-1, 1)) with half2
+    storage (fft2d_exec_h16) beside complex64 (fft2d_exec, autotuned), two
+    input/output pairs in turn; relative L2 error of each against the FP64
+    oracle of the input that path stored, with the half2 data quantised and
+    dequantised in numpy from the format's definition."""
+    import synth
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    t = cuda_timer(torch, stream)
+    peak, _ = measured_hbm_peak()
+    th = host_cores()
+    x = synth.uniform_complex(side, side, seed=side)
+    p32 = fft.fft2d_plan(side, side, fft.FFT2D_C64, fft.FFT2D_FORWARD)
+    p16 = fft.fft2d_plan(side, side, fft.FFT2D_C32H, fft.FFT2D_FORWARD)
+    try:
+        fft.fft2d_autotune(p32)
+        dx = [torch.from_numpy(x).cuda() for _ in range(2)]
+        dy = [torch.empty_like(dx[0]) for _ in range(2)]
+        ms32 = t(lambda i: fft.fft2d_exec(p32, dx[i & 1], dy[i & 1], sptr), reps)
+        ms32_rows = t(lambda i: fft.fft2d_exec_pass(p32, fft.FFT2D_PASS_ROWS, dx[i & 1],
+                                                    dy[i & 1], sptr), reps)
+        ms32_cols = t(lambda i: fft.fft2d_exec_pass(p32, fft.FFT2D_PASS_COLS, dy[i & 1],
+                                                    dy[i & 1], sptr), reps)
+        fft.fft2d_exec(p32, dx[0], dy[0], sptr)
+        torch.cuda.synchronize()
+        got32 = dy[0].cpu().numpy()
+        del dx, dy
+        q, e = h16_quantise_rows(x)
+        dq = [torch.from_numpy(q).cuda() for _ in range(2)]
+        de = torch.from_numpy(e).cuda()
+        dqo = [torch.empty_like(dq[0]) for _ in range(2)]
+        doe = [torch.empty(side, dtype=torch.int32, device="cuda") for _ in range(2)]
+        ms16 = t(lambda i: fft.fft2d_exec_h16(p16, dq[i & 1], de, fft.FFT2D_PASS_ROWS,
+                                              dqo[i & 1], doe[i & 1], sptr), reps)
+        fft.fft2d_exec_h16(p16, dq[0], de, fft.FFT2D_PASS_ROWS, dqo[0], doe[0], sptr)
+        torch.cuda.synchronize()
+        q_out, e_out = dqo[0].cpu().numpy(), doe[0].cpu().numpy()
+        del dq, dqo, doe
+        desc32 = fft.fft2d_plan_describe(p32)
+        desc16 = fft.fft2d_plan_describe(p16)
+    finally:
+        fft.fft2d_destroy(p32)
+        fft.fft2d_destroy(p16)
+    torch.cuda.empty_cache()
+    want32 = orc.fft2d(x, threads=th)
+    e32 = rel_l2(got32, want32)
+    del want32, got32
+    want16 = orc.fft2d(h16_dequantise(q, e, 0), threads=th)
+    e16 = rel_l2(h16_dequantise(q_out, e_out, 1), want16)
+    del want16
+    px = side * side
+    return {"fp16_ms": ms16, "fp32_ms": ms32, "speedup_fp16_vs_fp32": ms32 / ms16,
+            "fp32_row_pass_ms": ms32_rows, "fp32_col_pass_ms": ms32_cols,
+            "fp16_images_per_s": 1e3 / ms16, "fp32_images_per_s": 1e3 / ms32,
+            "fp16_hbm_frac": (16.0 * px / (ms16 * 1e-3) / 1e9) / peak,
+            "fp32_hbm_frac": (32.0 * px / (ms32 * 1e-3) / 1e9) / peak,
+            "fp16_rel_l2_vs_fp64_oracle": e16, "fp32_rel_l2_vs_fp64_oracle": e32,
+            "tolerance_fp16": 5e-3, "tolerance_fp32": 1e-5,
+            "fp32_kernels": desc32, "fp16_kernels": desc16,
+            "checking": "half2 input quantised and output dequantised in numpy"}
+
+
+def measure_batched(fft, torch, orc, steps, tune_plans=False):
+    """64 images with power-of-two sides log-uniform in 128..2048 (both
+    orientations), real part U[0,1): one step transforms all of them forward
+    through fft2d_exec_batched (grouped launches); the same images through
+    one fft2d_exec per image give the single-image path's figure.  Every
+    image of one batched step is checked against the FP64 oracle."""
+    import synth
+    shapes = synth.batch_shapes(64, seed=0)
+    imgs = synth.batch_images(shapes, seed=0)
+    if tune_plans:
+        tuned = set()
+        for r, c in shapes:
+            if (r, c) not in tuned:
+                p = fft.fft2d_plan(r, c, fft.FFT2D_C64, fft.FFT2D_FORWARD)
+                fft.fft2d_autotune(p)
+                fft.fft2d_destroy(p)
+                tuned.add((r, c))
+    plans = [fft.fft2d_plan(r, c, fft.FFT2D_C64, fft.FFT2D_FORWARD) for r, c in shapes]
+    ins = [torch.from_numpy(im).cuda() for im in imgs]
+    outs = [torch.empty_like(t) for t in ins]
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    px = sum(r * c for r, c in shapes)
+    t = cuda_timer(torch, stream)
+
+    def batched(_i=0):
+        fft.fft2d_exec_batched(plans, ins, outs, sptr)
+
+    def single(_i=0):
+        for p, x, o in zip(plans, ins, outs):
+            fft.fft2d_exec(p, x, o, sptr)
+
+    ms_default = t(batched, steps)
+    fft.fft2d_autotune_batched(plans, ins, outs, sptr)
+    R, C = fft.FFT2D_PASS_ROWS, fft.FFT2D_PASS_COLS
+    chosen = {f"{1 << L}": [fft.fft2d_batch_variant_name(R, fft.fft2d_batch_get_variant(R, L)),
+                            fft.fft2d_batch_variant_name(C, fft.fft2d_batch_get_variant(C, L))]
+              for L in sorted({(r.bit_length() - 1) for r, _ in shapes}
+                              | {(c.bit_length() - 1) for _, c in shapes})}
+    ms_b = t(batched, steps)
+    ms_s = t(single, steps)
+    peak, peak_src = measured_hbm_peak()
+    gbs = 32.0 * px / (ms_b * 1e-3) / 1e9
+    batched()
+    torch.cuda.synchronize()
+    th = host_cores()
+    errs = [rel_l2(o.cpu().numpy(), orc.fft2d(im, threads=th)) for o, im in zip(outs, imgs)]
+    for p in plans:
+        fft.fft2d_destroy(p)
+    return {"images_per_s": len(shapes) / (ms_b * 1e-3), "ms_per_step": ms_b,
+            "pixels_per_step": px,
+            "single_image_path": {"images_per_s": len(shapes) / (ms_s * 1e-3),
+                                  "ms_per_step": ms_s,
+                                  "call": "fft2d_exec per image"},
+            "speedup_vs_single": ms_s / ms_b,
+            "default_variants_ms_per_step": ms_default, "tuned_variants": chosen,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                         "frac": gbs / peak, "peak_source": peak_src,
+                         "algorithmic_bytes_per_step": 32 * px},
+            "rel_l2_max": max(errs), "rel_l2_median": float(np.median(errs)),
+            "images_checked": len(errs), "tolerance": 1e-5,
+            "gpu_launches_per_step": len({c for _, c in shapes}) + len({r for r, _ in shapes}),
+            "gpu_launches_per_step_single": 2 * len(shapes)}
+
+
 # ----------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -229,8 +451,13 @@ def run_ours(args):
     import synth
 
     side, B = args.side, args.images
-    imgs = [synth.blob_image(side, side, seed=sd) for sd in image_seeds(rank, B)]
-    xs = [torch.from_numpy(im).to(dev) for im in imgs]
+    nd = max(1, min(args.distinct, B))
+    imgs = [synth.blob_image(side, side, seed=sd) for sd in image_seeds(rank, nd)]
+    base = [torch.from_numpy(im).to(dev) for im in imgs]
+    # B resident images, copies of the nd distinct ones: every transform reads
+    # and writes its own buffers in HBM (B x 2 x 128 MiB, far beyond L2)
+    xs = [base[i % nd].clone() for i in range(B)]
+    del base
     Xs = [torch.empty_like(x) for x in xs]
     pf = fft.fft2d_plan(side, side, fft.FFT2D_C64, fft.FFT2D_FORWARD)
     pi = fft.fft2d_plan(side, side, fft.FFT2D_C64, fft.FFT2D_INVERSE)
@@ -239,17 +466,19 @@ def run_ours(args):
     ROWS, COLS = fft.FFT2D_PASS_ROWS, fft.FFT2D_PASS_COLS
     exec_pass = fft.fft2d_exec_pass
 
-    # the resident images are independent: each runs on its own stream,
-    # forked from and joined back into the timing stream, so one image's
-    # launch tails overlap another's
-    nstreams = min(args.streams if args.streams > 0 else B, B)
+    # the resident images are independent: they are spread over several
+    # streams, forked from and joined back into the timing stream, so one
+    # image's launch tails overlap another's
+    nstreams = min(args.streams if args.streams > 0 else 8, B)
     lanes = [stream] if nstreams == 1 else [torch.cuda.Stream(dev) for _ in range(nstreams)]
     fork = torch.cuda.Event()
     joins = [torch.cuda.Event() for _ in lanes]
+    kimg = min(B, 8)
 
     def step(evs=None):
         # forward then inverse of every resident image; with `evs`, an event
-        # brackets every kernel launch (rows fwd, cols fwd, rows inv, cols inv)
+        # brackets every kernel launch (rows fwd, cols fwd, rows inv, cols
+        # inv) of the first kimg images, all on the timing stream
         if evs is None and nstreams > 1:
             fork.record(stream)
             for ln in lanes:
@@ -261,7 +490,7 @@ def run_ours(args):
                 exec_pass(pf, COLS, X, X, lp)
                 exec_pass(pi, ROWS, X, X, lp)
                 exec_pass(pi, COLS, X, X, lp)
-            else:
+            elif i < kimg:
                 e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
                 e[0].record(stream)
                 exec_pass(pf, ROWS, x, X, sptr)
@@ -306,10 +535,10 @@ def run_ours(args):
     ms_local = t_start.elapsed_time(t_end)
     ms = max_over_ranks(ms_local, dist, dev)
 
-    # per-kernel durations: a second timed region of the same steps with an
-    # event between every two launches (the events themselves add about 2 us
-    # per launch, so the headline region above carries none)
-    kern_steps = max(args.steps // 4, 10)
+    # per-kernel durations: a second timed region with an event between every
+    # two launches (the events themselves add about 2 us per launch, so the
+    # headline region above carries none)
+    kern_steps = 10
     for _ in range(kern_steps):
         step(evs)
     torch.cuda.synchronize()
@@ -323,73 +552,91 @@ def run_ours(args):
     peak, peak_src = measured_hbm_peak()
     achieved = pass_bytes / (dom_ms * 1e-3) / 1e9
     value = job_value(2 * B * args.steps, ws, ms)
+    del xs, Xs
+    torch.cuda.empty_cache()
 
-    # end to end through the public host-buffer call: H2D, both passes, D2H
-    hin = [torch.from_numpy(im).pin_memory() for im in imgs]
+    # end to end through the public host-buffer call, every transform an
+    # independent image: upload, transform, download of its result
+    ne = min(B, 8)
+    hin = [torch.from_numpy(imgs[i % nd]).pin_memory() for i in range(ne)]
     hout = [torch.empty_like(h).pin_memory() for h in hin]
-    # one call per step: for every image its forward transform (hin -> hout)
-    # and then its inverse (hout -> hout); the inverse starts from the device
-    # copy of the forward result and overwrites it on the host, so each step
-    # uploads the B inputs and downloads the B round-trip results
-    step_plans, step_in, step_out = [], [], []
-    for b_ in range(B):
-        step_plans += [pf, pi]
-        step_in += [hin[b_], hout[b_]]
-        step_out += [hout[b_], hout[b_]]
-    fft.fft2d_exec_host_many(step_plans, step_in, step_out, sptr)    # allocate the pipeline
+    fft.fft2d_exec_host_many([pf] * ne, hin, hout, sptr)    # allocate the pipeline
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        # every transform uploads its input and downloads its result; the
-        # calls are queued back to back and the stream is synchronised once
-        fft.fft2d_exec_host_many_async(step_plans, step_in, step_out, sptr)
+        fft.fft2d_exec_host_many_async([pf] * ne, hin, hout, sptr)
     stream.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
     img_bytes = side * side * 8
-    e2e = {"value": 2 * B * args.e2e_steps * ws / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": B * img_bytes, "d2h_bytes_per_step": B * img_bytes,
-           "steps": args.e2e_steps,
-           "call": "fft2d_exec_host_many_async, one call per step: each image's forward "
-                   "transform, then its inverse from the device copy of the forward result "
-                   "into the same host buffer (the overwritten forward result is not copied "
-                   "back); stream synchronised after the last (pinned host buffers; uploads, "
-                   "transforms and downloads of consecutive images overlap)"}
-    # the same transforms one synchronous fft2d_exec_host call at a time
+    e2e = {"value": ne * args.e2e_steps * ws / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": ne * img_bytes, "d2h_bytes_per_step": ne * img_bytes,
+           "steps": args.e2e_steps, "images_per_step": ne,
+           "call": "fft2d_exec_host_many_async, one call per step of independent forward "
+                   "transforms: each image uploaded from pinned host memory, transformed and "
+                   "its result downloaded; uploads, transforms and downloads of consecutive "
+                   "images overlap; stream synchronised after the last call"}
+    # chained: each image's forward transform then its inverse in one call,
+    # the inverse starting from the device copy of the forward result and
+    # overwriting it on the host (the forward result is not downloaded)
+    step_plans, step_in, step_out = [], [], []
+    for b_ in range(ne):
+        step_plans += [pf, pi]
+        step_in += [hin[b_], hout[b_]]
+        step_out += [hout[b_], hout[b_]]
+    fft.fft2d_exec_host_many(step_plans, step_in, step_out, sptr)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        fft.fft2d_exec_host_many_async(step_plans, step_in, step_out, sptr)
+    stream.synchronize()
+    e2e["chained_forward_inverse"] = {
+        "value": 2 * ne * args.e2e_steps * ws / max_over_ranks(time.perf_counter() - t0, dist,
+                                                                dev),
+        "unit": UNIT, "h2d_bytes_per_step": ne * img_bytes, "d2h_bytes_per_step": ne * img_bytes,
+        "counting": "forward and inverse each count as one transform; one upload and one "
+                    "download per pair"}
+    # one synchronous fft2d_exec_host call per transform
     t0 = time.perf_counter()
     for h, o in zip(hin, hout):
         fft.fft2d_exec_host(pf, h, o, sptr)
-        fft.fft2d_exec_host(pi, o, o, sptr)
-    e2e["one_call_per_image"] = {"value": 2 * B * ws / max_over_ranks(
+    e2e["one_call_per_image"] = {"value": ne * ws / max_over_ranks(
         time.perf_counter() - t0, dist, dev), "call": "fft2d_exec_host"}
 
+    orc = None
     parity = None
     if rank == 0 and not args.no_parity:
         from oracle import oracle
         orc = oracle.get()
-        X = torch.empty_like(xs[0])
-        fft.fft2d_exec(pf, xs[0], X, sptr)
+        x0 = torch.from_numpy(imgs[0]).to(dev)
+        X = torch.empty_like(x0)
+        fft.fft2d_exec(pf, x0, X, sptr)
         Y = torch.empty_like(X)
         fft.fft2d_exec(pi, X, Y, sptr)
         torch.cuda.synchronize()
         Xh, Yh = X.cpu().numpy(), Y.cpu().numpy()
+        del x0, X, Y
         th = host_cores()
         want = orc.fft2d(imgs[0], threads=th)
         back = orc.fft2d(Xh, inverse=True, threads=th)
-        rl = lambda a, b: float(np.linalg.norm((a.astype(np.complex128) - b).ravel())
-                                / np.linalg.norm(b.ravel()))
-        parity = {"fwd_rel_l2": rl(Xh, want), "inv_rel_l2": rl(Yh, back),
-                  "round_trip_rel_l2": rl(Yh, imgs[0].astype(np.complex128)),
+        parity = {"fwd_rel_l2": rel_l2(Xh, want), "inv_rel_l2": rel_l2(Yh, back),
+                  "round_trip_rel_l2": rel_l2(Yh, imgs[0]),
                   "tolerance": 1e-5, "image": "blob 4096x4096 seed 0"}
+        del want, back
+
+    sub = {}
+    if rank == 0 and not args.no_sub:
+        if orc is None:
+            from oracle import oracle
+            orc = oracle.get()
+        sub["serve"] = measure_serve(fft, torch, args.serve_sample, args.rate, single=False)
+        sub["fp16"] = {"4096x4096": measure_fp16(fft, torch, orc, 4096, 20)}
+        sub["batched"] = measure_batched(fft, torch, orc, 50)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        th = host_cores()
-        v, n, dt = cpu_oracle_sample(side, args.cpu_seconds, th)
-        cpu = {"value": v, "unit": UNIT, "cores": th, "kind": "oracle",
-               "sample": f"{n} transforms ({n // 2} forward+inverse pairs) of one "
-                         f"{side}x{side} blob image, FP64 C oracle on {th} threads, {dt:.1f} s"}
+        cpu = cpu_baseline(side, args.cpu_seconds)
 
     if rank == 0:
         line = {
@@ -399,11 +646,14 @@ def run_ours(args):
             "dtype": "f32", "data": "synthetic (seeded Gaussian-blob + U[0,1) gray images)",
             "config": {"workload": f"{side}x{side} complex64 2D FFT, forward+inverse of "
                                    f"{B} resident images per GPU per step",
-                       "side": side, "images_per_gpu": B, "parallelism": f"replicas x{ws}",
+                       "side": side, "images_per_gpu": B,
+                       "distinct_images": f"{nd} seeded images, each resident {B // nd}x",
+                       "parallelism": f"replicas x{ws}",
                        "streams": nstreams,
                        "l2": f"inputs larger than L2 ({B} images x 2 buffers x "
-                             f"{img_bytes >> 20} MiB rotated)",
+                             f"{img_bytes >> 20} MiB)",
                        "transform_counting": "forward and inverse each count as one image"},
+            "timed_region_ms": ms,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": peak_src,
@@ -411,7 +661,8 @@ def run_ours(args):
                          "avg_launch_ms": dom_ms,
                          "traffic": ncu_traffic(dom)},
             "passes_ms": per,
-            "passes_timing": f"{kern_steps} steps with an event between every two launches",
+            "passes_timing": f"{kern_steps} steps of {kimg} images with an event between "
+                             "every two launches",
             "whole_transform_hbm_frac": (2 * pass_bytes / (ms / args.steps / (2 * B) * 1e-3)
                                          / 1e9) / peak,
             "cpu_baseline": cpu,
@@ -420,6 +671,7 @@ def run_ours(args):
             "clocks": clk,
             "parity": parity,
         }
+        line.update(sub)
         print(json.dumps(line), flush=True)
     for p in (pf, pi):
         fft.fft2d_destroy(p)
@@ -472,178 +724,47 @@ def run_reference(args):
 
 # ------------------------------------------------------- batched workload
 def run_batched(args):
-    """64 images with power-of-two sides log-uniform in 128..2048 (both
-    orientations), real part U[0,1): one step transforms all of them forward
-    through fft2d_exec_batched (grouped launches); the same images through
-    one fft2d_exec per image give the single-image path's figure."""
+    """The batched workload alone (see measure_batched), with every plan
+    shape autotuned first."""
     import torch
     torch.cuda.set_device(0)
     import __graft_entry__
     __graft_entry__.build()
     import paper_1505_08019_gb300 as fft
-    import synth
-    shapes = synth.batch_shapes(64, seed=0)
-    imgs = synth.batch_images(shapes, seed=0)
-    plans = [fft.fft2d_plan(r, c, fft.FFT2D_C64, fft.FFT2D_FORWARD) for r, c in shapes]
-    tuned = set()
-    for p, sh in zip(plans, shapes):
-        if sh not in tuned:
-            fft.fft2d_autotune(p)
-            tuned.add(sh)
-    plans = [fft.fft2d_plan(r, c, fft.FFT2D_C64, fft.FFT2D_FORWARD) for r, c in shapes]
-    ins = [torch.from_numpy(im).cuda() for im in imgs]
-    outs = [torch.empty_like(t) for t in ins]
-    stream = torch.cuda.current_stream()
-    sptr = stream.cuda_stream
-    px = sum(r * c for r, c in shapes)
-
-    def timed(fn, steps, warm):
-        for _ in range(warm):
-            fn()
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(steps):
-            fn()
-        b.record(stream)
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / steps
-
-    def batched():
-        fft.fft2d_exec_batched(plans, ins, outs, sptr)
-
-    def single():
-        for p, x, o in zip(plans, ins, outs):
-            fft.fft2d_exec(p, x, o, sptr)
-
-    steps = max(args.steps // 10, 20)
-    ms_default = timed(batched, steps, max(args.warmup, 3))
-    fft.fft2d_autotune_batched(plans, ins, outs, sptr)
-    R, C = fft.FFT2D_PASS_ROWS, fft.FFT2D_PASS_COLS
-    chosen = {f"{1 << L}": [fft.fft2d_batch_variant_name(R, fft.fft2d_batch_get_variant(R, L)),
-                            fft.fft2d_batch_variant_name(C, fft.fft2d_batch_get_variant(C, L))]
-              for L in sorted({(r.bit_length() - 1) for r, _ in shapes}
-                              | {(c.bit_length() - 1) for _, c in shapes})}
-    ms_b = timed(batched, steps, max(args.warmup, 3))
-    ms_s = timed(single, steps, max(args.warmup, 3))
-    peak, peak_src = measured_hbm_peak()
-    gbs = 32.0 * px / (ms_b * 1e-3) / 1e9
-    # accuracy of a sample against the oracle
     from oracle import oracle
-    orc = oracle.get()
-    batched()
-    torch.cuda.synchronize()
-    errs = []
-    for i in (0, 21, 42, 63):
-        want = orc.fft2d(imgs[i], threads=host_cores())
-        got = outs[i].cpu().numpy().astype(np.complex128)
-        errs.append(float(np.linalg.norm(got - want) / np.linalg.norm(want)))
+    steps = max(args.steps // 10, 20)
+    r = measure_batched(fft, torch, oracle.get(), steps, tune_plans=True)
     line = {
         "metric": "batched 2D FFT images/s (64 uneven power-of-two images, 128..2048 sides)",
-        "value": len(shapes) / (ms_b * 1e-3), "unit": "images/s", "n_gpus": 1, "steps": steps,
-        "warmup": max(args.warmup, 3), "ms_per_step": ms_b, "higher_is_better": True,
+        "value": r["images_per_s"], "unit": "images/s", "n_gpus": 1, "steps": steps,
+        "warmup": 3, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
         "dtype": "f32", "data": "synthetic (seeded U[0,1) gray images)",
         "config": {"workload": "64 images, log2 sides ~ U{7..11} each (seed 0), forward",
-                   "pixels_per_step": px, "l2": f"inputs larger than L2 ({px * 16 >> 20} MiB)"},
-        "single_image_path": {"value": len(shapes) / (ms_s * 1e-3), "ms_per_step": ms_s,
-                              "call": "fft2d_exec per image (autotuned plans)"},
-        "speedup_vs_single": ms_s / ms_b,
-        "default_variants_ms_per_step": ms_default,
-        "tuned_variants": chosen,
-        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
-                     "frac": gbs / peak, "peak_source": peak_src,
-                     "algorithmic_bytes_per_step": 32 * px},
-        "rel_l2_samples": errs, "tolerance": 1e-5,
-        "gpu_launches_per_step": len({c for _, c in shapes}) + len({r for r, _ in shapes}),
-        "gpu_launches_per_step_single": 2 * len(shapes),
-    }
+                   "pixels_per_step": r["pixels_per_step"],
+                   "l2": f"inputs larger than L2 ({r['pixels_per_step'] * 16 >> 20} MiB)"}}
+    line.update(r)
     print(json.dumps(line), flush=True)
 
 
 # ------------------------------------------------------------ fp16 workload
 def run_fp16(args):
-    """8192^2 and 16384^2 forward transforms of re, im ~ U[-1,1): half2
-    storage with per-line exponents (fft2d_exec_h16) beside complex64
-    (fft2d_exec) on the same GPU, with the relative L2 error of each against
-    the FP64 oracle."""
+    """Half2 storage against complex64 at each --fp16-sides size (see
+    measure_fp16)."""
     import torch
     torch.cuda.set_device(0)
     import __graft_entry__
     __graft_entry__.build()
     import paper_1505_08019_gb300 as fft
-    import synth
     from oracle import oracle
     orc = oracle.get()
-    stream = torch.cuda.current_stream()
-    sptr = stream.cuda_stream
     peak, peak_src = measured_hbm_peak()
-    results = {}
     sides = [int(v) for v in args.fp16_sides.split(",") if v]
+    results = {}
     for side in sides:
-        x = synth.uniform_complex(side, side, seed=side)
-        dx = torch.from_numpy(x).cuda()
-        y = torch.empty_like(dx)
-        p32 = fft.fft2d_plan(side, side, fft.FFT2D_C64, fft.FFT2D_FORWARD)
-        fft.fft2d_autotune(p32)
-        p16 = fft.fft2d_plan(side, side, fft.FFT2D_C32H, fft.FFT2D_FORWARD)
-        q = torch.empty((side, side, 2), dtype=torch.float16, device="cuda")
-        qe = torch.empty(side, dtype=torch.int32, device="cuda")
-        fft.fft2d_h16_pack(side, side, dx, q, qe, sptr)
-        qo = torch.empty_like(q)
-        oe = torch.empty(side, dtype=torch.int32, device="cuda")
-
-        def t(fn, n):
-            for _ in range(3):
-                fn()
-            torch.cuda.synchronize()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            for _ in range(n):
-                fn()
-            b.record(stream)
-            torch.cuda.synchronize()
-            return a.elapsed_time(b) / n
-
-        reps = 20 if side == 8192 else 8
-        ms32 = t(lambda: fft.fft2d_exec(p32, dx, y, sptr), reps)
-        ms32_rows = t(lambda: fft.fft2d_exec_pass(p32, fft.FFT2D_PASS_ROWS, dx, y, sptr), reps)
-        ms32_cols = t(lambda: fft.fft2d_exec_pass(p32, fft.FFT2D_PASS_COLS, y, y, sptr), reps)
-        ms16 = t(lambda: fft.fft2d_exec_h16(p16, q, qe, fft.FFT2D_PASS_ROWS, qo, oe, sptr), reps)
-        # accuracy against the FP64 oracle (of the input each path saw); the
-        # per-pass timings above overwrote y, so transform once more
-        fft.fft2d_exec(p32, dx, y, sptr)
-        th = host_cores()
-        xin = torch.empty_like(dx)
-        fft.fft2d_h16_unpack(side, side, q, qe, fft.FFT2D_PASS_ROWS, xin, sptr)
-        got16 = torch.empty_like(dx)
-        fft.fft2d_h16_unpack(side, side, qo, oe, fft.FFT2D_PASS_COLS, got16, sptr)
-        torch.cuda.synchronize()
-        want32 = orc.fft2d(x, threads=th)
-        e32 = float(np.linalg.norm(y.cpu().numpy().astype(np.complex128) - want32)
-                    / np.linalg.norm(want32))
-        del want32
-        want16 = orc.fft2d(xin.cpu().numpy(), threads=th)
-        e16 = float(np.linalg.norm(got16.cpu().numpy().astype(np.complex128) - want16)
-                    / np.linalg.norm(want16))
-        del want16
-        px = side * side
-        results[f"{side}x{side}"] = {
-            "fp16_ms": ms16, "fp32_ms": ms32, "speedup_fp16_vs_fp32": ms32 / ms16,
-            "fp32_row_pass_ms": ms32_rows, "fp32_col_pass_ms": ms32_cols,
-            "fp16_images_per_s": 1e3 / ms16, "fp32_images_per_s": 1e3 / ms32,
-            "fp16_hbm_frac": (16.0 * px / (ms16 * 1e-3) / 1e9) / peak,
-            "fp32_hbm_frac": (32.0 * px / (ms32 * 1e-3) / 1e9) / peak,
-            "fp16_rel_l2_vs_fp64_oracle": e16, "fp32_rel_l2_vs_fp64_oracle": e32,
-            "fp32_kernels": fft.fft2d_plan_describe(p32),
-            "tolerance_fp16": 5e-3, "tolerance_fp32": 1e-5}
-        for p in (p32, p16):
-            fft.fft2d_destroy(p)
-        del dx, y, q, qo, xin, got16
-        torch.cuda.empty_cache()
+        reps = 20 if side <= 8192 else 8
+        results[f"{side}x{side}"] = measure_fp16(fft, torch, orc, side, reps)
     big = results[f"{max(sides)}x{max(sides)}"]
-    line = {"metric": "2D FFT images/s, FP16 half2 storage vs complex64 (8192^2, 16384^2)",
+    line = {"metric": "2D FFT images/s, FP16 half2 storage vs complex64",
             "value": big["fp16_images_per_s"], "unit": "images/s", "n_gpus": 1,
             "higher_is_better": True, "dtype": "f32 (half2 storage)",
             "data": "synthetic (seeded re, im ~ U[-1,1))",
@@ -678,28 +799,24 @@ def serve_mix(n, seed=0):
     return out
 
 
-def run_serve(args):
-    import threading
-
-    import torch
-    torch.cuda.set_device(0)
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_1505_08019_gb300 as fft
+def measure_serve(fft, torch, n, rate, single=True):
+    """The serving loop on a seeded Poisson stream of n requests at `rate`
+    req/s (serve_mix; arrivals seed 1) under a 40 GB budget on 4 streams,
+    after one warm-up request per (shape, op, dtype); latency percentiles
+    overall and per storage type, throughput, and (with `single`) the
+    saturation capacity and the plain one-request-at-a-time complex64 path."""
     import synth
-    n, rate = args.requests, args.rate
     mix = serve_mix(n, seed=0)
     g = np.random.default_rng(1)
     arrivals = np.cumsum(g.exponential(1.0 / rate, n))
     shapes = sorted({(r, c) for _, r, c, _ in mix})
     # one pinned input image per shape; outputs are shared per shape (their
-    # contents are not inspected here -- the tests check results)
+    # contents are checked by the tests, not here)
     inp = {sh: torch.from_numpy(synth.uniform_real(sh[0], sh[1], seed=7)).pin_memory()
            for sh in shapes}
     outb = {sh: torch.empty(sh, dtype=torch.complex64).pin_memory() for sh in shapes}
     budget = 40 << 30
     srv = fft.fft2d_serve_create(budget, 4)
-    # warm up: resident plans and pooled buffers for every shape and type
     for sh in shapes:
         for op in (0, 1):
             for dt in (0, 1):
@@ -716,77 +833,93 @@ def run_serve(args):
     lat = np.array([fft.fft2d_serve_wait(srv, t) for t in tickets])
     wall = time.perf_counter() - t0
     st = fft.fft2d_serve_stats_get(srv)
-
-    # capacity: the same kind of requests submitted all at once (saturation)
-    m_sat = min(n, 4000)
-    sat_mix = serve_mix(m_sat, seed=2)
-    t2 = time.perf_counter()
-    sat_t = [fft.fft2d_serve_submit(srv, op, r, c, dt, inp[(r, c)], outb[(r, c)])
-             for op, r, c, dt in sat_mix]
-    sat_lat = np.array([fft.fft2d_serve_wait(srv, t) for t in sat_t])
-    sat_wall = time.perf_counter() - t2
-    st2 = fft.fft2d_serve_stats_get(srv)
+    dts = np.array([dt for *_, dt in mix])
+    done = st["completed"] - base["completed"]
+    nb = max(1, st["batches"] - base["batches"])
+    out = {
+        "requests": n, "offered_rps": rate,
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+        "throughput_rps": n / wall, "completed": done, "batches": nb,
+        "mean_batch_size": done / nb, "peak_device_bytes": st["peak_device_bytes"],
+        "by_dtype": {name: {"requests": int((dts == code).sum()),
+                            "p50_ms": float(np.percentile(lat[dts == code], 50)),
+                            "p99_ms": float(np.percentile(lat[dts == code], 99))}
+                     for name, code in (("complex64", 0), ("fp16", 1)) if (dts == code).any()},
+        "latency": "submit -> result in the host buffer, as the server stamps it",
+        "workload": f"{n} requests at {rate:g} req/s (Poisson, seed 1); long side 2^u, "
+                    "u~U{6..12}; 50% square, 50% 1:4; 50% forward, 50% "
+                    "FFT->LPF(sigma=side/8)->iFFT; 70% c64 / 30% half2; pinned host buffers, "
+                    "copies included; HBM budget 40 GB; 4 streams"}
+    if single:
+        # capacity: the same kind of requests submitted all at once
+        m_sat = min(n, 4000)
+        sat_mix = serve_mix(m_sat, seed=2)
+        t2 = time.perf_counter()
+        sat_t = [fft.fft2d_serve_submit(srv, op, r, c, dt, inp[(r, c)], outb[(r, c)])
+                 for op, r, c, dt in sat_mix]
+        sat_lat = np.array([fft.fft2d_serve_wait(srv, t) for t in sat_t])
+        sat_wall = time.perf_counter() - t2
+        st2 = fft.fft2d_serve_stats_get(srv)
+        out["saturation"] = {"requests": m_sat, "throughput_rps": m_sat / sat_wall,
+                             "mean_batch_size": m_sat / max(1, st2["batches"] - st["batches"]),
+                             "p50_ms": float(np.percentile(sat_lat, 50)),
+                             "p99_ms": float(np.percentile(sat_lat, 99)),
+                             "how": "all requests submitted at once; throughput = requests / "
+                                    "time to the last result"}
     fft.fft2d_serve_destroy(srv)
+    if single:
+        # the plain single-image FP32 path on the same requests, one at a
+        # time: copy in, transform(s), copy out, wait -- no queueing, no overlap
+        m = min(n, 2000)
+        stream = torch.cuda.current_stream()
+        sptr = stream.cuda_stream
+        plans = {}
 
-    # the plain single-image FP32 path on the same requests, one at a time:
-    # copy in, transform(s), copy out, wait -- no queueing, no overlap
-    m = min(n, 2000)
-    stream = torch.cuda.current_stream()
-    sptr = stream.cuda_stream
-    plans = {}
+        def plan(r, c, d):
+            if (r, c, d) not in plans:
+                plans[(r, c, d)] = fft.fft2d_plan(r, c, fft.FFT2D_C64, d)
+            return plans[(r, c, d)]
 
-    def plan(r, c, d):
-        if (r, c, d) not in plans:
-            plans[(r, c, d)] = fft.fft2d_plan(r, c, fft.FFT2D_C64, d)
-        return plans[(r, c, d)]
+        dev = {sh: torch.empty(sh, dtype=torch.complex64, device="cuda") for sh in shapes}
+        single_lat = []
+        t1 = time.perf_counter()
+        for op, r, c, _ in mix[:m]:
+            ts = time.perf_counter()
+            d = dev[(r, c)]
+            d.copy_(inp[(r, c)], non_blocking=True)
+            fft.fft2d_exec(plan(r, c, -1), d, d, sptr)
+            if op == 1:
+                fft.fft2d_lowpass(r, c, fft.FFT2D_C64, d, r / 8.0, c / 8.0, sptr)
+                fft.fft2d_exec(plan(r, c, 1), d, d, sptr)
+            outb[(r, c)].copy_(d, non_blocking=True)
+            torch.cuda.synchronize()
+            single_lat.append((time.perf_counter() - ts) * 1e3)
+        single_wall = time.perf_counter() - t1
+        for p in plans.values():
+            fft.fft2d_destroy(p)
+        out["single_image_path"] = {"requests": m, "throughput_rps": m / single_wall,
+                                    "p50_ms": float(np.percentile(single_lat, 50)),
+                                    "p99_ms": float(np.percentile(single_lat, 99)),
+                                    "how": "one request at a time: H2D, fft2d_exec (+ low-pass "
+                                           "and inverse), D2H, synchronize; complex64 for all"}
+    return out
 
-    dev = {sh: torch.empty(sh, dtype=torch.complex64, device="cuda") for sh in shapes}
-    single_lat = []
-    t1 = time.perf_counter()
-    for op, r, c, _ in mix[:m]:
-        ts = time.perf_counter()
-        d = dev[(r, c)]
-        d.copy_(inp[(r, c)], non_blocking=True)
-        fft.fft2d_exec(plan(r, c, -1), d, d, sptr)
-        if op == 1:
-            fft.fft2d_lowpass(r, c, fft.FFT2D_C64, d, r / 8.0, c / 8.0, sptr)
-            fft.fft2d_exec(plan(r, c, 1), d, d, sptr)
-        outb[(r, c)].copy_(d, non_blocking=True)
-        torch.cuda.synchronize()
-        single_lat.append((time.perf_counter() - ts) * 1e3)
-    single_wall = time.perf_counter() - t1
-    for p in plans.values():
-        fft.fft2d_destroy(p)
+
+def run_serve(args):
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1505_08019_gb300 as fft
+    r = measure_serve(fft, torch, args.requests, args.rate, single=True)
     line = {
         "metric": "serving p50/p99 latency & throughput (Poisson 2D FFT / FFT-filter-iFFT mix)",
-        "value": st["p99_ms"], "unit": "ms (p99)", "n_gpus": 1, "higher_is_better": False,
+        "value": r["p99_ms"], "unit": "ms (p99)", "n_gpus": 1, "higher_is_better": False,
         "dtype": "f32 (70% complex64, 30% half2 storage)",
         "data": "synthetic (seeded Poisson arrivals, U[0,1) gray images)",
-        "config": {"workload": f"{n} requests at {rate:g} req/s (Poisson, seed 1); long side "
-                               "2^u, u~U{6..12}; 50% square, 50% 1:4; 50% forward, 50% "
-                               "FFT->LPF(sigma=side/8)->iFFT; 70% c64 / 30% half2; host "
-                               "buffers (pinned), copies included; HBM budget 40 GB; 4 streams"},
-        "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
-        "max_ms": st["max_ms"],
-        "throughput_rps": n / wall, "offered_rps": rate,
-        "completed": st["completed"] - base["completed"],
-        "batches": st["batches"] - base["batches"],
-        "mean_batch_size": (st["completed"] - base["completed"]) / max(1, st["batches"] - base["batches"]),
-        "peak_device_bytes": st["peak_device_bytes"],
-        "client_latency_p50_ms": float(np.percentile(lat, 50)),
-        "client_latency_p99_ms": float(np.percentile(lat, 99)),
-        "saturation": {"requests": m_sat, "throughput_rps": m_sat / sat_wall,
-                       "mean_batch_size": m_sat / max(1, st2["batches"] - st["batches"]),
-                       "p50_ms": float(np.percentile(sat_lat, 50)),
-                       "p99_ms": float(np.percentile(sat_lat, 99)),
-                       "how": "all requests submitted at once; throughput = requests / "
-                              "time to the last result"},
-        "single_image_path": {"requests": m, "throughput_rps": m / single_wall,
-                              "p50_ms": float(np.percentile(single_lat, 50)),
-                              "p99_ms": float(np.percentile(single_lat, 99)),
-                              "how": "one request at a time: H2D, fft2d_exec (+ low-pass and "
-                                     "inverse), D2H, synchronize; complex64 for all"},
-    }
+        "config": {"workload": r["workload"]}}
+    line.update(r)
     print(json.dumps(line), flush=True)
 
 # ------------------------------------------------------------- DCT workload
