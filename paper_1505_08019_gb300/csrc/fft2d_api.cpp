@@ -875,6 +875,7 @@ fft2d_status fft2d_exec_h16(fft2d_plan_t p, const void *in, const int *in_exp, i
     a.in_exp = p->exp_rows;
     a.in_axis = FFT2D_PASS_ROWS;
     a.out_exp = out_exp;
+    a.err = p->dev_err;
     e = fft2d::launch_pass_h16(false, p->Lr, a, st);
     if (e != cudaSuccess)
         return cuda_fail(e, "half2 column pass");

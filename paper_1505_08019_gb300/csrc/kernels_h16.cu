@@ -2,8 +2,10 @@
 // the row and column passes (FP32 butterflies and exchanges, half2 global
 // traffic) and the pack / unpack conversions between complex64 and that
 // format.
+#include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 
+#include "col_h16.cuh"
 #include "line_fft.cuh"
 #include "passes.h"
 
@@ -11,11 +13,12 @@ namespace fft2d {
 
 namespace {
 
-template <class C, bool ROW, bool GENERIC>
-cudaError_t h16_launch(const H16PassArgs &a, cudaStream_t s)
+template <class C, bool ROW, bool GENERIC, int IA>
+cudaError_t h16_launch_axis(const H16PassArgs &a, cudaStream_t s)
 {
-    auto k = ROW ? row_pass_kernel<C, GENERIC, StoreH16> : col_pass_kernel<C, GENERIC, StoreH16>;
-    const int bytes = LineSmem<C, ROW, StoreH16>::BYTES;
+    using IO = StoreH16T<IA>;
+    auto k = ROW ? row_pass_kernel<C, GENERIC, IO> : col_pass_kernel<C, GENERIC, IO>;
+    const int bytes = LineSmem<C, ROW, IO>::BYTES;
     if (bytes > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e != cudaSuccess)
@@ -24,8 +27,78 @@ cudaError_t h16_launch(const H16PassArgs &a, cudaStream_t s)
     const int lines = ROW ? a.rows : a.cols;
     const int per = ROW ? C::LB : C::W;
     const unsigned grid = (unsigned)((lines + per - 1) / per);
-    StoreH16 io{a.in, a.out, a.in_exp, a.in_axis, a.out_exp};
+    IO io{a.in, a.out, a.in_exp, a.in_axis, a.out_exp};
     k<<<grid, C::T, bytes, s>>>(io, a.tw, lines, a.ld, a.scale, a.nst);
+    return cudaGetLastError();
+}
+
+// The input's exponent axis becomes a compile-time choice, so a line's
+// exponent is loaded once per unit where it runs along the line.
+template <class C, bool ROW, bool GENERIC>
+cudaError_t h16_launch(const H16PassArgs &a, cudaStream_t s)
+{
+    return a.in_axis == 0 ? h16_launch_axis<C, ROW, GENERIC, 0>(a, s)
+                          : h16_launch_axis<C, ROW, GENERIC, 1>(a, s);
+}
+
+// 3D tensor map over a half2 image (4-byte elements): x = column, y = row
+// within a block of 256 rows, z = block; box W x box_y x box_z.
+bool encode_h16_col_map(CUtensorMap *map, const __half2 *base, int rows, int cols, long long ld,
+                        int W, int box_y, int box_z)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 enc = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        return static_cast<PFN_cuTensorMapEncodeTiled_v12000>(nullptr);
+    }();
+    if (!enc || (reinterpret_cast<uintptr_t>(base) & 15) || ((ld * 4) & 15) || rows % 256 != 0)
+        return false;
+    cuuint64_t dims[3] = {(cuuint64_t)cols, 256, (cuuint64_t)(rows / 256)};
+    cuuint64_t strides[2] = {(cuuint64_t)ld * 4, (cuuint64_t)ld * 4 * 256};
+    cuuint32_t box[3] = {(cuuint32_t)W, (cuuint32_t)box_y, (cuuint32_t)box_z};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<__half2 *>(base), dims, strides,
+               box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+// The persistent TMA-fed half2 column pass (col_h16.cuh) for columns of
+// 2^L rows in 4-column tiles.  Returns cudaErrorNotSupported (nothing
+// launched) when the buffers or shape cannot feed it: the caller then takes
+// another kernel.
+template <int L>
+cudaError_t h16_launch_col_tma(const H16PassArgs &a, cudaStream_t s)
+{
+    using C = LineCfg<L, 2, 0, 32>;
+    using H = H16Col<C>;
+    if (a.in_axis != 0 || a.nst != L || !a.err || a.cols % C::W != 0 ||
+        (reinterpret_cast<uintptr_t>(a.tw) & 15))
+        return cudaErrorNotSupported;
+    CUtensorMap map, omap;
+    if (!encode_h16_col_map(&map, a.in, a.rows, a.cols, a.ld, C::W, H::BOX, H::NB) ||
+        !encode_h16_col_map(&omap, a.out, a.rows, a.cols, a.ld, C::W, H::BOX, H::NBOX))
+        return cudaErrorNotSupported;
+    auto k = col_h16_tma_kernel<C>;
+    static DeviceCache ready;
+    const int d = device_current();
+    if (!ready.get(d)) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             H::SMEM_BYTES);
+        if (e != cudaSuccess)
+            return e;
+        ready.set(d, 1);
+    }
+    const int ntiles = a.cols / C::W;
+    int grid = device_sm_count();
+    if (grid > ntiles)
+        grid = ntiles;
+    k<<<grid, C::T, H::SMEM_BYTES, s>>>(map, omap, a.tw, a.in_exp, a.out_exp, a.cols, a.scale,
+                                        a.err);
     return cudaGetLastError();
 }
 
@@ -38,6 +111,11 @@ cudaError_t h16_dispatch(bool row, const H16PassArgs &a, cudaStream_t s)
         return a.rows % C::LB ? h16_launch<C, true, true>(a, s) : h16_launch<C, true, false>(a, s);
     }
     using C = LineCfg<L, col_kw(L), 0>;
+    if constexpr (L == 12) {
+        const cudaError_t e = h16_launch_col_tma<L>(a, s);
+        if (e != cudaErrorNotSupported)
+            return e;
+    }
     if constexpr (L >= 12) {
         // from 4096 rows the single-CTA tile would be 2 or fewer columns
         // wide (8 bytes of half2 per row): split 8-column tiles over a

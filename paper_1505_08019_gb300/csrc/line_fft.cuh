@@ -192,20 +192,27 @@ __device__ __forceinline__ void run_stages(float2 (&a)[C::EPT], int v, int lo,
 //    every stored |q| < 2^14, well inside half precision's range.
 struct StoreC64 {
     static constexpr bool H16 = false;
+    static constexpr int AXIS = -1;
     using T = float2;
     const float2 *in;
     float2 *out;
 };
 
-struct StoreH16 {
+// IA: the input's exponent axis when fixed at compile time (0 per row, 1 per
+// column), -1 when it is taken from in_axis at run time.
+template <int IA = -1>
+struct StoreH16T {
     static constexpr bool H16 = true;
+    static constexpr int AXIS = IA;
     using T = __half2;
     const __half2 *in;
     __half2 *out;
     const int *in_exp;   // exponents of the input lines
     int in_axis;         // 0: one per row, 1: one per column
     int *out_exp;        // exponents of this pass's output lines
+    __device__ __forceinline__ int axis() const { return IA >= 0 ? IA : in_axis; }
 };
+using StoreH16 = StoreH16T<-1>;
 
 // 2^e as a float (exact), e clamped to the normal range.
 __device__ __forceinline__ float pow2f(int e)
@@ -237,19 +244,50 @@ __device__ __forceinline__ long long pix(const Geo &g, int lb, int i, int w)
     return ROW ? (g.r0 + lb) * g.ld + i : (g.r0 + (long long)i * g.rstep) * g.ld + g.c0 + w;
 }
 
+// Whether every value of one unit of group 0 (one line block lb, one
+// interleaved line w) shares its input exponent: the exponent runs along the
+// line being transformed.
 template <class IO, bool ROW>
-__device__ __forceinline__ float2 load_pix(const IO &io, const Geo &g, int lb, int i, int w)
+struct H16PerUnit {
+    static constexpr bool value = IO::H16 && ((ROW && IO::AXIS == 0) || (!ROW && IO::AXIS == 1));
+};
+
+// 2^e of the input line holding element i of line (lb, w).
+template <class IO, bool ROW>
+__device__ __forceinline__ float in_factor(const IO &io, const Geo &g, int lb, int i, int w)
+{
+    const long long line = io.axis() == 0 ? (ROW ? g.r0 + lb : g.r0 + (long long)i * g.rstep)
+                                          : (ROW ? (long long)i : g.c0 + w);
+    return pow2f(io.in_exp[line]);
+}
+
+// Element i of line (lb, w); for half2 storage, f is its line's 2^e when
+// the caller already knows it (H16PerUnit), else 0.
+template <class IO, bool ROW>
+__device__ __forceinline__ float2 load_pix(const IO &io, const Geo &g, int lb, int i, int w,
+                                           float f = 0.f)
 {
     const long long k = pix<ROW>(g, lb, i, w);
     if constexpr (IO::H16) {
         const float2 q = __half22float2(io.in[k]);
-        const long long line = io.in_axis == 0 ? (ROW ? g.r0 + lb : g.r0 + (long long)i * g.rstep)
-                                               : (ROW ? (long long)i : g.c0 + w);
-        const float f = pow2f(io.in_exp[line]);
+        if constexpr (!H16PerUnit<IO, ROW>::value)
+            f = in_factor<IO, ROW>(io, g, lb, i, w);
         return make_float2(q.x * f, q.y * f);
     } else {
         return ld_stream(io.in + k);
     }
+}
+
+// Max of m over the lanes of a warp that hold values of the same output
+// line, for a line index that is constant over the lane bits [B0, B1):
+// afterwards the lane with those bits clear holds the maximum.
+template <int B0, int B1>
+__device__ __forceinline__ float warp_line_max(float m)
+{
+#pragma unroll
+    for (int b = B0; b < B1; b++)
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1 << b));
+    return m;
 }
 
 // Store the units of a finished line group.  For half2 storage each line's
@@ -264,6 +302,15 @@ __device__ __forceinline__ void store_units(float2 (&a)[C::EPT], const IO &io, c
 {
     const int tid = threadIdx.x;
     if constexpr (IO::H16) {
+        // lanes of a warp that share an output line: row pass, lanes that
+        // differ only in the unit bits below the group's start (the line
+        // block is the unit index above them); column pass, lanes that
+        // differ only above the interleave bits (the line is u mod W)
+        constexpr int S0 = Gp::S0;
+        constexpr int RB0 = 0, RB1 = C::NG == 1 ? 0 : (S0 < 5 ? S0 : 5);
+        constexpr int CB0 = C::KW < 5 ? C::KW : 5, CB1 = 5;
+        constexpr int B0 = ROW ? RB0 : CB0, B1 = ROW ? RB1 : CB1;
+        constexpr unsigned LMASK = ((1u << B1) - 1u) & ~((1u << B0) - 1u);
 #pragma unroll
         for (int v = 0; v < Gp::V; v++) {
             const int u = tid + v * C::T;
@@ -274,7 +321,8 @@ __device__ __forceinline__ void store_units(float2 (&a)[C::EPT], const IO &io, c
 #pragma unroll
             for (int r = 0; r < Gp::R; r++)
                 m = fmaxf(m, fmaxf(fabsf(a[v * Gp::R + r].x), fabsf(a[v * Gp::R + r].y)));
-            if (ok)
+            m = warp_line_max<B0, B1>(m);
+            if (ok && (tid & LMASK) == 0)
                 atomicMax(sred + (ROW ? lb : w), __float_as_int(m * scale));
         }
         __syncthreads();
@@ -326,10 +374,13 @@ __device__ __forceinline__ void group_first(float2 (&a)[C::EPT], float2 *sm, con
         const int hib = u2 & ((1 << Gp::HB) - 1);
         const int lb = u2 >> Gp::HB;
         const bool ok = !GENERIC || (ROW ? lb < nvalid : w < nvalid);
+        float f = 0.f;
+        if constexpr (H16PerUnit<IO, ROW>::value)
+            f = ok ? in_factor<IO, ROW>(io, g, lb, 0, w) : 0.f;
 #pragma unroll
         for (int r = 0; r < Gp::R; r++) {
             const int i = (brev_c(r, Gp::G) << Gp::HB) | hib;
-            a[v * Gp::R + r] = ok ? load_pix<IO, ROW>(io, g, lb, i, w) : make_float2(0.f, 0.f);
+            a[v * Gp::R + r] = ok ? load_pix<IO, ROW>(io, g, lb, i, w, f) : make_float2(0.f, 0.f);
         }
     }
 #pragma unroll

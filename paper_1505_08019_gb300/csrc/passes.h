@@ -96,6 +96,7 @@ struct H16PassArgs {
     const int *in_exp;   // input exponents, one per row (in_axis 0) or column (1)
     int in_axis;
     int *out_exp;        // output exponents: per row (row pass) or column (column pass)
+    int *err = nullptr;  // device status word (bounded waits of the TMA-fed column pass)
 };
 cudaError_t launch_pass_h16(bool row, int L, const H16PassArgs &a, cudaStream_t s);
 cudaError_t launch_h16_pack(const float2 *in, __half2 *out, int *exp_rows, int rows, int cols,
