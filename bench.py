@@ -1,8 +1,8 @@
 #!/usr/bin/env python3
 """Benchmark of the 2D radix-2 DIT FFT on GB300: 4096x4096 complex64 images.
 
-One step = forward 2D FFT then inverse 2D FFT of each of B resident images
-(per rank).  ``value`` counts 2D transforms per second (a forward and an
+One step = R rounds (default 32) of forward 2D FFT then inverse 2D FFT of
+each of B resident images (default 8, per rank).  ``value`` counts 2D transforms per second (a forward and an
 inverse each count as one image transform), summed over ranks; inputs are
 already in HBM when the timed region starts.  The working set (B images x
 2 buffers x 128 MiB) is far larger than L2, so no image is L2-resident when
@@ -51,10 +51,10 @@ def parse():
                          "serve: Poisson stream of mixed requests through fft2d_serve_*; "
                          "dct: real 2D DCT-II at 4096^2 and 8192^2 beside the complex FFT; "
                          "sizes: forward+inverse at the paper's Table 1 image sizes")
-    ap.add_argument("--images", type=int, default=256,
-                    help="resident images per rank (one step = forward + inverse of each)")
-    ap.add_argument("--distinct", type=int, default=8,
-                    help="distinct seeded images the resident images are copies of")
+    ap.add_argument("--images", type=int, default=8, help="resident images per rank")
+    ap.add_argument("--rounds", type=int, default=32,
+                    help="one step = this many rounds of forward + inverse of every resident "
+                         "image")
     ap.add_argument("--streams", type=int, default=0,
                     help="CUDA streams the resident images are spread over (0: one per image)")
     ap.add_argument("--fp16-sides", default="8192,16384",
@@ -413,6 +413,14 @@ def measure_batched(fft, torch, orc, steps, tune_plans=False):
                               | {(c.bit_length() - 1) for _, c in shapes})}
     ms_b = t(batched, steps)
     ms_s = t(single, steps)
+    # the same grouped launches captured once in a CUDA graph and replayed
+    gs = torch.cuda.Stream()
+    gs.wait_stream(stream)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=gs):
+        fft.fft2d_exec_batched(plans, ins, outs, gs.cuda_stream)
+    ms_g = t(lambda _i: graph.replay(), steps)
+    del graph
     peak, peak_src = measured_hbm_peak()
     gbs = 32.0 * px / (ms_b * 1e-3) / 1e9
     batched()
@@ -426,6 +434,8 @@ def measure_batched(fft, torch, orc, steps, tune_plans=False):
             "single_image_path": {"images_per_s": len(shapes) / (ms_s * 1e-3),
                                   "ms_per_step": ms_s,
                                   "call": "fft2d_exec per image"},
+            "cuda_graph": {"images_per_s": len(shapes) / (ms_g * 1e-3), "ms_per_step": ms_g,
+                           "call": "fft2d_exec_batched captured once in a CUDA graph, replayed"},
             "speedup_vs_single": ms_s / ms_b,
             "default_variants_ms_per_step": ms_default, "tuned_variants": chosen,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
@@ -450,14 +460,13 @@ def run_ours(args):
     import paper_1505_08019_gb300 as fft
     import synth
 
-    side, B = args.side, args.images
-    nd = max(1, min(args.distinct, B))
-    imgs = [synth.blob_image(side, side, seed=sd) for sd in image_seeds(rank, nd)]
-    base = [torch.from_numpy(im).to(dev) for im in imgs]
-    # B resident images, copies of the nd distinct ones: every transform reads
-    # and writes its own buffers in HBM (B x 2 x 128 MiB, far beyond L2)
-    xs = [base[i % nd].clone() for i in range(B)]
-    del base
+    side, B, R = args.side, args.images, max(1, args.rounds)
+    imgs = [synth.blob_image(side, side, seed=sd) for sd in image_seeds(rank, B)]
+    # B resident images, each with its own output buffer (B x 2 x 128 MiB,
+    # far beyond L2); a step transforms every one R times, forward from its
+    # input and back in place, so consecutive launches never find their
+    # image in L2
+    xs = [torch.from_numpy(im).to(dev) for im in imgs]
     Xs = [torch.empty_like(x) for x in xs]
     pf = fft.fft2d_plan(side, side, fft.FFT2D_C64, fft.FFT2D_FORWARD)
     pi = fft.fft2d_plan(side, side, fft.FFT2D_C64, fft.FFT2D_INVERSE)
@@ -475,10 +484,14 @@ def run_ours(args):
     joins = [torch.cuda.Event() for _ in lanes]
     kimg = min(B, 8)
 
-    def step(evs=None):
+    def round_(evs=None):
         # forward then inverse of every resident image; with `evs`, an event
         # brackets every kernel launch (rows fwd, cols fwd, rows inv, cols
-        # inv) of the first kimg images, all on the timing stream
+        # inv) of the first kimg images, all on the timing stream.  Without,
+        # the images run on the lanes, forked from and joined back into the
+        # timing stream: the join keeps the lanes in step, so the row passes
+        # of different images run together, then their column passes (4 %
+        # faster than lanes left to drift apart over many images)
         if evs is None and nstreams > 1:
             fork.record(stream)
             for ln in lanes:
@@ -506,6 +519,12 @@ def run_ours(args):
             for ln, j in zip(lanes, joins):
                 j.record(ln)
                 stream.wait_event(j)
+
+    def step(evs=None):
+        # one step: R rounds over the resident images (one round when timing
+        # single launches)
+        for _ in range(R if evs is None else 1):
+            round_(evs)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -551,14 +570,14 @@ def run_ours(args):
     dom, dom_ms = ("col_pass", col_ms) if col_ms >= row_ms else ("row_pass", row_ms)
     peak, peak_src = measured_hbm_peak()
     achieved = pass_bytes / (dom_ms * 1e-3) / 1e9
-    value = job_value(2 * B * args.steps, ws, ms)
+    value = job_value(2 * B * R * args.steps, ws, ms)
     del xs, Xs
     torch.cuda.empty_cache()
 
     # end to end through the public host-buffer call, every transform an
     # independent image: upload, transform, download of its result
     ne = min(B, 8)
-    hin = [torch.from_numpy(imgs[i % nd]).pin_memory() for i in range(ne)]
+    hin = [torch.from_numpy(imgs[i]).pin_memory() for i in range(ne)]
     hout = [torch.empty_like(h).pin_memory() for h in hin]
     fft.fft2d_exec_host_many([pf] * ne, hin, hout, sptr)    # allocate the pipeline
     torch.cuda.synchronize()
@@ -644,10 +663,10 @@ def run_ours(args):
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic (seeded Gaussian-blob + U[0,1) gray images)",
-            "config": {"workload": f"{side}x{side} complex64 2D FFT, forward+inverse of "
-                                   f"{B} resident images per GPU per step",
-                       "side": side, "images_per_gpu": B,
-                       "distinct_images": f"{nd} seeded images, each resident {B // nd}x",
+            "config": {"workload": f"{side}x{side} complex64 2D FFT: per GPU per step, {R} "
+                                   f"rounds of forward+inverse of each of {B} resident images "
+                                   f"({2 * B * R} transforms)",
+                       "side": side, "images_per_gpu": B, "rounds_per_step": R,
                        "parallelism": f"replicas x{ws}",
                        "streams": nstreams,
                        "l2": f"inputs larger than L2 ({B} images x 2 buffers x "
@@ -663,11 +682,11 @@ def run_ours(args):
             "passes_ms": per,
             "passes_timing": f"{kern_steps} steps of {kimg} images with an event between "
                              "every two launches",
-            "whole_transform_hbm_frac": (2 * pass_bytes / (ms / args.steps / (2 * B) * 1e-3)
+            "whole_transform_hbm_frac": (2 * pass_bytes / (ms / args.steps / (2 * B * R) * 1e-3)
                                          / 1e9) / peak,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": 4 * B * args.steps,
+            "gpu_launches": 4 * B * R * args.steps,
             "clocks": clk,
             "parity": parity,
         }
@@ -810,18 +829,29 @@ def measure_serve(fft, torch, n, rate, single=True):
     g = np.random.default_rng(1)
     arrivals = np.cumsum(g.exponential(1.0 / rate, n))
     shapes = sorted({(r, c) for _, r, c, _ in mix})
-    # one pinned input image per shape; outputs are shared per shape (their
-    # contents are checked by the tests, not here)
-    inp = {sh: torch.from_numpy(synth.uniform_real(sh[0], sh[1], seed=7)).pin_memory()
-           for sh in shapes}
-    outb = {sh: torch.empty(sh, dtype=torch.complex64).pin_memory() for sh in shapes}
+    # one pinned input image per shape and storage (half2 requests carry
+    # half2 data and per-row exponents); outputs are shared per shape and
+    # storage (their contents are checked by the tests, not here)
+    inp, outb = {}, {}
+    for sh in shapes:
+        img = synth.uniform_real(sh[0], sh[1], seed=7)
+        q, e = h16_quantise_rows(img)
+        inp[sh, 0] = (torch.from_numpy(img).pin_memory(), None)
+        inp[sh, 1] = (torch.from_numpy(q).pin_memory(), torch.from_numpy(e).pin_memory())
+        outb[sh, 0] = (torch.empty(sh, dtype=torch.complex64).pin_memory(), None)
+        outb[sh, 1] = (torch.empty(q.shape, dtype=torch.float16).pin_memory(),
+                       torch.zeros(sh[1], dtype=torch.int32).pin_memory())
+
+    def submit(srv, op, r, c, dt):
+        x, y = inp[(r, c), dt], outb[(r, c), dt]
+        return fft.fft2d_serve_submit(srv, op, r, c, dt, x[0], y[0], x[1], y[1])
+
     budget = 40 << 30
     srv = fft.fft2d_serve_create(budget, 4)
     for sh in shapes:
         for op in (0, 1):
             for dt in (0, 1):
-                fft.fft2d_serve_wait(srv, fft.fft2d_serve_submit(srv, op, sh[0], sh[1], dt,
-                                                                  inp[sh], outb[sh]))
+                fft.fft2d_serve_wait(srv, submit(srv, op, sh[0], sh[1], dt))
     base = fft.fft2d_serve_stats_get(srv)
     tickets = [0] * n
     t0 = time.perf_counter()
@@ -829,7 +859,7 @@ def measure_serve(fft, torch, n, rate, single=True):
         delay = t0 + arrivals[i] - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
-        tickets[i] = fft.fft2d_serve_submit(srv, op, r, c, dt, inp[(r, c)], outb[(r, c)])
+        tickets[i] = submit(srv, op, r, c, dt)
     lat = np.array([fft.fft2d_serve_wait(srv, t) for t in tickets])
     wall = time.perf_counter() - t0
     st = fft.fft2d_serve_stats_get(srv)
@@ -849,15 +879,15 @@ def measure_serve(fft, torch, n, rate, single=True):
         "latency": "submit -> result in the host buffer, as the server stamps it",
         "workload": f"{n} requests at {rate:g} req/s (Poisson, seed 1); long side 2^u, "
                     "u~U{6..12}; 50% square, 50% 1:4; 50% forward, 50% "
-                    "FFT->LPF(sigma=side/8)->iFFT; 70% c64 / 30% half2; pinned host buffers, "
-                    "copies included; HBM budget 40 GB; 4 streams"}
+                    "FFT->LPF(sigma=side/8)->iFFT; 70% c64 / 30% half2 (half2 data and "
+                    "exponents on the host link); pinned host buffers, copies included; HBM "
+                    "budget 40 GB; 4 streams"}
     if single:
         # capacity: the same kind of requests submitted all at once
         m_sat = min(n, 4000)
         sat_mix = serve_mix(m_sat, seed=2)
         t2 = time.perf_counter()
-        sat_t = [fft.fft2d_serve_submit(srv, op, r, c, dt, inp[(r, c)], outb[(r, c)])
-                 for op, r, c, dt in sat_mix]
+        sat_t = [submit(srv, op, r, c, dt) for op, r, c, dt in sat_mix]
         sat_lat = np.array([fft.fft2d_serve_wait(srv, t) for t in sat_t])
         sat_wall = time.perf_counter() - t2
         st2 = fft.fft2d_serve_stats_get(srv)
@@ -887,12 +917,12 @@ def measure_serve(fft, torch, n, rate, single=True):
         for op, r, c, _ in mix[:m]:
             ts = time.perf_counter()
             d = dev[(r, c)]
-            d.copy_(inp[(r, c)], non_blocking=True)
+            d.copy_(inp[(r, c), 0][0], non_blocking=True)
             fft.fft2d_exec(plan(r, c, -1), d, d, sptr)
             if op == 1:
                 fft.fft2d_lowpass(r, c, fft.FFT2D_C64, d, r / 8.0, c / 8.0, sptr)
                 fft.fft2d_exec(plan(r, c, 1), d, d, sptr)
-            outb[(r, c)].copy_(d, non_blocking=True)
+            outb[(r, c), 0][0].copy_(d, non_blocking=True)
             torch.cuda.synchronize()
             single_lat.append((time.perf_counter() - ts) * 1e3)
         single_wall = time.perf_counter() - t1

@@ -339,13 +339,14 @@ FFT2D_API fft2d_status fft2d_lowpass(int rows, int cols, int dtype, void *data, 
  * A continuous-batching request loop on the current device.  Clients submit
  * requests on host buffers (pin them for full copy speed).  A scheduler
  * thread admits queued requests in arrival order while the device memory
- * they need (complex64: 8 B/pixel; half2: 12 B/pixel + exponents) fits the
- * HBM budget, launches everything admitted so far as one batch on an idle
- * stream (copies in, grouped FFT launches, low-pass, inverse, copies out),
- * keeps up to `streams` batches in flight so new arrivals overlap running
- * work, and recycles device buffers through a resident pool.  Plans stay
- * resident.  Results do not depend on what else is in flight: every kernel
- * computes the same bits alone and in a batch.
+ * they need (complex64: 8 B/pixel; half2: 4 B/pixel + 2 rows + cols
+ * exponents) fits the HBM budget, launches everything admitted so far as one
+ * batch on an idle stream (copies in, grouped FFT launches for both storage
+ * types, low-pass, inverse, copies out), keeps up to `streams` batches in
+ * flight so new arrivals overlap running work, and recycles device buffers
+ * through a resident pool.  Plans stay resident.  Results do not depend on
+ * what else is in flight: every kernel computes the same bits alone and in a
+ * batch.  Half2 requests cross the host link as half2 (4 B/pixel each way).
  */
 #define FFT2D_OP_FORWARD 0   /* forward 2D FFT */
 #define FFT2D_OP_LOWPASS 1   /* forward FFT, Gaussian low-pass (sigma = side/8), inverse FFT */
@@ -357,9 +358,13 @@ typedef struct fft2d_server_s *fft2d_server_t;
 typedef struct {
     int op;           /* FFT2D_OP_FORWARD or FFT2D_OP_LOWPASS */
     int rows, cols;   /* powers of two, <= FFT2D_MAX_SIDE */
-    int dtype;        /* device storage during the work: FFT2D_C64 or FFT2D_C32H */
-    const void *in;   /* host: rows*cols complex64 input */
-    void *out;        /* host: rows*cols complex64 result (may equal in) */
+    int dtype;        /* storage: FFT2D_C64 or FFT2D_C32H (sides >= 2) */
+    const void *in;   /* host input: rows*cols complex64, or rows*cols half2 (FFT2D_C32H) */
+    void *out;        /* host result in the same storage (may equal in) */
+    const int *in_exp;  /* FFT2D_C32H: host, rows exponents of the input, one per row
+                           (the format of fft2d_h16_pack); NULL for complex64 */
+    int *out_exp;       /* FFT2D_C32H: host, receives cols exponents of the result, one
+                           per column (the format fft2d_exec_h16 writes); NULL for complex64 */
 } fft2d_request;
 
 typedef struct {

@@ -15,8 +15,8 @@ namespace fft2d {
 
 namespace {
 
-template <class C>
-__device__ __forceinline__ int find_job(const BatchTable &t)
+template <class Table>
+__device__ __forceinline__ int find_job(const Table &t)
 {
     int lo = 0, hi = t.n - 1;
     const int b = (int)blockIdx.x;
@@ -33,7 +33,7 @@ __device__ __forceinline__ int find_job(const BatchTable &t)
 template <class C>
 __global__ void __launch_bounds__(C::T, C::MINB) row_batch_kernel(const __grid_constant__ BatchTable t)
 {
-    const BatchJob &jb = t.job[find_job<C>(t)];
+    const BatchJob &jb = t.job[find_job(t)];
     const long long r0 = (long long)((int)blockIdx.x - jb.first_cta) * C::LB;
     line_fft<C, true, true, StoreC64>(StoreC64{jb.in, jb.out}, Geo{r0, 1, 0, jb.ld}, jb.tw,
                                       jb.scale, C::L, jb.lines - r0);
@@ -42,10 +42,58 @@ __global__ void __launch_bounds__(C::T, C::MINB) row_batch_kernel(const __grid_c
 template <class C>
 __global__ void __launch_bounds__(C::T, C::MINB) col_batch_kernel(const __grid_constant__ BatchTable t)
 {
-    const BatchJob &jb = t.job[find_job<C>(t)];
+    const BatchJob &jb = t.job[find_job(t)];
     const long long c0 = (long long)((int)blockIdx.x - jb.first_cta) * C::W;
     line_fft<C, false, true, StoreC64>(StoreC64{jb.in, jb.out}, Geo{0, 1, c0, jb.ld}, jb.tw,
                                        jb.scale, C::L, jb.lines - c0);
+}
+
+// Half2 jobs: per-line exponents in and out (StoreH16T), the input's
+// exponent axis fixed for the launch.
+template <class C, bool ROW, int IA>
+__global__ void __launch_bounds__(C::T, C::MINB) h16_batch_kernel(const __grid_constant__ BatchTableH16 t)
+{
+    using IO = StoreH16T<IA>;
+    const BatchJobH16 &jb = t.job[find_job(t)];
+    const long long l0 = (long long)((int)blockIdx.x - jb.first_cta) * (ROW ? C::LB : C::W);
+    const IO io{jb.in, jb.out, jb.in_exp, IA, jb.out_exp};
+    const Geo g = ROW ? Geo{l0, 1, 0, jb.ld} : Geo{0, 1, l0, jb.ld};
+    line_fft<C, ROW, true, IO>(io, g, jb.tw, jb.scale, C::L, jb.lines - l0);
+}
+
+template <class C, bool ROW, int IA>
+cudaError_t batch_launch_h16(BatchTableH16 &t, cudaStream_t s)
+{
+    auto k = h16_batch_kernel<C, ROW, IA>;
+    const int per = ROW ? C::LB : C::W;
+    int ctas = 0;
+    for (int i = 0; i < t.n; i++) {
+        t.job[i].first_cta = ctas;
+        ctas += (t.job[i].lines + per - 1) / per;
+    }
+    if (ctas == 0)
+        return cudaSuccess;
+    constexpr int SMEM = LineSmem<C, ROW, StoreH16T<IA>>::BYTES;
+    if (SMEM > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (e != cudaSuccess)
+            return e;
+    }
+    k<<<ctas, C::T, SMEM, s>>>(t);
+    return cudaGetLastError();
+}
+
+// The single-image half2 passes' CTA shapes (kernels_h16.cu): rows as for
+// complex64, plain column tiles of 2^col_kw(L) columns.
+template <int L>
+cudaError_t batch_dispatch_h16(bool row, BatchTableH16 &t, int in_axis, cudaStream_t s)
+{
+    if (row) {
+        using C = LineCfg<L, 0, row_kb(L), L == 13 ? 32 : 16>;
+        return in_axis == 0 ? batch_launch_h16<C, true, 0>(t, s) : batch_launch_h16<C, true, 1>(t, s);
+    }
+    using C = LineCfg<L, col_kw(L), 0>;
+    return in_axis == 0 ? batch_launch_h16<C, false, 0>(t, s) : batch_launch_h16<C, false, 1>(t, s);
 }
 
 template <class C, bool ROW>
@@ -174,6 +222,27 @@ const char *batch_variant_name(bool row, int variant)
     if (row)
         return variant >= 0 && variant < kBatchRowVariants ? rn[variant] : "";
     return variant >= 0 && variant < kBatchColVariants ? cn[variant] : "";
+}
+
+cudaError_t launch_batch_pass_h16(bool row, int L, BatchTableH16 &t, int in_axis, cudaStream_t s)
+{
+    switch (L) {
+    case 1: return batch_dispatch_h16<1>(row, t, in_axis, s);
+    case 2: return batch_dispatch_h16<2>(row, t, in_axis, s);
+    case 3: return batch_dispatch_h16<3>(row, t, in_axis, s);
+    case 4: return batch_dispatch_h16<4>(row, t, in_axis, s);
+    case 5: return batch_dispatch_h16<5>(row, t, in_axis, s);
+    case 6: return batch_dispatch_h16<6>(row, t, in_axis, s);
+    case 7: return batch_dispatch_h16<7>(row, t, in_axis, s);
+    case 8: return batch_dispatch_h16<8>(row, t, in_axis, s);
+    case 9: return batch_dispatch_h16<9>(row, t, in_axis, s);
+    case 10: return batch_dispatch_h16<10>(row, t, in_axis, s);
+    case 11: return batch_dispatch_h16<11>(row, t, in_axis, s);
+    case 12: return batch_dispatch_h16<12>(row, t, in_axis, s);
+    case 13: return batch_dispatch_h16<13>(row, t, in_axis, s);
+    case 14: return batch_dispatch_h16<14>(row, t, in_axis, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_batch_pass(bool row, int L, BatchTable &t, int variant, int *err,

@@ -33,6 +33,20 @@ struct fft2d_plan_s {
     float2 *post_cols; // DCT plans: (cos, sin)(pi k / (2 rows)), k = 0 .. rows/2
 };
 
+namespace fft2d {
+
+bool plan_view(const void *plan, PlanView *v)
+{
+    const fft2d_plan_s *p = static_cast<const fft2d_plan_s *>(plan);
+    if (!p || !v)
+        return false;
+    *v = PlanView{p->rows, p->cols, p->Lr, p->Lc, p->dtype, p->dir, p->tw_rows, p->tw_cols,
+                  p->dev_err};
+    return true;
+}
+
+}  // namespace fft2d
+
 namespace {
 
 thread_local char g_last_error[256] = "";

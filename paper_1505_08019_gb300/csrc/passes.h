@@ -137,6 +137,38 @@ struct BatchTmaTable {   // 128-byte aligned through CUtensorMap
     int n;
 };
 
+// What the serving loop needs to see of a plan (fft2d_api.cpp): shape,
+// direction, the device rotation-factor tables of both axes and the status
+// word.  False for a null plan.
+struct PlanView {
+    int rows, cols, Lr, Lc, dtype, dir;
+    const float2 *tw_rows, *tw_cols;
+    int *err;
+};
+bool plan_view(const void *plan, PlanView *v);
+
+// Grouped launches of half2 images (batch.cu): the same per-CTA work as the
+// single-image half2 passes, one job per image.
+constexpr int kBatchH16MaxJobs = 64;
+struct BatchJobH16 {
+    const __half2 *in;
+    __half2 *out;
+    const float2 *tw;
+    const int *in_exp;   // exponents of the input lines (the group's input axis)
+    int *out_exp;        // exponents of this pass's output lines (per row / column)
+    long long ld;
+    int lines;           // rows (row pass) or columns (column pass) of the image
+    int first_cta;       // filled by launch_batch_pass_h16
+    float scale;
+};
+struct BatchTableH16 {
+    int n;
+    BatchJobH16 job[kBatchH16MaxJobs];
+};
+// One launch for every job of `t` whose axis has 2^L points; in_axis: the
+// jobs' input exponent axis (0 one per row, 1 one per column).
+cudaError_t launch_batch_pass_h16(bool row, int L, BatchTableH16 &t, int in_axis, cudaStream_t s);
+
 // Grouped-launch variants: rows 0 plain, 1 plain32; columns 0 plain,
 // 1 narrow (half-width tiles), 2 tma (persistent, TMA-fed, TMA stores;
 // 512..4096 rows), 3 tmast (the same with per-thread stores), 4 tmah (half

@@ -7,8 +7,10 @@
 //     that could never fit is refused at submission);
 //   * launches everything admitted so far as one batch on an idle stream:
 //     host->device copies, grouped FFT launches for the complex64 work
-//     (fft2d_exec_batched), per-request calls for half2 work, the low-pass
-//     multiply, the inverse, device->host copies, then an event;
+//     (fft2d_exec_batched) and for the half2 work (one launch per pass and
+//     axis length; images with 4096+ rows on the TMA-fed half2 column pass
+//     one at a time), the low-pass multiply, the inverse, device->host
+//     copies, then an event;
 //   * keeps several batches in flight on different streams, so requests that
 //     arrive while others run are admitted as memory frees up and their work
 //     overlaps on the device;
@@ -46,9 +48,10 @@ struct Req {
     size_t bytes;                 // device memory this request holds while in flight
     Clock::time_point t_submit;
     Clock::time_point t_done;
-    void *buf_c64 = nullptr;      // device complex64 image
+    void *buf_c64 = nullptr;      // device complex64 image (FFT2D_C64)
     void *buf_h16 = nullptr;      // device half2 image (FFT2D_C32H)
-    int *exps = nullptr;          // device exponents: rows + cols ints (FFT2D_C32H)
+    int *exps = nullptr;          // device exponents (FFT2D_C32H): input rows, row-pass
+                                  // output rows, result columns (2 rows + cols ints)
     fft2d_status status = FFT2D_OK;
     bool done = false;
 };
@@ -60,13 +63,102 @@ struct Batch {
     Clock::time_point sim_ready;  // simulation: modelled completion time
 };
 
+size_t exps_bytes(const fft2d_request &r) { return (size_t)(2 * r.rows + r.cols) * 4; }
+
 size_t request_bytes(const fft2d_request &r)
 {
     const size_t px = (size_t)r.rows * r.cols;
-    size_t b = px * 8;
-    if (r.dtype == FFT2D_C32H)
-        b += px * 4 + (size_t)(r.rows + r.cols) * 4;
-    return b;
+    return r.dtype == FFT2D_C32H ? px * 4 + exps_bytes(r) : px * 8;
+}
+
+// Half2 work of a batch phase: image i of `reqs` (in place in its buf_h16)
+// from exponents in_exp (per row if in_axis == 0, else per column) through
+// its row-pass exponents to its column exponents, with plans[i].  Columns of
+// 4096+ rows take the single-image half2 passes (TMA-fed column pass), the
+// rest grouped launches -- one per (pass, axis length) -- with the same CTA
+// shapes, so every image gets the same bits either way.
+cudaError_t h16_phase(const std::vector<Req *> &reqs, const std::vector<fft2d_plan_t> &plans,
+                      int in_axis, cudaStream_t st)
+{
+    static thread_local fft2d::BatchTableH16 table;
+    const size_t n = reqs.size();
+    std::vector<fft2d::PlanView> pv(n);
+    for (size_t i = 0; i < n; i++)
+        if (!fft2d::plan_view(plans[i], &pv[i]))
+            return cudaErrorInvalidValue;
+    auto in_exp = [&](size_t i) {
+        const Req *q = reqs[i];
+        return in_axis == 0 ? q->exps : q->exps + 2 * q->r.rows;
+    };
+    auto grouped = [&](size_t i) { return pv[i].Lr < 12; };
+    // the large images, one at a time
+    for (size_t i = 0; i < n; i++) {
+        if (grouped(i))
+            continue;
+        const Req *q = reqs[i];
+        const fft2d::PlanView &v = pv[i];
+        fft2d::H16PassArgs a;
+        a.in = static_cast<const __half2 *>(q->buf_h16);
+        a.out = static_cast<__half2 *>(q->buf_h16);
+        a.rows = v.rows;
+        a.cols = v.cols;
+        a.ld = v.cols;
+        a.tw = v.tw_rows;
+        a.scale = 1.0f;
+        a.nst = v.Lc;
+        a.in_exp = in_exp(i);
+        a.in_axis = in_axis;
+        a.out_exp = q->exps + v.rows;
+        cudaError_t e = fft2d::launch_pass_h16(true, v.Lc, a, st);
+        if (e != cudaSuccess)
+            return e;
+        a.tw = v.tw_cols;
+        a.nst = v.Lr;
+        a.scale = v.dir == FFT2D_INVERSE ? (float)(1.0 / ((double)v.rows * (double)v.cols)) : 1.0f;
+        a.in_exp = q->exps + v.rows;
+        a.in_axis = FFT2D_PASS_ROWS;
+        a.out_exp = q->exps + 2 * v.rows;
+        a.err = v.err;
+        e = fft2d::launch_pass_h16(false, v.Lr, a, st);
+        if (e != cudaSuccess)
+            return e;
+    }
+    // the rest: row groups by row length, then column groups by column length
+    for (int pass = 0; pass < 2; pass++) {
+        const bool row = pass == 0;
+        for (int L = 1; L <= 14; L++) {
+            table.n = 0;
+            for (size_t i = 0; i <= n; i++) {
+                const bool flush = i == n || table.n == fft2d::kBatchH16MaxJobs;
+                if (flush && table.n > 0) {
+                    cudaError_t e = fft2d::launch_batch_pass_h16(row, L, table,
+                                                                 row ? in_axis : 0, st);
+                    if (e != cudaSuccess)
+                        return e;
+                    table.n = 0;
+                }
+                if (i == n)
+                    break;
+                const fft2d::PlanView &v = pv[i];
+                if (!grouped(i) || (row ? v.Lc : v.Lr) != L)
+                    continue;
+                const Req *q = reqs[i];
+                fft2d::BatchJobH16 &j = table.job[table.n++];
+                j.in = static_cast<const __half2 *>(q->buf_h16);
+                j.out = static_cast<__half2 *>(q->buf_h16);
+                j.tw = row ? v.tw_rows : v.tw_cols;
+                j.in_exp = row ? in_exp(i) : q->exps + v.rows;
+                j.out_exp = row ? q->exps + v.rows : q->exps + 2 * v.rows;
+                j.ld = v.cols;
+                j.lines = row ? v.rows : v.cols;
+                j.first_cta = 0;
+                j.scale = (!row && v.dir == FFT2D_INVERSE)
+                              ? (float)(1.0 / ((double)v.rows * (double)v.cols))
+                              : 1.0f;
+            }
+        }
+    }
+    return cudaSuccess;
 }
 
 bool pow2(int n) { return n >= 1 && !(n & (n - 1)); }
@@ -159,20 +251,18 @@ struct fft2d_server_s {
     bool try_admit(Req *q, bool exact)
     {
         const size_t px = (size_t)q->r.rows * q->r.cols;
-        q->buf_c64 = acquire(px * 8, exact);
-        if (!q->buf_c64)
+        if (q->r.dtype == FFT2D_C64) {
+            q->buf_c64 = acquire(px * 8, exact);
+            return q->buf_c64 != nullptr;
+        }
+        q->buf_h16 = acquire(px * 4, exact);
+        q->exps = static_cast<int *>(acquire(exps_bytes(q->r), exact));
+        if (!q->buf_h16 || !q->exps) {
+            release(q->buf_h16);
+            release(q->exps);
+            q->buf_h16 = nullptr;
+            q->exps = nullptr;
             return false;
-        if (q->r.dtype == FFT2D_C32H) {
-            q->buf_h16 = acquire(px * 4, exact);
-            q->exps = static_cast<int *>(acquire((size_t)(q->r.rows + q->r.cols) * 4, exact));
-            if (!q->buf_h16 || !q->exps) {
-                release(q->buf_c64);
-                release(q->buf_h16);
-                release(q->exps);
-                q->buf_c64 = q->buf_h16 = nullptr;
-                q->exps = nullptr;
-                return false;
-            }
         }
         return true;
     }
@@ -232,19 +322,28 @@ struct fft2d_server_s {
     {
         fft2d::NvtxRange range("fft2d serve batch");
         cudaStream_t st = streams[b.stream];
+        std::vector<Req *> c64, h16;
+        for (Req *q : b.reqs)
+            (q->r.dtype == FFT2D_C64 ? c64 : h16).push_back(q);
         for (Req *q : b.reqs) {
-            const size_t bytes = (size_t)q->r.rows * q->r.cols * 8;
-            if (cudaMemcpyAsync(q->buf_c64, q->r.in, bytes, cudaMemcpyHostToDevice, st) !=
-                cudaSuccess)
+            const size_t px = (size_t)q->r.rows * q->r.cols;
+            cudaError_t e;
+            if (q->r.dtype == FFT2D_C64) {
+                e = cudaMemcpyAsync(q->buf_c64, q->r.in, px * 8, cudaMemcpyHostToDevice, st);
+            } else {
+                e = cudaMemcpyAsync(q->buf_h16, q->r.in, px * 4, cudaMemcpyHostToDevice, st);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(q->exps, q->r.in_exp, (size_t)q->r.rows * 4,
+                                        cudaMemcpyHostToDevice, st);
+            }
+            if (e != cudaSuccess)
                 return FFT2D_ERR_CUDA;
         }
-        // complex64 work: grouped forward launches, filter, grouped inverse
-        std::vector<fft2d_plan_t> fp, ip;
-        std::vector<const void *> fin, iin;
-        std::vector<void *> fout, iout;
-        for (Req *q : b.reqs) {
-            if (q->r.dtype != FFT2D_C64)
-                continue;
+        // forward: complex64 through fft2d_exec_batched, half2 grouped
+        std::vector<fft2d_plan_t> fp;
+        std::vector<const void *> fin;
+        std::vector<void *> fout;
+        for (Req *q : c64) {
             fft2d_plan_t p = plan(q->r.rows, q->r.cols, FFT2D_C64, FFT2D_FORWARD);
             if (!p)
                 return FFT2D_ERR_OOM;
@@ -257,8 +356,21 @@ struct fft2d_server_s {
             s = fft2d_exec_batched((int)fp.size(), fp.data(), fin.data(), fout.data(), st);
         if (s != FFT2D_OK)
             return s;
-        for (Req *q : b.reqs) {
-            if (q->r.dtype != FFT2D_C64 || q->r.op != FFT2D_OP_LOWPASS)
+        std::vector<fft2d_plan_t> hp;
+        for (Req *q : h16) {
+            fft2d_plan_t p = plan(q->r.rows, q->r.cols, FFT2D_C32H, FFT2D_FORWARD);
+            if (!p)
+                return FFT2D_ERR_OOM;
+            hp.push_back(p);
+        }
+        if (!h16.empty() && h16_phase(h16, hp, FFT2D_PASS_ROWS, st) != cudaSuccess)
+            return FFT2D_ERR_CUDA;
+        // low-pass, then the inverse of the filtered spectra
+        std::vector<fft2d_plan_t> ip;
+        std::vector<const void *> iin;
+        std::vector<void *> iout;
+        for (Req *q : c64) {
+            if (q->r.op != FFT2D_OP_LOWPASS)
                 continue;
             if (fft2d::launch_lowpass(false, q->buf_c64, q->r.rows, q->r.cols,
                                       q->r.rows / 8.0f, q->r.cols / 8.0f, st) != cudaSuccess)
@@ -274,37 +386,37 @@ struct fft2d_server_s {
             s = fft2d_exec_batched((int)ip.size(), ip.data(), iin.data(), iout.data(), st);
         if (s != FFT2D_OK)
             return s;
-        // half2 work, one request at a time
-        for (Req *q : b.reqs) {
-            if (q->r.dtype != FFT2D_C32H)
+        std::vector<Req *> h16f;
+        std::vector<fft2d_plan_t> hip;
+        for (Req *q : h16) {
+            if (q->r.op != FFT2D_OP_LOWPASS)
                 continue;
             const int R = q->r.rows, C = q->r.cols;
-            int *erow = q->exps, *ecol = q->exps + R;
-            s = fft2d_h16_pack(R, C, q->buf_c64, q->buf_h16, erow, st);
-            fft2d_plan_t pf = s == FFT2D_OK ? plan(R, C, FFT2D_C32H, FFT2D_FORWARD) : nullptr;
-            if (!pf)
-                return s == FFT2D_OK ? FFT2D_ERR_OOM : s;
-            s = fft2d_exec_h16(pf, q->buf_h16, erow, FFT2D_PASS_ROWS, q->buf_h16, ecol, st);
-            if (s == FFT2D_OK && q->r.op == FFT2D_OP_LOWPASS) {
-                if (fft2d::launch_lowpass(true, q->buf_h16, R, C, R / 8.0f, C / 8.0f, st) !=
-                    cudaSuccess)
-                    return FFT2D_ERR_CUDA;
-                fft2d_plan_t pi = plan(R, C, FFT2D_C32H, FFT2D_INVERSE);
-                if (!pi)
-                    return FFT2D_ERR_OOM;
-                // in place: the inverse reads per-column exponents and
-                // writes new per-column exponents into the same vector
-                s = fft2d_exec_h16(pi, q->buf_h16, ecol, FFT2D_PASS_COLS, q->buf_h16, ecol, st);
-            }
-            if (s == FFT2D_OK)
-                s = fft2d_h16_unpack(R, C, q->buf_h16, ecol, FFT2D_PASS_COLS, q->buf_c64, st);
-            if (s != FFT2D_OK)
-                return s;
-        }
-        for (Req *q : b.reqs) {
-            const size_t bytes = (size_t)q->r.rows * q->r.cols * 8;
-            if (cudaMemcpyAsync(q->r.out, q->buf_c64, bytes, cudaMemcpyDeviceToHost, st) !=
+            if (fft2d::launch_lowpass(true, q->buf_h16, R, C, R / 8.0f, C / 8.0f, st) !=
                 cudaSuccess)
+                return FFT2D_ERR_CUDA;
+            fft2d_plan_t p = plan(R, C, FFT2D_C32H, FFT2D_INVERSE);
+            if (!p)
+                return FFT2D_ERR_OOM;
+            h16f.push_back(q);
+            hip.push_back(p);
+        }
+        // the inverse reads the spectrum's per-column exponents and writes
+        // new per-column exponents into the same vector
+        if (!h16f.empty() && h16_phase(h16f, hip, FFT2D_PASS_COLS, st) != cudaSuccess)
+            return FFT2D_ERR_CUDA;
+        for (Req *q : b.reqs) {
+            const size_t px = (size_t)q->r.rows * q->r.cols;
+            cudaError_t e;
+            if (q->r.dtype == FFT2D_C64) {
+                e = cudaMemcpyAsync(q->r.out, q->buf_c64, px * 8, cudaMemcpyDeviceToHost, st);
+            } else {
+                e = cudaMemcpyAsync(q->r.out, q->buf_h16, px * 4, cudaMemcpyDeviceToHost, st);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(q->r.out_exp, q->exps + 2 * q->r.rows,
+                                        (size_t)q->r.cols * 4, cudaMemcpyDeviceToHost, st);
+            }
+            if (e != cudaSuccess)
                 return FFT2D_ERR_CUDA;
         }
         if (cudaEventRecord(b.ev, st) != cudaSuccess)
@@ -469,6 +581,8 @@ fft2d_status fft2d_serve_submit(fft2d_server_t s, const fft2d_request *req,
         return FFT2D_ERR_TOO_LARGE;
     if (r.dtype == FFT2D_C32H && (r.rows < 2 || r.cols < 2))
         return FFT2D_ERR_UNSUPPORTED;
+    if (r.dtype == FFT2D_C32H && (!r.in_exp || !r.out_exp))
+        return FFT2D_ERR_ARG;
     Req *q = new (std::nothrow) Req();
     if (!q)
         return FFT2D_ERR_OOM;

@@ -93,7 +93,8 @@ for _name, (_args, _res) in _sigs.items():
 
 class fft2d_request(ctypes.Structure):
     _fields_ = [("op", ctypes.c_int), ("rows", ctypes.c_int), ("cols", ctypes.c_int),
-                ("dtype", ctypes.c_int), ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+                ("dtype", ctypes.c_int), ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("in_exp", ctypes.c_void_p), ("out_exp", ctypes.c_void_p)]
 
 
 class fft2d_serve_stats(ctypes.Structure):
@@ -341,10 +342,15 @@ def fft2d_serve_create(hbm_budget_bytes: int, streams: int = 4, flags: int = 0) 
 
 
 def fft2d_serve_submit(srv: int, op: int, rows: int, cols: int, dtype: int, inp_host,
-                       out_host) -> int:
+                       out_host, in_exp=None, out_exp=None) -> int:
     """Queue a request on host buffers (torch CPU tensors, numpy arrays or raw
-    pointers); returns its ticket.  Keep the buffers alive until it is done."""
-    req = fft2d_request(op, rows, cols, dtype, _hptr(inp_host), _hptr(out_host))
+    pointers); returns its ticket.  Keep the buffers alive until it is done.
+    FFT2D_C32H requests pass half2 data with per-row input exponents
+    (``in_exp``, rows int32) and receive half2 data with per-column
+    exponents (``out_exp``, cols int32)."""
+    req = fft2d_request(op, rows, cols, dtype, _hptr(inp_host), _hptr(out_host),
+                        None if in_exp is None else _hptr(in_exp),
+                        None if out_exp is None else _hptr(out_exp))
     t = ctypes.c_ulonglong()
     _check(lib.fft2d_serve_submit(srv, ctypes.byref(req), ctypes.byref(t)), "fft2d_serve_submit")
     return t.value

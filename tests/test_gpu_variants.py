@@ -140,6 +140,44 @@ def test_batched_uneven_64_images_mixed_directions(env):
             fft.fft2d_destroy(p)
 
 
+def test_batched_from_a_captured_cuda_graph(env):
+    """The 64-image batch as one captured CUDA graph: after one direct call
+    (the kernels' first-use set-up), fft2d_exec_batched is captured on a side
+    stream -- its grouped launches on the internal streams join the capture
+    through events -- and each replay gives the direct call's bits; every
+    image also matches the oracle."""
+    torch, fft, orc = env
+    shapes = synth.batch_shapes(64, seed=0)
+    imgs = synth.batch_images(shapes, seed=0)
+    plans = [fft.fft2d_plan(r, c, fft.FFT2D_C64, fft.FFT2D_FORWARD) for r, c in shapes]
+    try:
+        ins = [torch.from_numpy(im).cuda() for im in imgs]
+        outs = [torch.empty_like(t) for t in ins]
+        fft.fft2d_exec_batched(plans, ins, outs)
+        torch.cuda.synchronize()
+        want = [o.cpu().numpy() for o in outs]
+        for o in outs:
+            o.zero_()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            fft.fft2d_exec_batched(plans, ins, outs, s.cuda_stream)
+        for _ in range(2):
+            g.replay()
+            torch.cuda.synchronize()
+            for i, (o, w) in enumerate(zip(outs, want)):
+                assert np.array_equal(o.cpu().numpy(), w), f"image {i} {shapes[i]}"
+        for p in plans:
+            fft.fft2d_sync_status(p)
+        errs = [rel(w, orc.fft2d(im, threads=16)) for w, im in zip(want, imgs)]
+        print(f"[batched graph] 64 images, worst rel_l2 vs oracle {max(errs):.2e}")
+        assert max(errs) <= TOL
+    finally:
+        for p in plans:
+            fft.fft2d_destroy(p)
+
+
 def test_batched_more_images_than_one_table(env):
     """More images than one launch's job table holds (128): split launches."""
     torch, fft, _ = env

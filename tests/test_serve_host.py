@@ -28,7 +28,8 @@ def test_all_requests_complete_and_stats(fft):
             r, c = 1 << int(g.integers(4, 11)), 1 << int(g.integers(4, 11))
             op = int(g.integers(0, 2))
             dt = fft.FFT2D_C32H if i % 3 == 0 else fft.FFT2D_C64
-            tickets.append(fft.fft2d_serve_submit(srv, op, r, c, dt, buf, buf))
+            ex = buf if dt == fft.FFT2D_C32H else None
+            tickets.append(fft.fft2d_serve_submit(srv, op, r, c, dt, buf, buf, ex, ex))
         lats = [fft.fft2d_serve_wait(srv, t, 10000) for t in tickets]
         st = fft.fft2d_serve_stats_get(srv)
         assert st["completed"] == 200 and st["rejected"] == 0 and st["queued"] == 0
@@ -137,19 +138,33 @@ def test_wait_timeout_and_unknown_ticket(fft):
 
 def test_oversized_pooled_buffer_does_not_stall_admission(fft):
     """A 128x128 complex64 request leaves a 128 KiB buffer in the pool.  The
-    next request, a 64x128 half2 one, takes it for its 64 KiB complex64
-    buffer (pooled buffers up to twice the size are reused) and would then
-    find no room for its half2 buffer under a 140 000-byte budget, with
+    next request, a 128x128 half2 one, takes it for its 64 KiB half2 buffer
+    (pooled buffers up to twice the size are reused) and would then find no
+    room for its 1.5 KiB of exponents under a 132 000-byte budget, with
     nothing in flight to free memory.  The server must fall back to exact
     sizes instead of waiting for ever."""
-    srv = make(fft, 140000, streams=1)
+    srv = make(fft, 132000, streams=1)
     buf = np.zeros(8, np.complex64)
+    ex = np.zeros(512, np.int32)
     try:
         t = fft.fft2d_serve_submit(srv, 0, 128, 128, fft.FFT2D_C64, buf, buf)
         fft.fft2d_serve_wait(srv, t, 10000)
-        t = fft.fft2d_serve_submit(srv, 1, 64, 128, fft.FFT2D_C32H, buf, buf)
+        t = fft.fft2d_serve_submit(srv, 1, 128, 128, fft.FFT2D_C32H, buf, buf, ex, ex)
         fft.fft2d_serve_wait(srv, t, 10000)
         st = fft.fft2d_serve_stats_get(srv)
-        assert st["completed"] == 2 and st["peak_device_bytes"] <= 140000
+        assert st["completed"] == 2 and st["peak_device_bytes"] <= 132000
+    finally:
+        fft.fft2d_serve_destroy(srv)
+
+
+def test_half2_request_needs_its_exponent_vectors(fft):
+    srv = make(fft, 1 << 30)
+    buf = np.zeros(8, np.complex64)
+    ex = np.zeros(64, np.int32)
+    try:
+        for a, b in ((None, ex), (ex, None)):
+            with pytest.raises(fft.FFT2DError) as ei:
+                fft.fft2d_serve_submit(srv, 0, 64, 64, fft.FFT2D_C32H, buf, buf, a, b)
+            assert ei.value.status == fft.FFT2D_ERR_ARG
     finally:
         fft.fft2d_serve_destroy(srv)
