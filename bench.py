@@ -309,7 +309,7 @@ def cuda_timer(torch, stream):
     return t
 
 
-def measure_fp16(fft, torch, orc, side, reps):
+def measure_fp16(fft, torch, orc, side, reps, check=True):
     """Forward 2D FFT of a side x side image (re, im ~ U[-1, 1)) with half2
     storage (fft2d_exec_h16) beside complex64 (fft2d_exec, autotuned), two
     input/output pairs in turn; relative L2 error of each against the FP64
@@ -354,12 +354,14 @@ def measure_fp16(fft, torch, orc, side, reps):
         fft.fft2d_destroy(p32)
         fft.fft2d_destroy(p16)
     torch.cuda.empty_cache()
-    want32 = orc.fft2d(x, threads=th)
-    e32 = rel_l2(got32, want32)
-    del want32, got32
-    want16 = orc.fft2d(h16_dequantise(q, e, 0), threads=th)
-    e16 = rel_l2(h16_dequantise(q_out, e_out, 1), want16)
-    del want16
+    e32 = e16 = None
+    if check:
+        want32 = orc.fft2d(x, threads=th)
+        e32 = rel_l2(got32, want32)
+        del want32, got32
+        want16 = orc.fft2d(h16_dequantise(q, e, 0), threads=th)
+        e16 = rel_l2(h16_dequantise(q_out, e_out, 1), want16)
+        del want16
     px = side * side
     return {"fp16_ms": ms16, "fp32_ms": ms32, "speedup_fp16_vs_fp32": ms32 / ms16,
             "fp32_row_pass_ms": ms32_rows, "fp32_col_pass_ms": ms32_cols,
@@ -781,7 +783,8 @@ def run_fp16(args):
     results = {}
     for side in sides:
         reps = 20 if side <= 8192 else 8
-        results[f"{side}x{side}"] = measure_fp16(fft, torch, orc, side, reps)
+        results[f"{side}x{side}"] = measure_fp16(fft, torch, orc, side, reps,
+                                                 check=not args.no_parity)
     big = results[f"{max(sides)}x{max(sides)}"]
     line = {"metric": "2D FFT images/s, FP16 half2 storage vs complex64",
             "value": big["fp16_images_per_s"], "unit": "images/s", "n_gpus": 1,
