@@ -1,0 +1,600 @@
+// col_group.cuh -- persistent column pass for columns of 2^(L+c) rows whose
+// 4-column tile is too large for one SM, split over a cluster of CS = 2^c
+// CTAs (c = 1: a CTA pair for 8192 rows; c = 2: four CTAs for 16384 rows).
+//
+// The DIT structure (Section 2 eqs. 2-3) splits the transform without any
+// extra pass over memory.  After the scramble, the positions P = k + 2^L q,
+// k < 2^L, q < CS, with the same q hold the rows m = CS m' + rev_c(q) in the
+// bit-reversed order of a 2^L-point line, and stages 1..L never mix
+// different q.  So CTA q of the cluster loads rows CS m' + rev_c(q) of the
+// tile by TMA (a tensor map with CS times the row pitch), runs stages 1..L
+// on them with the same engine as the single-CTA column pass (prefetch
+// region, three stage groups, rotation factors in shared memory) and ends
+// with Y_q[k], k < 2^L, in registers.  The last c stages each pair values
+// of two CTAs: stage L+1+j pairs positions that differ in bit L+j, i.e. the
+// CTAs q and q ^ 2^j, with
+//     X[P] = Y[P] + W^i Y[P + 2^(L+j)],  X[P + 2^(L+j)] = Y[P] - W^i Y[P + 2^(L+j)],
+// W = W_{2^(L+j+1)}, i = P mod 2^(L+j).  Thread t holds the same indices k
+// in every CTA, so in round j the two partners split the k that are still
+// theirs by bit L-1-j of k: each keeps one half, writes the values of the
+// other half into a send buffer, and one thread moves the whole buffer into
+// the partner's shared memory with a single bulk copy that completes on the
+// partner's mbarrier.  After c rounds CTA q holds, for a contiguous quarter
+// (c = 2) or half (c = 1) of the k, all CS outputs X[k + 2^L t] and writes
+// them with TMA stores.
+//
+// With half2 storage (H16) the tile arrives as half2 (16-byte TMA box rows)
+// and group 0 widens each value with its row's factor 2^e, as in the
+// single-CTA half2 column pass; at the end every CTA max-reduces its part of
+// each column, the partial maxima travel to every CTA of the cluster with the
+// last exchange round's barrier, and all CTAs pick the same exponent per
+// column before staging their ranges as half2.
+//
+// Cluster barriers have no time limit, so every CTA always executes the same
+// sequence of them: a CTA that lost a TMA transfer still reaches the first
+// cluster barrier of the tile, where all CTAs have exchanged "lost" flags,
+// and the whole cluster leaves together.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "line_fft.cuh"
+
+namespace fft2d {
+
+__device__ __forceinline__ void cluster_arrive_release()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void cluster_wait_acquire()
+{
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+// Bulk copy from this CTA's shared memory into another CTA's (dst and its
+// mbarrier are shared::cluster addresses); completes on that mbarrier.
+__device__ __forceinline__ void bulk_copy_to_peer(uint32_t dst, const void *src, uint32_t bytes,
+                                                  uint32_t peer_bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+        "[%3];" ::"r"(dst),
+        "r"(smem_addr(src)), "r"(bytes), "r"(peer_bar)
+        : "memory");
+}
+
+// Tile geometry of the group kernel for a local engine C (2^L rows, W
+// columns, 512 threads x 32 values) and a cluster of 2^CL CTAs.
+template <class C, int CL>
+struct GroupCol {
+    using S = TmaSplit<C>;
+    using Gl = Grp<C, C::NG - 1>;
+    static constexpr int CS = 1 << CL;
+    static constexpr int L = C::L;                        // local stages
+    static constexpr int NL = C::N;                       // rows held by one CTA
+    static constexpr int XVALS = 16;                      // values exchanged per thread per round
+    static constexpr uint32_t XBYTES = (uint32_t)XVALS * C::T * 8u;   // per CTA per round
+    static constexpr int KEEP_R = Gl::R >> CL;            // register indices r kept at the end
+    static constexpr int OUT_ROWS = NL / CS;              // rows k of one CTA's output range
+    static constexpr int OUT_BOX_Z = OUT_ROWS / S::BOX;   // 256-row blocks of one range
+    static constexpr int STAGE_T = (C::E / 2) / (OUT_ROWS * C::W);   // ranges per staging fill
+    static_assert(C::EPT == 32 && C::NG == 3 && C::LB == 1, "512 threads x 32 values, 3 groups");
+    static_assert(CL >= 1 && CL <= 2, "two or four CTAs");
+    static_assert(Gl::S0 + Gl::G == L && (NL >> Gl::S0) == Gl::R,
+                  "the last group's register index is the top bits of k");
+    static_assert(Gl::V * (Gl::R / 2) == XVALS, "half of a thread's values per round");
+    static_assert(XBYTES <= (uint32_t)C::E * 4u, "the receive buffer fits in half the tile region");
+    static_assert(OUT_ROWS % S::BOX == 0, "output ranges are whole 256-row blocks");
+    static_assert(STAGE_T >= 1 && CS % STAGE_T == 0, "whole output ranges per staging fill");
+};
+
+// One exchange round J of the last CL stages.  On entry s[] holds, for the
+// 2^J outputs t and the register indices r in [rb, rb + NK) of both units v,
+// s[t * 2 NK + v NK + (r - rb)] (NK = 16 >> J); on return it holds the same
+// for 2^(J+1) outputs and the half [rk, rk + NK/2) kept by this CTA.
+// Twiddles wk[] were loaded for the kept half, in the order of the loop.
+template <class C, int J>
+__device__ __forceinline__ void group_round_compute(float2 (&s)[32], const float2 *recv,
+                                                    const float2 (&wk)[16], int bitj)
+{
+    using Gl = Grp<C, C::NG - 1>;
+    constexpr int NT = 1 << J;
+    constexpr int NK = Gl::R >> J;
+    constexpr int NH = NK / 2;
+    const int tid = threadIdx.x;
+    float2 n[32];
+#pragma unroll
+    for (int t = 0; t < NT; t++) {
+#pragma unroll
+        for (int v = 0; v < Gl::V; v++) {
+#pragma unroll
+            for (int ih = 0; ih < NH; ih++) {
+                const int j = (t * Gl::V + v) * NH + ih;     // send / receive slot, twiddle
+                const float2 lo_half = s[t * 2 * NK + v * NK + ih];
+                const float2 hi_half = s[t * 2 * NK + v * NK + NH + ih];
+                const float2 mine = bitj == 0 ? lo_half : hi_half;
+                const float2 theirs = recv[j * C::T + tid];
+                float2 x0 = bitj == 0 ? mine : theirs;
+                float2 x1 = bitj == 0 ? theirs : mine;
+                butterfly_w(x0, x1, wk[j]);
+                n[t * 2 * NH + v * NH + ih] = x0;                 // output t (bit L+J clear)
+                n[(t + NT) * 2 * NH + v * NH + ih] = x1;          // output t + 2^J
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 32; i++)
+        s[i] = n[i];
+}
+
+// The half of round J's values this CTA gives away, into the send buffer.
+template <class C, int J>
+__device__ __forceinline__ void group_round_send(const float2 (&s)[32], float2 *sendb, int bitj)
+{
+    using Gl = Grp<C, C::NG - 1>;
+    constexpr int NT = 1 << J;
+    constexpr int NK = Gl::R >> J;
+    constexpr int NH = NK / 2;
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int t = 0; t < NT; t++) {
+#pragma unroll
+        for (int v = 0; v < Gl::V; v++) {
+#pragma unroll
+            for (int ih = 0; ih < NH; ih++) {
+                const int j = (t * Gl::V + v) * NH + ih;
+                const float2 lo_half = s[t * 2 * NK + v * NK + ih];
+                const float2 hi_half = s[t * 2 * NK + v * NK + NH + ih];
+                sendb[j * C::T + tid] = bitj == 0 ? hi_half : lo_half;
+            }
+        }
+    }
+}
+
+// Rotation factors of round J for the kept half: W_{2^(L+J+1)}^i with
+// i = k + 2^L t, read from the plan's table (stage L+J+1 starts at entry
+// 2^(L+J) - 1), k = lo_v + 2^S0 r for the kept r.
+template <class C, int J>
+__device__ __forceinline__ void group_round_twiddles(float2 (&wk)[16],
+                                                     const float2 *__restrict__ tw, int rk)
+{
+    using Gl = Grp<C, C::NG - 1>;
+    constexpr int NT = 1 << J;
+    constexpr int NH = (Gl::R >> J) / 2;
+    const float2 *tws = tw + ((1 << (C::L + J)) - 1);
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int t = 0; t < NT; t++) {
+#pragma unroll
+        for (int v = 0; v < Gl::V; v++) {
+            const int u = tid + v * C::T;
+            const int lo = (u >> C::KW) & ((1 << Gl::S0) - 1);
+#pragma unroll
+            for (int ih = 0; ih < NH; ih++) {
+                const int k = lo | ((rk + ih) << Gl::S0);
+                wk[(t * Gl::V + v) * NH + ih] = __ldg(tws + k + (t << C::L));
+            }
+        }
+    }
+}
+
+// Shared-memory layout of the half2 group kernel (byte offsets): the FP32
+// tile / exchange region, the early half of the next half2 tile, the
+// rotation factors, the factors 2^e of this CTA's rows.
+template <class C>
+struct GroupH16 {
+    static constexpr int BOX = 256;
+    static constexpr int NBOX = C::N / BOX;
+    static constexpr int NB = NBOX / 2;
+    static constexpr int BOXV = BOX * C::W;                  // half2 values per block
+    static constexpr uint32_t HALF_BYTES = (uint32_t)NB * BOXV * 4u;
+    static constexpr int PREF_OFF = C::E * 8;
+    static constexpr int TW_OFF = PREF_OFF + (int)HALF_BYTES;
+    static constexpr int RF_OFF = TW_OFF + C::N * 8;
+    static constexpr int SMEM_BYTES = RF_OFF + C::N * 4;
+    static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
+};
+
+// Storage of the group kernel's input and output: complex64, or half2 with
+// the input's exponents per row (row_exp) and the output's per column.
+struct GroupIO {
+    const int *row_exp;
+    int *out_exp;
+};
+
+// C: the local engine; cluster of 2^CL CTAs, this CTA's rank q.  lmap: this
+// CTA's load map (rows CS m + rev_CL(q) of the image; box W x 256 x NB);
+// omap: store map over the output (box W x 256 x OUT_BOX_Z); tw: the plan's
+// rotation-factor table of the column axis (2^(L+CL) entries with padding:
+// the local stages read entries [0, 2^L), round j stage L+1+j).
+template <class C, int CL, bool H16>
+__device__ __forceinline__ void col_group_body(const CUtensorMap *lmap, const CUtensorMap *omap,
+                                               int ntiles, const float2 *__restrict__ tw,
+                                               float scale, int *err, int withhold,
+                                               const GroupIO &io)
+{
+    namespace cg = cooperative_groups;
+    using S = TmaSplit<C>;
+    using GC = GroupCol<C, CL>;
+    using GH = GroupH16<C>;
+    using Gl = Grp<C, C::NG - 1>;
+    using G0 = Grp<C, 0>;
+    constexpr int CS = GC::CS;
+    extern __shared__ __align__(1024) float2 sm[];
+    __shared__ __align__(8) uint64_t bar_early, bar_late, bar_recv;
+    __shared__ int lost_flag[CS];   // slot p: written by CTA p of the cluster
+    __shared__ int cmax[CS][C::W];  // half2: partial column maxima, slot p from CTA p
+    __shared__ int cmax_local[C::W];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int q = (int)cluster.block_rank();
+    const int tid = threadIdx.x;
+    const int nclusters = (int)gridDim.x / CS;
+    unsigned char *smb = reinterpret_cast<unsigned char *>(sm);
+    float2 *stw = H16 ? reinterpret_cast<float2 *>(smb + GH::TW_OFF) : sm + S::TW_OFF;
+    float *rf = reinterpret_cast<float *>(smb + GH::RF_OFF);
+    const uint32_t tw_bytes = H16 ? (uint32_t)C::N * 8u : S::TW_BYTES;
+    // the first and second half of a tile's TMA boxes
+    auto issue_early = [&](int t) {
+        if constexpr (H16) {
+            mbar_arrive_expect_tx(&bar_early, GH::HALF_BYTES);
+            tma_load_3d(smb + GH::PREF_OFF, lmap, t * C::W, 0, 0, &bar_early);
+        } else {
+            split_issue_early<C>(sm, lmap, t * C::W, &bar_early);
+        }
+    };
+    auto issue_late = [&](int t) {
+        if constexpr (H16) {
+            mbar_arrive_expect_tx(&bar_late, GH::HALF_BYTES);
+            tma_load_3d(smb, lmap, t * C::W, 0, GH::NB, &bar_late);
+        } else {
+            split_issue_late<C>(sm, lmap, t * C::W, &bar_late);
+        }
+    };
+    // after the last read of a tile: the lower half of the tile region
+    // receives the partner's values, the upper half holds the values sent
+    // and then stages the output
+    float2 *recvb = sm;
+    float2 *sendb = sm + C::E / 2;
+    uint32_t peer_recv[CL], peer_bar[CL];
+#pragma unroll
+    for (int j = 0; j < CL; j++) {
+        peer_recv[j] = mapa_shared(smem_addr(recvb), (uint32_t)(q ^ (1 << j)));
+        peer_bar[j] = mapa_shared(smem_addr(&bar_recv), (uint32_t)(q ^ (1 << j)));
+    }
+    // the k this CTA keeps at the end: register indices [rk_end, rk_end + KEEP_R)
+    int rk_end = 0;
+#pragma unroll
+    for (int j = 0; j < CL; j++)
+        rk_end += ((q >> j) & 1) * ((Gl::R >> j) / 2);
+    const int k_base = rk_end << Gl::S0;   // first row k of this CTA's output ranges
+    int lost_recv = 0;
+    int tile = (int)blockIdx.x / CS;
+
+    if (tid == 0) {
+        mbar_init(&bar_early, 1);
+        mbar_init(&bar_late, 1);
+        mbar_init(&bar_recv, 1);
+        fence_mbar_init();
+    }
+    if constexpr (H16) {
+        // the factors of this CTA's rows CS m + rev_CL(q)
+        const int res = brev_rt(q, CL);
+        for (int i = tid; i < C::N; i += C::T)
+            rf[i] = pow2f(io.row_exp[(long long)i * CS + res]);
+        if (tid < C::W)
+            cmax_local[tid] = 0;
+    }
+    __syncthreads();
+    // issued / waited phases of each mbarrier (thread 0 issues, all wait)
+    int n_early = 0, n_late = 0, w_early = 0, w_late = 0;
+    if (tile < ntiles) {
+        if (tid == 0) {
+            mbar_expect_tx(&bar_early, tw_bytes);
+            bulk_load(stw, tw, tw_bytes, &bar_early);
+            issue_early(tile);
+            // (self-test: CTA 0 withholds its first late boxes)
+            if (!(withhold && blockIdx.x == 0))
+                issue_late(tile);
+        }
+        n_early = n_late = 1;
+    }
+    bool lost = false;
+    int w_recv = 0;   // completed phases of bar_recv
+    float2 a[C::EPT];
+    for (; tile < ntiles; tile += nclusters) {
+        const int next = tile + nclusters;
+        const bool ok = mbar_wait_bounded(&bar_early, (uint32_t)(w_early & 1)) &&
+                        mbar_wait_bounded(&bar_late, (uint32_t)(w_late & 1));
+        // a receive that timed out on the previous tile counts as lost too
+        const int lost_here = __syncthreads_or((ok ? 0 : 1) | lost_recv);
+        // the "lost" flags for the first cluster barrier and the arming of
+        // the receive mbarrier, early so the remote flag stores are long done
+        // when that barrier is arrived at (the peers read the flags after it
+        // and the next ones are written only after the tile's second barrier)
+        if (tid == 0) {
+            if (!lost_recv)   // (a phase that timed out may still be open)
+                mbar_arrive_expect_tx(&bar_recv, GC::XBYTES);
+#pragma unroll
+            for (int p = 0; p < CS; p++)
+                *cluster.map_shared_rank(lost_flag + q, p) = lost_here;
+        }
+        if (!lost_here) {
+            w_early++;
+            w_late++;
+            if constexpr (H16) {
+                // group 0: scrambled gather of the half2 tile, widened and
+                // scaled by the row factors
+                const __half2 *pref = reinterpret_cast<const __half2 *>(smb + GH::PREF_OFF);
+                const __half2 *late = reinterpret_cast<const __half2 *>(smb);
+#pragma unroll
+                for (int v = 0; v < G0::V; v++) {
+                    const int u = tid + v * C::T;
+                    const int w = u & (C::W - 1);
+                    const int hib = (u >> C::KW) & ((1 << G0::HB) - 1);
+#pragma unroll
+                    for (int r = 0; r < G0::R; r++) {
+                        const int top = brev_c(r, G0::G) << G0::HB;   // compile-time
+                        const int kb = top / GH::BOX;
+                        const int in_box = ((top % GH::BOX) | hib) * C::W + w;
+                        const __half2 *bx = kb < GH::NB ? pref + kb * GH::BOXV
+                                                        : late + (kb - GH::NB) * GH::BOXV;
+                        const float2 hv = __half22float2(bx[in_box]);
+                        const float f = rf[top | hib];
+                        a[v * G0::R + r] = make_float2(hv.x * f, hv.y * f);
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < G0::V; v++)
+                    run_stages<C, 0, false, true>(a, v, 0, stw, C::L);
+                fence_proxy_async_smem();
+                if (tid == 0)
+                    bulk_wait_read_all();   // the previous tile's stores have read it
+                __syncthreads();            // every slot of both input regions has been read
+                if (tid == 0 && next < ntiles)
+                    issue_early(next);
+#pragma unroll
+                for (int v = 0; v < G0::V; v++) {
+                    const int u = tid + v * C::T;
+                    const int w = u & (C::W - 1);
+                    const int hib = (u >> C::KW) & ((1 << G0::HB) - 1);
+                    const int hi = brev_rt(hib, G0::HB);
+#pragma unroll
+                    for (int r = 0; r < G0::R; r++)
+                        sm[sidx<C>(0, r | (hi << G0::G), w)] = a[v * G0::R + r];
+                }
+            } else {
+                group_first_split<C>(
+                    a, sm, stw,
+                    [&] {
+                        if (tid == 0)
+                            bulk_wait_read_all();   // the previous tile's stores have read it
+                    },
+                    [&] {
+                        if (tid == 0 && next < ntiles)
+                            issue_early(next);
+                    });
+            }
+            if (next < ntiles)
+                n_early++;
+            __syncthreads();
+            group_smem<C, 1, false, false, true>(a, sm, stw, C::L);
+            __syncthreads();
+            group_last_read<C>(a, sm);
+            __syncthreads();   // the tile region is free
+        }
+        // cluster barrier A0, arrive: this CTA's tile region is free and its
+        // receive mbarrier armed; the "lost" flags travel with it
+        cluster_arrive_release();
+        float2 wk[16];
+        if (!lost_here) {
+#pragma unroll
+            for (int v = 0; v < Gl::V; v++) {
+                const int u = tid + v * C::T;
+                const int lo = (u >> C::KW) & ((1 << Gl::S0) - 1);
+                run_stages<C, C::NG - 1, false, true>(a, v, lo, stw, C::L);
+            }
+            group_round_send<C, 0>(a, sendb, q & 1);
+            fence_proxy_async_smem();
+        }
+        __syncthreads();   // the send buffer is complete
+        group_round_twiddles<C, 0>(wk, tw, (q & 1) * (Gl::R / 2));
+        cluster_wait_acquire();
+        {
+            int any = 0;
+#pragma unroll
+            for (int p = 0; p < CS; p++)
+                any |= lost_flag[p];
+            if (any) {
+                lost = true;
+                break;
+            }
+        }
+        // round 0: the partner's receive region is free; one bulk copy of
+        // the send buffer into it, completing on the partner's mbarrier
+        if (tid == 0)
+            bulk_copy_to_peer(peer_recv[0], sendb, GC::XBYTES, peer_bar[0]);
+        lost_recv = mbar_wait_bounded(&bar_recv, (uint32_t)(w_recv & 1)) ? 0 : 1;
+        if (!lost_recv)
+            w_recv++;
+        // cluster barrier B0, arrive: the partner's send buffer has been read
+        // (half2, last round: after the column maxima, further down)
+        if constexpr (!(H16 && CL == 1))
+            cluster_arrive_release();
+        group_round_compute<C, 0>(a, recvb, wk, q & 1);
+        if constexpr (CL == 2) {
+            const int rk1 = ((q & 1) * (Gl::R / 2)) + ((q >> 1) & 1) * (Gl::R / 4);
+            group_round_twiddles<C, 1>(wk, tw, rk1);
+            fence_proxy_async_smem();
+            __syncthreads();   // the receive buffer has been read
+            if (tid == 0 && !lost_recv)
+                mbar_arrive_expect_tx(&bar_recv, GC::XBYTES);
+            cluster_wait_acquire();   // B0: this CTA's send buffer is free
+            group_round_send<C, 1>(a, sendb, (q >> 1) & 1);
+            fence_proxy_async_smem();
+            __syncthreads();   // the send buffer is complete
+            // cluster barrier A1: every receive region is free and armed
+            cluster_arrive_release();
+            cluster_wait_acquire();
+            if (tid == 0)
+                bulk_copy_to_peer(peer_recv[1], sendb, GC::XBYTES, peer_bar[1]);
+            const int lr = mbar_wait_bounded(&bar_recv, (uint32_t)(w_recv & 1)) ? 0 : 1;
+            if (!lr)
+                w_recv++;
+            lost_recv |= lr;
+            // cluster barrier B1, arrive: the partner's send buffer has been read
+            // (half2: after the column maxima, further down)
+            if constexpr (!H16)
+                cluster_arrive_release();
+            group_round_compute<C, 1>(a, recvb, wk, (q >> 1) & 1);
+        }
+        if constexpr (H16) {
+            // this CTA's part of each column's largest |component| (a
+            // thread's values all belong to column tid mod W), to every CTA
+            // of the cluster with the last B barrier
+            float m = 0.f;
+#pragma unroll
+            for (int i = 0; i < 32; i++)
+                m = fmaxf(m, fmaxf(fabsf(a[i].x), fabsf(a[i].y)));
+            m = warp_line_max<C::KW, 5>(m);
+            if ((tid & (31 & ~(C::W - 1))) == 0)
+                atomicMax(&cmax_local[tid & (C::W - 1)], __float_as_int(m * scale));
+            __syncthreads();
+            if (tid < C::W) {
+                const int mine = cmax_local[tid];
+                cmax_local[tid] = 0;
+#pragma unroll
+                for (int p = 0; p < CS; p++)
+                    *cluster.map_shared_rank(&cmax[q][tid], p) = mine;
+            }
+            cluster_arrive_release();
+        }
+        fence_proxy_async_smem();
+        __syncthreads();   // the receive buffer has been read
+        if (tid == 0 && next < ntiles)
+            issue_late(next);
+        if (next < ntiles)
+            n_late++;
+        // the last B barrier, wait: this CTA's send buffer is free for staging
+        cluster_wait_acquire();
+
+        if constexpr (H16) {
+            // every CTA of the cluster picks the same exponent per column
+            const int w = tid & (C::W - 1);
+            int mb = 0;
+#pragma unroll
+            for (int p = 0; p < CS; p++)
+                mb = max(mb, cmax[p][w]);
+            const int e = line_exponent(__int_as_float(mb));
+            const float f = scale * pow2f(-e);
+            __half2 *stage = reinterpret_cast<__half2 *>(sendb);
+#pragma unroll
+            for (int t = 0; t < CS; t++) {
+#pragma unroll
+                for (int v = 0; v < Gl::V; v++) {
+                    const int u = tid + v * C::T;
+                    const int lo = (u >> C::KW) & ((1 << Gl::S0) - 1);
+#pragma unroll
+                    for (int i = 0; i < GC::KEEP_R; i++) {
+                        const float2 x = a[t * 2 * GC::KEEP_R + v * GC::KEEP_R + i];
+                        stage[(t * GC::OUT_ROWS + ((i << Gl::S0) | lo)) * C::W + w] =
+                            __floats2half2_rn(x.x * f, x.y * f);
+                    }
+                }
+            }
+            if (q == 0 && tid < C::W)
+                io.out_exp[tile * C::W + tid] = e;
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+#pragma unroll
+                for (int t = 0; t < CS; t++) {
+                    const int z = ((t << C::L) + k_base) / S::BOX;
+                    tma_store_3d(omap, tile * C::W, 0, z, stage + t * GC::OUT_ROWS * C::W);
+                }
+                bulk_commit();
+            }
+            continue;
+        }
+
+        // outputs t = 0 .. CS-1: rows k_base + [0, OUT_ROWS) + 2^L t, STAGE_T
+        // ranges per fill of the staging buffer (the send buffer), each
+        // range one TMA store
+#pragma unroll
+        for (int f = 0; f < CS / GC::STAGE_T; f++) {
+            if (f > 0) {
+                if (tid == 0)
+                    bulk_wait_read_all();
+                __syncthreads();
+            }
+#pragma unroll
+            for (int ts = 0; ts < GC::STAGE_T; ts++) {
+                const int t = f * GC::STAGE_T + ts;
+#pragma unroll
+                for (int v = 0; v < Gl::V; v++) {
+                    const int u = tid + v * C::T;
+                    const int w = u & (C::W - 1);
+                    const int lo = (u >> C::KW) & ((1 << Gl::S0) - 1);
+#pragma unroll
+                    for (int i = 0; i < GC::KEEP_R; i++) {
+                        const float2 x = a[t * 2 * GC::KEEP_R + v * GC::KEEP_R + i];
+                        sendb[(ts * GC::OUT_ROWS + ((i << Gl::S0) | lo)) * C::W + w] =
+                            make_float2(x.x * scale, x.y * scale);
+                    }
+                }
+            }
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+#pragma unroll
+                for (int ts = 0; ts < GC::STAGE_T; ts++) {
+                    const int t = f * GC::STAGE_T + ts;
+                    const int z = ((t << C::L) + k_base) / S::BOX;
+                    tma_store_3d(omap, tile * C::W, 0, z, sendb + ts * GC::OUT_ROWS * C::W);
+                }
+                bulk_commit();
+            }
+        }
+    }
+
+    if (__syncthreads_or((lost || lost_recv) ? 1 : 0)) {
+        if (tid == 0)
+            atomicExch(err, kDevErrTmaTimeout);
+        // let transfers still in flight land before the CTA leaves
+        if (n_early > w_early)
+            mbar_wait_bounded(&bar_early, (uint32_t)(w_early & 1));
+        if (n_late > w_late)
+            mbar_wait_bounded(&bar_late, (uint32_t)(w_late & 1));
+        if (lost_recv)
+            mbar_wait_bounded(&bar_recv, (uint32_t)(w_recv & 1));
+    }
+    if (tid == 0)
+        bulk_wait_all();   // shared memory stays valid until the stores are done
+}
+
+// rank q loads map[rev_CL(q)] -- the rows of residue rev_CL(q) mod 2^CL
+template <class C, int CL, bool H16 = false>
+__global__ void __launch_bounds__(C::T, 1) col_group_kernel(const __grid_constant__ CUtensorMap map0,
+                                                            const __grid_constant__ CUtensorMap map1,
+                                                            const __grid_constant__ CUtensorMap map2,
+                                                            const __grid_constant__ CUtensorMap map3,
+                                                            const __grid_constant__ CUtensorMap omap,
+                                                            const float2 *__restrict__ tw,
+                                                            int cols, float scale, int *err,
+                                                            int withhold, const GroupIO io)
+{
+    const int q = (int)cooperative_groups::this_cluster().block_rank();
+    const int res = brev_rt(q, CL);
+    const CUtensorMap *m = res == 0 ? &map0 : res == 1 ? &map1 : res == 2 ? &map2 : &map3;
+    col_group_body<C, CL, H16>(m, &omap, cols / C::W, tw, scale, err, withhold, io);
+}
+
+}  // namespace fft2d

@@ -7,7 +7,7 @@
 #include <cstring>
 #include <mutex>
 
-#include "col_pair.cuh"
+#include "col_group.cuh"
 #include "col_tmem.cuh"
 #include "line_fft.cuh"
 #include "passes.h"
@@ -219,32 +219,37 @@ cudaError_t col_launch_tmem(const PassArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// Column pass over 2^(L+1)-row columns split over a CTA pair
-// (col_pair_kernel, local engine C of 2^L rows): one load map per CTA (rows
-// of one parity), one store map, a persistent grid of as many pairs as can
-// be resident at once.
-template <class C>
-bool col_pair_usable(const PassArgs &a)
+// Column pass over 2^(L+CL)-row columns split over a cluster of 2^CL CTAs
+// (col_group_kernel, local engine C of 2^L rows): one load map per row
+// residue modulo 2^CL, one store map, a persistent grid of as many clusters
+// as can be resident at once.
+template <class C, int CL>
+bool col_group_usable(const PassArgs &a)
 {
-    return col_tma_usable<C>(a) && a.rows == 2 * C::N;
+    return col_tma_usable<C>(a) && a.rows == (C::N << CL);
 }
 
-template <class C>
-cudaError_t col_launch_pair(const PassArgs &a, cudaStream_t s)
+template <class C, int CL>
+cudaError_t col_launch_group(const PassArgs &a, cudaStream_t s)
 {
     using S = TmaSplit<C>;
-    using PC = PairCol<C>;
-    CUtensorMap m0, m1, om;
-    if (!encode_col_map(&m0, a.in, a.rows / 2, a.cols, 2 * a.ld, C::W, S::BOX, S::NB) ||
-        !encode_col_map(&m1, a.in + a.ld, a.rows / 2, a.cols, 2 * a.ld, C::W, S::BOX, S::NB) ||
-        !encode_col_map(&om, a.out, a.rows, a.cols, a.ld, C::W, S::BOX, PC::OUT_BOX_Z))
-        return col_launch_any<LineCfg<C::L + 1, C::KW, 0>>(a, s);
-    auto k = col_pair_kernel<C>;
+    using GC = GroupCol<C, CL>;
+    constexpr int CS = 1 << CL;
+    CUtensorMap m[4], om;
+    for (int r = 0; r < CS; r++)
+        if (!encode_col_map(&m[r], a.in + r * a.ld, a.rows / CS, a.cols, CS * a.ld, C::W, S::BOX,
+                            S::NB))
+            return col_launch_any<LineCfg<C::L + CL, C::KW, 0>>(a, s);
+    for (int r = CS; r < 4; r++)
+        m[r] = m[0];
+    if (!encode_col_map(&om, a.out, a.rows, a.cols, a.ld, C::W, S::BOX, GC::OUT_BOX_Z))
+        return col_launch_any<LineCfg<C::L + CL, C::KW, 0>>(a, s);
+    auto k = col_group_kernel<C, CL, false>;
     constexpr int SMEM = S::SMEM_BYTES;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.x = CS;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     cfg.blockDim = dim3(C::T);
@@ -252,24 +257,25 @@ cudaError_t col_launch_pair(const PassArgs &a, cudaStream_t s)
     cfg.stream = s;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    static DeviceCache pairs;
+    static DeviceCache groups;
     const int d = current_device();
-    if (!pairs.get(d)) {
+    if (!groups.get(d)) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              SMEM);
         if (e != cudaSuccess)
             return e;
-        cfg.gridDim = dim3((unsigned)(2 * (sm_count() / 2)));
+        cfg.gridDim = dim3((unsigned)(CS * (sm_count() / CS)));
         int n = 0;
         e = cudaOccupancyMaxActiveClusters(&n, k, &cfg);
         if (e != cudaSuccess)
             return e;
-        pairs.set(d, n > 0 ? n : 1);
+        groups.set(d, n > 0 ? n : 1);
     }
     const int ntiles = a.cols / C::W;
-    const int np = pairs.get(d) < ntiles ? pairs.get(d) : ntiles;
-    cfg.gridDim = dim3((unsigned)(2 * np));
-    return cudaLaunchKernelEx(&cfg, k, m0, m1, om, a.tw, a.cols, a.scale, a.err, a.withhold);
+    const int ng = groups.get(d) < ntiles ? groups.get(d) : ntiles;
+    cfg.gridDim = dim3((unsigned)(CS * ng));
+    return cudaLaunchKernelEx(&cfg, k, m[0], m[1], m[2], m[3], om, a.tw, a.cols, a.scale, a.err,
+                              a.withhold, GroupIO{nullptr, nullptr});
 }
 
 template <class CC>
@@ -350,11 +356,15 @@ struct ColVariants {
         if constexpr (HASTMEM && tma_store_ok<Tma32>())
             t.v[t.n++] = {"tma32h", Tma32::W, 32, col_tma_usable<Tma32>,
                           col_launch_tma<Tma32, true, true>, true};
-        // 8192 rows: 4-column tiles over a CTA pair, the 4096-row engine on
-        // each half and the last stage through remote stores
+        // 8192 and 16384 rows: 4-column tiles over a cluster of 2 or 4 CTAs,
+        // the 4096-row engine on each CTA's rows and the last one or two
+        // stages through bulk copies between the CTAs' shared memories
         if constexpr (L == 13)
-            t.v[t.n++] = {"pair", PairLocal::W, 32, col_pair_usable<PairLocal>,
-                          col_launch_pair<PairLocal>, true};
+            t.v[t.n++] = {"pair", PairLocal::W, 32, col_group_usable<PairLocal, 1>,
+                          col_launch_group<PairLocal, 1>, true};
+        if constexpr (L == 14)
+            t.v[t.n++] = {"quad", PairLocal::W, 32, col_group_usable<PairLocal, 2>,
+                          col_launch_group<PairLocal, 2>, true};
         return t;
     }
     static const Variant *table(int *n)
@@ -387,7 +397,7 @@ struct ColVariants {
         else if constexpr (L == 13)
             return index_of("pair");      // 4-column tiles over a CTA pair
         else if constexpr (L == 14)
-            return index_of("cluster");   // 4-column tiles over 4 CTAs: 32-byte row segments
+            return index_of("quad");      // 4-column tiles over 4 CTAs (1.83 vs 2.00 ms for "cluster")
         else
             return 0;
     }

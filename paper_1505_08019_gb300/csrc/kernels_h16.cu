@@ -5,6 +5,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 
+#include "col_group.cuh"
 #include "col_h16.cuh"
 #include "line_fft.cuh"
 #include "passes.h"
@@ -102,6 +103,62 @@ cudaError_t h16_launch_col_tma(const H16PassArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Columns of 2^(12+CL) rows on a cluster of 2^CL CTAs (col_group.cuh, half2
+// storage): the 4096-row engine on each CTA's rows, the last CL stages by
+// bulk copies between the CTAs.  cudaErrorNotSupported (nothing launched)
+// when the buffers or shape cannot feed it.
+template <int CL>
+cudaError_t h16_launch_col_group(const H16PassArgs &a, cudaStream_t s)
+{
+    using C = LineCfg<12, 2, 0, 32>;
+    using GH = GroupH16<C>;
+    using GC = GroupCol<C, CL>;
+    constexpr int CS = 1 << CL;
+    if (a.in_axis != 0 || a.nst != 12 + CL || !a.err || a.cols % C::W != 0 ||
+        a.rows != (C::N << CL) || (reinterpret_cast<uintptr_t>(a.tw) & 15))
+        return cudaErrorNotSupported;
+    CUtensorMap m[4], om;
+    for (int r = 0; r < CS; r++)
+        if (!encode_h16_col_map(&m[r], a.in + r * a.ld, a.rows / CS, a.cols, CS * a.ld, C::W,
+                                GH::BOX, GH::NB))
+            return cudaErrorNotSupported;
+    for (int r = CS; r < 4; r++)
+        m[r] = m[0];
+    if (!encode_h16_col_map(&om, a.out, a.rows, a.cols, a.ld, C::W, GH::BOX, GC::OUT_BOX_Z))
+        return cudaErrorNotSupported;
+    auto k = col_group_kernel<C, CL, true>;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(C::T);
+    cfg.dynamicSmemBytes = GH::SMEM_BYTES;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    static DeviceCache groups;
+    const int d = device_current();
+    if (!groups.get(d)) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             GH::SMEM_BYTES);
+        if (e != cudaSuccess)
+            return e;
+        cfg.gridDim = dim3((unsigned)(CS * (device_sm_count() / CS)));
+        int n = 0;
+        e = cudaOccupancyMaxActiveClusters(&n, k, &cfg);
+        if (e != cudaSuccess)
+            return e;
+        groups.set(d, n > 0 ? n : 1);
+    }
+    const int ntiles = a.cols / C::W;
+    const int ng = groups.get(d) < ntiles ? groups.get(d) : ntiles;
+    cfg.gridDim = dim3((unsigned)(CS * ng));
+    return cudaLaunchKernelEx(&cfg, k, m[0], m[1], m[2], m[3], om, a.tw, a.cols, a.scale, a.err,
+                              0, GroupIO{a.in_exp, a.out_exp});
+}
+
 template <int L>
 cudaError_t h16_dispatch(bool row, const H16PassArgs &a, cudaStream_t s)
 {
@@ -113,6 +170,11 @@ cudaError_t h16_dispatch(bool row, const H16PassArgs &a, cudaStream_t s)
     using C = LineCfg<L, col_kw(L), 0>;
     if constexpr (L == 12) {
         const cudaError_t e = h16_launch_col_tma<L>(a, s);
+        if (e != cudaErrorNotSupported)
+            return e;
+    }
+    if constexpr (L == 13 || L == 14) {
+        const cudaError_t e = h16_launch_col_group<L - 12>(a, s);
         if (e != cudaErrorNotSupported)
             return e;
     }

@@ -295,13 +295,15 @@ def test_unaligned_buffers_take_the_plain_path(env):
         fft.fft2d_destroy(plan)
 
 
-@pytest.mark.parametrize("rows,variant", [(4096, "tma32"), (4096, "tmem"), (8192, "pair")])
+@pytest.mark.parametrize("rows,variant", [(4096, "tma32"), (4096, "tmem"), (8192, "pair"),
+                                          (16384, "quad")])
 def test_withheld_tma_load_times_out_cleanly(env, rows, variant):
     """Failure path of the persistent TMA-fed column kernels: CTA 0 never
     issues one TMA load of its first tile, its bounded wait gives up, the
     kernel (for the CTA pair: both CTAs, agreeing at their cluster barrier)
     leaves cleanly, the host reads FFT2D_ERR_TIMEOUT, and the same plan then
-    transforms correctly."""
+    transforms correctly.  For the CTA pair and the four-CTA cluster every CTA
+    learns of the loss at the tile's first cluster barrier and leaves."""
     torch, fft, orc = env
     cols = 256
     plan = fft.fft2d_plan(rows, cols, fft.FFT2D_C64, fft.FFT2D_FORWARD)
