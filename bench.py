@@ -43,14 +43,20 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--requests", type=int, default=20000, help="serving workload: requests")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving workload: mean req/s")
-    ap.add_argument("--workload", choices=["fft4096", "batched", "fp16", "serve", "dct", "sizes"],
+    ap.add_argument("--workload", choices=["fft4096", "batched", "fp16", "serve", "dct", "sizes",
+                                           "passes"],
                     default="fft4096",
                     help="fft4096: the 4096x4096 forward+inverse benchmark (default); "
                          "batched: 64 uneven images through the grouped executor; "
                          "fp16: half2 storage vs complex64 at 8192^2 and 16384^2; "
                          "serve: Poisson stream of mixed requests through fft2d_serve_*; "
                          "dct: real 2D DCT-II at 4096^2 and 8192^2 beside the complex FFT; "
-                         "sizes: forward+inverse at the paper's Table 1 image sizes")
+                         "sizes: forward+inverse at the paper's Table 1 image sizes; "
+                         "passes: the default row and column kernels of one --shape image "
+                         "(--dtype c64 or h16), timed one pass at a time (for profiling)")
+    ap.add_argument("--shape", default="16384x512", help="passes workload: RxC")
+    ap.add_argument("--dtype", choices=["c64", "h16"], default="c64",
+                    help="passes workload: complex64 or half2 storage")
     ap.add_argument("--images", type=int, default=8, help="resident images per rank")
     ap.add_argument("--rounds", type=int, default=32,
                     help="one step = this many rounds of forward + inverse of every resident "
@@ -1196,6 +1202,53 @@ def run_sizes(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------- single passes
+def run_passes(args):
+    """The plan's default kernels on one --shape image (re, im ~ U[-1, 1)):
+    complex64 row and column passes timed separately, or the half2
+    transform (both passes) -- a small, fixed launch sequence for profiling
+    one kernel.  Two input/output pairs alternate."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1505_08019_gb300 as fft
+    import synth
+    R, _, C = args.shape.partition("x")
+    R, C = int(R), int(C or R)
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    t = cuda_timer(torch, stream)
+    x = synth.uniform_complex(R, C, seed=R + C)
+    reps = max(1, args.steps)
+    peak, _ = measured_hbm_peak()
+    out = {}
+    if args.dtype == "c64":
+        p = fft.fft2d_plan(R, C, fft.FFT2D_C64, fft.FFT2D_FORWARD)
+        dx = [torch.from_numpy(x).cuda() for _ in range(2)]
+        dy = [torch.empty_like(dx[0]) for _ in range(2)]
+        for name, ps in (("rows", fft.FFT2D_PASS_ROWS), ("cols", fft.FFT2D_PASS_COLS)):
+            ms = t(lambda i: fft.fft2d_exec_pass(p, ps, dx[i & 1], dy[i & 1], sptr), reps)
+            out[name] = {"ms": ms, "hbm_frac": 16.0 * R * C / (ms * 1e-3) / 1e9 / peak}
+        out["kernels"] = fft.fft2d_plan_describe(p)
+        fft.fft2d_sync_status(p)
+        fft.fft2d_destroy(p)
+    else:
+        p = fft.fft2d_plan(R, C, fft.FFT2D_C32H, fft.FFT2D_FORWARD)
+        q, e = h16_quantise_rows(x)
+        dq = [torch.from_numpy(q).cuda() for _ in range(2)]
+        de = torch.from_numpy(e).cuda()
+        do = [torch.empty_like(dq[0]) for _ in range(2)]
+        oe = torch.empty(C, dtype=torch.int32, device="cuda")
+        ms = t(lambda i: fft.fft2d_exec_h16(p, dq[i & 1], de, fft.FFT2D_PASS_ROWS, do[i & 1], oe,
+                                            sptr), reps)
+        out["both"] = {"ms": ms, "hbm_frac": 16.0 * R * C / (ms * 1e-3) / 1e9 / peak}
+        fft.fft2d_sync_status(p)
+        fft.fft2d_destroy(p)
+    print(json.dumps({"workload": "passes", "shape": [R, C], "dtype": args.dtype,
+                      "reps": reps, "passes": out}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1210,6 +1263,8 @@ def main():
         run_dct(args)
     elif args.workload == "sizes":
         run_sizes(args)
+    elif args.workload == "passes":
+        run_passes(args)
     else:
         run_ours(args)
 
