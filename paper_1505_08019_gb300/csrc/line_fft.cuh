@@ -142,11 +142,29 @@ __device__ __forceinline__ void butterfly_w(float2 &x0, float2 &x1, float2 w)
 }
 
 // Stages S0+1 .. S0+G on unit v of a[]: pairs (r, r + 2^t) at stage S0+1+t use
-// W_{2^s}^j with j = lo + (r mod 2^t) 2^S0.
+// W_{2^s}^j with j = lo + m 2^S0, m = r mod 2^t.
+//
+// Half of each stage's rotation factors come from the other half: for
+// m >= 2^(t-1), j = j0 + 2^(s-2) with j0 = lo + (m - 2^(t-1)) 2^S0, and
+// W_{2^s}^{j0 + 2^(s-2)} = W_4^1 W_{2^s}^{j0} -- a quarter turn, -i forward
+// and +i inverse, exact in floating point (a swap and a sign).  The plan's
+// tables hold the same values bit for bit (they are built with exact
+// quarter-turn symmetry), so a unit loads 2^(t-1) factors instead of 2^t
+// and the results do not change.  The turn's sign p = -Im W_4^1 (+1 forward,
+// -1 inverse) is read once from the stage-2 entry of the table; adding 0
+// turns the -0 of p * 0 into the table's +0.
+__device__ __forceinline__ float2 quarter_turn(float2 w, float p)
+{
+    return make_float2(__fmaf_rn(p, w.y, 0.0f), __fmaf_rn(-p, w.x, 0.0f));
+}
+
 template <class Gp, bool FIRST, bool GENERIC, bool TWS = false, int NA>
 __device__ __forceinline__ void run_stages_g(float2 (&a)[NA], int v, int lo,
                                              const float2 *__restrict__ tw, int nst)
 {
+    float p = 0.f;
+    if constexpr (Gp::G >= 2)
+        p = -ld_tw<TWS>(tw + 2).y;
 #pragma unroll
     for (int t = 0; t < Gp::G; t++) {
         const int s = Gp::S0 + 1 + t;
@@ -157,15 +175,20 @@ __device__ __forceinline__ void run_stages_g(float2 (&a)[NA], int v, int lo,
         for (int r = 0; r < Gp::R; r++) {
             if (r & (1 << t))
                 continue;
-            const int jc = (r & ((1 << t) - 1)) << Gp::S0;
+            const int m = r & ((1 << t) - 1);
             float2 &x0 = a[v * Gp::R + r];
             float2 &x1 = a[v * Gp::R + (r | (1 << t))];
-            if (FIRST && jc == 0) {   // W = 1
-                const float2 m = x1;
-                x1 = make_float2(__fsub_rn(x0.x, m.x), __fsub_rn(x0.y, m.y));
-                x0 = make_float2(__fadd_rn(x0.x, m.x), __fadd_rn(x0.y, m.y));
+            if (FIRST && m == 0) {   // W = 1
+                const float2 d = x1;
+                x1 = make_float2(__fsub_rn(x0.x, d.x), __fsub_rn(x0.y, d.y));
+                x0 = make_float2(__fadd_rn(x0.x, d.x), __fadd_rn(x0.y, d.y));
+            } else if (t >= 1 && m >= (1 << (t - 1))) {   // a quarter turn of a lower entry
+                const int m0 = m - (1 << (t - 1));
+                const float2 w0 = (FIRST && m0 == 0) ? make_float2(1.0f, 0.0f)
+                                                     : ld_tw<TWS>(tws + lo + (m0 << Gp::S0));
+                butterfly_w(x0, x1, quarter_turn(w0, p));
             } else {
-                butterfly_w(x0, x1, ld_tw<TWS>(tws + lo + jc));
+                butterfly_w(x0, x1, ld_tw<TWS>(tws + lo + (m << Gp::S0)));
             }
         }
     }

@@ -104,3 +104,23 @@ def test_no_gpu_plan_fails_cleanly(fft):
     st = fft.lib.fft2d_plan(8, 8, 0, -1, ctypes.byref(h))
     assert st == fft.FFT2D_ERR_CUDA
     assert h.value is None
+
+
+def test_stage_tables_have_exact_quarter_turn_symmetry(fft):
+    """The stage engine reads only the first quarter of each stage's rotation
+    factors and rotates them by W_4^1 (-i forward, +i inverse) for the second
+    quarter; that equals the table bit for bit only if the plan's FP64 -> FP32
+    tables hold W^{j + M/4} = W_4^1 W^j exactly, which this checks for every
+    axis length and both directions."""
+    for L in range(2, 15):
+        for d in (fft.FFT2D_FORWARD, fft.FFT2D_INVERSE):
+            t = fft.fft2d_stage_table(L, d).view(np.float32).reshape(-1, 2)
+            p = np.float32(-t[2, 1])                       # -Im W_4^1
+            assert p == (1.0 if d == fft.FFT2D_FORWARD else -1.0)
+            for s in range(2, L + 1):
+                M = 1 << s
+                off, q = M // 2 - 1, M // 4
+                w, w2 = t[off:off + q], t[off + q:off + 2 * q]
+                turned = np.stack([p * w[:, 1] + np.float32(0), -p * w[:, 0] + np.float32(0)],
+                                  axis=1).astype(np.float32)
+                assert np.array_equal(turned.view(np.uint32), w2.view(np.uint32)), (L, d, s)
