@@ -118,6 +118,27 @@ def test_h16_forward_matches_oracle(env, shape):
     assert err <= TOL_H16
 
 
+@pytest.mark.parametrize("shape,direction", [((8192, 256), -1), ((8192, 256), 1),
+                                             ((16384, 64), -1), ((16384, 64), 1),
+                                             ((4096, 1024), 1)],
+                         ids=lambda p: str(p))
+def test_h16_cluster_and_tma_column_kernels_both_directions(env, shape, direction):
+    """The half2 column kernels of 4096, 8192 and 16384 rows (one CTA, a CTA
+    pair, four CTAs) in both directions, on narrow images: the inverse
+    carries the 1/(rows cols) scale into the exponent choice."""
+    torch, fft, orc = env
+    R, C = shape
+    x = synth.uniform_complex(R, C, seed=R + C + direction)
+    q, e = quantise_rows(x)
+    xin = dequantise(q, e, 0)
+    out, oe = h16_fft(env, q, e, fft.FFT2D_PASS_ROWS, direction)
+    check_column_format(out, oe)
+    want = orc.fft2d(xin, inverse=(direction == 1), threads=16)
+    err = rel(dequantise(out, oe, 1), want)
+    print(f"[h16] {R}x{C} dir={direction} rel_l2={err:.3e}")
+    assert err <= TOL_H16
+
+
 def test_h16_round_trip(env):
     torch, fft, orc = env
     R, C = 1024, 2048

@@ -96,6 +96,19 @@ SHAPES = [(1, 1), (1, 2), (2, 1), (2, 2), (4, 8), (8, 4), (16, 16), (32, 64), (6
           (16, 16384), (16384, 16), (1, 4096), (4096, 1), (2, 16384), (16384, 2)]
 
 
+@pytest.mark.parametrize("shape", [(8192, 128), (16384, 64)], ids=lambda s: f"{s[0]}x{s[1]}")
+def test_cluster_column_kernels_in_place(env, shape):
+    """The CTA-pair and four-CTA column kernels with in == out, both
+    directions (each CTA's output ranges are other CTAs' input rows)."""
+    _, _, orc = env
+    R, C = shape
+    x = synth.uniform_complex(R, C, seed=R - C)
+    for d, inv in ((-1, False), (1, True)):
+        err = rel(gpu_fft(env, x, d, inplace=True), orc.fft2d(x, inverse=inv, threads=16))
+        report(f"{R}x{C} in place {'inv' if inv else 'fwd'}", err)
+        assert err <= TOL
+
+
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"{s[0]}x{s[1]}")
 def test_shapes_both_directions(env, shape):
     _, _, orc = env
