@@ -84,13 +84,15 @@ def test_dct_small_shapes(env, rows, cols):
 
 @pytest.mark.parametrize("rows,cols", [(64, 256), (256, 64), (2, 1024), (1024, 2),
                                        (512, 512), (128, 2048), (1024, 1024),
-                                       (2048, 64), (4096, 32), (2048, 8), (4096, 4)])
+                                       (2048, 64), (4096, 32), (2048, 8), (4096, 4),
+                                       (8192, 16), (8192, 4)])
 def test_dct_whole_outputs(env, rows, cols):
     """Non-square and wide/tall images spanning several CTAs and a partly
     filled last CTA (2 rows: one complex line), whole outputs compared.
     Columns of 2048 and 4096 rows run on the TMA-fed column kernel when the
     image is at least two tiles wide (64 and 32 columns here) and on the
-    plain kernel otherwise (8 and 4 columns)."""
+    plain kernel otherwise (8 and 4 columns); columns of 8192 rows on the
+    CTA-pair kernel (16 columns: two tiles) or the plain kernel (4)."""
     _, _, orc = env
     x = synth.gray_real(rows, cols, seed=7)
     err = rel(gpu_dct(env, x), orc.dct2d(x))
@@ -294,11 +296,12 @@ def test_dct_round_trip(env, rows, cols):
     assert err <= TOL, err
 
 
-@pytest.mark.parametrize("rows,inverse", [(4096, False), (2048, True)])
+@pytest.mark.parametrize("rows,inverse", [(4096, False), (2048, True), (8192, False)])
 def test_dct_withheld_load_times_out_cleanly(env, rows, inverse):
     """Failure path of the TMA-fed DCT column kernels: CTA 0 never issues the
     second load of its first tile, its bounded wait gives up, the host reads
-    FFT2D_ERR_TIMEOUT, and the same plan then transforms correctly."""
+    FFT2D_ERR_TIMEOUT, and the same plan then transforms correctly (8192
+    rows: the CTA-pair kernel, both CTAs leave together)."""
     torch, fft, orc = env
     cols = 64
     plan = fft.fft2d_plan(rows, cols, fft.FFT2D_R32_DCT2,
