@@ -1587,6 +1587,302 @@ __global__ void __launch_bounds__(C::T, 1) col_idct_tma_kernel(
         bulk_wait_all();
 }
 
+// ---------------------------------------------------------------------------
+// Inverse DCT column pass for columns of 2^(L+1) points over a CTA pair.
+// CTA b runs the DIT half of the inverse DFT whose inputs are the spectrum
+// positions k = 2m + b (the rows of parity b, one tensor map with twice the
+// row pitch).  The pre-rotation pairs k with N - k, which has the same
+// parity, so it stays inside the CTA: in local positions m pairs with
+// 2^L - m for b = 0 (m = 0 alone, m = 2^(L-1) with itself) and with
+// 2^L - 1 - m for b = 1.  A thread takes the group-0 units h and, for b = 0,
+// 2^HB - h (unit 0 with 2^(HB-1), both paired within themselves) or, for
+// b = 1, 2^HB - 1 - h.  After stages 1..L and the exchange round of stage
+// L+1, CTA b holds v[n] and v[n + 2^L] for n in [b 2^(L-1), (b+1) 2^(L-1));
+// x[2n] = v[n] and x[2n'+1] = v[N-1-n'] are two contiguous ranges of the
+// even and the odd output rows, each staged and stored with one TMA store.
+template <class C>
+__global__ void __launch_bounds__(C::T, 1) col_idct_pair_kernel(
+    const __grid_constant__ CUtensorMap m0, const __grid_constant__ CUtensorMap m1,
+    const __grid_constant__ CUtensorMap oe, const __grid_constant__ CUtensorMap oo, int ntiles,
+    const float2 *__restrict__ tw, const float2 *__restrict__ post, float scale, int *err,
+    int withhold)
+{
+    namespace cg = cooperative_groups;
+    using S = TmaSplit<C>;
+    using GC = GroupCol<C, 1>;
+    using G0 = Grp<C, 0>;
+    using Gl = Grp<C, C::NG - 1>;
+    constexpr int N = 2 * C::N;
+    constexpr int R = G0::R, HH = 1 << (G0::HB - 1);
+    static_assert(G0::V == 2 && (C::T >> C::KW) == HH, "threads cover half the group-0 units");
+    extern __shared__ __align__(1024) float2 sm[];
+    __shared__ __align__(8) uint64_t bar_early, bar_late, bar_recv;
+    __shared__ int lost_flag[2];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int b = (int)cluster.block_rank();
+    const int tid = threadIdx.x;
+    const int nclusters = (int)gridDim.x / 2;
+    const CUtensorMap *lmap = b == 0 ? &m0 : &m1;
+    float2 *stw = sm + S::TW_OFF;
+    float2 *recvb = sm;
+    float2 *sendb = sm + C::E / 2;
+    const uint32_t peer_recv = mapa_shared(smem_addr(recvb), (uint32_t)(b ^ 1));
+    const uint32_t peer_bar = mapa_shared(smem_addr(&bar_recv), (uint32_t)(b ^ 1));
+    const int w = tid & (C::W - 1);
+    const int h = tid >> C::KW;
+    const int h1 = b == 0 ? (h == 0 ? HH : 2 * HH - h) : 2 * HH - 1 - h;
+    int lost_recv = 0;
+    int tile = (int)blockIdx.x / 2;
+    if (tid == 0) {
+        mbar_init(&bar_early, 1);
+        mbar_init(&bar_late, 1);
+        mbar_init(&bar_recv, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    int n_early = 0, n_late = 0, w_early = 0, w_late = 0;
+    if (tile < ntiles) {
+        if (tid == 0) {
+            mbar_expect_tx(&bar_early, S::TW_BYTES);
+            bulk_load(stw, tw, S::TW_BYTES, &bar_early);
+            split_issue_early<C>(sm, lmap, tile * C::W, &bar_early);
+            if (!(withhold && blockIdx.x == 0))   // self-test: the first late half never comes
+                split_issue_late<C>(sm, lmap, tile * C::W, &bar_late);
+        }
+        n_early = n_late = 1;
+    }
+    bool lost = false;
+    int w_recv = 0;
+    float2 a[C::EPT];
+    for (; tile < ntiles; tile += nclusters) {
+        const int next = tile + nclusters;
+        const bool ok = mbar_wait_bounded(&bar_early, (uint32_t)(w_early & 1)) &&
+                        mbar_wait_bounded(&bar_late, (uint32_t)(w_late & 1));
+        const int lost_here = __syncthreads_or((ok ? 0 : 1) | lost_recv);
+        if (tid == 0) {
+            if (!lost_recv)
+                mbar_arrive_expect_tx(&bar_recv, GC::XBYTES);
+            lost_flag[b] = lost_here;
+            *cluster.map_shared_rank(lost_flag + b, b ^ 1) = lost_here;
+        }
+        if (!lost_here) {
+            w_early++;
+            w_late++;
+#pragma unroll
+            for (int v = 0; v < 2; v++) {
+                const int hib = v ? h1 : h;
+#pragma unroll
+                for (int r = 0; r < R; r++) {
+                    const int top = brev_c(r, G0::G) << G0::HB;   // compile-time
+                    const int kb = top / S::BOX;
+                    const float2 *bx = kb < S::NB ? sm + C::E + kb * S::BOX_VALS
+                                                  : sm + (kb - S::NB) * S::BOX_VALS;
+                    a[v * R + r] = bx[((top % S::BOX) | hib) * C::W + w];
+                }
+            }
+            // pre-rotation of the pairs (k, N - k), k = 2 (local position) + b
+            float2 yk, yp;
+            if (b == 1 || h != 0) {
+#pragma unroll
+                for (int r = 0; r < R; r++) {
+                    const int rc = r ^ (R - 1);
+                    if (brev_c(r, G0::G) < R / 2) {
+                        const int ks = 2 * ((brev_c(r, G0::G) << G0::HB) + h) + b;
+                        idct_pre(a[r], a[R + rc], __ldg(post + ks), yk, yp);
+                        a[r] = yk;
+                        a[R + rc] = yp;
+                    } else {
+                        const int ks = 2 * ((brev_c(rc, G0::G) << G0::HB) + h1) + b;
+                        idct_pre(a[R + rc], a[r], __ldg(post + ks), yk, yp);
+                        a[R + rc] = yk;
+                        a[r] = yp;
+                    }
+                }
+            } else {
+                // b = 0, h = 0: unit 0 (positions brev(r) 2^HB) pairs b' with
+                // R - b' (k = 0 alone, k = N/2 with itself); unit HH pairs r
+                // with r ^ (R - 1)
+#pragma unroll
+                for (int bb = 1; bb < R / 2; bb++) {
+                    const int r = brev_c(bb, G0::G), r2 = brev_c(R - bb, G0::G);
+                    idct_pre(a[r], a[r2], __ldg(post + 2 * (bb << G0::HB)), yk, yp);
+                    a[r] = yk;
+                    a[r2] = yp;
+                }
+                constexpr int r8 = brev_c(R / 2, G0::G);
+                idct_pre(a[r8], a[r8], __ldg(post + N / 2), yk, yp);
+                a[r8] = yk;
+#pragma unroll
+                for (int r = 0; r < R; r++) {
+                    if (brev_c(r, G0::G) >= R / 2)
+                        continue;
+                    const int rc = r ^ (R - 1);
+                    idct_pre(a[R + r], a[R + rc],
+                             __ldg(post + 2 * ((brev_c(r, G0::G) << G0::HB) + HH)), yk, yp);
+                    a[R + r] = yk;
+                    a[R + rc] = yp;
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < 2; v++)
+                run_stages<C, 0, false, true>(a, v, 0, stw, C::L);
+            fence_proxy_async_smem();
+            if (tid == 0)
+                bulk_wait_read_all();   // the previous tile's stores have read the staging
+            __syncthreads();
+            if (tid == 0 && next < ntiles)
+                split_issue_early<C>(sm, lmap, next * C::W, &bar_early);
+            if (next < ntiles)
+                n_early++;
+#pragma unroll
+            for (int v = 0; v < 2; v++) {
+                const int hi = brev_rt(v ? h1 : h, G0::HB);
+#pragma unroll
+                for (int r = 0; r < R; r++)
+                    sm[sidx<C>(0, r | (hi << G0::G), w)] = a[v * R + r];
+            }
+            __syncthreads();
+            group_smem<C, 1, false, false, true>(a, sm, stw, C::L);
+            __syncthreads();
+            group_last_read<C>(a, sm);
+            __syncthreads();   // the tile region is free
+        }
+        cluster_arrive_release();   // A0
+        float2 wk[16];
+        if (!lost_here) {
+#pragma unroll
+            for (int v = 0; v < Gl::V; v++) {
+                const int u = tid + v * C::T;
+                const int lo = (u >> C::KW) & ((1 << Gl::S0) - 1);
+                run_stages<C, C::NG - 1, false, true>(a, v, lo, stw, C::L);
+            }
+            group_round_send<C, 0>(a, sendb, b);
+            fence_proxy_async_smem();
+        }
+        __syncthreads();
+        group_round_twiddles<C, 0>(wk, tw, b * (Gl::R / 2));
+        cluster_wait_acquire();
+        if (lost_flag[0] | lost_flag[1]) {
+            lost = true;
+            break;
+        }
+        if (tid == 0)
+            bulk_copy_to_peer(peer_recv, sendb, GC::XBYTES, peer_bar);
+        lost_recv = mbar_wait_bounded(&bar_recv, (uint32_t)(w_recv & 1)) ? 0 : 1;
+        if (!lost_recv)
+            w_recv++;
+        cluster_arrive_release();   // B0: the partner's send buffer has been read
+        // stage L+1: a[t 16 + v 8 + i] = v[n + 2^L t], n = lo_v + 2^S0 (8b + i)
+        group_round_compute<C, 0>(a, recvb, wk, b);
+        fence_proxy_async_smem();
+        __syncthreads();   // the receive buffer has been read
+        if (tid == 0 && next < ntiles)
+            split_issue_late<C>(sm, lmap, next * C::W, &bar_late);
+        if (next < ntiles)
+            n_late++;
+        cluster_wait_acquire();   // B0: this CTA's send buffer is free for staging
+        // x[2n] = v[n]: even rows n in [b 2^(L-1), ...), one store; then
+        // x[2j+1] = v[N-1-j] = v[n + 2^L] for j = 2^L - 1 - n: odd rows
+        // j in [2^(L-1) (1 - b), ...), staged in reverse
+#pragma unroll
+        for (int t = 0; t < 2; t++) {
+            if (t == 1) {
+                if (tid == 0)
+                    bulk_wait_read_all();
+                __syncthreads();
+            }
+#pragma unroll
+            for (int v = 0; v < Gl::V; v++) {
+                const int lo = ((tid + v * C::T) >> C::KW) & ((1 << Gl::S0) - 1);
+#pragma unroll
+                for (int i = 0; i < 8; i++) {
+                    const int off = (i << Gl::S0) | lo;   // n - b 2^(L-1)
+                    const int slot = t == 0 ? off : (C::N / 2 - 1) - off;
+                    const float2 x = a[t * 16 + v * 8 + i];
+                    sendb[slot * C::W + w] = make_float2(x.x * scale, x.y * scale);
+                }
+            }
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                if (t == 0)
+                    tma_store_3d(&oe, tile * C::W, 0, b * (C::N / 2 / S::BOX), sendb);
+                else
+                    tma_store_3d(&oo, tile * C::W, 0, (1 - b) * (C::N / 2 / S::BOX), sendb);
+                bulk_commit();
+            }
+        }
+    }
+
+    if (__syncthreads_or((lost || lost_recv) ? 1 : 0)) {
+        if (tid == 0)
+            atomicExch(err, kDevErrTmaTimeout);
+        if (n_early > w_early)
+            mbar_wait_bounded(&bar_early, (uint32_t)(w_early & 1));
+        if (n_late > w_late)
+            mbar_wait_bounded(&bar_late, (uint32_t)(w_late & 1));
+        if (lost_recv)
+            mbar_wait_bounded(&bar_recv, (uint32_t)(w_recv & 1));
+    }
+    if (tid == 0)
+        bulk_wait_all();
+}
+
+// The pair kernel for inverse DCT columns of 8192 points when the image
+// allows it; cudaErrorNotSupported otherwise.
+cudaError_t idct_col_pair_launch(const DctIO &d, const float2 *tw, const float2 *post,
+                                 float scale, int *err, int withhold, cudaStream_t s)
+{
+    using C = LineCfg<12, 2, 0, 32>;
+    using S = TmaSplit<C>;
+    using D = DctPair<C>;
+    const long long cc = d.cols / 2;
+    if (!err || d.rows != 2 * C::N || cc % C::W != 0 || (reinterpret_cast<uintptr_t>(d.in) & 15) ||
+        (reinterpret_cast<uintptr_t>(d.out) & 15) || (reinterpret_cast<uintptr_t>(tw) & 15) ||
+        (cc * 8) % 16 != 0 || !tensor_maps_available())
+        return cudaErrorNotSupported;
+    const float2 *in = reinterpret_cast<const float2 *>(d.in);
+    float2 *out = reinterpret_cast<float2 *>(d.out);
+    CUtensorMap lm[2], oe, oo;
+    for (int b = 0; b < 2; b++)
+        if (!encode_col_map(&lm[b], in + b * cc, C::N, (int)cc, 2 * cc, C::W, S::BOX, S::NB))
+            return cudaErrorNotSupported;
+    if (!encode_col_map(&oe, out, C::N, (int)cc, 2 * cc, C::W, S::BOX, D::NBH) ||
+        !encode_col_map(&oo, out + cc, C::N, (int)cc, 2 * cc, C::W, S::BOX, D::NBH))
+        return cudaErrorNotSupported;
+    auto k = col_idct_pair_kernel<C>;
+    constexpr int SMEM = S::SMEM_BYTES;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(C::T);
+    cfg.dynamicSmemBytes = SMEM;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    static DeviceCache pairs;
+    const int dev = device_current();
+    if (!pairs.get(dev)) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (e != cudaSuccess)
+            return e;
+        cfg.gridDim = dim3((unsigned)(2 * (device_sm_count() / 2)));
+        int n = 0;
+        e = cudaOccupancyMaxActiveClusters(&n, k, &cfg);
+        if (e != cudaSuccess)
+            return e;
+        pairs.set(dev, n > 0 ? n : 1);
+    }
+    const int ntiles = (int)(cc / C::W);
+    const int np = pairs.get(dev) < ntiles ? pairs.get(dev) : ntiles;
+    cfg.gridDim = dim3((unsigned)(2 * np));
+    return cudaLaunchKernelEx(&cfg, k, lm[0], lm[1], oe, oo, ntiles, tw, post, scale, err,
+                              withhold);
+}
+
 template <class C>
 cudaError_t idct_col_tma_launch(const DctIO &d, const float2 *tw, const float2 *post, float scale,
                                 int *err, int withhold, cudaStream_t s)
@@ -1636,8 +1932,8 @@ cudaError_t dct_dispatch(bool row, bool inverse, const DctIO &d, const float2 *t
                            : dct_col_tma_launch<LineCfg<L, col_kw(L), 0, 32>>(d, tw, post, scale,
                                                                                err, 1, s);
         if constexpr (L == 13)
-            if (!inverse)
-                return dct_col_pair_launch(d, tw, post, scale, err, 1, s);
+            return inverse ? idct_col_pair_launch(d, tw, post, scale, err, 1, s)
+                           : dct_col_pair_launch(d, tw, post, scale, err, 1, s);
         return cudaErrorNotSupported;
     }
     if (inverse) {
@@ -1650,6 +1946,11 @@ cudaError_t dct_dispatch(bool row, bool inverse, const DctIO &d, const float2 *t
         if constexpr (L == 11 || L == 12) {
             const cudaError_t e =
                 idct_col_tma_launch<LineCfg<L, col_kw(L), 0, 32>>(d, tw, post, scale, err, 0, s);
+            if (e != cudaErrorNotSupported)
+                return e;
+        }
+        if constexpr (L == 13) {
+            const cudaError_t e = idct_col_pair_launch(d, tw, post, scale, err, 0, s);
             if (e != cudaErrorNotSupported)
                 return e;
         }

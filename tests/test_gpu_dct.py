@@ -235,7 +235,8 @@ def test_idct_small_shapes(env, rows, cols):
 
 
 @pytest.mark.parametrize("rows,cols", [(64, 256), (256, 64), (2, 1024), (1024, 2),
-                                       (512, 512), (2048, 64), (4096, 32), (128, 2048)])
+                                       (512, 512), (2048, 64), (4096, 32), (128, 2048),
+                                       (8192, 16), (8192, 4)])
 def test_idct_whole_outputs(env, rows, cols):
     _, _, orc = env
     X = synth.gray_real(rows, cols, seed=9) - np.float32(0.5)
@@ -296,7 +297,8 @@ def test_dct_round_trip(env, rows, cols):
     assert err <= TOL, err
 
 
-@pytest.mark.parametrize("rows,inverse", [(4096, False), (2048, True), (8192, False)])
+@pytest.mark.parametrize("rows,inverse", [(4096, False), (2048, True), (8192, False),
+                                          (8192, True)])
 def test_dct_withheld_load_times_out_cleanly(env, rows, inverse):
     """Failure path of the TMA-fed DCT column kernels: CTA 0 never issues the
     second load of its first tile, its bounded wait gives up, the host reads
