@@ -201,8 +201,15 @@ FFT2D_API fft2d_status fft2d_plan_info(fft2d_plan_t plan, int *rows, int *cols, 
  * in and out are device pointers to rows*cols pixels; in == out is allowed
  * (in place).  Partial overlap of in and out is not allowed.  Two launches.
  * Once the plan has run on its device (the first launch of each kernel sets
- * its shared-memory limit), the call allocates nothing and may be captured
- * in a CUDA graph on `stream`.
+ * its shared-memory limit), the call may be captured in a CUDA graph on
+ * `stream`.  It makes no allocation then, except that the column pass of
+ * 8192 or 16384 rows takes a scratch block (about 20 MB) for the exchange
+ * between the CTAs of a cluster stream-ordered from the library's own
+ * device memory pool and returns it on `stream` after the launch
+ * (cudaMallocFromPoolAsync / cudaFreeAsync: no device synchronisation; the
+ * pool keeps its memory, so after the first calls no driver allocation
+ * happens; under capture the two become graph memory nodes).  Calls on
+ * different streams therefore never share scratch.
  */
 FFT2D_API fft2d_status fft2d_exec(fft2d_plan_t plan, const void *in, void *out, void *stream);
 

@@ -187,6 +187,63 @@ __device__ __forceinline__ void group_round_twiddles(float2 (&wk)[16],
     }
 }
 
+// The same two steps of round J with the exchanged values in global memory:
+// slot j of this thread at at(j), written and read through L2 only.
+template <class C, int J, class At>
+__device__ __forceinline__ void group_round_send_g(const float2 (&s)[32], At at, int bitj)
+{
+    using Gl = Grp<C, C::NG - 1>;
+    constexpr int NT = 1 << J;
+    constexpr int NK = Gl::R >> J;
+    constexpr int NH = NK / 2;
+#pragma unroll
+    for (int t = 0; t < NT; t++) {
+#pragma unroll
+        for (int v = 0; v < Gl::V; v++) {
+#pragma unroll
+            for (int ih = 0; ih < NH; ih++) {
+                const int j = (t * Gl::V + v) * NH + ih;
+                const float2 lo_half = s[t * 2 * NK + v * NK + ih];
+                const float2 hi_half = s[t * 2 * NK + v * NK + NH + ih];
+                __stcg(at(j), bitj == 0 ? hi_half : lo_half);
+            }
+        }
+    }
+}
+
+template <class C, int J, class At>
+__device__ __forceinline__ void group_round_compute_g(float2 (&s)[32], At at,
+                                                      const float2 (&wk)[16], int bitj)
+{
+    using Gl = Grp<C, C::NG - 1>;
+    constexpr int NT = 1 << J;
+    constexpr int NK = Gl::R >> J;
+    constexpr int NH = NK / 2;
+    float2 n[32];
+#pragma unroll
+    for (int t = 0; t < NT; t++) {
+#pragma unroll
+        for (int v = 0; v < Gl::V; v++) {
+#pragma unroll
+            for (int ih = 0; ih < NH; ih++) {
+                const int j = (t * Gl::V + v) * NH + ih;
+                const float2 lo_half = s[t * 2 * NK + v * NK + ih];
+                const float2 hi_half = s[t * 2 * NK + v * NK + NH + ih];
+                const float2 mine = bitj == 0 ? lo_half : hi_half;
+                const float2 theirs = __ldcg(at(j));
+                float2 x0 = bitj == 0 ? mine : theirs;
+                float2 x1 = bitj == 0 ? theirs : mine;
+                butterfly_w(x0, x1, wk[j]);
+                n[t * 2 * NH + v * NH + ih] = x0;
+                n[(t + NT) * 2 * NH + v * NH + ih] = x1;
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 32; i++)
+        s[i] = n[i];
+}
+
 // Shared-memory layout of the half2 group kernel (byte offsets): the FP32
 // tile / exchange region, the early half of the next half2 tile, the
 // rotation factors, the factors 2^e of this CTA's rows.
@@ -595,6 +652,221 @@ __global__ void __launch_bounds__(C::T, 1) col_group_kernel(const __grid_constan
     const int res = brev_rt(q, CL);
     const CUtensorMap *m = res == 0 ? &map0 : res == 1 ? &map1 : res == 2 ? &map2 : &map3;
     col_group_body<C, CL, H16>(m, &omap, cols / C::W, tw, scale, err, withhold, io);
+}
+
+// The same column pass with the exchange rounds through a scratch buffer in
+// global memory (resident in L2) instead of bulk copies between shared
+// memories.  Each round, every CTA writes the half it gives away into its
+// slot of the buffer (one contiguous 64 KB slot per CTA and round), the
+// cluster barrier (release / acquire at cluster scope) makes the writes
+// visible, and the partner reads them straight into registers.  Nothing of
+// the exchange lives in shared memory, so the tile region is free as soon
+// as the last group has read it: the next tile's second half is requested
+// then, and one cluster barrier per round suffices (against two with bulk
+// copies, which must wait until the receiving region is free and again
+// until the copy has left).  The output leaves through TMA stores from the
+// staging half of the tile region.
+//
+// Slots are reused safely with two per CTA: a slot is written again only
+// after a later cluster barrier, which every partner arrives at after its
+// reads of the slot (c = 1: the slot alternates per tile; c = 2: round j
+// uses slot j).  The "lost" flags alternate per tile for the same reason.
+// xbuf: 2 CS XVALS T values per cluster of the launch, cluster-major; it
+// belongs to this launch alone.
+template <class C, int CL>
+__device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const CUtensorMap *omap,
+                                                  int ntiles, const float2 *__restrict__ tw,
+                                                  float scale, int *err, int withhold,
+                                                  float2 *xbuf)
+{
+    namespace cg = cooperative_groups;
+    using S = TmaSplit<C>;
+    using GC = GroupCol<C, CL>;
+    using Gl = Grp<C, C::NG - 1>;
+    constexpr int CS = GC::CS;
+    constexpr int XV = GC::XVALS * C::T;   // values given away per CTA per round
+    extern __shared__ __align__(1024) float2 sm[];
+    __shared__ __align__(8) uint64_t bar_early, bar_late;
+    __shared__ int lost_flag[2][CS];       // [tile parity][slot p: written by CTA p]
+    cg::cluster_group cluster = cg::this_cluster();
+    const int q = (int)cluster.block_rank();
+    const int tid = threadIdx.x;
+    const int nclusters = (int)gridDim.x / CS;
+    const int cid = (int)blockIdx.x / CS;
+    float2 *stw = sm + S::TW_OFF;
+    float2 *stage = sm + C::E / 2;
+    float2 *xb = xbuf + (long long)cid * (2 * CS * XV) + tid;
+    int rk_end = 0;
+#pragma unroll
+    for (int j = 0; j < CL; j++)
+        rk_end += ((q >> j) & 1) * ((Gl::R >> j) / 2);
+    const int k_base = rk_end << Gl::S0;   // first row k of this CTA's output ranges
+    int tile = cid;
+
+    if (tid == 0) {
+        mbar_init(&bar_early, 1);
+        mbar_init(&bar_late, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    int n_early = 0, n_late = 0, w_early = 0, w_late = 0;
+    if (tile < ntiles) {
+        if (tid == 0) {
+            mbar_expect_tx(&bar_early, S::TW_BYTES);
+            bulk_load(stw, tw, S::TW_BYTES, &bar_early);
+            split_issue_early<C>(sm, lmap, tile * C::W, &bar_early);
+            // (self-test: CTA 0 withholds its first late boxes)
+            if (!(withhold && blockIdx.x == 0))
+                split_issue_late<C>(sm, lmap, tile * C::W, &bar_late);
+        }
+        n_early = n_late = 1;
+    }
+    bool lost = false;
+    float2 a[C::EPT];
+    for (int it = 0; tile < ntiles; tile += nclusters, it++) {
+        const int next = tile + nclusters;
+        const int par = it & 1;
+        const bool ok = mbar_wait_bounded(&bar_early, (uint32_t)(w_early & 1)) &&
+                        mbar_wait_bounded(&bar_late, (uint32_t)(w_late & 1));
+        const int lost_here = __syncthreads_or(ok ? 0 : 1);
+        if (tid == 0) {
+#pragma unroll
+            for (int p = 0; p < CS; p++)
+                *cluster.map_shared_rank(&lost_flag[par][q], p) = lost_here;
+        }
+        // round 0 slots: alternate per tile for a pair, slot 0 for four CTAs
+        float2 *x0 = xb + (CL == 1 ? par : 0) * (CS * XV);
+        if (!lost_here) {
+            w_early++;
+            w_late++;
+            group_first_split<C>(
+                a, sm, stw,
+                [&] {
+                    if (tid == 0)
+                        bulk_wait_read_all();   // the previous tile's stores have read it
+                },
+                [&] {
+                    if (tid == 0 && next < ntiles)
+                        split_issue_early<C>(sm, lmap, next * C::W, &bar_early);
+                });
+            if (next < ntiles)
+                n_early++;
+            __syncthreads();
+            group_smem<C, 1, false, false, true>(a, sm, stw, C::L);
+            __syncthreads();
+            group_last_read<C>(a, sm);
+            fence_proxy_async_smem();
+            __syncthreads();   // the tile region is free: the next tile's second half
+            if (tid == 0 && next < ntiles)
+                split_issue_late<C>(sm, lmap, next * C::W, &bar_late);
+            if (next < ntiles)
+                n_late++;
+#pragma unroll
+            for (int v = 0; v < Gl::V; v++) {
+                const int u = tid + v * C::T;
+                const int lo = (u >> C::KW) & ((1 << Gl::S0) - 1);
+                run_stages<C, C::NG - 1, false, true>(a, v, lo, stw, C::L);
+            }
+            float2 *mine = x0 + q * XV;
+            group_round_send_g<C, 0>(a, [&](int j) { return mine + j * C::T; }, q & 1);
+        }
+        // round 0 barrier: the flags and the values given away are visible
+        cluster_arrive_release();
+        float2 wk[16];
+        group_round_twiddles<C, 0>(wk, tw, (q & 1) * (Gl::R / 2));
+        cluster_wait_acquire();
+        {
+            int any = 0;
+#pragma unroll
+            for (int p = 0; p < CS; p++)
+                any |= lost_flag[par][p];
+            if (any) {
+                lost = true;
+                break;
+            }
+        }
+        {
+            const float2 *theirs = x0 + (q ^ 1) * XV;
+            group_round_compute_g<C, 0>(a, [&](int j) { return theirs + j * C::T; }, wk, q & 1);
+        }
+        if constexpr (CL == 2) {
+            const int rk1 = ((q & 1) * (Gl::R / 2)) + ((q >> 1) & 1) * (Gl::R / 4);
+            group_round_twiddles<C, 1>(wk, tw, rk1);
+            float2 *x1 = xb + CS * XV;
+            float2 *mine = x1 + q * XV;
+            group_round_send_g<C, 1>(a, [&](int j) { return mine + j * C::T; }, (q >> 1) & 1);
+            cluster_arrive_release();
+            cluster_wait_acquire();
+            const float2 *theirs = x1 + (q ^ 2) * XV;
+            group_round_compute_g<C, 1>(a, [&](int j) { return theirs + j * C::T; }, wk,
+                                        (q >> 1) & 1);
+        }
+        // outputs t = 0 .. CS-1: rows k_base + [0, OUT_ROWS) + 2^L t, STAGE_T
+        // ranges per fill of the staging half, each range one TMA store
+#pragma unroll
+        for (int f = 0; f < CS / GC::STAGE_T; f++) {
+            if (f > 0) {
+                if (tid == 0)
+                    bulk_wait_read_all();
+                __syncthreads();
+            }
+#pragma unroll
+            for (int ts = 0; ts < GC::STAGE_T; ts++) {
+                const int t = f * GC::STAGE_T + ts;
+#pragma unroll
+                for (int v = 0; v < Gl::V; v++) {
+                    const int u = tid + v * C::T;
+                    const int w = u & (C::W - 1);
+                    const int lo = (u >> C::KW) & ((1 << Gl::S0) - 1);
+#pragma unroll
+                    for (int i = 0; i < GC::KEEP_R; i++) {
+                        const float2 x = a[t * 2 * GC::KEEP_R + v * GC::KEEP_R + i];
+                        stage[(ts * GC::OUT_ROWS + ((i << Gl::S0) | lo)) * C::W + w] =
+                            make_float2(x.x * scale, x.y * scale);
+                    }
+                }
+            }
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+#pragma unroll
+                for (int ts = 0; ts < GC::STAGE_T; ts++) {
+                    const int t = f * GC::STAGE_T + ts;
+                    const int z = ((t << C::L) + k_base) / S::BOX;
+                    tma_store_3d(omap, tile * C::W, 0, z, stage + ts * GC::OUT_ROWS * C::W);
+                }
+                bulk_commit();
+            }
+        }
+    }
+
+    if (__syncthreads_or(lost ? 1 : 0)) {
+        if (tid == 0)
+            atomicExch(err, kDevErrTmaTimeout);
+        // let transfers still in flight land before the CTA leaves
+        if (n_early > w_early)
+            mbar_wait_bounded(&bar_early, (uint32_t)(w_early & 1));
+        if (n_late > w_late)
+            mbar_wait_bounded(&bar_late, (uint32_t)(w_late & 1));
+    }
+    if (tid == 0)
+        bulk_wait_all();   // shared memory stays valid until the stores are done
+}
+
+template <class C, int CL>
+__global__ void __launch_bounds__(C::T, 1) col_group_l2_kernel(const __grid_constant__ CUtensorMap map0,
+                                                               const __grid_constant__ CUtensorMap map1,
+                                                               const __grid_constant__ CUtensorMap map2,
+                                                               const __grid_constant__ CUtensorMap map3,
+                                                               const __grid_constant__ CUtensorMap omap,
+                                                               const float2 *__restrict__ tw,
+                                                               int cols, float scale, int *err,
+                                                               int withhold, float2 *xbuf)
+{
+    const int q = (int)cooperative_groups::this_cluster().block_rank();
+    const int res = brev_rt(q, CL);
+    const CUtensorMap *m = res == 0 ? &map0 : res == 1 ? &map1 : res == 2 ? &map2 : &map3;
+    col_group_l2_body<C, CL>(m, &omap, cols / C::W, tw, scale, err, withhold, xbuf);
 }
 
 }  // namespace fft2d

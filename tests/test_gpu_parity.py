@@ -109,6 +109,40 @@ def test_cluster_column_kernels_in_place(env, shape):
         assert err <= TOL
 
 
+@pytest.mark.parametrize("rows", [8192, 16384])
+def test_l2_exchange_column_pass_on_concurrent_streams(env, rows):
+    """The cluster column kernels that exchange through L2 take a scratch
+    block per launch: the column passes of four images issued together on
+    four streams with one plan give the same bits as one after another."""
+    torch, fft, _ = env
+    cols = 1024 if rows == 8192 else 512
+    plan = fft.fft2d_plan(rows, cols, fft.FFT2D_C64, fft.FFT2D_FORWARD)
+    try:
+        assert "l2" in fft.fft2d_plan_describe(plan)
+        dx = [torch.from_numpy(synth.uniform_complex(rows, cols, seed=rows + i)).cuda()
+              for i in range(4)]
+        want = []
+        for d in dx:
+            o = torch.empty_like(d)
+            fft.fft2d_exec_pass(plan, fft.FFT2D_PASS_COLS, d, o)
+            torch.cuda.synchronize()
+            want.append(o.cpu().numpy())
+        streams = [torch.cuda.Stream() for _ in range(4)]
+        outs = [torch.empty_like(d) for d in dx]
+        for _ in range(3):
+            for o in outs:
+                o.zero_()
+            torch.cuda.synchronize()
+            for st, d, o in zip(streams, dx, outs):
+                fft.fft2d_exec_pass(plan, fft.FFT2D_PASS_COLS, d, o, st.cuda_stream)
+            torch.cuda.synchronize()
+            for i, (o, w) in enumerate(zip(outs, want)):
+                assert np.array_equal(o.cpu().numpy(), w), f"image {i}"
+        fft.fft2d_sync_status(plan)
+    finally:
+        fft.fft2d_destroy(plan)
+
+
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"{s[0]}x{s[1]}")
 def test_shapes_both_directions(env, shape):
     _, _, orc = env
@@ -309,7 +343,7 @@ def test_unaligned_buffers_take_the_plain_path(env):
 
 
 @pytest.mark.parametrize("rows,variant", [(4096, "tma32"), (4096, "tmem"), (8192, "pair"),
-                                          (16384, "quad")])
+                                          (16384, "quad"), (8192, "pairl2"), (16384, "quadl2")])
 def test_withheld_tma_load_times_out_cleanly(env, rows, variant):
     """Failure path of the persistent TMA-fed column kernels: CTA 0 never
     issues one TMA load of its first tile, its bounded wait gives up, the
@@ -405,10 +439,12 @@ def test_table1_sizes_max_error(env, side, paper_err):
     assert max_err <= paper_err / 100
 
 
-@pytest.mark.parametrize("side", [256, 4096])
+@pytest.mark.parametrize("side", [256, 4096, 8192])
 def test_exec_in_a_cuda_graph(env, side):
     """Once a plan has run, fft2d_exec can be captured in a CUDA graph: the
-    replayed forward + inverse give the same bits as the direct calls."""
+    replayed forward + inverse give the same bits as the direct calls (at
+    8192^2 the column pass's stream-ordered scratch becomes graph memory
+    nodes)."""
     torch, fft, _ = env
     x = synth.uniform_complex(side, side, seed=side + 1)
     pf = fft.fft2d_plan(side, side, fft.FFT2D_C64, fft.FFT2D_FORWARD)
