@@ -656,23 +656,29 @@ __global__ void __launch_bounds__(C::T, 1) col_group_kernel(const __grid_constan
 
 // The same column pass with the exchange rounds through a scratch buffer in
 // global memory (resident in L2) instead of bulk copies between shared
-// memories.  Each round, every CTA writes the half it gives away into its
-// slot of the buffer (one contiguous 64 KB slot per CTA and round), the
-// cluster barrier (release / acquire at cluster scope) makes the writes
-// visible, and the partner reads them straight into registers.  Nothing of
-// the exchange lives in shared memory, so the tile region is free as soon
-// as the last group has read it: the next tile's second half is requested
-// then, and one cluster barrier per round suffices (against two with bulk
-// copies, which must wait until the receiving region is free and again
-// until the copy has left).  The output leaves through TMA stores from the
-// staging half of the tile region.
+// memories.  Every CTA writes the values it gives away into its slots of the
+// buffer (contiguous per thread index), the cluster barrier (release /
+// acquire at cluster scope) makes the writes visible, and the partners read
+// them straight into registers.  Nothing of the exchange lives in shared
+// memory, so the tile region is free as soon as the last group has read it:
+// the next tile's second half is requested then, and one cluster barrier per
+// exchange suffices (against two with bulk copies, which must wait until the
+// receiving region is free and again until the copy has left).  The output
+// leaves through TMA stores from the staging half of the tile region.
 //
-// Slots are reused safely with two per CTA: a slot is written again only
-// after a later cluster barrier, which every partner arrives at after its
-// reads of the slot (c = 1: the slot alternates per tile; c = 2: round j
-// uses slot j).  The "lost" flags alternate per tile for the same reason.
-// xbuf: 2 CS XVALS T values per cluster of the launch, cluster-major; it
-// belongs to this launch alone.
+// Four CTAs (c = 2) run both cross stages after a single exchange: CTA q
+// sends each partner p the values at p's final rows k (8 per thread) and
+// receives the three partners' values at its own, then runs stage L+1 on
+// the pairs of blocks (0, 1), (2, 3) and stage L+2 on (0, 2), (1, 3) in
+// registers -- the same butterflies on the same operands as two rounds of
+// pairwise swaps, with one barrier and 96 KB each way per CTA instead of two
+// and 128 KB.
+//
+// Slots alternate per tile: a slot is written again only after the next
+// tile's barrier, which every reader arrives at after its reads of the slot.
+// The "lost" flags alternate per tile for the same reason.  xbuf: per
+// cluster of the launch, 2 CS XVALS T values (pair) or 2 CS^2 2 KEEP_R T
+// (four CTAs), cluster-major; it belongs to this launch alone.
 template <class C, int CL>
 __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const CUtensorMap *omap,
                                                   int ntiles, const float2 *__restrict__ tw,
@@ -695,7 +701,12 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
     const int cid = (int)blockIdx.x / CS;
     float2 *stw = sm + S::TW_OFF;
     float2 *stage = sm + C::E / 2;
-    float2 *xb = xbuf + (long long)cid * (2 * CS * XV) + tid;
+    // four CTAs exchange once per tile (both cross stages, radix 4); slots
+    // [tile parity][source][destination][2 KEEP_R values][T]
+    constexpr bool R4 = CL == 2;
+    constexpr int R4V = 2 * GC::KEEP_R;                   // values per source and destination
+    constexpr long long XPER = R4 ? 2LL * CS * CS * R4V * C::T : 2LL * CS * XV;
+    float2 *xb = xbuf + (long long)cid * XPER + tid;
     int rk_end = 0;
 #pragma unroll
     for (int j = 0; j < CL; j++)
@@ -767,13 +778,44 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
                 const int lo = (u >> C::KW) & ((1 << Gl::S0) - 1);
                 run_stages<C, C::NG - 1, false, true>(a, v, lo, stw, C::L);
             }
-            float2 *mine = x0 + q * XV;
-            group_round_send_g<C, 0>(a, [&](int j) { return mine + j * C::T; }, q & 1);
+            if constexpr (R4) {
+                // value r of unit v goes to the CTA whose final rows hold k's
+                // top bits r: p = bit 3 of r | bit 2 of r << 1
+                float2 *src = xb + par * (CS * CS * R4V * C::T) + q * (CS * R4V * C::T);
+#pragma unroll
+                for (int v = 0; v < Gl::V; v++) {
+#pragma unroll
+                    for (int r = 0; r < Gl::R; r++) {
+                        const int p = ((r >> 3) & 1) | (((r >> 2) & 1) << 1);
+                        if (p != q)
+                            __stcg(src + (p * R4V + v * GC::KEEP_R + (r & 3)) * C::T,
+                                   a[v * Gl::R + r]);
+                    }
+                }
+            } else {
+                float2 *mine = x0 + q * XV;
+                group_round_send_g<C, 0>(a, [&](int j) { return mine + j * C::T; }, q & 1);
+            }
         }
         // round 0 barrier: the flags and the values given away are visible
         cluster_arrive_release();
         float2 wk[16];
-        group_round_twiddles<C, 0>(wk, tw, (q & 1) * (Gl::R / 2));
+        if constexpr (R4) {
+            // stage L+1 and L+2 factors of this CTA's 2 x KEEP_R rows k
+#pragma unroll
+            for (int v = 0; v < Gl::V; v++) {
+                const int u = tid + v * C::T;
+                const int lo = (u >> C::KW) & ((1 << Gl::S0) - 1);
+#pragma unroll
+                for (int i = 0; i < GC::KEEP_R; i++) {
+                    const int k = lo | ((rk_end + i) << Gl::S0);
+                    wk[v * GC::KEEP_R + i] = __ldg(tw + ((1 << C::L) - 1) + k);
+                    wk[R4V + v * GC::KEEP_R + i] = __ldg(tw + ((1 << (C::L + 1)) - 1) + k);
+                }
+            }
+        } else {
+            group_round_twiddles<C, 0>(wk, tw, (q & 1) * (Gl::R / 2));
+        }
         cluster_wait_acquire();
         {
             int any = 0;
@@ -785,21 +827,43 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
                 break;
             }
         }
-        {
+        if constexpr (R4) {
+            // Y_t (t = 0..3, the four CTAs' blocks) at this CTA's rows k:
+            // stage L+1 pairs (Y0, Y1) and (Y2, Y3) with W_{2^(L+1)}^k,
+            // stage L+2 pairs (Z0, Z2) with W_{2^(L+2)}^k and (Z1, Z3) with
+            // W_{2^(L+2)}^(k + 2^L), a quarter turn of it; outputs
+            // X_t = a[t * R4V + v * KEEP_R + i] at rows k + 2^L t
+            const float pq = -ld_tw<false>(tw + 2).y;
+            const float2 *base = xb + par * (CS * CS * R4V * C::T) + q * (R4V * C::T);
+            float2 y[4][R4V];
+#pragma unroll
+            for (int v = 0; v < Gl::V; v++) {
+#pragma unroll
+                for (int i = 0; i < GC::KEEP_R; i++) {
+                    const int jj = v * GC::KEEP_R + i;
+                    const float2 o0 = a[v * Gl::R + 0 + i], o1 = a[v * Gl::R + 8 + i];
+                    const float2 o2 = a[v * Gl::R + 4 + i], o3 = a[v * Gl::R + 12 + i];
+                    const float2 own = q == 0 ? o0 : q == 1 ? o1 : q == 2 ? o2 : o3;
+#pragma unroll
+                    for (int t = 0; t < CS; t++)
+                        y[t][jj] = t == q ? own : __ldcg(base + (t * CS * R4V + jj) * C::T);
+                }
+            }
+#pragma unroll
+            for (int jj = 0; jj < R4V; jj++) {
+                float2 z0 = y[0][jj], z1 = y[1][jj], z2 = y[2][jj], z3 = y[3][jj];
+                butterfly_w(z0, z1, wk[jj]);
+                butterfly_w(z2, z3, wk[jj]);
+                butterfly_w(z0, z2, wk[R4V + jj]);
+                butterfly_w(z1, z3, quarter_turn(wk[R4V + jj], pq));
+                a[0 * R4V + jj] = z0;
+                a[1 * R4V + jj] = z1;
+                a[2 * R4V + jj] = z2;
+                a[3 * R4V + jj] = z3;
+            }
+        } else {
             const float2 *theirs = x0 + (q ^ 1) * XV;
             group_round_compute_g<C, 0>(a, [&](int j) { return theirs + j * C::T; }, wk, q & 1);
-        }
-        if constexpr (CL == 2) {
-            const int rk1 = ((q & 1) * (Gl::R / 2)) + ((q >> 1) & 1) * (Gl::R / 4);
-            group_round_twiddles<C, 1>(wk, tw, rk1);
-            float2 *x1 = xb + CS * XV;
-            float2 *mine = x1 + q * XV;
-            group_round_send_g<C, 1>(a, [&](int j) { return mine + j * C::T; }, (q >> 1) & 1);
-            cluster_arrive_release();
-            cluster_wait_acquire();
-            const float2 *theirs = x1 + (q ^ 2) * XV;
-            group_round_compute_g<C, 1>(a, [&](int j) { return theirs + j * C::T; }, wk,
-                                        (q >> 1) & 1);
         }
         // outputs t = 0 .. CS-1: rows k_base + [0, OUT_ROWS) + 2^L t, STAGE_T
         // ranges per fill of the staging half, each range one TMA store

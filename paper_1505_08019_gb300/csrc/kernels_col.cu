@@ -361,7 +361,9 @@ cudaError_t col_launch_group_l2(const PassArgs &a, cudaStream_t s)
     const int ntiles = a.cols / C::W;
     const int ng = groups.get(d) < ntiles ? groups.get(d) : ntiles;
     void *xbuf = nullptr;
-    cudaError_t e = scratch_take(&xbuf, (size_t)ng * 2 * CS * GC::XVALS * C::T * sizeof(float2), s);
+    const size_t per = CL == 2 ? (size_t)2 * CS * CS * 2 * GC::KEEP_R * C::T
+                               : (size_t)2 * CS * GC::XVALS * C::T;
+    cudaError_t e = scratch_take(&xbuf, (size_t)ng * per * sizeof(float2), s);
     if (e != cudaSuccess)
         return e;
     cfg.gridDim = dim3((unsigned)(CS * ng));
@@ -458,7 +460,8 @@ struct ColVariants {
         if constexpr (L == 14)
             t.v[t.n++] = {"quad", PairLocal::W, 32, col_group_usable<PairLocal, 2>,
                           col_launch_group<PairLocal, 2>, true};
-        // the same with the exchange rounds through L2 (a scratch buffer)
+        // the same with the exchange through L2 (a scratch buffer); four
+        // CTAs in one radix-4 round
         if constexpr (L == 13)
             t.v[t.n++] = {"pairl2", PairLocal::W, 32, col_group_usable<PairLocal, 1>,
                           col_launch_group_l2<PairLocal, 1>, true};
