@@ -87,6 +87,10 @@ struct GroupCol {
     static constexpr int OUT_ROWS = NL / CS;              // rows k of one CTA's output range
     static constexpr int OUT_BOX_Z = OUT_ROWS / S::BOX;   // 256-row blocks of one range
     static constexpr int STAGE_T = (C::E / 2) / (OUT_ROWS * C::W);   // ranges per staging fill
+    // scratch of the L2 exchange per cluster (col_group_l2_kernel): two
+    // tiles' slots, CS XVALS T values (pair) or CS^2 2 KEEP_R T (four CTAs)
+    static constexpr long long L2_SCRATCH_VALS =
+        CL == 2 ? 2LL * CS * CS * 2 * KEEP_R * C::T : 2LL * CS * XVALS * C::T;
     static_assert(C::EPT == 32 && C::NG == 3 && C::LB == 1, "512 threads x 32 values, 3 groups");
     static_assert(CL >= 1 && CL <= 2, "two or four CTAs");
     static_assert(Gl::S0 + Gl::G == L && (NL >> Gl::S0) == Gl::R,
@@ -679,34 +683,57 @@ __global__ void __launch_bounds__(C::T, 1) col_group_kernel(const __grid_constan
 // The "lost" flags alternate per tile for the same reason.  xbuf: per
 // cluster of the launch, 2 CS XVALS T values (pair) or 2 CS^2 2 KEEP_R T
 // (four CTAs), cluster-major; it belongs to this launch alone.
-template <class C, int CL>
+template <class C, int CL, bool H16>
 __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const CUtensorMap *omap,
                                                   int ntiles, const float2 *__restrict__ tw,
                                                   float scale, int *err, int withhold,
-                                                  float2 *xbuf)
+                                                  float2 *xbuf, const GroupIO &io)
 {
     namespace cg = cooperative_groups;
     using S = TmaSplit<C>;
     using GC = GroupCol<C, CL>;
+    using GH = GroupH16<C>;
     using Gl = Grp<C, C::NG - 1>;
+    using G0 = Grp<C, 0>;
     constexpr int CS = GC::CS;
     constexpr int XV = GC::XVALS * C::T;   // values given away per CTA per round
     extern __shared__ __align__(1024) float2 sm[];
     __shared__ __align__(8) uint64_t bar_early, bar_late;
     __shared__ int lost_flag[2][CS];       // [tile parity][slot p: written by CTA p]
+    __shared__ int cmax[2][CS][C::W];      // half2: [tile parity][CTA p's partial column maxima]
+    __shared__ int cmax_local[C::W];
     cg::cluster_group cluster = cg::this_cluster();
     const int q = (int)cluster.block_rank();
     const int tid = threadIdx.x;
     const int nclusters = (int)gridDim.x / CS;
     const int cid = (int)blockIdx.x / CS;
-    float2 *stw = sm + S::TW_OFF;
+    unsigned char *smb = reinterpret_cast<unsigned char *>(sm);
+    float2 *stw = H16 ? reinterpret_cast<float2 *>(smb + GH::TW_OFF) : sm + S::TW_OFF;
+    float *rf = reinterpret_cast<float *>(smb + GH::RF_OFF);
+    const uint32_t tw_bytes = H16 ? (uint32_t)C::N * 8u : S::TW_BYTES;
     float2 *stage = sm + C::E / 2;
+    // the first and second half of a tile's TMA boxes
+    auto issue_early = [&](int t) {
+        if constexpr (H16) {
+            mbar_arrive_expect_tx(&bar_early, GH::HALF_BYTES);
+            tma_load_3d(smb + GH::PREF_OFF, lmap, t * C::W, 0, 0, &bar_early);
+        } else {
+            split_issue_early<C>(sm, lmap, t * C::W, &bar_early);
+        }
+    };
+    auto issue_late = [&](int t) {
+        if constexpr (H16) {
+            mbar_arrive_expect_tx(&bar_late, GH::HALF_BYTES);
+            tma_load_3d(smb, lmap, t * C::W, 0, GH::NB, &bar_late);
+        } else {
+            split_issue_late<C>(sm, lmap, t * C::W, &bar_late);
+        }
+    };
     // four CTAs exchange once per tile (both cross stages, radix 4); slots
     // [tile parity][source][destination][2 KEEP_R values][T]
     constexpr bool R4 = CL == 2;
     constexpr int R4V = 2 * GC::KEEP_R;                   // values per source and destination
-    constexpr long long XPER = R4 ? 2LL * CS * CS * R4V * C::T : 2LL * CS * XV;
-    float2 *xb = xbuf + (long long)cid * XPER + tid;
+    float2 *xb = xbuf + (long long)cid * GC::L2_SCRATCH_VALS + tid;
     int rk_end = 0;
 #pragma unroll
     for (int j = 0; j < CL; j++)
@@ -719,16 +746,24 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
         mbar_init(&bar_late, 1);
         fence_mbar_init();
     }
+    if constexpr (H16) {
+        // the factors of this CTA's rows CS m + rev_CL(q)
+        const int res = brev_rt(q, CL);
+        for (int i = tid; i < C::N; i += C::T)
+            rf[i] = pow2f(io.row_exp[(long long)i * CS + res]);
+        if (tid < C::W)
+            cmax_local[tid] = 0;
+    }
     __syncthreads();
     int n_early = 0, n_late = 0, w_early = 0, w_late = 0;
     if (tile < ntiles) {
         if (tid == 0) {
-            mbar_expect_tx(&bar_early, S::TW_BYTES);
-            bulk_load(stw, tw, S::TW_BYTES, &bar_early);
-            split_issue_early<C>(sm, lmap, tile * C::W, &bar_early);
+            mbar_expect_tx(&bar_early, tw_bytes);
+            bulk_load(stw, tw, tw_bytes, &bar_early);
+            issue_early(tile);
             // (self-test: CTA 0 withholds its first late boxes)
             if (!(withhold && blockIdx.x == 0))
-                split_issue_late<C>(sm, lmap, tile * C::W, &bar_late);
+                issue_late(tile);
         }
         n_early = n_late = 1;
     }
@@ -750,16 +785,59 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
         if (!lost_here) {
             w_early++;
             w_late++;
-            group_first_split<C>(
-                a, sm, stw,
-                [&] {
-                    if (tid == 0)
-                        bulk_wait_read_all();   // the previous tile's stores have read it
-                },
-                [&] {
-                    if (tid == 0 && next < ntiles)
-                        split_issue_early<C>(sm, lmap, next * C::W, &bar_early);
-                });
+            if constexpr (H16) {
+                // group 0: scrambled gather of the half2 tile, widened and
+                // scaled by the row factors
+                const __half2 *pref = reinterpret_cast<const __half2 *>(smb + GH::PREF_OFF);
+                const __half2 *late = reinterpret_cast<const __half2 *>(smb);
+#pragma unroll
+                for (int v = 0; v < G0::V; v++) {
+                    const int u = tid + v * C::T;
+                    const int w = u & (C::W - 1);
+                    const int hib = (u >> C::KW) & ((1 << G0::HB) - 1);
+#pragma unroll
+                    for (int r = 0; r < G0::R; r++) {
+                        const int top = brev_c(r, G0::G) << G0::HB;   // compile-time
+                        const int kb = top / GH::BOX;
+                        const int in_box = ((top % GH::BOX) | hib) * C::W + w;
+                        const __half2 *bx = kb < GH::NB ? pref + kb * GH::BOXV
+                                                        : late + (kb - GH::NB) * GH::BOXV;
+                        const float2 hv = __half22float2(bx[in_box]);
+                        const float f = rf[top | hib];
+                        a[v * G0::R + r] = make_float2(hv.x * f, hv.y * f);
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < G0::V; v++)
+                    run_stages<C, 0, false, true>(a, v, 0, stw, C::L);
+                fence_proxy_async_smem();
+                if (tid == 0)
+                    bulk_wait_read_all();   // the previous tile's stores have read it
+                __syncthreads();            // every slot of both input regions has been read
+                if (tid == 0 && next < ntiles)
+                    issue_early(next);
+#pragma unroll
+                for (int v = 0; v < G0::V; v++) {
+                    const int u = tid + v * C::T;
+                    const int w = u & (C::W - 1);
+                    const int hib = (u >> C::KW) & ((1 << G0::HB) - 1);
+                    const int hi = brev_rt(hib, G0::HB);
+#pragma unroll
+                    for (int r = 0; r < G0::R; r++)
+                        sm[sidx<C>(0, r | (hi << G0::G), w)] = a[v * G0::R + r];
+                }
+            } else {
+                group_first_split<C>(
+                    a, sm, stw,
+                    [&] {
+                        if (tid == 0)
+                            bulk_wait_read_all();   // the previous tile's stores have read it
+                    },
+                    [&] {
+                        if (tid == 0 && next < ntiles)
+                            issue_early(next);
+                    });
+            }
             if (next < ntiles)
                 n_early++;
             __syncthreads();
@@ -769,7 +847,7 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
             fence_proxy_async_smem();
             __syncthreads();   // the tile region is free: the next tile's second half
             if (tid == 0 && next < ntiles)
-                split_issue_late<C>(sm, lmap, next * C::W, &bar_late);
+                issue_late(next);
             if (next < ntiles)
                 n_late++;
 #pragma unroll
@@ -865,6 +943,64 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
             const float2 *theirs = x0 + (q ^ 1) * XV;
             group_round_compute_g<C, 0>(a, [&](int j) { return theirs + j * C::T; }, wk, q & 1);
         }
+        if constexpr (H16) {
+            // this CTA's part of each column's largest |component| (a
+            // thread's values all belong to column tid mod W) to every CTA of
+            // the cluster, one more cluster barrier, then every CTA picks the
+            // same exponent per column and stages all its ranges as half2
+            float m = 0.f;
+#pragma unroll
+            for (int i = 0; i < 32; i++)
+                m = fmaxf(m, fmaxf(fabsf(a[i].x), fabsf(a[i].y)));
+            m = warp_line_max<C::KW, 5>(m);
+            if ((tid & (31 & ~(C::W - 1))) == 0)
+                atomicMax(&cmax_local[tid & (C::W - 1)], __float_as_int(m * scale));
+            __syncthreads();
+            if (tid < C::W) {
+                const int mine = cmax_local[tid];
+                cmax_local[tid] = 0;
+#pragma unroll
+                for (int p = 0; p < CS; p++)
+                    *cluster.map_shared_rank(&cmax[par][q][tid], p) = mine;
+            }
+            cluster_arrive_release();
+            cluster_wait_acquire();
+            const int w = tid & (C::W - 1);
+            int mb = 0;
+#pragma unroll
+            for (int p = 0; p < CS; p++)
+                mb = max(mb, cmax[par][p][w]);
+            const int e = line_exponent(__int_as_float(mb));
+            const float f = scale * pow2f(-e);
+            __half2 *hst = reinterpret_cast<__half2 *>(stage);
+#pragma unroll
+            for (int t = 0; t < CS; t++) {
+#pragma unroll
+                for (int v = 0; v < Gl::V; v++) {
+                    const int u = tid + v * C::T;
+                    const int lo = (u >> C::KW) & ((1 << Gl::S0) - 1);
+#pragma unroll
+                    for (int i = 0; i < GC::KEEP_R; i++) {
+                        const float2 x = a[t * 2 * GC::KEEP_R + v * GC::KEEP_R + i];
+                        hst[(t * GC::OUT_ROWS + ((i << Gl::S0) | lo)) * C::W + w] =
+                            __floats2half2_rn(x.x * f, x.y * f);
+                    }
+                }
+            }
+            if (q == 0 && tid < C::W)
+                io.out_exp[tile * C::W + tid] = e;
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+#pragma unroll
+                for (int t = 0; t < CS; t++) {
+                    const int z = ((t << C::L) + k_base) / S::BOX;
+                    tma_store_3d(omap, tile * C::W, 0, z, hst + t * GC::OUT_ROWS * C::W);
+                }
+                bulk_commit();
+            }
+            continue;
+        }
         // outputs t = 0 .. CS-1: rows k_base + [0, OUT_ROWS) + 2^L t, STAGE_T
         // ranges per fill of the staging half, each range one TMA store
 #pragma unroll
@@ -917,7 +1053,7 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
         bulk_wait_all();   // shared memory stays valid until the stores are done
 }
 
-template <class C, int CL>
+template <class C, int CL, bool H16 = false>
 __global__ void __launch_bounds__(C::T, 1) col_group_l2_kernel(const __grid_constant__ CUtensorMap map0,
                                                                const __grid_constant__ CUtensorMap map1,
                                                                const __grid_constant__ CUtensorMap map2,
@@ -925,12 +1061,13 @@ __global__ void __launch_bounds__(C::T, 1) col_group_l2_kernel(const __grid_cons
                                                                const __grid_constant__ CUtensorMap omap,
                                                                const float2 *__restrict__ tw,
                                                                int cols, float scale, int *err,
-                                                               int withhold, float2 *xbuf)
+                                                               int withhold, float2 *xbuf,
+                                                               const GroupIO io)
 {
     const int q = (int)cooperative_groups::this_cluster().block_rank();
     const int res = brev_rt(q, CL);
     const CUtensorMap *m = res == 0 ? &map0 : res == 1 ? &map1 : res == 2 ? &map2 : &map3;
-    col_group_l2_body<C, CL>(m, &omap, cols / C::W, tw, scale, err, withhold, xbuf);
+    col_group_l2_body<C, CL, H16>(m, &omap, cols / C::W, tw, scale, err, withhold, xbuf, io);
 }
 
 }  // namespace fft2d

@@ -878,6 +878,7 @@ fft2d_status fft2d_exec_h16(fft2d_plan_t p, const void *in, const int *in_exp, i
     a.in_exp = in_exp;
     a.in_axis = in_axis;
     a.out_exp = p->exp_rows;
+    a.err = p->dev_err;
     cudaError_t e = fft2d::launch_pass_h16(true, p->Lc, a, st);
     if (e != cudaSuccess)
         return cuda_fail(e, "half2 row pass");
@@ -889,7 +890,6 @@ fft2d_status fft2d_exec_h16(fft2d_plan_t p, const void *in, const int *in_exp, i
     a.in_exp = p->exp_rows;
     a.in_axis = FFT2D_PASS_ROWS;
     a.out_exp = out_exp;
-    a.err = p->dev_err;
     e = fft2d::launch_pass_h16(false, p->Lr, a, st);
     if (e != cudaSuccess)
         return cuda_fail(e, "half2 column pass");

@@ -278,40 +278,6 @@ cudaError_t col_launch_group(const PassArgs &a, cudaStream_t s)
                               a.withhold, GroupIO{nullptr, nullptr});
 }
 
-// Stream-ordered scratch for the exchange rounds of col_group_l2_kernel,
-// from a memory pool of the library's own per device (kept cached: its
-// release threshold is unlimited, so after the first calls taking and
-// returning a block costs no driver allocation).  A block is taken on the
-// launch's stream and given back on it after the launch, so launches on
-// different streams never share one, and under stream capture the pair
-// becomes graph memory nodes.
-cudaError_t scratch_take(void **p, size_t bytes, cudaStream_t s)
-{
-    static std::mutex mu;
-    static cudaMemPool_t pool[kMaxDev] = {};
-    const int d = current_device();
-    {
-        std::lock_guard<std::mutex> g(mu);
-        if (!pool[d]) {
-            cudaMemPoolProps props = {};
-            props.allocType = cudaMemAllocationTypePinned;
-            props.location.type = cudaMemLocationTypeDevice;
-            props.location.id = d;
-            cudaMemPool_t mp;
-            cudaError_t e = cudaMemPoolCreate(&mp, &props);
-            if (e != cudaSuccess)
-                return e;
-            uint64_t keep = ~0ull;
-            e = cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &keep);
-            if (e != cudaSuccess) {
-                cudaMemPoolDestroy(mp);
-                return e;
-            }
-            pool[d] = mp;
-        }
-    }
-    return cudaMallocFromPoolAsync(p, bytes, pool[d], s);
-}
 
 // Column pass over 2^(L+CL)-row columns on clusters of 2^CL CTAs with the
 // exchange rounds through L2 (col_group_l2_kernel); the same tensor maps and
@@ -331,7 +297,7 @@ cudaError_t col_launch_group_l2(const PassArgs &a, cudaStream_t s)
         m[r] = m[0];
     if (!encode_col_map(&om, a.out, a.rows, a.cols, a.ld, C::W, S::BOX, GC::OUT_BOX_Z))
         return col_launch_any<LineCfg<C::L + CL, C::KW, 0>>(a, s);
-    auto k = col_group_l2_kernel<C, CL>;
+    auto k = col_group_l2_kernel<C, CL, false>;
     constexpr int SMEM = S::SMEM_BYTES;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
@@ -361,14 +327,12 @@ cudaError_t col_launch_group_l2(const PassArgs &a, cudaStream_t s)
     const int ntiles = a.cols / C::W;
     const int ng = groups.get(d) < ntiles ? groups.get(d) : ntiles;
     void *xbuf = nullptr;
-    const size_t per = CL == 2 ? (size_t)2 * CS * CS * 2 * GC::KEEP_R * C::T
-                               : (size_t)2 * CS * GC::XVALS * C::T;
-    cudaError_t e = scratch_take(&xbuf, (size_t)ng * per * sizeof(float2), s);
+    cudaError_t e = scratch_take(&xbuf, (size_t)ng * GC::L2_SCRATCH_VALS * sizeof(float2), s);
     if (e != cudaSuccess)
         return e;
     cfg.gridDim = dim3((unsigned)(CS * ng));
     e = cudaLaunchKernelEx(&cfg, k, m[0], m[1], m[2], m[3], om, a.tw, a.cols, a.scale, a.err,
-                           a.withhold, static_cast<float2 *>(xbuf));
+                           a.withhold, static_cast<float2 *>(xbuf), GroupIO{nullptr, nullptr});
     const cudaError_t f = cudaFreeAsync(xbuf, s);
     return e != cudaSuccess ? e : f;
 }
@@ -569,6 +533,42 @@ bool col_pass_is_tma_fed(int L, const PassArgs &a)
 {
     const Variant *v = select_col_variant(L, a);
     return v && v->tma_fed;
+}
+
+// Stream-ordered scratch for the exchange rounds of col_group_l2_kernel,
+// from a memory pool of the library's own per device (kept cached: its
+// release threshold is unlimited, so after the first calls taking and
+// returning a block costs no driver allocation).  A block is taken on the
+// launch's stream and given back on it after the launch, so launches on
+// different streams never share one, and under stream capture the pair
+// becomes graph memory nodes.
+cudaError_t scratch_take(void **p, size_t bytes, cudaStream_t s)
+{
+    constexpr int kMaxDev = 64;
+    static std::mutex mu;
+    static cudaMemPool_t pool[kMaxDev] = {};
+    const int d = device_current();
+    {
+        std::lock_guard<std::mutex> g(mu);
+        if (!pool[d]) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = d;
+            cudaMemPool_t mp;
+            cudaError_t e = cudaMemPoolCreate(&mp, &props);
+            if (e != cudaSuccess)
+                return e;
+            uint64_t keep = ~0ull;
+            e = cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &keep);
+            if (e != cudaSuccess) {
+                cudaMemPoolDestroy(mp);
+                return e;
+            }
+            pool[d] = mp;
+        }
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool[d], s);
 }
 
 }  // namespace fft2d

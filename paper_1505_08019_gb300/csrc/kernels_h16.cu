@@ -103,10 +103,11 @@ cudaError_t h16_launch_col_tma(const H16PassArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// Columns of 2^(12+CL) rows on a cluster of 2^CL CTAs (col_group.cuh, half2
-// storage): the 4096-row engine on each CTA's rows, the last CL stages by
-// bulk copies between the CTAs.  cudaErrorNotSupported (nothing launched)
-// when the buffers or shape cannot feed it.
+// Columns of 2^(12+CL) rows on a cluster of 2^CL CTAs (col_group_l2_kernel,
+// half2 storage): the 4096-row engine on each CTA's rows, the last CL stages
+// after an exchange through a stream-ordered scratch block in L2.
+// cudaErrorNotSupported (nothing launched) when the buffers or shape cannot
+// feed it.
 template <int CL>
 cudaError_t h16_launch_col_group(const H16PassArgs &a, cudaStream_t s)
 {
@@ -126,7 +127,7 @@ cudaError_t h16_launch_col_group(const H16PassArgs &a, cudaStream_t s)
         m[r] = m[0];
     if (!encode_h16_col_map(&om, a.out, a.rows, a.cols, a.ld, C::W, GH::BOX, GC::OUT_BOX_Z))
         return cudaErrorNotSupported;
-    auto k = col_group_kernel<C, CL, true>;
+    auto k = col_group_l2_kernel<C, CL, true>;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -154,18 +155,31 @@ cudaError_t h16_launch_col_group(const H16PassArgs &a, cudaStream_t s)
     }
     const int ntiles = a.cols / C::W;
     const int ng = groups.get(d) < ntiles ? groups.get(d) : ntiles;
+    void *xbuf = nullptr;
+    cudaError_t e = scratch_take(&xbuf, (size_t)ng * GC::L2_SCRATCH_VALS * sizeof(float2), s);
+    if (e != cudaSuccess)
+        return e;
     cfg.gridDim = dim3((unsigned)(CS * ng));
-    return cudaLaunchKernelEx(&cfg, k, m[0], m[1], m[2], m[3], om, a.tw, a.cols, a.scale, a.err,
-                              0, GroupIO{a.in_exp, a.out_exp});
+    e = cudaLaunchKernelEx(&cfg, k, m[0], m[1], m[2], m[3], om, a.tw, a.cols, a.scale, a.err, 0,
+                           static_cast<float2 *>(xbuf), GroupIO{a.in_exp, a.out_exp});
+    const cudaError_t f = cudaFreeAsync(xbuf, s);
+    return e != cudaSuccess ? e : f;
 }
 
 template <int L>
 cudaError_t h16_dispatch(bool row, const H16PassArgs &a, cudaStream_t s)
 {
     if (row) {
-        // 8192-point rows: 32 values per thread (256 threads), as for complex64
-        using C = LineCfg<L, 0, row_kb(L), L == 13 ? 32 : 16>;
-        return a.rows % C::LB ? h16_launch<C, true, true>(a, s) : h16_launch<C, true, false>(a, s);
+        if constexpr (L >= 13) {
+            // rows of 8192 and 16384 points: groups of 5 stages, 32 values a
+            // thread (three groups instead of four), as for complex64
+            using C5 = LineCfg<L, 0, 0, 32, 5>;
+            return h16_launch<C5, true, false>(a, s);
+        } else {
+            using C = LineCfg<L, 0, row_kb(L), 16>;
+            return a.rows % C::LB ? h16_launch<C, true, true>(a, s)
+                                  : h16_launch<C, true, false>(a, s);
+        }
     }
     using C = LineCfg<L, col_kw(L), 0>;
     if constexpr (L == 12) {

@@ -10,6 +10,8 @@
 //                dense whole blocks only)
 //   4  split   : persistent, one row per CTA at a time with the next row's
 //                first half prefetched (rows of 4096..16384 points)
+#include <cstring>
+
 #include "line_fft.cuh"
 #include "passes.h"
 
@@ -223,9 +225,15 @@ struct RowVariants {
     static constexpr bool HAS2X = L >= 5 && L <= 13 && Plain2x::E * 8 <= 128 * 1024;
     static constexpr bool HASTMA = L >= 5 && L <= 13;
     static constexpr bool HASSPLIT = L >= 12;
+    // groups of 5 stages (32 values a thread) where they save a group:
+    // 512, 1024, 8192 and 16384 points
+    using G5 = LineCfg<L, 0, row_kb(L), 32, 5>;
+    static constexpr bool HASG5 = (L == 9 || L == 10 || L == 13 || L == 14) && G5::E >= 32;
+    using Split5 = LineCfg<L, 0, 0, 32, 5>;
+    static constexpr bool HASSPLIT5 = L >= 13;
 
     struct Table {
-        Variant v[5];
+        Variant v[7];
         int n = 0;
     };
     static Table build()
@@ -240,6 +248,10 @@ struct RowVariants {
             t.v[t.n++] = {"tma", 1 << row_kb(L), 16, row_tma_usable<Plain>, row_launch_tma<Plain>};
         if constexpr (HASSPLIT)
             t.v[t.n++] = {"split", 1, 16, row_split_usable<Plain>, row_launch_split<Plain>};
+        if constexpr (HASG5)
+            t.v[t.n++] = {"plain32g5", 1 << row_kb(L), 32, whole_stages, row_launch_any<G5>};
+        if constexpr (HASSPLIT5)
+            t.v[t.n++] = {"split32g5", 1, 32, row_split_usable<Split5>, row_launch_split<Split5>};
         return t;
     }
     static const Variant *table(int *n)
@@ -273,9 +285,21 @@ const Variant *row_variants(int L, int *n)
     }
 }
 
-// plain everywhere except 8192-point rows, where 32 values per thread
-// (256 threads, 64 KB of shared memory, three CTAs per SM) measured faster
-int row_default_variant(int L) { return L == 13 ? 1 : 0; }
+// plain everywhere except 8192- and 16384-point rows, where groups of 5
+// stages (32 values a thread, three groups instead of four) measured faster:
+// 0.183 against 0.218 ms (8192^2, "plain32") and 0.906 against 1.04 ms
+// (16384^2, "split")
+int row_default_variant(int L)
+{
+    if (L != 13 && L != 14)
+        return 0;
+    int n = 0;
+    const Variant *v = row_variants(L, &n);
+    for (int i = 0; i < n; i++)
+        if (std::strcmp(v[i].name, "plain32g5") == 0)
+            return i;
+    return 0;
+}
 
 cudaError_t launch_row_pass(int L, const PassArgs &a, cudaStream_t s)
 {

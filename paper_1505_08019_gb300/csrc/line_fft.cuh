@@ -69,14 +69,19 @@ __device__ __forceinline__ int brev_rt(int v, int bits)
 
 // Geometry of one CTA's work: lines of 2^L points, 2^KW interleaved lines
 // (adjacent in memory: the column pass), 2^KB separate line blocks (the row
-// pass), EPT (16 or 32) values per thread.
-template <int L_, int KW_, int KB_, int EPT_ = 16>
+// pass), EPT (16 or 32) values per thread, stage groups of GS stages (4, or
+// 5 with 32 values a thread: one unit of 32 values, fewer groups and so
+// fewer exchanges through shared memory for lines of 2^9, 2^10, 2^13 and
+// 2^14 points).  The grouping changes where values wait between stages,
+// not the butterflies, so every GS gives the same bits.
+template <int L_, int KW_, int KB_, int EPT_ = 16, int GS_ = 4>
 struct LineCfg {
-    static constexpr int L = L_, KW = KW_, KB = KB_, EPT = EPT_;
+    static constexpr int L = L_, KW = KW_, KB = KB_, EPT = EPT_, GS = GS_;
     static constexpr int N = 1 << L, W = 1 << KW, LB = 1 << KB;
     static constexpr int E = N * W * LB;
     static constexpr int T = E / EPT;
-    static constexpr int NG = (L + 3) / 4;
+    static constexpr int NG = (L + GS - 1) / GS;
+    static_assert(GS == 4 || (GS == 5 && EPT == 32), "groups of 4 stages, or 5 with 32 values");
     // lanes of a half-warp that are not spent on the interleave index
     static constexpr int K = KW >= 4 ? 0 : 4 - KW;
     static constexpr bool SWZ = K > 0 && L >= 2 * K;
@@ -101,9 +106,10 @@ struct GrpSG {
     static constexpr int HB = L - S0 - G;        // bits above the group
 };
 
-// Group GI of the stage groups of a CTA config: bits [4 GI, 4 GI + G).
+// Group GI of the stage groups of a CTA config: bits [GS GI, GS GI + G).
 template <class C, int GI>
-struct Grp : GrpSG<C::L, 4 * GI, ((C::L - 4 * GI) < 4 ? (C::L - 4 * GI) : 4), C::EPT> {};
+struct Grp : GrpSG<C::L, C::GS * GI, ((C::L - C::GS * GI) < C::GS ? (C::L - C::GS * GI) : C::GS),
+                   C::EPT> {};
 
 // Shared-memory slot of (line block lb, position p, interleaved line w).
 template <class C>
@@ -178,7 +184,8 @@ __device__ __forceinline__ void run_stages_g(float2 (&a)[NA], int v, int lo,
             const int m = r & ((1 << t) - 1);
             float2 &x0 = a[v * Gp::R + r];
             float2 &x1 = a[v * Gp::R + (r | (1 << t))];
-            if (FIRST && m == 0) {   // W = 1
+            if (FIRST && m == 0 && t < 4) {   // W = 1 (a 5th stage of group 0 takes the
+                                              // table's W^0 as a 4-stage grouping does)
                 const float2 d = x1;
                 x1 = make_float2(__fsub_rn(x0.x, d.x), __fsub_rn(x0.y, d.y));
                 x0 = make_float2(__fadd_rn(x0.x, d.x), __fadd_rn(x0.y, d.y));

@@ -217,6 +217,13 @@ bool tensor_maps_available();
 
 cudaError_t launch_row_pass(int L, const PassArgs &a, cudaStream_t s);
 
+// Stream-ordered device scratch from the library's own memory pool of the
+// current device (kernels_col.cu): taken on `s` (cudaMallocFromPoolAsync),
+// given back by the caller with cudaFreeAsync on `s` after its launches.
+// The pool keeps what it has allocated, so after the first calls no driver
+// allocation happens; launches on different streams never share a block.
+cudaError_t scratch_take(void **p, size_t bytes, cudaStream_t s);
+
 // Streaming multiprocessors of the current device (cached per device).
 int device_sm_count();
 

@@ -109,6 +109,7 @@ cudaError_t h16_phase(const std::vector<Req *> &reqs, const std::vector<fft2d_pl
         a.in_exp = in_exp(i);
         a.in_axis = in_axis;
         a.out_exp = q->exps + v.rows;
+        a.err = v.err;
         cudaError_t e = fft2d::launch_pass_h16(true, v.Lc, a, st);
         if (e != cudaSuccess)
             return e;
@@ -118,7 +119,6 @@ cudaError_t h16_phase(const std::vector<Req *> &reqs, const std::vector<fft2d_pl
         a.in_exp = q->exps + v.rows;
         a.in_axis = FFT2D_PASS_ROWS;
         a.out_exp = q->exps + 2 * v.rows;
-        a.err = v.err;
         e = fft2d::launch_pass_h16(false, v.Lr, a, st);
         if (e != cudaSuccess)
             return e;
