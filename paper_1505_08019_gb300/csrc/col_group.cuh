@@ -16,19 +16,23 @@
 //     X[P] = Y[P] + W^i Y[P + 2^(L+j)],  X[P + 2^(L+j)] = Y[P] - W^i Y[P + 2^(L+j)],
 // W = W_{2^(L+j+1)}, i = P mod 2^(L+j).  Thread t holds the same indices k
 // in every CTA, so in round j the two partners split the k that are still
-// theirs by bit L-1-j of k: each keeps one half, writes the values of the
-// other half into a send buffer, and one thread moves the whole buffer into
-// the partner's shared memory with a single bulk copy that completes on the
-// partner's mbarrier.  After c rounds CTA q holds, for a contiguous quarter
-// (c = 2) or half (c = 1) of the k, all CS outputs X[k + 2^L t] and writes
-// them with TMA stores.
+// theirs by bit L-1-j of k: each keeps one half and hands the values of the
+// other half to its partner.  After c rounds CTA q holds, for a contiguous
+// quarter (c = 2) or half (c = 1) of the k, all CS outputs X[k + 2^L t] and
+// writes them with TMA stores.
 //
-// With half2 storage (H16) the tile arrives as half2 (16-byte TMA box rows)
-// and group 0 widens each value with its row's factor 2^e, as in the
-// single-CTA half2 column pass; at the end every CTA max-reduces its part of
-// each column, the partial maxima travel to every CTA of the cluster with the
-// last exchange round's barrier, and all CTAs pick the same exponent per
-// column before staging their ranges as half2.
+// Two kernels move the values.  col_group_kernel: one thread moves a send
+// buffer into the partner's shared memory with a single bulk copy that
+// completes on the partner's mbarrier, two cluster barriers per round.
+// col_group_l2_kernel (the default): the values go through a scratch block
+// in global memory, resident in L2, one cluster barrier per exchange, and
+// four CTAs exchange once and run both cross stages together (radix 4).
+// Only the second has a half2 storage mode (H16): the tile arrives as half2
+// (16-byte TMA box rows) and group 0 widens each value with its row's factor
+// 2^e, as in the single-CTA half2 column pass; at the end every CTA
+// max-reduces its part of each column, the partial maxima travel to every
+// CTA of the cluster through one more cluster barrier, and all CTAs pick the
+// same exponent per column before staging their ranges as half2.
 //
 // Cluster barriers have no time limit, so every CTA always executes the same
 // sequence of them: a CTA that lost a TMA transfer still reaches the first
@@ -277,49 +281,27 @@ struct GroupIO {
 // omap: store map over the output (box W x 256 x OUT_BOX_Z); tw: the plan's
 // rotation-factor table of the column axis (2^(L+CL) entries with padding:
 // the local stages read entries [0, 2^L), round j stage L+1+j).
-template <class C, int CL, bool H16>
+template <class C, int CL>
 __device__ __forceinline__ void col_group_body(const CUtensorMap *lmap, const CUtensorMap *omap,
                                                int ntiles, const float2 *__restrict__ tw,
-                                               float scale, int *err, int withhold,
-                                               const GroupIO &io)
+                                               float scale, int *err, int withhold)
 {
     namespace cg = cooperative_groups;
     using S = TmaSplit<C>;
     using GC = GroupCol<C, CL>;
-    using GH = GroupH16<C>;
     using Gl = Grp<C, C::NG - 1>;
-    using G0 = Grp<C, 0>;
     constexpr int CS = GC::CS;
     extern __shared__ __align__(1024) float2 sm[];
     __shared__ __align__(8) uint64_t bar_early, bar_late, bar_recv;
     __shared__ int lost_flag[CS];   // slot p: written by CTA p of the cluster
-    __shared__ int cmax[CS][C::W];  // half2: partial column maxima, slot p from CTA p
-    __shared__ int cmax_local[C::W];
     cg::cluster_group cluster = cg::this_cluster();
     const int q = (int)cluster.block_rank();
     const int tid = threadIdx.x;
     const int nclusters = (int)gridDim.x / CS;
-    unsigned char *smb = reinterpret_cast<unsigned char *>(sm);
-    float2 *stw = H16 ? reinterpret_cast<float2 *>(smb + GH::TW_OFF) : sm + S::TW_OFF;
-    float *rf = reinterpret_cast<float *>(smb + GH::RF_OFF);
-    const uint32_t tw_bytes = H16 ? (uint32_t)C::N * 8u : S::TW_BYTES;
+    float2 *stw = sm + S::TW_OFF;
     // the first and second half of a tile's TMA boxes
-    auto issue_early = [&](int t) {
-        if constexpr (H16) {
-            mbar_arrive_expect_tx(&bar_early, GH::HALF_BYTES);
-            tma_load_3d(smb + GH::PREF_OFF, lmap, t * C::W, 0, 0, &bar_early);
-        } else {
-            split_issue_early<C>(sm, lmap, t * C::W, &bar_early);
-        }
-    };
-    auto issue_late = [&](int t) {
-        if constexpr (H16) {
-            mbar_arrive_expect_tx(&bar_late, GH::HALF_BYTES);
-            tma_load_3d(smb, lmap, t * C::W, 0, GH::NB, &bar_late);
-        } else {
-            split_issue_late<C>(sm, lmap, t * C::W, &bar_late);
-        }
-    };
+    auto issue_early = [&](int t) { split_issue_early<C>(sm, lmap, t * C::W, &bar_early); };
+    auto issue_late = [&](int t) { split_issue_late<C>(sm, lmap, t * C::W, &bar_late); };
     // after the last read of a tile: the lower half of the tile region
     // receives the partner's values, the upper half holds the values sent
     // and then stages the output
@@ -346,21 +328,13 @@ __device__ __forceinline__ void col_group_body(const CUtensorMap *lmap, const CU
         mbar_init(&bar_recv, 1);
         fence_mbar_init();
     }
-    if constexpr (H16) {
-        // the factors of this CTA's rows CS m + rev_CL(q)
-        const int res = brev_rt(q, CL);
-        for (int i = tid; i < C::N; i += C::T)
-            rf[i] = pow2f(io.row_exp[(long long)i * CS + res]);
-        if (tid < C::W)
-            cmax_local[tid] = 0;
-    }
     __syncthreads();
     // issued / waited phases of each mbarrier (thread 0 issues, all wait)
     int n_early = 0, n_late = 0, w_early = 0, w_late = 0;
     if (tile < ntiles) {
         if (tid == 0) {
-            mbar_expect_tx(&bar_early, tw_bytes);
-            bulk_load(stw, tw, tw_bytes, &bar_early);
+            mbar_expect_tx(&bar_early, S::TW_BYTES);
+            bulk_load(stw, tw, S::TW_BYTES, &bar_early);
             issue_early(tile);
             // (self-test: CTA 0 withholds its first late boxes)
             if (!(withhold && blockIdx.x == 0))
@@ -391,59 +365,16 @@ __device__ __forceinline__ void col_group_body(const CUtensorMap *lmap, const CU
         if (!lost_here) {
             w_early++;
             w_late++;
-            if constexpr (H16) {
-                // group 0: scrambled gather of the half2 tile, widened and
-                // scaled by the row factors
-                const __half2 *pref = reinterpret_cast<const __half2 *>(smb + GH::PREF_OFF);
-                const __half2 *late = reinterpret_cast<const __half2 *>(smb);
-#pragma unroll
-                for (int v = 0; v < G0::V; v++) {
-                    const int u = tid + v * C::T;
-                    const int w = u & (C::W - 1);
-                    const int hib = (u >> C::KW) & ((1 << G0::HB) - 1);
-#pragma unroll
-                    for (int r = 0; r < G0::R; r++) {
-                        const int top = brev_c(r, G0::G) << G0::HB;   // compile-time
-                        const int kb = top / GH::BOX;
-                        const int in_box = ((top % GH::BOX) | hib) * C::W + w;
-                        const __half2 *bx = kb < GH::NB ? pref + kb * GH::BOXV
-                                                        : late + (kb - GH::NB) * GH::BOXV;
-                        const float2 hv = __half22float2(bx[in_box]);
-                        const float f = rf[top | hib];
-                        a[v * G0::R + r] = make_float2(hv.x * f, hv.y * f);
-                    }
-                }
-#pragma unroll
-                for (int v = 0; v < G0::V; v++)
-                    run_stages<C, 0, false, true>(a, v, 0, stw, C::L);
-                fence_proxy_async_smem();
-                if (tid == 0)
-                    bulk_wait_read_all();   // the previous tile's stores have read it
-                __syncthreads();            // every slot of both input regions has been read
-                if (tid == 0 && next < ntiles)
-                    issue_early(next);
-#pragma unroll
-                for (int v = 0; v < G0::V; v++) {
-                    const int u = tid + v * C::T;
-                    const int w = u & (C::W - 1);
-                    const int hib = (u >> C::KW) & ((1 << G0::HB) - 1);
-                    const int hi = brev_rt(hib, G0::HB);
-#pragma unroll
-                    for (int r = 0; r < G0::R; r++)
-                        sm[sidx<C>(0, r | (hi << G0::G), w)] = a[v * G0::R + r];
-                }
-            } else {
-                group_first_split<C>(
-                    a, sm, stw,
-                    [&] {
-                        if (tid == 0)
-                            bulk_wait_read_all();   // the previous tile's stores have read it
-                    },
-                    [&] {
-                        if (tid == 0 && next < ntiles)
-                            issue_early(next);
-                    });
-            }
+            group_first_split<C>(
+                a, sm, stw,
+                [&] {
+                    if (tid == 0)
+                        bulk_wait_read_all();   // the previous tile's stores have read it
+                },
+                [&] {
+                    if (tid == 0 && next < ntiles)
+                        issue_early(next);
+                });
             if (next < ntiles)
                 n_early++;
             __syncthreads();
@@ -488,8 +419,7 @@ __device__ __forceinline__ void col_group_body(const CUtensorMap *lmap, const CU
             w_recv++;
         // cluster barrier B0, arrive: the partner's send buffer has been read
         // (half2, last round: after the column maxima, further down)
-        if constexpr (!(H16 && CL == 1))
-            cluster_arrive_release();
+        cluster_arrive_release();
         group_round_compute<C, 0>(a, recvb, wk, q & 1);
         if constexpr (CL == 2) {
             const int rk1 = ((q & 1) * (Gl::R / 2)) + ((q >> 1) & 1) * (Gl::R / 4);
@@ -512,31 +442,8 @@ __device__ __forceinline__ void col_group_body(const CUtensorMap *lmap, const CU
                 w_recv++;
             lost_recv |= lr;
             // cluster barrier B1, arrive: the partner's send buffer has been read
-            // (half2: after the column maxima, further down)
-            if constexpr (!H16)
-                cluster_arrive_release();
-            group_round_compute<C, 1>(a, recvb, wk, (q >> 1) & 1);
-        }
-        if constexpr (H16) {
-            // this CTA's part of each column's largest |component| (a
-            // thread's values all belong to column tid mod W), to every CTA
-            // of the cluster with the last B barrier
-            float m = 0.f;
-#pragma unroll
-            for (int i = 0; i < 32; i++)
-                m = fmaxf(m, fmaxf(fabsf(a[i].x), fabsf(a[i].y)));
-            m = warp_line_max<C::KW, 5>(m);
-            if ((tid & (31 & ~(C::W - 1))) == 0)
-                atomicMax(&cmax_local[tid & (C::W - 1)], __float_as_int(m * scale));
-            __syncthreads();
-            if (tid < C::W) {
-                const int mine = cmax_local[tid];
-                cmax_local[tid] = 0;
-#pragma unroll
-                for (int p = 0; p < CS; p++)
-                    *cluster.map_shared_rank(&cmax[q][tid], p) = mine;
-            }
             cluster_arrive_release();
+            group_round_compute<C, 1>(a, recvb, wk, (q >> 1) & 1);
         }
         fence_proxy_async_smem();
         __syncthreads();   // the receive buffer has been read
@@ -546,45 +453,6 @@ __device__ __forceinline__ void col_group_body(const CUtensorMap *lmap, const CU
             n_late++;
         // the last B barrier, wait: this CTA's send buffer is free for staging
         cluster_wait_acquire();
-
-        if constexpr (H16) {
-            // every CTA of the cluster picks the same exponent per column
-            const int w = tid & (C::W - 1);
-            int mb = 0;
-#pragma unroll
-            for (int p = 0; p < CS; p++)
-                mb = max(mb, cmax[p][w]);
-            const int e = line_exponent(__int_as_float(mb));
-            const float f = scale * pow2f(-e);
-            __half2 *stage = reinterpret_cast<__half2 *>(sendb);
-#pragma unroll
-            for (int t = 0; t < CS; t++) {
-#pragma unroll
-                for (int v = 0; v < Gl::V; v++) {
-                    const int u = tid + v * C::T;
-                    const int lo = (u >> C::KW) & ((1 << Gl::S0) - 1);
-#pragma unroll
-                    for (int i = 0; i < GC::KEEP_R; i++) {
-                        const float2 x = a[t * 2 * GC::KEEP_R + v * GC::KEEP_R + i];
-                        stage[(t * GC::OUT_ROWS + ((i << Gl::S0) | lo)) * C::W + w] =
-                            __floats2half2_rn(x.x * f, x.y * f);
-                    }
-                }
-            }
-            if (q == 0 && tid < C::W)
-                io.out_exp[tile * C::W + tid] = e;
-            fence_proxy_async_smem();
-            __syncthreads();
-            if (tid == 0) {
-#pragma unroll
-                for (int t = 0; t < CS; t++) {
-                    const int z = ((t << C::L) + k_base) / S::BOX;
-                    tma_store_3d(omap, tile * C::W, 0, z, stage + t * GC::OUT_ROWS * C::W);
-                }
-                bulk_commit();
-            }
-            continue;
-        }
 
         // outputs t = 0 .. CS-1: rows k_base + [0, OUT_ROWS) + 2^L t, STAGE_T
         // ranges per fill of the staging buffer (the send buffer), each
@@ -642,7 +510,7 @@ __device__ __forceinline__ void col_group_body(const CUtensorMap *lmap, const CU
 }
 
 // rank q loads map[rev_CL(q)] -- the rows of residue rev_CL(q) mod 2^CL
-template <class C, int CL, bool H16 = false>
+template <class C, int CL>
 __global__ void __launch_bounds__(C::T, 1) col_group_kernel(const __grid_constant__ CUtensorMap map0,
                                                             const __grid_constant__ CUtensorMap map1,
                                                             const __grid_constant__ CUtensorMap map2,
@@ -650,12 +518,12 @@ __global__ void __launch_bounds__(C::T, 1) col_group_kernel(const __grid_constan
                                                             const __grid_constant__ CUtensorMap omap,
                                                             const float2 *__restrict__ tw,
                                                             int cols, float scale, int *err,
-                                                            int withhold, const GroupIO io)
+                                                            int withhold)
 {
     const int q = (int)cooperative_groups::this_cluster().block_rank();
     const int res = brev_rt(q, CL);
     const CUtensorMap *m = res == 0 ? &map0 : res == 1 ? &map1 : res == 2 ? &map2 : &map3;
-    col_group_body<C, CL, H16>(m, &omap, cols / C::W, tw, scale, err, withhold, io);
+    col_group_body<C, CL>(m, &omap, cols / C::W, tw, scale, err, withhold);
 }
 
 // The same column pass with the exchange rounds through a scratch buffer in

@@ -244,7 +244,7 @@ cudaError_t col_launch_group(const PassArgs &a, cudaStream_t s)
         m[r] = m[0];
     if (!encode_col_map(&om, a.out, a.rows, a.cols, a.ld, C::W, S::BOX, GC::OUT_BOX_Z))
         return col_launch_any<LineCfg<C::L + CL, C::KW, 0>>(a, s);
-    auto k = col_group_kernel<C, CL, false>;
+    auto k = col_group_kernel<C, CL>;
     constexpr int SMEM = S::SMEM_BYTES;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
@@ -275,7 +275,7 @@ cudaError_t col_launch_group(const PassArgs &a, cudaStream_t s)
     const int ng = groups.get(d) < ntiles ? groups.get(d) : ntiles;
     cfg.gridDim = dim3((unsigned)(CS * ng));
     return cudaLaunchKernelEx(&cfg, k, m[0], m[1], m[2], m[3], om, a.tw, a.cols, a.scale, a.err,
-                              a.withhold, GroupIO{nullptr, nullptr});
+                              a.withhold);
 }
 
 
