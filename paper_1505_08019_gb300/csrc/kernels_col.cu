@@ -157,8 +157,12 @@ cudaError_t col_launch_tma(const PassArgs &a, cudaStream_t s)
 {
     CUtensorMap map, omap;
     using S = TmaSplit<C>;
+    // store boxes: half a 256-row block per box (4-stage groups), or the
+    // first half of the tile in one box (one unit a thread)
+    constexpr bool ROWHALF = Grp<C, C::NG - 1>::V == 1;
     if (!encode_col_map(&map, a.in, a.rows, a.cols, a.ld, C::W, S::BOX, S::NB) ||
-        !encode_col_map(&omap, a.out, a.rows, a.cols, a.ld, C::W, tma_store_rows(C::L), S::NBOX))
+        !encode_col_map(&omap, a.out, a.rows, a.cols, a.ld, C::W,
+                        ROWHALF ? S::BOX : tma_store_rows(C::L), ROWHALF ? S::NB : S::NBOX))
         return col_launch_any<LineCfg<C::L, C::KW, 0>>(a, s);
     auto k = col_tma2_kernel<C, TS, HYB>;
     constexpr int SMEM = TmaSplit<C>::SMEM_BYTES;
@@ -364,6 +368,7 @@ struct ColVariants {
     using PairLocal = LineCfg<12, 2, 0, 32>;
     using Tma32 = LineCfg<L, col_kw(L), 0, col_tma_ept(L)>;
     using Tma16 = LineCfg<L, col_kw(L), 0, 16>;
+    using Tma64 = LineCfg<L, col_kw(L), 0, 64, 6>;
     static constexpr int KWN = col_kw(L) - 1;                 // narrower tiles
     static constexpr bool HASNARROW = L >= 5 && KWN >= 2;
 
@@ -379,7 +384,7 @@ struct ColVariants {
     using Clu8 = ClusterColCfg<(L >= 13 ? L : 13), 3, (L >= 13 ? L - 11 : 2)>;
 
     struct Table {
-        Variant v[10];
+        Variant v[12];
         int n = 0;
     };
     static Table build()
@@ -415,6 +420,11 @@ struct ColVariants {
         if constexpr (HASTMEM && tma_store_ok<Tma32>())
             t.v[t.n++] = {"tma32h", Tma32::W, 32, col_tma_usable<Tma32>,
                           col_launch_tma<Tma32, true, true>, true};
+        // 4096 rows in two groups of 6 stages (256 threads x 64 values): one
+        // exchange through shared memory per tile instead of two
+        if constexpr (L == 12)
+            t.v[t.n++] = {"tma64", Tma64::W, 64, col_tma_usable<Tma64>,
+                          col_launch_tma<Tma64, true, true>, true};
         // 8192 and 16384 rows: 4-column tiles over a cluster of 2 or 4 CTAs,
         // the 4096-row engine on each CTA's rows and the last one or two
         // stages through bulk copies between the CTAs' shared memories
@@ -451,8 +461,9 @@ struct ColVariants {
     }
     // The default per column length, from timings of every variant on a
     // GB300 (512..4096 rows, square and 1:4 images): narrow tiles for 512 and
-    // 1024 rows, the TMA pass with per-thread stores for 2048, and the TMA
-    // pass with half TMA / half per-thread stores for 4096.
+    // 1024 rows, the TMA pass with per-thread stores for 2048, and for 4096
+    // the TMA pass in two groups of 6 stages with half TMA / half per-thread
+    // stores.
     static int preferred()
     {
         if constexpr (L == 9 || L == 10)
@@ -460,7 +471,7 @@ struct ColVariants {
         else if constexpr (L == 11)
             return index_of("tma32st");
         else if constexpr (L == 12)
-            return index_of("tma32h");
+            return index_of("tma64");     // 61.8 vs 66.0 us for "tma32h" at 4096^2
         else if constexpr (L == 13)
             return index_of("pairl2");    // 4-column tiles over a CTA pair (0.327 vs 0.334 ms for "pair")
         else if constexpr (L == 14)

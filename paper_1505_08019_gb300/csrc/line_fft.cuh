@@ -69,11 +69,12 @@ __device__ __forceinline__ int brev_rt(int v, int bits)
 
 // Geometry of one CTA's work: lines of 2^L points, 2^KW interleaved lines
 // (adjacent in memory: the column pass), 2^KB separate line blocks (the row
-// pass), EPT (16 or 32) values per thread, stage groups of GS stages (4, or
-// 5 with 32 values a thread: one unit of 32 values, fewer groups and so
-// fewer exchanges through shared memory for lines of 2^9, 2^10, 2^13 and
-// 2^14 points).  The grouping changes where values wait between stages,
-// not the butterflies, so every GS gives the same bits.
+// pass), EPT (16, 32 or 64) values per thread, stage groups of GS stages (4;
+// 5 with 32 values a thread; 6 with 64: one unit of 2^GS values, fewer
+// groups and so fewer exchanges through shared memory, e.g. two instead of
+// three groups for lines of 2^12 points with GS = 6).  The grouping changes
+// where values wait between stages, not the butterflies, so every GS gives
+// the same bits.
 template <int L_, int KW_, int KB_, int EPT_ = 16, int GS_ = 4>
 struct LineCfg {
     static constexpr int L = L_, KW = KW_, KB = KB_, EPT = EPT_, GS = GS_;
@@ -81,18 +82,19 @@ struct LineCfg {
     static constexpr int E = N * W * LB;
     static constexpr int T = E / EPT;
     static constexpr int NG = (L + GS - 1) / GS;
-    static_assert(GS == 4 || (GS == 5 && EPT == 32), "groups of 4 stages, or 5 with 32 values");
+    static_assert(GS == 4 || (GS == 5 && EPT == 32) || (GS == 6 && EPT == 64),
+                  "groups of 4 stages, 5 with 32 values a thread or 6 with 64");
     // lanes of a half-warp that are not spent on the interleave index
     static constexpr int K = KW >= 4 ? 0 : 4 - KW;
     static constexpr bool SWZ = K > 0 && L >= 2 * K;
     static constexpr int SMEM_BYTES = NG > 1 ? E * 8 : 0;
     // resident CTAs per SM asked of the register allocator: 64 registers a
-    // thread with 16 values, 128 with 32
-    static constexpr int REGS = EPT == 16 ? 64 : 128;
+    // thread with 16 values, 128 with 32, up to 255 with 64
+    static constexpr int REGS = EPT == 16 ? 64 : (EPT == 32 ? 128 : 255);
     static constexpr int MINB = 65536 / (T * REGS) > 0 ? 65536 / (T * REGS) : 1;
     static_assert(L >= 1 && L <= 14, "line length out of range");
     static_assert(E >= EPT, "CTA must hold at least one thread's values");
-    static_assert(EPT == 16 || EPT == 32, "16 or 32 values per thread");
+    static_assert(EPT == 16 || EPT == 32 || EPT == 64, "16, 32 or 64 values per thread");
 };
 
 // A group of G consecutive stages S0+1 .. S0+G (bits [S0, S0 + G) of p) on
@@ -827,6 +829,44 @@ __device__ __forceinline__ void group_last_finish_hybrid(float2 (&a)[C::EPT], fl
     }
 }
 
+// ... or, with one unit a thread (groups of 6 stages, 64 values a thread:
+// the last group's unit holds rows lo + r 2^S0, r < R), split the unit by
+// its values: rows [0, N/2) (r < R/2) go out through the staging buffer and
+// one TMA store (box W x 256 x N/512 of the load map's shape, rows 0 ..
+// N/2-1 of the tile), rows [N/2, N) straight from registers.
+template <class C, bool TWS = false>
+__device__ __forceinline__ void group_last_finish_rowhalf(float2 (&a)[C::EPT], float2 *stage,
+                                                          const CUtensorMap *omap, int c0,
+                                                          float2 *out, long long ld,
+                                                          const float2 *__restrict__ tw,
+                                                          float scale, int nst)
+{
+    using Gp = Grp<C, C::NG - 1>;
+    constexpr int S0 = Gp::S0;
+    static_assert(Gp::V == 1 && Gp::HB == 0 && C::LB == 1, "one unit a thread, the last group");
+    const int tid = threadIdx.x;
+    const int w = tid & (C::W - 1);
+    const int lo = (tid >> C::KW) & ((1 << S0) - 1);
+    run_stages<C, C::NG - 1, false, TWS>(a, 0, lo, tw, nst);
+#pragma unroll
+    for (int r = 0; r < Gp::R / 2; r++) {
+        const float2 x = a[r];
+        stage[((r << S0) | lo) * C::W + w] = make_float2(x.x * scale, x.y * scale);
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+        tma_store_3d(omap, c0, 0, 0, stage);   // rows 0 .. N/2-1
+        bulk_commit();
+    }
+    float2 *dst = out + (long long)lo * ld + w;
+#pragma unroll
+    for (int r = Gp::R / 2; r < Gp::R; r++) {
+        const float2 x = a[r];
+        st_stream(dst + (long long)(r << S0) * ld, make_float2(x.x * scale, x.y * scale));
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Persistent row pass fed by TMA bulk copies, double buffered: while a CTA
 // transforms its current block of LB rows in one shared-memory buffer, the
@@ -1105,7 +1145,11 @@ __device__ __forceinline__ void col_tma2_body(const Src &src, int ntiles,
         __syncthreads();   // the tile region is free
         if (tid == 0 && next < ntiles)
             split_issue_late<C>(sm, src.tmap(next), src.col(next), &bar_late);
-        if constexpr (TS && HYB)
+        if constexpr (TS && HYB && Grp<C, C::NG - 1>::V == 1)
+            group_last_finish_rowhalf<C, true>(a, sm + C::E / 2, src.omap(tile), src.col(tile),
+                                               src.dst(tile), src.pitch(tile), stw, src.scl(tile),
+                                               C::L);
+        else if constexpr (TS && HYB)
             group_last_finish_hybrid<C, true>(a, sm + C::E / 2, src.omap(tile), src.col(tile),
                                               src.dst(tile), src.pitch(tile), stw, src.scl(tile),
                                               C::L);

@@ -342,7 +342,8 @@ def test_unaligned_buffers_take_the_plain_path(env):
         fft.fft2d_destroy(plan)
 
 
-@pytest.mark.parametrize("rows,variant", [(4096, "tma32"), (4096, "tmem"), (8192, "pair"),
+@pytest.mark.parametrize("rows,variant", [(4096, "tma32"), (4096, "tmem"), (4096, "tma64"),
+                                          (8192, "pair"),
                                           (16384, "quad"), (8192, "pairl2"), (16384, "quadl2")])
 def test_withheld_tma_load_times_out_cleanly(env, rows, variant):
     """Failure path of the persistent TMA-fed column kernels: CTA 0 never
