@@ -8,6 +8,8 @@
 // parameter; each CTA finds its image by binary search over the table's CTA
 // offsets and then runs exactly the per-CTA work of the single-image kernels,
 // so a batched image is bit-for-bit the image transformed alone.
+#include <type_traits>
+
 #include "line_fft.cuh"
 #include "passes.h"
 
@@ -129,14 +131,18 @@ cudaError_t batch_launch_tma(const BatchTable &t, int *err, cudaStream_t s, bool
     static thread_local BatchTmaTable tt;
     if (t.n > kBatchTmaMaxJobs || !err || (reinterpret_cast<uintptr_t>(t.job[0].tw) & 15))
         return cudaSuccess;
+    // one unit a thread (groups of 6 stages): the half of each tile that
+    // leaves by TMA is its first N/2 rows, one box of the load map's shape
+    constexpr bool ROWHALF = Grp<C, C::NG - 1>::V == 1;
     int tiles = 0;
     for (int i = 0; i < t.n; i++) {
         const BatchJob &j = t.job[i];
         if (j.lines % C::W != 0 ||
             !encode_col_map(&tt.map[i], j.in, C::N, j.lines, j.ld, C::W, TmaSplit<C>::BOX,
                             TmaSplit<C>::NB) ||
-            !encode_col_map(&tt.omap[i], j.out, C::N, j.lines, j.ld, C::W, tma_store_rows(C::L),
-                            TmaSplit<C>::NBOX))
+            !encode_col_map(&tt.omap[i], j.out, C::N, j.lines, j.ld, C::W,
+                            ROWHALF ? TmaSplit<C>::BOX : tma_store_rows(C::L),
+                            ROWHALF ? TmaSplit<C>::NB : TmaSplit<C>::NBOX))
             return cudaSuccess;
         tt.out[i] = j.out;
         tt.ld[i] = j.ld;
@@ -150,7 +156,7 @@ cudaError_t batch_launch_tma(const BatchTable &t, int *err, cudaStream_t s, bool
         *used = true;
         return cudaSuccess;
     }
-    constexpr bool TS = MODE != 1 && tma_store_ok<C>();
+    constexpr bool TS = ROWHALF ? MODE == 2 : (MODE != 1 && tma_store_ok<C>());
     auto k = col_tma2_batch_kernel<C, TS, TS && MODE == 2>;
     constexpr int SMEM = TmaSplit<C>::SMEM_BYTES;
     constexpr int kMaxDev = 64;
@@ -185,10 +191,13 @@ cudaError_t batch_dispatch(bool row, BatchTable &t, int variant, int *err, cudaS
     if constexpr (L >= 9 && L <= 12) {
         if (variant >= 2 && variant <= 4) {
             using C = LineCfg<L, col_kw(L), 0, col_tma_ept(L)>;
+            // half of each: 4096 rows in two groups of 6 stages, as the
+            // single-image default
+            using CH = typename std::conditional<L == 12, LineCfg<L, col_kw(L), 0, 64, 6>, C>::type;
             bool used = false;
             cudaError_t e = variant == 2   ? batch_launch_tma<C, 0>(t, err, s, &used)
                             : variant == 3 ? batch_launch_tma<C, 1>(t, err, s, &used)
-                                           : batch_launch_tma<C, 2>(t, err, s, &used);
+                                           : batch_launch_tma<CH, 2>(t, err, s, &used);
             if (e != cudaSuccess || used)
                 return e;
         }

@@ -2,7 +2,8 @@
 // power-of-two exponent per line, FP32 arithmetic).
 //
 // The arithmetic is the FP32 column engine's (a tile of W = 4 whole columns
-// of 2^L rows, 512 threads x 32 values, three groups of radix-2 DIT stages,
+// of 2^L rows; 256 threads x 64 values in two groups of radix-2 DIT stages,
+// or 512 x 32 in three,
 // Section 2 eqs. 2-3 / Section 3.1 eq. 4, the scramble of Section 3.2 fused
 // into the first read), so the results are those of the complex64 column
 // pass on the dequantised input, rounded once to half precision at the end.
@@ -46,8 +47,10 @@ struct H16Col {
     static constexpr int RF_OFF = TW_OFF + (int)TW_BYTES;         // 2^e of every image row
     static constexpr int SMEM_BYTES = RF_OFF + C::N * 4;
     static constexpr int STAGE_OFF = X_BYTES / 2;           // finished half2 tile
-    static_assert(C::W == 4 && C::EPT == 32 && C::NG == 3 && C::LB == 1,
-                  "4-column tiles, 512 threads x 32 values, three stage groups");
+    static_assert(C::W == 4 && C::LB == 1 &&
+                      ((C::EPT == 32 && C::NG == 3) || (C::EPT == 64 && C::NG == 2)),
+                  "4-column tiles; 512 threads x 32 values in three stage groups or 256 x 64 "
+                  "in two");
     static_assert(NB >= 1 && 2 * NB == NBOX, "two equal halves of whole blocks");
     static_assert(LATE_BYTES <= (uint32_t)STAGE_OFF, "the late half and the staging never overlap");
     static_assert(STAGE_OFF + C::E * 4 <= X_BYTES, "the staging fits in the exchange region");
@@ -159,8 +162,10 @@ __global__ void __launch_bounds__(C::T, 1) col_h16_tma_kernel(const __grid_const
                 sm[sidx<C>(0, r | (hi << G0::G), w)] = a[v * G0::R + r];
         }
         __syncthreads();
-        group_smem<C, 1, false, false, true>(a, sm, stw, C::L);
-        __syncthreads();
+        if constexpr (C::NG >= 3) {
+            group_smem<C, 1, false, false, true>(a, sm, stw, C::L);
+            __syncthreads();
+        }
         group_last_read<C>(a, sm);
         fence_proxy_async_smem();
         __syncthreads();   // the exchange region is free

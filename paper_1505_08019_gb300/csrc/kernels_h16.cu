@@ -75,7 +75,7 @@ bool encode_h16_col_map(CUtensorMap *map, const __half2 *base, int rows, int col
 template <int L>
 cudaError_t h16_launch_col_tma(const H16PassArgs &a, cudaStream_t s)
 {
-    using C = LineCfg<L, 2, 0, 32>;
+    using C = LineCfg<L, 2, 0, 64, 6>;   // two groups of 6 stages, as the complex64 pass
     using H = H16Col<C>;
     if (a.in_axis != 0 || a.nst != L || !a.err || a.cols % C::W != 0 ||
         (reinterpret_cast<uintptr_t>(a.tw) & 15))
