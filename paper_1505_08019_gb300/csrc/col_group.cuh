@@ -85,17 +85,20 @@ struct GroupCol {
     static constexpr int CS = 1 << CL;
     static constexpr int L = C::L;                        // local stages
     static constexpr int NL = C::N;                       // rows held by one CTA
-    static constexpr int XVALS = 16;                      // values exchanged per thread per round
+    static constexpr int XVALS = C::EPT / 2;              // values exchanged per thread per round
     static constexpr uint32_t XBYTES = (uint32_t)XVALS * C::T * 8u;   // per CTA per round
     static constexpr int KEEP_R = Gl::R >> CL;            // register indices r kept at the end
     static constexpr int OUT_ROWS = NL / CS;              // rows k of one CTA's output range
     static constexpr int OUT_BOX_Z = OUT_ROWS / S::BOX;   // 256-row blocks of one range
     static constexpr int STAGE_T = (C::E / 2) / (OUT_ROWS * C::W);   // ranges per staging fill
+    // values a thread keeps per output t at the end (all its units)
+    static constexpr int KEEP_V = Gl::V * KEEP_R;
     // scratch of the L2 exchange per cluster (col_group_l2_kernel): two
-    // tiles' slots, CS XVALS T values (pair) or CS^2 2 KEEP_R T (four CTAs)
+    // tiles' slots, CS XVALS T values (pair) or CS^2 KEEP_V T (four CTAs)
     static constexpr long long L2_SCRATCH_VALS =
-        CL == 2 ? 2LL * CS * CS * 2 * KEEP_R * C::T : 2LL * CS * XVALS * C::T;
-    static_assert(C::EPT == 32 && C::NG == 3 && C::LB == 1, "512 threads x 32 values, 3 groups");
+        CL == 2 ? 2LL * CS * CS * KEEP_V * C::T : 2LL * CS * XVALS * C::T;
+    static_assert(C::LB == 1 && ((C::EPT == 32 && C::NG == 3) || (C::EPT == 64 && C::NG == 2)),
+                  "512 threads x 32 values in 3 groups, or 256 x 64 in 2");
     static_assert(CL >= 1 && CL <= 2, "two or four CTAs");
     static_assert(Gl::S0 + Gl::G == L && (NL >> Gl::S0) == Gl::R,
                   "the last group's register index is the top bits of k");
@@ -171,8 +174,8 @@ __device__ __forceinline__ void group_round_send(const float2 (&s)[32], float2 *
 // Rotation factors of round J for the kept half: W_{2^(L+J+1)}^i with
 // i = k + 2^L t, read from the plan's table (stage L+J+1 starts at entry
 // 2^(L+J) - 1), k = lo_v + 2^S0 r for the kept r.
-template <class C, int J>
-__device__ __forceinline__ void group_round_twiddles(float2 (&wk)[16],
+template <class C, int J, int NW>
+__device__ __forceinline__ void group_round_twiddles(float2 (&wk)[NW],
                                                      const float2 *__restrict__ tw, int rk)
 {
     using Gl = Grp<C, C::NG - 1>;
@@ -197,13 +200,14 @@ __device__ __forceinline__ void group_round_twiddles(float2 (&wk)[16],
 
 // The same two steps of round J with the exchanged values in global memory:
 // slot j of this thread at at(j), written and read through L2 only.
-template <class C, int J, class At>
-__device__ __forceinline__ void group_round_send_g(const float2 (&s)[32], At at, int bitj)
+template <class C, int J, class At, int NA>
+__device__ __forceinline__ void group_round_send_g(const float2 (&s)[NA], At at, int bitj)
 {
     using Gl = Grp<C, C::NG - 1>;
     constexpr int NT = 1 << J;
     constexpr int NK = Gl::R >> J;
     constexpr int NH = NK / 2;
+    static_assert(NA == C::EPT, "a thread's values");
 #pragma unroll
     for (int t = 0; t < NT; t++) {
 #pragma unroll
@@ -211,23 +215,24 @@ __device__ __forceinline__ void group_round_send_g(const float2 (&s)[32], At at,
 #pragma unroll
             for (int ih = 0; ih < NH; ih++) {
                 const int j = (t * Gl::V + v) * NH + ih;
-                const float2 lo_half = s[t * 2 * NK + v * NK + ih];
-                const float2 hi_half = s[t * 2 * NK + v * NK + NH + ih];
+                const float2 lo_half = s[(t * Gl::V + v) * NK + ih];
+                const float2 hi_half = s[(t * Gl::V + v) * NK + NH + ih];
                 __stcg(at(j), bitj == 0 ? hi_half : lo_half);
             }
         }
     }
 }
 
-template <class C, int J, class At>
-__device__ __forceinline__ void group_round_compute_g(float2 (&s)[32], At at,
-                                                      const float2 (&wk)[16], int bitj)
+template <class C, int J, class At, int NA, int NW>
+__device__ __forceinline__ void group_round_compute_g(float2 (&s)[NA], At at,
+                                                      const float2 (&wk)[NW], int bitj)
 {
     using Gl = Grp<C, C::NG - 1>;
     constexpr int NT = 1 << J;
     constexpr int NK = Gl::R >> J;
     constexpr int NH = NK / 2;
-    float2 n[32];
+    static_assert(NA == C::EPT && NW >= NT * Gl::V * NH, "a thread's values and factors");
+    float2 n[NA];
 #pragma unroll
     for (int t = 0; t < NT; t++) {
 #pragma unroll
@@ -235,20 +240,20 @@ __device__ __forceinline__ void group_round_compute_g(float2 (&s)[32], At at,
 #pragma unroll
             for (int ih = 0; ih < NH; ih++) {
                 const int j = (t * Gl::V + v) * NH + ih;
-                const float2 lo_half = s[t * 2 * NK + v * NK + ih];
-                const float2 hi_half = s[t * 2 * NK + v * NK + NH + ih];
+                const float2 lo_half = s[(t * Gl::V + v) * NK + ih];
+                const float2 hi_half = s[(t * Gl::V + v) * NK + NH + ih];
                 const float2 mine = bitj == 0 ? lo_half : hi_half;
                 const float2 theirs = __ldcg(at(j));
                 float2 x0 = bitj == 0 ? mine : theirs;
                 float2 x1 = bitj == 0 ? theirs : mine;
                 butterfly_w(x0, x1, wk[j]);
-                n[t * 2 * NH + v * NH + ih] = x0;
-                n[(t + NT) * 2 * NH + v * NH + ih] = x1;
+                n[(t * Gl::V + v) * NH + ih] = x0;                 // output t
+                n[((t + NT) * Gl::V + v) * NH + ih] = x1;          // output t + 2^J
             }
         }
     }
 #pragma unroll
-    for (int i = 0; i < 32; i++)
+    for (int i = 0; i < NA; i++)
         s[i] = n[i];
 }
 
@@ -600,7 +605,7 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
     // four CTAs exchange once per tile (both cross stages, radix 4); slots
     // [tile parity][source][destination][2 KEEP_R values][T]
     constexpr bool R4 = CL == 2;
-    constexpr int R4V = 2 * GC::KEEP_R;                   // values per source and destination
+    constexpr int R4V = GC::KEEP_V;                       // values per source and destination
     float2 *xb = xbuf + (long long)cid * GC::L2_SCRATCH_VALS + tid;
     int rk_end = 0;
 #pragma unroll
@@ -709,8 +714,10 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
             if (next < ntiles)
                 n_early++;
             __syncthreads();
-            group_smem<C, 1, false, false, true>(a, sm, stw, C::L);
-            __syncthreads();
+            if constexpr (C::NG >= 3) {
+                group_smem<C, 1, false, false, true>(a, sm, stw, C::L);
+                __syncthreads();
+            }
             group_last_read<C>(a, sm);
             fence_proxy_async_smem();
             __syncthreads();   // the tile region is free: the next tile's second half
@@ -726,15 +733,16 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
             }
             if constexpr (R4) {
                 // value r of unit v goes to the CTA whose final rows hold k's
-                // top bits r: p = bit 3 of r | bit 2 of r << 1
+                // top bits r: p = bit G-1 of r | bit G-2 of r << 1
                 float2 *src = xb + par * (CS * CS * R4V * C::T) + q * (CS * R4V * C::T);
 #pragma unroll
                 for (int v = 0; v < Gl::V; v++) {
 #pragma unroll
                     for (int r = 0; r < Gl::R; r++) {
-                        const int p = ((r >> 3) & 1) | (((r >> 2) & 1) << 1);
+                        const int p = ((r >> (Gl::G - 1)) & 1) | (((r >> (Gl::G - 2)) & 1) << 1);
                         if (p != q)
-                            __stcg(src + (p * R4V + v * GC::KEEP_R + (r & 3)) * C::T,
+                            __stcg(src + (p * R4V + v * GC::KEEP_R + (r & (GC::KEEP_R - 1))) *
+                                             C::T,
                                    a[v * Gl::R + r]);
                     }
                 }
@@ -745,9 +753,9 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
         }
         // round 0 barrier: the flags and the values given away are visible
         cluster_arrive_release();
-        float2 wk[16];
+        float2 wk[R4 ? 2 * R4V : GC::XVALS];
         if constexpr (R4) {
-            // stage L+1 and L+2 factors of this CTA's 2 x KEEP_R rows k
+            // stage L+1 and L+2 factors of this CTA's V x KEEP_R rows k
 #pragma unroll
             for (int v = 0; v < Gl::V; v++) {
                 const int u = tid + v * C::T;
@@ -787,8 +795,11 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
 #pragma unroll
                 for (int i = 0; i < GC::KEEP_R; i++) {
                     const int jj = v * GC::KEEP_R + i;
-                    const float2 o0 = a[v * Gl::R + 0 + i], o1 = a[v * Gl::R + 8 + i];
-                    const float2 o2 = a[v * Gl::R + 4 + i], o3 = a[v * Gl::R + 12 + i];
+                    // this CTA's own rows: r = rk_end + i, rk_end = (q & 1) R/2 + (q >> 1) R/4
+                    const float2 o0 = a[v * Gl::R + 0 * (Gl::R / 4) + i];
+                    const float2 o1 = a[v * Gl::R + 2 * (Gl::R / 4) + i];
+                    const float2 o2 = a[v * Gl::R + 1 * (Gl::R / 4) + i];
+                    const float2 o3 = a[v * Gl::R + 3 * (Gl::R / 4) + i];
                     const float2 own = q == 0 ? o0 : q == 1 ? o1 : q == 2 ? o2 : o3;
 #pragma unroll
                     for (int t = 0; t < CS; t++)
@@ -818,7 +829,7 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
             // same exponent per column and stages all its ranges as half2
             float m = 0.f;
 #pragma unroll
-            for (int i = 0; i < 32; i++)
+            for (int i = 0; i < C::EPT; i++)
                 m = fmaxf(m, fmaxf(fabsf(a[i].x), fabsf(a[i].y)));
             m = warp_line_max<C::KW, 5>(m);
             if ((tid & (31 & ~(C::W - 1))) == 0)
@@ -849,7 +860,7 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
                     const int lo = (u >> C::KW) & ((1 << Gl::S0) - 1);
 #pragma unroll
                     for (int i = 0; i < GC::KEEP_R; i++) {
-                        const float2 x = a[t * 2 * GC::KEEP_R + v * GC::KEEP_R + i];
+                        const float2 x = a[(t * Gl::V + v) * GC::KEEP_R + i];
                         hst[(t * GC::OUT_ROWS + ((i << Gl::S0) | lo)) * C::W + w] =
                             __floats2half2_rn(x.x * f, x.y * f);
                     }
@@ -888,7 +899,7 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
                     const int lo = (u >> C::KW) & ((1 << Gl::S0) - 1);
 #pragma unroll
                     for (int i = 0; i < GC::KEEP_R; i++) {
-                        const float2 x = a[t * 2 * GC::KEEP_R + v * GC::KEEP_R + i];
+                        const float2 x = a[(t * Gl::V + v) * GC::KEEP_R + i];
                         stage[(ts * GC::OUT_ROWS + ((i << Gl::S0) | lo)) * C::W + w] =
                             make_float2(x.x * scale, x.y * scale);
                     }

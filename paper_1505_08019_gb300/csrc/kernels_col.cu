@@ -366,6 +366,7 @@ struct ColVariants {
     static constexpr bool HASTMA = L >= 9 && L <= 12;
     static constexpr bool HASTMEM = HASTMA && col_tma_ept(L) == 32;
     using PairLocal = LineCfg<12, 2, 0, 32>;
+    using PairLocal6 = LineCfg<12, 2, 0, 64, 6>;
     using Tma32 = LineCfg<L, col_kw(L), 0, col_tma_ept(L)>;
     using Tma16 = LineCfg<L, col_kw(L), 0, 16>;
     using Tma64 = LineCfg<L, col_kw(L), 0, 64, 6>;
@@ -434,14 +435,15 @@ struct ColVariants {
         if constexpr (L == 14)
             t.v[t.n++] = {"quad", PairLocal::W, 32, col_group_usable<PairLocal, 2>,
                           col_launch_group<PairLocal, 2>, true};
-        // the same with the exchange through L2 (a scratch buffer); four
-        // CTAs in one radix-4 round
+        // the same with the exchange through L2 (a scratch buffer; four CTAs
+        // in one radix-4 round) and the local engine in two groups of 6
+        // stages (256 threads x 64 values)
         if constexpr (L == 13)
-            t.v[t.n++] = {"pairl2", PairLocal::W, 32, col_group_usable<PairLocal, 1>,
-                          col_launch_group_l2<PairLocal, 1>, true};
+            t.v[t.n++] = {"pairl2", PairLocal6::W, 64, col_group_usable<PairLocal6, 1>,
+                          col_launch_group_l2<PairLocal6, 1>, true};
         if constexpr (L == 14)
-            t.v[t.n++] = {"quadl2", PairLocal::W, 32, col_group_usable<PairLocal, 2>,
-                          col_launch_group_l2<PairLocal, 2>, true};
+            t.v[t.n++] = {"quadl2", PairLocal6::W, 64, col_group_usable<PairLocal6, 2>,
+                          col_launch_group_l2<PairLocal6, 2>, true};
         return t;
     }
     static const Variant *table(int *n)
@@ -473,9 +475,9 @@ struct ColVariants {
         else if constexpr (L == 12)
             return index_of("tma64");     // 61.8 vs 66.0 us for "tma32h" at 4096^2
         else if constexpr (L == 13)
-            return index_of("pairl2");    // 4-column tiles over a CTA pair (0.327 vs 0.334 ms for "pair")
+            return index_of("pairl2");    // 4-column tiles over a CTA pair (0.316 vs 0.334 ms for "pair")
         else if constexpr (L == 14)
-            return index_of("quadl2");    // 4-column tiles over 4 CTAs (1.64 vs 1.83 ms for "quad")
+            return index_of("quadl2");    // 4-column tiles over 4 CTAs (1.24 vs 1.83 ms for "quad")
         else
             return 0;
     }
