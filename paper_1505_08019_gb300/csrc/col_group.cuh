@@ -556,11 +556,24 @@ __global__ void __launch_bounds__(C::T, 1) col_group_kernel(const __grid_constan
 // The "lost" flags alternate per tile for the same reason.  xbuf: per
 // cluster of the launch, 2 CS XVALS T values (pair) or 2 CS^2 2 KEEP_R T
 // (four CTAs), cluster-major; it belongs to this launch alone.
-template <class C, int CL, bool H16>
+// DCT: the forward DCT-II of real columns (Section 5's similar transforms;
+// the reduction of a length-N DCT-II to a length-N complex DFT of the
+// reordered line v[j] = x[2j], v[N-1-j] = x[2j+1], X[k] = Re(e^{-i pi k /
+// (2N)} V[k]), Makhoul 1980), one complex line per real column, imaginary
+// part zero: no pairing of outputs (k, N-k) is needed.  A tile is W real
+// columns; CTA q's local line u[m] = v[CS m + rev(q)] is, for m < NL/2, the
+// rows 2 CS m + 2 rev(q) (lmap) and for m >= NL/2 the rows
+// 2 CS (NL-1-m) + 2 CS - 1 - 2 rev(q) read backwards (lmap2: ascending rows
+// 2 CS m' + 2 CS - 1 - 2 rev(q)); both maps have 2-float (8-byte) elements,
+// W/2 per box row.  The outputs X[k] (post = (cos, sin)(pi k / (2N)),
+// k <= N/2) leave as floats through the real output map omap.
+template <class C, int CL, bool H16, bool DCT = false>
 __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const CUtensorMap *omap,
                                                   int ntiles, const float2 *__restrict__ tw,
                                                   float scale, int *err, int withhold,
-                                                  float2 *xbuf, const GroupIO &io)
+                                                  float2 *xbuf, const GroupIO &io,
+                                                  const CUtensorMap *lmap2 = nullptr,
+                                                  const float2 *__restrict__ post = nullptr)
 {
     namespace cg = cooperative_groups;
     using S = TmaSplit<C>;
@@ -585,9 +598,14 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
     float *rf = reinterpret_cast<float *>(smb + GH::RF_OFF);
     const uint32_t tw_bytes = H16 ? (uint32_t)C::N * 8u : S::TW_BYTES;
     float2 *stage = sm + C::E / 2;
+    static_assert(!(H16 && DCT), "one storage mode");
+    constexpr uint32_t DCT_HALF_BYTES = (uint32_t)(C::N / 2) * C::W * 4u;   // floats
     // the first and second half of a tile's TMA boxes
     auto issue_early = [&](int t) {
-        if constexpr (H16) {
+        if constexpr (DCT) {
+            mbar_arrive_expect_tx(&bar_early, DCT_HALF_BYTES);
+            tma_load_3d(sm + C::E, lmap, t * (C::W / 2), 0, 0, &bar_early);
+        } else if constexpr (H16) {
             mbar_arrive_expect_tx(&bar_early, GH::HALF_BYTES);
             tma_load_3d(smb + GH::PREF_OFF, lmap, t * C::W, 0, 0, &bar_early);
         } else {
@@ -595,7 +613,10 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
         }
     };
     auto issue_late = [&](int t) {
-        if constexpr (H16) {
+        if constexpr (DCT) {
+            mbar_arrive_expect_tx(&bar_late, DCT_HALF_BYTES);
+            tma_load_3d(sm, lmap2, t * (C::W / 2), 0, 0, &bar_late);
+        } else if constexpr (H16) {
             mbar_arrive_expect_tx(&bar_late, GH::HALF_BYTES);
             tma_load_3d(smb, lmap, t * C::W, 0, GH::NB, &bar_late);
         } else {
@@ -658,7 +679,45 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
         if (!lost_here) {
             w_early++;
             w_late++;
-            if constexpr (H16) {
+            if constexpr (DCT) {
+                // group 0: scrambled gather of the reordered real columns
+                // (the second half of the local line read backwards), as
+                // complex values with imaginary part zero
+                const float *pref = reinterpret_cast<const float *>(sm + C::E);
+                const float *late = reinterpret_cast<const float *>(sm);
+#pragma unroll
+                for (int v = 0; v < G0::V; v++) {
+                    const int u = tid + v * C::T;
+                    const int w = u & (C::W - 1);
+                    const int hib = (u >> C::KW) & ((1 << G0::HB) - 1);
+#pragma unroll
+                    for (int r = 0; r < G0::R; r++) {
+                        const int top = brev_c(r, G0::G) << G0::HB;   // compile-time
+                        const float x = top < C::N / 2 ? pref[(top | hib) * C::W + w]
+                                                       : late[(C::N - 1 - (top | hib)) * C::W + w];
+                        a[v * G0::R + r] = make_float2(x, 0.f);
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < G0::V; v++)
+                    run_stages<C, 0, false, true>(a, v, 0, stw, C::L);
+                fence_proxy_async_smem();
+                if (tid == 0)
+                    bulk_wait_read_all();   // the previous tile's stores have read it
+                __syncthreads();            // every slot of both input regions has been read
+                if (tid == 0 && next < ntiles)
+                    issue_early(next);
+#pragma unroll
+                for (int v = 0; v < G0::V; v++) {
+                    const int u = tid + v * C::T;
+                    const int w = u & (C::W - 1);
+                    const int hib = (u >> C::KW) & ((1 << G0::HB) - 1);
+                    const int hi = brev_rt(hib, G0::HB);
+#pragma unroll
+                    for (int r = 0; r < G0::R; r++)
+                        sm[sidx<C>(0, r | (hi << G0::G), w)] = a[v * G0::R + r];
+                }
+            } else if constexpr (H16) {
                 // group 0: scrambled gather of the half2 tile, widened and
                 // scaled by the row factors
                 const __half2 *pref = reinterpret_cast<const __half2 *>(smb + GH::PREF_OFF);
@@ -822,6 +881,43 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
             const float2 *theirs = x0 + (q ^ 1) * XV;
             group_round_compute_g<C, 0>(a, [&](int j) { return theirs + j * C::T; }, wk, q & 1);
         }
+        if constexpr (DCT) {
+            // X[K] = cos(theta) Re V[K] + sin(theta) Im V[K], theta = pi K /
+            // (2N), K = k + 2^L t; (cos, sin) of K > N/2 is (sin, cos) of N - K
+            constexpr int NN = C::N << CL;
+            float *fst = reinterpret_cast<float *>(stage);
+#pragma unroll
+            for (int t = 0; t < CS; t++) {
+#pragma unroll
+                for (int v = 0; v < Gl::V; v++) {
+                    const int u = tid + v * C::T;
+                    const int w = u & (C::W - 1);
+                    const int lo = (u >> C::KW) & ((1 << Gl::S0) - 1);
+#pragma unroll
+                    for (int i = 0; i < GC::KEEP_R; i++) {
+                        const int row = (i << Gl::S0) | lo;
+                        const int K = (t << C::L) + k_base + row;
+                        const float2 cs = K <= NN / 2 ? __ldg(post + K) : __ldg(post + (NN - K));
+                        const float c = K <= NN / 2 ? cs.x : cs.y;
+                        const float sn = K <= NN / 2 ? cs.y : cs.x;
+                        const float2 z = a[(t * Gl::V + v) * GC::KEEP_R + i];
+                        fst[(t * GC::OUT_ROWS + row) * C::W + w] = (c * z.x + sn * z.y) * scale;
+                    }
+                }
+            }
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+#pragma unroll
+                for (int t = 0; t < CS; t++) {
+                    const int z = ((t << C::L) + k_base) / S::BOX;
+                    tma_store_3d(omap, tile * (C::W / 2), 0, z,
+                                 fst + t * GC::OUT_ROWS * C::W);
+                }
+                bulk_commit();
+            }
+            continue;
+        }
         if constexpr (H16) {
             // this CTA's part of each column's largest |component| (a
             // thread's values all belong to column tid mod W) to every CTA of
@@ -930,6 +1026,28 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
     }
     if (tid == 0)
         bulk_wait_all();   // shared memory stays valid until the stores are done
+}
+
+// The forward DCT-II column pass of real columns on the same kernel (DCT
+// mode above): per residue rev(q) a map of the ascending rows (first half of
+// the local line) and one of the rows read backwards (second half).
+struct DctL2Maps {
+    CUtensorMap early[4], late[4];
+    CUtensorMap out;
+};
+
+template <class C, int CL>
+__global__ void __launch_bounds__(C::T, 1) col_dct_l2_kernel(const __grid_constant__ DctL2Maps maps,
+                                                             const float2 *__restrict__ tw,
+                                                             const float2 *__restrict__ post,
+                                                             int ntiles, float scale, int *err,
+                                                             int withhold, float2 *xbuf)
+{
+    const int q = (int)cooperative_groups::this_cluster().block_rank();
+    const int res = brev_rt(q, CL);
+    col_group_l2_body<C, CL, false, true>(&maps.early[res], &maps.out, ntiles, tw, scale, err,
+                                          withhold, xbuf, GroupIO{nullptr, nullptr},
+                                          &maps.late[res], post);
 }
 
 template <class C, int CL, bool H16 = false>

@@ -85,14 +85,15 @@ def test_dct_small_shapes(env, rows, cols):
 @pytest.mark.parametrize("rows,cols", [(64, 256), (256, 64), (2, 1024), (1024, 2),
                                        (512, 512), (128, 2048), (1024, 1024),
                                        (2048, 64), (4096, 32), (2048, 8), (4096, 4),
-                                       (8192, 16), (8192, 4)])
+                                       (8192, 16), (8192, 4), (16384, 4)])
 def test_dct_whole_outputs(env, rows, cols):
     """Non-square and wide/tall images spanning several CTAs and a partly
     filled last CTA (2 rows: one complex line), whole outputs compared.
     Columns of 2048 and 4096 rows run on the TMA-fed column kernel when the
     image is at least two tiles wide (64 and 32 columns here) and on the
     plain kernel otherwise (8 and 4 columns); columns of 8192 rows on the
-    CTA-pair kernel (16 columns: two tiles) or the plain kernel (4)."""
+    CTA-pair kernel (16 columns: two tiles) or the plain kernel (4); forward
+    columns of 16384 rows on the four-CTA kernel (4 real columns: one tile)."""
     _, _, orc = env
     x = synth.gray_real(rows, cols, seed=7)
     err = rel(gpu_dct(env, x), orc.dct2d(x))
@@ -154,7 +155,7 @@ def test_dct_large_sampled(env, side, nsamp):
 @pytest.mark.parametrize("rows,cols,inplace", [(4096, 4096, False), (2048, 16384, False),
                                                (8192, 8192, False), (16384, 512, False),
                                                (4096, 64, False), (2048, 1024, True),
-                                               (4096, 8192, True)])
+                                               (4096, 8192, True), (16384, 256, True)])
 def test_dct_separable_full(env, rows, cols, inplace):
     """A separable image x[m][n] = f[m] g[n] (small integers: the products
     are exact in FP32) has X[k][l] = F[k] G[l] with F, G the 1D transforms
@@ -298,12 +299,13 @@ def test_dct_round_trip(env, rows, cols):
 
 
 @pytest.mark.parametrize("rows,inverse", [(4096, False), (2048, True), (8192, False),
-                                          (8192, True)])
+                                          (8192, True), (16384, False)])
 def test_dct_withheld_load_times_out_cleanly(env, rows, inverse):
     """Failure path of the TMA-fed DCT column kernels: CTA 0 never issues the
     second load of its first tile, its bounded wait gives up, the host reads
     FFT2D_ERR_TIMEOUT, and the same plan then transforms correctly (8192
-    rows: the CTA-pair kernel, both CTAs leave together)."""
+    rows: the CTA-pair kernel, both CTAs leave together; 16384 rows: the
+    four-CTA kernel, all four leave together)."""
     torch, fft, orc = env
     cols = 64
     plan = fft.fft2d_plan(rows, cols, fft.FFT2D_R32_DCT2,
