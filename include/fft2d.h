@@ -106,10 +106,10 @@ FFT2D_API fft2d_status fft2d_plan(int rows, int cols, int dtype, int dir, fft2d_
  * line (even samples ascending, odd samples descending) followed by a
  * rotation by exp(-i pi k / (2N)) (Makhoul, 1980); the inverse rotates
  * first, then runs the inverse DFT and undoes the reordering.  Two real
- * lines share one complex line, except in the forward column pass of 16384
- * rows, where each real column is its own complex line (imaginary part
- * zero) and the pass runs in place: called out of place it first copies
- * `in` to `out` on the stream.  The plan also holds the
+ * lines share one complex line, except in the column pass of 16384 rows
+ * (both directions), where each real column is its own complex line and the
+ * pass runs in place: called out of place it first copies `in` to `out` on
+ * the stream.  The plan also holds the
  * (cos, sin)(pi k / (2N)) tables, built in FP64 and rounded to FP32.
  * Errors: FFT2D_ERR_UNSUPPORTED for a side of 1.  The other entry points
  * reject these plans with FFT2D_ERR_ARG, except fft2d_exec_host,
@@ -141,8 +141,8 @@ FFT2D_API fft2d_status fft2d_selftest_timeout(fft2d_plan_t plan, void *stream);
  * transform into shared memory): runs the plan's column pass over `in` into
  * `out` (device images of the plan's shape and dtype, row pitch = cols;
  * for FFT2D_R32_DCT2 plans the DCT column pass of the plan's direction,
- * which is TMA-fed for columns of 2048, 4096 and 8192 points, and of 16384
- * points forward), except that CTA 0 never issues the second TMA load of its
+ * which is TMA-fed for columns of 2048 to 16384 points), except that CTA 0
+ * never issues the second TMA load of its
  * first tile.  That CTA's bounded wait gives up after about one second, the
  * kernel records the timeout -- for the cluster kernels of 8192- and
  * 16384-row columns every CTA of the cluster learns of it at the tile's
@@ -207,7 +207,7 @@ FFT2D_API fft2d_status fft2d_plan_info(fft2d_plan_t plan, int *rows, int *cols, 
  * Once the plan has run on its device (the first launch of each kernel sets
  * its shared-memory limit), the call may be captured in a CUDA graph on
  * `stream`.  It makes no allocation then, except that the column pass of
- * 8192 or 16384 rows (and the forward DCT column pass of 16384 rows) takes a
+ * 8192 or 16384 rows (and the DCT column pass of 16384 rows) takes a
  * scratch block (about 20 MB) for the exchange
  * between the CTAs of a cluster stream-ordered from the library's own
  * device memory pool and returns it on `stream` after the launch

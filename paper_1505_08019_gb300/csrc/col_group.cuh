@@ -567,13 +567,24 @@ __global__ void __launch_bounds__(C::T, 1) col_group_kernel(const __grid_constan
 // 2 CS m' + 2 CS - 1 - 2 rev(q)); both maps have 2-float (8-byte) elements,
 // W/2 per box row.  The outputs X[k] (post = (cos, sin)(pi k / (2N)),
 // k <= N/2) leave as floats through the real output map omap.
-template <class C, int CL, bool H16, bool DCT = false>
+//
+// DCT == 2: the inverse, DCT-III, of real columns, one real line per complex
+// line: V[k] = e^{i pi k / (2N)} (X[k] - i X[N-k]) (X[N] = 0), v = IDFT(V)
+// (the plan's conjugate rotation factors), x[2n] = v[n], x[2n+1] =
+// v[N-1-n].  CTA q's local line holds k = CS m + rev(q), the rows of that
+// residue (lmap, ascending); X[N-k] lies in the rows of residue
+// (CS - rev(q)) mod CS read backwards (lmap2): index NL-1-m, or (NL-m) mod
+// NL for residue 0, where m = 0 takes X[N] = 0.  Outputs n < N/2 go to the
+// even rows (omap: rows 2n'), the others in reverse order to the odd rows
+// (omap2: rows 2n'+1).
+template <class C, int CL, bool H16, int DCT = 0>
 __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const CUtensorMap *omap,
                                                   int ntiles, const float2 *__restrict__ tw,
                                                   float scale, int *err, int withhold,
                                                   float2 *xbuf, const GroupIO &io,
                                                   const CUtensorMap *lmap2 = nullptr,
-                                                  const float2 *__restrict__ post = nullptr)
+                                                  const float2 *__restrict__ post = nullptr,
+                                                  const CUtensorMap *omap2 = nullptr)
 {
     namespace cg = cooperative_groups;
     using S = TmaSplit<C>;
@@ -600,11 +611,18 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
     float2 *stage = sm + C::E / 2;
     static_assert(!(H16 && DCT), "one storage mode");
     constexpr uint32_t DCT_HALF_BYTES = (uint32_t)(C::N / 2) * C::W * 4u;   // floats
+    constexpr int DCT_HALF_FLOATS = (C::N / 2) * C::W;
     // the first and second half of a tile's TMA boxes
     auto issue_early = [&](int t) {
-        if constexpr (DCT) {
+        if constexpr (DCT == 1) {
             mbar_arrive_expect_tx(&bar_early, DCT_HALF_BYTES);
             tma_load_3d(sm + C::E, lmap, t * (C::W / 2), 0, 0, &bar_early);
+        } else if constexpr (DCT == 2) {
+            // first halves of the natural and the mirrored rows
+            float *pf = reinterpret_cast<float *>(sm + C::E);
+            mbar_arrive_expect_tx(&bar_early, 2 * DCT_HALF_BYTES);
+            tma_load_3d(pf, lmap, t * (C::W / 2), 0, 0, &bar_early);
+            tma_load_3d(pf + DCT_HALF_FLOATS, lmap2, t * (C::W / 2), 0, 0, &bar_early);
         } else if constexpr (H16) {
             mbar_arrive_expect_tx(&bar_early, GH::HALF_BYTES);
             tma_load_3d(smb + GH::PREF_OFF, lmap, t * C::W, 0, 0, &bar_early);
@@ -613,9 +631,15 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
         }
     };
     auto issue_late = [&](int t) {
-        if constexpr (DCT) {
+        if constexpr (DCT == 1) {
             mbar_arrive_expect_tx(&bar_late, DCT_HALF_BYTES);
             tma_load_3d(sm, lmap2, t * (C::W / 2), 0, 0, &bar_late);
+        } else if constexpr (DCT == 2) {
+            // second halves, at the start of the tile region
+            float *lf = reinterpret_cast<float *>(sm);
+            mbar_arrive_expect_tx(&bar_late, 2 * DCT_HALF_BYTES);
+            tma_load_3d(lf, lmap, t * (C::W / 2), 0, S::NB, &bar_late);
+            tma_load_3d(lf + DCT_HALF_FLOATS, lmap2, t * (C::W / 2), 0, S::NB, &bar_late);
         } else if constexpr (H16) {
             mbar_arrive_expect_tx(&bar_late, GH::HALF_BYTES);
             tma_load_3d(smb, lmap, t * C::W, 0, GH::NB, &bar_late);
@@ -679,7 +703,57 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
         if (!lost_here) {
             w_early++;
             w_late++;
-            if constexpr (DCT) {
+            if constexpr (DCT == 2) {
+                // group 0: scrambled gather of the spectrum rows k = CS i +
+                // res and their mirrors N - k, pre-rotated into V[k]
+                const int res = brev_rt(q, CL);
+                constexpr int NN = C::N << CL;
+                const float *pn = reinterpret_cast<const float *>(sm + C::E);
+                const float *pm = pn + DCT_HALF_FLOATS;
+                const float *ln = reinterpret_cast<const float *>(sm);
+                const float *lm = ln + DCT_HALF_FLOATS;
+#pragma unroll
+                for (int v = 0; v < G0::V; v++) {
+                    const int u = tid + v * C::T;
+                    const int w = u & (C::W - 1);
+                    const int hib = (u >> C::KW) & ((1 << G0::HB) - 1);
+#pragma unroll
+                    for (int r = 0; r < G0::R; r++) {
+                        const int top = brev_c(r, G0::G) << G0::HB;   // compile-time
+                        const int i = top | hib;
+                        const float xn = top < C::N / 2 ? pn[i * C::W + w]
+                                                        : ln[(i - C::N / 2) * C::W + w];
+                        const int j = res == 0 ? ((C::N - i) & (C::N - 1)) : C::N - 1 - i;
+                        float xm = j < C::N / 2 ? pm[j * C::W + w] : lm[(j - C::N / 2) * C::W + w];
+                        if (res == 0 && i == 0)
+                            xm = 0.f;   // X[N] = 0
+                        const int k = CS * i + res;
+                        const float2 cs = k <= NN / 2 ? __ldg(post + k) : __ldg(post + (NN - k));
+                        const float c = k <= NN / 2 ? cs.x : cs.y;
+                        const float sn = k <= NN / 2 ? cs.y : cs.x;
+                        a[v * G0::R + r] = make_float2(c * xn + sn * xm, sn * xn - c * xm);
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < G0::V; v++)
+                    run_stages<C, 0, false, true>(a, v, 0, stw, C::L);
+                fence_proxy_async_smem();
+                if (tid == 0)
+                    bulk_wait_read_all();   // the previous tile's stores have read it
+                __syncthreads();            // every slot of both input regions has been read
+                if (tid == 0 && next < ntiles)
+                    issue_early(next);
+#pragma unroll
+                for (int v = 0; v < G0::V; v++) {
+                    const int u = tid + v * C::T;
+                    const int w = u & (C::W - 1);
+                    const int hib = (u >> C::KW) & ((1 << G0::HB) - 1);
+                    const int hi = brev_rt(hib, G0::HB);
+#pragma unroll
+                    for (int r = 0; r < G0::R; r++)
+                        sm[sidx<C>(0, r | (hi << G0::G), w)] = a[v * G0::R + r];
+                }
+            } else if constexpr (DCT == 1) {
                 // group 0: scrambled gather of the reordered real columns
                 // (the second half of the local line read backwards), as
                 // complex values with imaginary part zero
@@ -881,7 +955,47 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
             const float2 *theirs = x0 + (q ^ 1) * XV;
             group_round_compute_g<C, 0>(a, [&](int j) { return theirs + j * C::T; }, wk, q & 1);
         }
-        if constexpr (DCT) {
+        if constexpr (DCT == 2) {
+            // x[2n] = Re v[n] (n < N/2, the even rows), x[2(N-1-n)+1] = Re
+            // v[n] (the odd rows, in reverse order within a range)
+            float *fst = reinterpret_cast<float *>(stage);
+#pragma unroll
+            for (int t = 0; t < CS; t++) {
+                const bool odd = t >= CS / 2;
+#pragma unroll
+                for (int v = 0; v < Gl::V; v++) {
+                    const int u = tid + v * C::T;
+                    const int w = u & (C::W - 1);
+                    const int lo = (u >> C::KW) & ((1 << Gl::S0) - 1);
+#pragma unroll
+                    for (int i = 0; i < GC::KEEP_R; i++) {
+                        const int row = (i << Gl::S0) | lo;
+                        const int slot = odd ? GC::OUT_ROWS - 1 - row : row;
+                        fst[(t * GC::OUT_ROWS + slot) * C::W + w] =
+                            a[(t * Gl::V + v) * GC::KEEP_R + i].x * scale;
+                    }
+                }
+            }
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                constexpr int NN = C::N << CL;
+#pragma unroll
+                for (int t = 0; t < CS; t++) {
+                    const int n0 = (t << C::L) + k_base;
+                    if (t < CS / 2)
+                        tma_store_3d(omap, tile * (C::W / 2), 0, n0 / S::BOX,
+                                     fst + t * GC::OUT_ROWS * C::W);
+                    else
+                        tma_store_3d(omap2, tile * (C::W / 2), 0,
+                                     (NN - n0 - GC::OUT_ROWS) / S::BOX,
+                                     fst + t * GC::OUT_ROWS * C::W);
+                }
+                bulk_commit();
+            }
+            continue;
+        }
+        if constexpr (DCT == 1) {
             // X[K] = cos(theta) Re V[K] + sin(theta) Im V[K], theta = pi K /
             // (2N), K = k + 2^L t; (cos, sin) of K > N/2 is (sin, cos) of N - K
             constexpr int NN = C::N << CL;
@@ -1045,9 +1159,32 @@ __global__ void __launch_bounds__(C::T, 1) col_dct_l2_kernel(const __grid_consta
 {
     const int q = (int)cooperative_groups::this_cluster().block_rank();
     const int res = brev_rt(q, CL);
-    col_group_l2_body<C, CL, false, true>(&maps.early[res], &maps.out, ntiles, tw, scale, err,
-                                          withhold, xbuf, GroupIO{nullptr, nullptr},
-                                          &maps.late[res], post);
+    col_group_l2_body<C, CL, false, 1>(&maps.early[res], &maps.out, ntiles, tw, scale, err,
+                                       withhold, xbuf, GroupIO{nullptr, nullptr}, &maps.late[res],
+                                       post);
+}
+
+// The inverse DCT-III column pass of real columns (DCT == 2 above): per
+// residue a map of its rows (the mirror of residue r is residue (CS-r) mod
+// CS), and store maps over the even and the odd rows of the output.
+struct IdctL2Maps {
+    CUtensorMap rows[4];
+    CUtensorMap even, odd;
+};
+
+template <class C, int CL>
+__global__ void __launch_bounds__(C::T, 1) col_idct_l2_kernel(const __grid_constant__ IdctL2Maps maps,
+                                                              const float2 *__restrict__ tw,
+                                                              const float2 *__restrict__ post,
+                                                              int ntiles, float scale, int *err,
+                                                              int withhold, float2 *xbuf)
+{
+    constexpr int CS = 1 << CL;
+    const int q = (int)cooperative_groups::this_cluster().block_rank();
+    const int res = brev_rt(q, CL);
+    col_group_l2_body<C, CL, false, 2>(&maps.rows[res], &maps.even, ntiles, tw, scale, err,
+                                       withhold, xbuf, GroupIO{nullptr, nullptr},
+                                       &maps.rows[(CS - res) & (CS - 1)], post, &maps.odd);
 }
 
 template <class C, int CL, bool H16 = false>

@@ -1342,6 +1342,80 @@ cudaError_t dct_col_quad_launch(const DctIO &din, const float2 *tw, const float2
     return e != cudaSuccess ? e : f;
 }
 
+// Inverse DCT columns of 16384 points on the same four-CTA kernel
+// (col_idct_l2_kernel, one real line per complex line), in place for the
+// same reason as the forward pass; cudaErrorNotSupported (nothing launched)
+// when the image does not allow it.
+cudaError_t idct_col_quad_launch(const DctIO &din, const float2 *tw, const float2 *post,
+                                 float scale, int *err, int withhold, cudaStream_t s)
+{
+    using C = LineCfg<12, 2, 0, 64, 6>;
+    using S = TmaSplit<C>;
+    using GC = GroupCol<C, 2>;
+    constexpr int CS = GC::CS;
+    const long long cc = din.cols / 2;   // 8-byte elements per row
+    if (!err || din.rows != (long long)CS * C::N || din.cols % C::W != 0 ||
+        (reinterpret_cast<uintptr_t>(din.in) & 15) || (reinterpret_cast<uintptr_t>(din.out) & 15) ||
+        (reinterpret_cast<uintptr_t>(tw) & 15) || !tensor_maps_available())
+        return cudaErrorNotSupported;
+    const DctIO d{din.out, din.out, din.rows, din.cols};
+    const float2 *in = reinterpret_cast<const float2 *>(d.in);
+    float2 *out = reinterpret_cast<float2 *>(d.out);
+    IdctL2Maps m;
+    for (int r = 0; r < CS; r++)
+        if (!encode_col_map(&m.rows[r], in + r * cc, C::N, (int)cc, CS * cc, C::W / 2, S::BOX,
+                            S::NB))
+            return cudaErrorNotSupported;
+    if (!encode_col_map(&m.even, out, (int)(d.rows / 2), (int)cc, 2 * cc, C::W / 2, S::BOX,
+                        GC::OUT_BOX_Z) ||
+        !encode_col_map(&m.odd, out + cc, (int)(d.rows / 2), (int)cc, 2 * cc, C::W / 2, S::BOX,
+                        GC::OUT_BOX_Z))
+        return cudaErrorNotSupported;
+    auto k = col_idct_l2_kernel<C, 2>;
+    constexpr int SMEM = S::SMEM_BYTES;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(C::T);
+    cfg.dynamicSmemBytes = SMEM;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    static DeviceCache groups;
+    const int dev = device_current();
+    if (!groups.get(dev)) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (e != cudaSuccess)
+            return e;
+        cfg.gridDim = dim3((unsigned)(CS * (device_sm_count() / CS)));
+        int n = 0;
+        e = cudaOccupancyMaxActiveClusters(&n, k, &cfg);
+        if (e != cudaSuccess)
+            return e;
+        groups.set(dev, n > 0 ? n : 1);
+    }
+    const int ntiles = (int)(d.cols / C::W);
+    const int ng = groups.get(dev) < ntiles ? groups.get(dev) : ntiles;
+    if (din.in != din.out) {
+        cudaError_t e = cudaMemcpyAsync(din.out, din.in, (size_t)(din.rows * din.cols) * sizeof(float),
+                                        cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess)
+            return e;
+    }
+    void *xbuf = nullptr;
+    cudaError_t e = scratch_take(&xbuf, (size_t)ng * GC::L2_SCRATCH_VALS * sizeof(float2), s);
+    if (e != cudaSuccess)
+        return e;
+    cfg.gridDim = dim3((unsigned)(CS * ng));
+    e = cudaLaunchKernelEx(&cfg, k, m, tw, post, ntiles, scale, err, withhold,
+                           static_cast<float2 *>(xbuf));
+    const cudaError_t f = cudaFreeAsync(xbuf, s);
+    return e != cudaSuccess ? e : f;
+}
+
 template <class C, bool ROW>
 cudaError_t dct_launch(const DctIO &d, const float2 *tw, const float2 *post, long long nlines,
                        float scale, cudaStream_t s)
@@ -2015,7 +2089,7 @@ cudaError_t dct_dispatch(bool row, bool inverse, const DctIO &d, const float2 *t
             return inverse ? idct_col_pair_launch(d, tw, post, scale, err, 1, s)
                            : dct_col_pair_launch(d, tw, post, scale, err, 1, s);
         if constexpr (L == 14)
-            return inverse ? cudaErrorNotSupported
+            return inverse ? idct_col_quad_launch(d, tw, post, scale, err, 1, s)
                            : dct_col_quad_launch(d, tw, post, scale, err, 1, s);
         return cudaErrorNotSupported;
     }
@@ -2034,6 +2108,11 @@ cudaError_t dct_dispatch(bool row, bool inverse, const DctIO &d, const float2 *t
         }
         if constexpr (L == 13) {
             const cudaError_t e = idct_col_pair_launch(d, tw, post, scale, err, 0, s);
+            if (e != cudaErrorNotSupported)
+                return e;
+        }
+        if constexpr (L == 14) {
+            const cudaError_t e = idct_col_quad_launch(d, tw, post, scale, err, 0, s);
             if (e != cudaErrorNotSupported)
                 return e;
         }

@@ -237,7 +237,7 @@ def test_idct_small_shapes(env, rows, cols):
 
 @pytest.mark.parametrize("rows,cols", [(64, 256), (256, 64), (2, 1024), (1024, 2),
                                        (512, 512), (2048, 64), (4096, 32), (128, 2048),
-                                       (8192, 16), (8192, 4)])
+                                       (8192, 16), (8192, 4), (16384, 4)])
 def test_idct_whole_outputs(env, rows, cols):
     _, _, orc = env
     X = synth.gray_real(rows, cols, seed=9) - np.float32(0.5)
@@ -273,7 +273,8 @@ def test_idct_in_place_and_passes(env):
 
 @pytest.mark.parametrize("rows,cols,inplace", [(4096, 4096, False), (2048, 16384, False),
                                                (8192, 8192, False), (16384, 512, False),
-                                               (2048, 1024, True), (4096, 8192, True)])
+                                               (2048, 1024, True), (4096, 8192, True),
+                                               (16384, 256, True)])
 def test_idct_separable_full(env, rows, cols, inplace):
     """Separable spectrum F[k] G[l] (small integers): the inverse is the outer
     product of the 1D inverses, every output checked."""
@@ -299,7 +300,7 @@ def test_dct_round_trip(env, rows, cols):
 
 
 @pytest.mark.parametrize("rows,inverse", [(4096, False), (2048, True), (8192, False),
-                                          (8192, True), (16384, False)])
+                                          (8192, True), (16384, False), (16384, True)])
 def test_dct_withheld_load_times_out_cleanly(env, rows, inverse):
     """Failure path of the TMA-fed DCT column kernels: CTA 0 never issues the
     second load of its first tile, its bounded wait gives up, the host reads
