@@ -194,9 +194,12 @@ cudaError_t batch_dispatch(bool row, BatchTable &t, int variant, int *err, cudaS
             // half of each: 4096 rows in two groups of 6 stages, as the
             // single-image default
             using CH = typename std::conditional<L == 12, LineCfg<L, col_kw(L), 0, 64, 6>, C>::type;
+            // per-thread stores: 2048 rows in two groups (6 + 5), as the
+            // single-image default
+            using CS = typename std::conditional<L == 11, LineCfg<L, col_kw(L), 0, 64, 6>, C>::type;
             bool used = false;
             cudaError_t e = variant == 2   ? batch_launch_tma<C, 0>(t, err, s, &used)
-                            : variant == 3 ? batch_launch_tma<C, 1>(t, err, s, &used)
+                            : variant == 3 ? batch_launch_tma<CS, 1>(t, err, s, &used)
                                            : batch_launch_tma<CH, 2>(t, err, s, &used);
             if (e != cudaSuccess || used)
                 return e;

@@ -426,6 +426,10 @@ struct ColVariants {
         if constexpr (L == 12)
             t.v[t.n++] = {"tma64", Tma64::W, 64, col_tma_usable<Tma64>,
                           col_launch_tma<Tma64, true, true>, true};
+        // 1024 and 2048 rows in two groups (6 + 4, 6 + 5), per-thread stores
+        if constexpr (L == 10 || L == 11)
+            t.v[t.n++] = {"tma64st", Tma64::W, 64, col_tma_usable<Tma64>,
+                          col_launch_tma<Tma64, false>, true};
         // 8192 and 16384 rows: 4-column tiles over a cluster of 2 or 4 CTAs,
         // the 4096-row engine on each CTA's rows and the last one or two
         // stages through bulk copies between the CTAs' shared memories
@@ -463,15 +467,14 @@ struct ColVariants {
     }
     // The default per column length, from timings of every variant on a
     // GB300 (512..4096 rows, square and 1:4 images): narrow tiles for 512 and
-    // 1024 rows, the TMA pass with per-thread stores for 2048, and for 4096
-    // the TMA pass in two groups of 6 stages with half TMA / half per-thread
-    // stores.
+    // 1024 rows; the TMA pass in two groups of 6 stages with per-thread
+    // stores for 2048, and with half TMA / half per-thread stores for 4096.
     static int preferred()
     {
         if constexpr (L == 9 || L == 10)
             return index_of("narrow");
         else if constexpr (L == 11)
-            return index_of("tma32st");
+            return index_of("tma64st");   // 20.7 vs 22.5 us for "tma32st" at 2048^2
         else if constexpr (L == 12)
             return index_of("tma64");     // 61.8 vs 66.0 us for "tma32h" at 4096^2
         else if constexpr (L == 13)
