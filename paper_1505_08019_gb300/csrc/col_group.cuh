@@ -76,8 +76,9 @@ __device__ __forceinline__ void bulk_copy_to_peer(uint32_t dst, const void *src,
         : "memory");
 }
 
-// Tile geometry of the group kernel for a local engine C (2^L rows, W
-// columns, 512 threads x 32 values) and a cluster of 2^CL CTAs.
+// Tile geometry of the group kernels for a local engine C (2^L rows, W
+// columns; 512 threads x 32 values in three stage groups, or 256 x 64 in
+// two) and a cluster of 2^CL CTAs.
 template <class C, int CL>
 struct GroupCol {
     using S = TmaSplit<C>;
@@ -544,7 +545,7 @@ __global__ void __launch_bounds__(C::T, 1) col_group_kernel(const __grid_constan
 // leaves through TMA stores from the staging half of the tile region.
 //
 // Four CTAs (c = 2) run both cross stages after a single exchange: CTA q
-// sends each partner p the values at p's final rows k (8 per thread) and
+// sends each partner p the values at p's final rows k (KEEP_V per thread) and
 // receives the three partners' values at its own, then runs stage L+1 on
 // the pairs of blocks (0, 1), (2, 3) and stage L+2 on (0, 2), (1, 3) in
 // registers -- the same butterflies on the same operands as two rounds of
@@ -554,9 +555,10 @@ __global__ void __launch_bounds__(C::T, 1) col_group_kernel(const __grid_constan
 // Slots alternate per tile: a slot is written again only after the next
 // tile's barrier, which every reader arrives at after its reads of the slot.
 // The "lost" flags alternate per tile for the same reason.  xbuf: per
-// cluster of the launch, 2 CS XVALS T values (pair) or 2 CS^2 2 KEEP_R T
+// cluster of the launch, 2 CS XVALS T values (pair) or 2 CS^2 KEEP_V T
 // (four CTAs), cluster-major; it belongs to this launch alone.
-// DCT: the forward DCT-II of real columns (Section 5's similar transforms;
+//
+// DCT == 1: the forward DCT-II of real columns (Section 5's similar transforms;
 // the reduction of a length-N DCT-II to a length-N complex DFT of the
 // reordered line v[j] = x[2j], v[N-1-j] = x[2j+1], X[k] = Re(e^{-i pi k /
 // (2N)} V[k]), Makhoul 1980), one complex line per real column, imaginary
@@ -648,7 +650,7 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
         }
     };
     // four CTAs exchange once per tile (both cross stages, radix 4); slots
-    // [tile parity][source][destination][2 KEEP_R values][T]
+    // [tile parity][source][destination][KEEP_V values][T]
     constexpr bool R4 = CL == 2;
     constexpr int R4V = GC::KEEP_V;                       // values per source and destination
     float2 *xb = xbuf + (long long)cid * GC::L2_SCRATCH_VALS + tid;
