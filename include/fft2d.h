@@ -301,8 +301,10 @@ FFT2D_API fft2d_status fft2d_exec_host_many_async(int n, const fft2d_plan_t *pla
  * overlap).  Images are grouped by axis length and direction: one launch per
  * group runs the row pass of all its images (a job table travels as a kernel
  * parameter), then one launch per group the column pass -- a handful of
- * launches for any number of images.  Every image's result is bit for bit
- * the one fft2d_exec gives.  complex64 plans only.
+ * launches for any number of images.  Lines of 8192 and 16384 points run
+ * each image's single-image pass instead (the cluster column kernels), on
+ * the group's internal stream.  Every image's result is bit for bit the one
+ * fft2d_exec gives.  complex64 plans only.
  */
 FFT2D_API fft2d_status fft2d_exec_batched(int n, const fft2d_plan_t *plans, const void *const *in,
                                 void *const *out, void *stream);

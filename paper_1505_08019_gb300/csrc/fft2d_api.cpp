@@ -549,7 +549,33 @@ fft2d_status batched_impl(int n, const fft2d_plan_t *plans, const void *const *i
                     const bool flush = (i == n) || table.n == fft2d::kBatchTmaMaxJobs;
                     if (flush && table.n > 0) {
                         const int nv = row ? fft2d::kBatchRowVariants : fft2d::kBatchColVariants;
-                        if (!timing) {
+                        if (!timing && L >= 13) {
+                            // lines of 8192 and 16384 points: each image's
+                            // single-image pass (the cluster column kernels,
+                            // the 5-stage-group rows), the same bits
+                            cudaStream_t ls = bl->s[group++ % kBatchLanes];
+                            cudaError_t e = cudaSuccess;
+                            for (int jj = 0; jj < table.n && e == cudaSuccess; jj++) {
+                                const fft2d::BatchJob &j = table.job[jj];
+                                fft2d::PassArgs a;
+                                a.in = j.in;
+                                a.out = j.out;
+                                a.tw = j.tw;
+                                a.rows = row ? j.lines : (1 << L);
+                                a.cols = row ? (1 << L) : j.lines;
+                                a.ld = j.ld;
+                                a.scale = j.scale;
+                                a.nst = L;
+                                a.partial = false;
+                                a.err = err;
+                                e = row ? fft2d::launch_row_pass(L, a, ls)
+                                        : fft2d::launch_col_pass(L, a, ls);
+                            }
+                            if (e != cudaSuccess) {
+                                result = cuda_fail(e, "batched pass");
+                                break;
+                            }
+                        } else if (!timing) {
                             const int v = batch_variant(plans[first]->device, pass, L);
                             cudaStream_t ls = bl->s[group++ % kBatchLanes];
                             cudaError_t e = fft2d::launch_batch_pass(row, L, table, v, err, ls);

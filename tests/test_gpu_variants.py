@@ -217,7 +217,7 @@ def _run_batched(env, plans, imgs):
 
 
 BATCH_SHAPES = [(512, 1024), (1024, 512), (4096, 512), (512, 4096), (2048, 2048), (128, 256),
-                (256, 128), (1024, 1024), (64, 8192)]
+                (256, 128), (1024, 1024), (64, 8192), (8192, 64), (16384, 32), (32, 16384)]
 
 
 def test_batched_every_grouped_variant_is_bit_identical(env):
