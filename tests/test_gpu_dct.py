@@ -290,7 +290,7 @@ def test_idct_separable_full(env, rows, cols, inplace):
     assert err <= TOL, err
 
 
-@pytest.mark.parametrize("rows,cols", [(4096, 4096), (8192, 1024), (256, 16384)])
+@pytest.mark.parametrize("rows,cols", [(4096, 4096), (8192, 1024), (256, 16384), (16384, 64)])
 def test_dct_round_trip(env, rows, cols):
     """Forward then inverse on the GPU gives the image back."""
     x = synth.gray_real(rows, cols, seed=12)
