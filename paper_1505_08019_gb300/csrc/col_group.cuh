@@ -98,6 +98,10 @@ struct GroupCol {
     // tiles' slots, CS XVALS T values (pair) or CS^2 KEEP_V T (four CTAs)
     static constexpr long long L2_SCRATCH_VALS =
         CL == 2 ? 2LL * CS * CS * KEEP_V * C::T : 2LL * CS * XVALS * C::T;
+    // the mirror exchange of the paired forward DCT per cluster, after the
+    // slots above: per CTA a receive region of CS/2 output blocks, KEEP_V
+    // values per thread each
+    static constexpr long long MIRROR_VALS = (long long)CS * (CS / 2) * KEEP_V * C::T;
     static_assert(C::LB == 1 && ((C::EPT == 32 && C::NG == 3) || (C::EPT == 64 && C::NG == 2)),
                   "512 threads x 32 values in 3 groups, or 256 x 64 in 2");
     static_assert(CL >= 1 && CL <= 2, "two or four CTAs");
@@ -280,7 +284,22 @@ struct GroupH16 {
 struct GroupIO {
     const int *row_exp;
     int *out_exp;
+    float2 *mid_row = nullptr;   // paired forward DCT: output row N/2
 };
+
+// The "two for one" split of Z = DFT(v_a + i v_b) into the DCT-II outputs of
+// the real lines a and b (Makhoul's reduction): from Z[k], Z[k'] (k' = N - k)
+// and (c, s) = (cos, sin)(pi k / (2N)),
+//   xk = (X_a[k], X_b[k]),  xp = (X_a[k'], X_b[k']),  both times scale.
+__device__ __forceinline__ void dct_pair(float2 zk, float2 zp, float2 cs, float scale,
+                                         float2 &xk, float2 &xp)
+{
+    const float c = cs.x * 0.5f * scale, s = cs.y * 0.5f * scale;
+    const float sr = zk.x + zp.x, dr = zp.x - zk.x;   // Zr[k] + Zr[k'], Zr[k'] - Zr[k]
+    const float si = zk.y + zp.y, di = zk.y - zp.y;   // Zi[k] + Zi[k'], Zi[k] - Zi[k']
+    xk = make_float2(c * sr + s * di, c * si + s * dr);     // (X_a[k], X_b[k])
+    xp = make_float2(s * sr - c * di, s * si - c * dr);     // (X_a[k'], X_b[k'])
+}
 
 // C: the local engine; cluster of 2^CL CTAs, this CTA's rank q.  lmap: this
 // CTA's load map (rows CS m + rev_CL(q) of the image; box W x 256 x NB);
@@ -579,6 +598,23 @@ __global__ void __launch_bounds__(C::T, 1) col_group_kernel(const __grid_constan
 // NL for residue 0, where m = 0 takes X[N] = 0.  Outputs n < N/2 go to the
 // even rows (omap: rows 2n'), the others in reverse order to the odd rows
 // (omap2: rows 2n'+1).
+//
+// DCT == 3: the forward DCT-II with two real columns per complex line (the
+// "two for one" split, dct_pair): a tile is W complex = 2W real columns
+// (32-byte rows), the local line is gathered as in DCT == 1 from complex
+// maps (lmap ascending, lmap2 backwards), so half the butterflies of DCT ==
+// 1 per real column.  Output K needs Z[K] and Z[N-K].  CTA q holds K = NL t
+// + k_base + row (row < OUT_ROWS); N - K is row OUT_ROWS - row of block
+// CS-1-t in CTA CS-1-q (k_base(q) + k_base(CS-1-q) = NL - OUT_ROWS), except
+// for row 0, whose mirror is row 0 of the CTA with k_base = NL - k_base(q)
+// (CTA 0 and the CTA at NL/2: itself; CTAs 2 and 3 of four: each other).  So
+// every CTA forms the pairs of its blocks t < CS/2 and sends its blocks t >=
+// CS/2 through a second exchange in L2 to the thread that holds the mirror
+// (unit 2^S0 - lo, index KEEP_R-1-i; KEEP_R-i for lo = 0).  X[K] leaves by
+// TMA from the staged ranges, X[N-K] from the ranges staged in reverse
+// through omap2 (W x 256 boxes at any row; the one row past the image, the
+// mirror of K = 0, is outside the map and not written); X[N/2], which pairs
+// with itself, is stored by CTA 0's threads of row 0 (io.mid_row).
 template <class C, int CL, bool H16, int DCT = 0>
 __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const CUtensorMap *omap,
                                                   int ntiles, const float2 *__restrict__ tw,
@@ -619,6 +655,9 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
         if constexpr (DCT == 1) {
             mbar_arrive_expect_tx(&bar_early, DCT_HALF_BYTES);
             tma_load_3d(sm + C::E, lmap, t * (C::W / 2), 0, 0, &bar_early);
+        } else if constexpr (DCT == 3) {
+            mbar_arrive_expect_tx(&bar_early, S::EARLY_BYTES);
+            tma_load_3d(sm + C::E, lmap, t * C::W, 0, 0, &bar_early);
         } else if constexpr (DCT == 2) {
             // first halves of the natural and the mirrored rows
             float *pf = reinterpret_cast<float *>(sm + C::E);
@@ -636,6 +675,9 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
         if constexpr (DCT == 1) {
             mbar_arrive_expect_tx(&bar_late, DCT_HALF_BYTES);
             tma_load_3d(sm, lmap2, t * (C::W / 2), 0, 0, &bar_late);
+        } else if constexpr (DCT == 3) {
+            mbar_arrive_expect_tx(&bar_late, S::LATE_BYTES);
+            tma_load_3d(sm, lmap2, t * C::W, 0, 0, &bar_late);
         } else if constexpr (DCT == 2) {
             // second halves, at the start of the tile region
             float *lf = reinterpret_cast<float *>(sm);
@@ -653,7 +695,8 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
     // [tile parity][source][destination][KEEP_V values][T]
     constexpr bool R4 = CL == 2;
     constexpr int R4V = GC::KEEP_V;                       // values per source and destination
-    float2 *xb = xbuf + (long long)cid * GC::L2_SCRATCH_VALS + tid;
+    constexpr long long XSTRIDE = GC::L2_SCRATCH_VALS + (DCT == 3 ? GC::MIRROR_VALS : 0);
+    float2 *xb = xbuf + (long long)cid * XSTRIDE + tid;
     int rk_end = 0;
 #pragma unroll
     for (int j = 0; j < CL; j++)
@@ -734,6 +777,42 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
                         const float c = k <= NN / 2 ? cs.x : cs.y;
                         const float sn = k <= NN / 2 ? cs.y : cs.x;
                         a[v * G0::R + r] = make_float2(c * xn + sn * xm, sn * xn - c * xm);
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < G0::V; v++)
+                    run_stages<C, 0, false, true>(a, v, 0, stw, C::L);
+                fence_proxy_async_smem();
+                if (tid == 0)
+                    bulk_wait_read_all();   // the previous tile's stores have read it
+                __syncthreads();            // every slot of both input regions has been read
+                if (tid == 0 && next < ntiles)
+                    issue_early(next);
+#pragma unroll
+                for (int v = 0; v < G0::V; v++) {
+                    const int u = tid + v * C::T;
+                    const int w = u & (C::W - 1);
+                    const int hib = (u >> C::KW) & ((1 << G0::HB) - 1);
+                    const int hi = brev_rt(hib, G0::HB);
+#pragma unroll
+                    for (int r = 0; r < G0::R; r++)
+                        sm[sidx<C>(0, r | (hi << G0::G), w)] = a[v * G0::R + r];
+                }
+            } else if constexpr (DCT == 3) {
+                // group 0: scrambled gather of the reordered pairs of real
+                // columns (the second half of the local line read backwards)
+                const float2 *pref = sm + C::E;
+                const float2 *late = sm;
+#pragma unroll
+                for (int v = 0; v < G0::V; v++) {
+                    const int u = tid + v * C::T;
+                    const int w = u & (C::W - 1);
+                    const int hib = (u >> C::KW) & ((1 << G0::HB) - 1);
+#pragma unroll
+                    for (int r = 0; r < G0::R; r++) {
+                        const int top = brev_c(r, G0::G) << G0::HB;   // compile-time
+                        a[v * G0::R + r] = top < C::N / 2 ? pref[(top | hib) * C::W + w]
+                                                          : late[(C::N - 1 - (top | hib)) * C::W + w];
                     }
                 }
 #pragma unroll
@@ -957,6 +1036,110 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
             const float2 *theirs = x0 + (q ^ 1) * XV;
             group_round_compute_g<C, 0>(a, [&](int j) { return theirs + j * C::T; }, wk, q & 1);
         }
+        if constexpr (DCT == 3) {
+            constexpr int NN = C::N << CL;   // line length
+            constexpr int HT = CS / 2;       // blocks t < HT are paired here
+            constexpr int KR = GC::KEEP_R;
+            constexpr int MREG = HT * GC::KEEP_V * C::T;
+            static_assert(Gl::V == 1 && C::T == (1 << (Gl::S0 + C::KW)), "one unit per thread");
+            float2 *mb = xbuf + (long long)cid * XSTRIDE + GC::L2_SCRATCH_VALS;
+            const int w = tid & (C::W - 1);
+            const int lo = tid >> C::KW;
+            {
+                // blocks t >= HT to CTA CS-1-q, each value in the slot of
+                // the thread and index that pair it
+                float2 *dst = mb + (CS - 1 - q) * MREG;
+                const int tid_r = ((((1 << Gl::S0) - lo) & ((1 << Gl::S0) - 1)) << C::KW) | w;
+#pragma unroll
+                for (int t = HT; t < CS; t++) {
+#pragma unroll
+                    for (int i = 0; i < KR; i++) {
+                        if (lo == 0 && i == 0)
+                            continue;
+                        const int i_r = lo != 0 ? KR - 1 - i : KR - i;
+                        __stcg(dst + ((CS - 1 - t) * KR + i_r) * C::T + tid_r, a[t * KR + i]);
+                    }
+                }
+                // row 0 of CTAs 2 and 3 of four: the other one pairs it
+                if (CL == 2 && q >= 2 && lo == 0) {
+                    float2 *d2 = mb + (q ^ 1) * MREG;
+#pragma unroll
+                    for (int t = HT; t < CS; t++)
+                        __stcg(d2 + (CS - 1 - t) * KR * C::T + w, a[t * KR]);
+                }
+            }
+            cluster_arrive_release();   // the mirror values are visible
+            float2 r0[CS];              // row 0 of every block
+#pragma unroll
+            for (int t = 0; t < CS; t++)
+                r0[t] = a[t * KR];
+            if (q == 0 && lo == 0) {
+                // K = N/2: row 0 of block HT in CTA 0, its own mirror
+                float2 xk, xp;
+                dct_pair(r0[HT], r0[HT], __ldg(post + NN / 2), scale, xk, xp);
+                st_stream(io.mid_row + (long long)tile * C::W + w, xk);
+            }
+            cluster_wait_acquire();
+            const float2 *src = mb + q * MREG + tid;
+#pragma unroll
+            for (int t = 0; t < HT; t++) {
+#pragma unroll
+                for (int i = 0; i < KR; i++) {
+                    const int K = (t << C::L) + k_base + ((i << Gl::S0) | lo);
+                    const float2 zk = a[t * KR + i];
+                    float2 zp;
+                    if (i == 0 && lo == 0 && q == 0)
+                        zp = t == 0 ? zk : r0[CS - t];   // K = 0 and NL t: CTA 0's own
+                    else if (i == 0 && lo == 0 && k_base == C::N / 2)
+                        zp = r0[CS - 1 - t];             // k = NL/2 mirrors itself
+                    else
+                        zp = __ldcg(src + (t * KR + i) * C::T);
+                    float2 xk, xp;
+                    dct_pair(zk, zp, __ldg(post + K), scale, xk, xp);
+                    a[t * KR + i] = xk;
+                    a[(t + HT) * KR + i] = xp;
+                }
+            }
+            // X[K] of blocks t < HT: one staging fill, one TMA store per range
+#pragma unroll
+            for (int t = 0; t < HT; t++)
+#pragma unroll
+                for (int i = 0; i < KR; i++)
+                    stage[(t * GC::OUT_ROWS + ((i << Gl::S0) | lo)) * C::W + w] = a[t * KR + i];
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+#pragma unroll
+                for (int t = 0; t < HT; t++)
+                    tma_store_3d(omap, tile * C::W, 0, ((t << C::L) + k_base) / S::BOX,
+                                 stage + t * GC::OUT_ROWS * C::W);
+                bulk_commit();
+                bulk_wait_read_all();
+            }
+            __syncthreads();
+            // X[N-K]: the same ranges in reverse, rows y0 + s, y0 = N - NL t
+            // - k_base - OUT_ROWS + 1, in 256-row boxes of omap2
+#pragma unroll
+            for (int t = 0; t < HT; t++)
+#pragma unroll
+                for (int i = 0; i < KR; i++)
+                    stage[(t * GC::OUT_ROWS + GC::OUT_ROWS - 1 - ((i << Gl::S0) | lo)) * C::W + w] =
+                        a[(t + HT) * KR + i];
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+#pragma unroll
+                for (int t = 0; t < HT; t++) {
+                    const int y0 = NN - (t << C::L) - k_base - GC::OUT_ROWS + 1;
+#pragma unroll
+                    for (int j = 0; j < GC::OUT_BOX_Z; j++)
+                        tma_store_3d(omap2, tile * C::W, y0 + j * S::BOX, 0,
+                                     stage + (t * GC::OUT_ROWS + j * S::BOX) * C::W);
+                }
+                bulk_commit();
+            }
+            continue;
+        }
         if constexpr (DCT == 2) {
             // x[2n] = Re v[n] (n < N/2, the even rows), x[2(N-1-n)+1] = Re
             // v[n] (the odd rows, in reverse order within a range)
@@ -1164,6 +1347,29 @@ __global__ void __launch_bounds__(C::T, 1) col_dct_l2_kernel(const __grid_consta
     col_group_l2_body<C, CL, false, 1>(&maps.early[res], &maps.out, ntiles, tw, scale, err,
                                        withhold, xbuf, GroupIO{nullptr, nullptr}, &maps.late[res],
                                        post);
+}
+
+// The forward DCT-II column pass with two real columns per complex line
+// (DCT == 3 above): per residue the complex maps of the ascending and the
+// backwards rows, the output map of whole ranges, the any-row map of the
+// reversed ranges, and the output row N/2.
+struct DctPackMaps {
+    CUtensorMap early[4], late[4];
+    CUtensorMap out, out2;
+    float2 *mid_row;
+};
+
+template <class C, int CL>
+__global__ void __launch_bounds__(C::T, 1) col_dct_pack_l2_kernel(
+    const __grid_constant__ DctPackMaps maps, const float2 *__restrict__ tw,
+    const float2 *__restrict__ post, int ntiles, float scale, int *err, int withhold,
+    float2 *xbuf)
+{
+    const int q = (int)cooperative_groups::this_cluster().block_rank();
+    const int res = brev_rt(q, CL);
+    col_group_l2_body<C, CL, false, 3>(&maps.early[res], &maps.out, ntiles, tw, scale, err,
+                                       withhold, xbuf, GroupIO{nullptr, nullptr, maps.mid_row},
+                                       &maps.late[res], post, &maps.out2);
 }
 
 // The inverse DCT-III column pass of real columns (DCT == 2 above): per

@@ -31,7 +31,10 @@
 //  * row_dct_kernel / row_idct_kernel: rows of 2^10 .. 2^14 points, 32
 //    values per thread, loads, pairing and stores in registers;
 //  * col_dct_tma_kernel / col_idct_tma_kernel: persistent TMA-fed column
-//    passes for columns of 2^11 and 2^12 points.
+//    passes for columns of 2^11 and 2^12 points;
+//  * col_dct_pack_l2_kernel (col_group.cuh): forward columns of 2^13 and
+//    2^14 points on a cluster of 2 or 4 CTAs, two real columns per complex
+//    line; col_idct_pair_kernel and col_idct_l2_kernel: the inverse.
 #include <cmath>
 
 #include "col_group.cuh"
@@ -70,17 +73,8 @@ __device__ __forceinline__ float2 dct_load(const DctIO &d, long long line0, int 
     }
 }
 
-// The outputs at k and k' = (N - k) mod N of the two real lines of a
-// complex line, from Z[k] and Z[k'] (see the header); (c, s) belong to k.
-__device__ __forceinline__ void dct_pair(float2 zk, float2 zp, float2 cs, float scale,
-                                         float2 &xk, float2 &xp)
-{
-    const float c = cs.x * 0.5f * scale, s = cs.y * 0.5f * scale;
-    const float sr = zk.x + zp.x, dr = zp.x - zk.x;   // Zr[k] + Zr[k'], Zr[k'] - Zr[k]
-    const float si = zk.y + zp.y, di = zk.y - zp.y;   // Zi[k] + Zi[k'], Zi[k] - Zi[k']
-    xk = make_float2(c * sr + s * di, c * si + s * dr);     // (X_a[k], X_b[k])
-    xp = make_float2(s * sr - c * di, s * si - c * dr);     // (X_a[k'], X_b[k'])
-}
+// dct_pair (col_group.cuh): the outputs at k and k' = (N - k) mod N of
+// the two real lines of a complex line, from Z[k] and Z[k'].
 
 template <class C, bool ROW>
 __device__ __forceinline__ void dct_store(const DctIO &d, long long line0, int lb, int w, int k,
@@ -926,26 +920,8 @@ cudaError_t dct_col_tma_launch(const DctIO &d, const float2 *tw, const float2 *p
 }
 
 // ---------------------------------------------------------------------------
-// Forward DCT column pass for columns of 2^(L+1) points over a CTA pair
-// (the complex column engine of col_group.cuh with the DCT's reorder and
-// pairing).  Tiles of W complex columns (2W real columns).
-//
-//  * Reorder.  CTA b's local line is u_b[m] = v[2m + b] (the DIT split of
-//    the reordered line v): for m < 2^(L-1) the real row 4m + 2b, ascending;
-//    for m >= 2^(L-1) the row 4(2^L - 1 - m) + 3 - 2b, i.e. the rows
-//    3 - 2b, 7 - 2b, .. read backwards.  Two tensor maps per CTA (row pitch
-//    4 ld, bases 2b and 3 - 2b) bring the two halves in ascending row order;
-//    group 0 reads the second half at slot 2^L - 1 - m.
-//  * Stages 1..L locally, stage L+1 by one exchange round: CTA b then holds
-//    Z[k] and Z[k + 2^L] for k in [b 2^(L-1), (b+1) 2^(L-1)).
-//  * Pairing.  Output k needs Z[k] and Z[N - k] (N = 2^(L+1)), and N - k
-//    lies in the partner's second range, so the pair swaps those ranges in a
-//    second exchange, each value landing in the slot of the thread that
-//    holds its partner k (unit lo pairs with unit 256 - lo).  CTA b then
-//    forms X[k] and X[N - k] for its k: X[k] leaves through a staging buffer
-//    and one TMA store (a contiguous range of rows), X[N - k] with per-thread
-//    stores.  Self-pairs: k = 0 (CTA 0) and k = N/2 (CTA 0, from its own
-//    Z[2^L]); CTA 1's k = 2^(L-1) pairs with its own Z[N - k].
+// Tile geometry of the inverse DCT column pass over a CTA pair (below): the
+// local engine's 2^L rows in two halves of whole 256-row blocks.
 template <class C>
 struct DctPair {
     using S = TmaSplit<C>;
@@ -957,315 +933,11 @@ struct DctPair {
     static_assert(HBYTES == S::EARLY_BYTES && HBYTES == S::LATE_BYTES, "two halves of the split");
 };
 
-template <class C>
-__global__ void __launch_bounds__(C::T, 1) col_dct_pair_kernel(
-    const __grid_constant__ CUtensorMap e0, const __grid_constant__ CUtensorMap e1,
-    const __grid_constant__ CUtensorMap l0, const __grid_constant__ CUtensorMap l1,
-    const __grid_constant__ CUtensorMap omap, float2 *out, long long ld, int ntiles,
-    const float2 *__restrict__ tw, const float2 *__restrict__ post, float scale, int *err,
-    int withhold)
-{
-    namespace cg = cooperative_groups;
-    using S = TmaSplit<C>;
-    using D = DctPair<C>;
-    using GC = GroupCol<C, 1>;
-    using G0 = Grp<C, 0>;
-    using Gl = Grp<C, C::NG - 1>;
-    constexpr int N = 2 * C::N;                 // line length
-    extern __shared__ __align__(1024) float2 sm[];
-    __shared__ __align__(8) uint64_t bar_early, bar_late, bar_recv;
-    __shared__ int lost_flag[2];
-    cg::cluster_group cluster = cg::this_cluster();
-    const int b = (int)cluster.block_rank();
-    const int tid = threadIdx.x;
-    const int nclusters = (int)gridDim.x / 2;
-    const CUtensorMap *emap = b == 0 ? &e0 : &e1;
-    const CUtensorMap *lmap = b == 0 ? &l0 : &l1;
-    float2 *pref = sm + C::E;
-    float2 *stw = sm + S::TW_OFF;
-    float2 *recvb = sm;
-    float2 *sendb = sm + C::E / 2;
-    const uint32_t peer_recv = mapa_shared(smem_addr(recvb), (uint32_t)(b ^ 1));
-    const uint32_t peer_bar = mapa_shared(smem_addr(&bar_recv), (uint32_t)(b ^ 1));
-    const int w = tid & (C::W - 1);
-    auto issue_early = [&](int t) {
-        mbar_arrive_expect_tx(&bar_early, D::HBYTES);
-        tma_load_3d(pref, emap, t * C::W, 0, 0, &bar_early);
-    };
-    auto issue_late = [&](int t) {
-        mbar_arrive_expect_tx(&bar_late, D::HBYTES);
-        tma_load_3d(sm, lmap, t * C::W, 0, 0, &bar_late);
-    };
-    int lost_recv = 0;
-    int tile = (int)blockIdx.x / 2;
-    if (tid == 0) {
-        mbar_init(&bar_early, 1);
-        mbar_init(&bar_late, 1);
-        mbar_init(&bar_recv, 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    int n_early = 0, n_late = 0, w_early = 0, w_late = 0;
-    if (tile < ntiles) {
-        if (tid == 0) {
-            mbar_expect_tx(&bar_early, S::TW_BYTES);
-            bulk_load(stw, tw, S::TW_BYTES, &bar_early);
-            issue_early(tile);
-            if (!(withhold && blockIdx.x == 0))   // self-test: the first late half never comes
-                issue_late(tile);
-        }
-        n_early = n_late = 1;
-    }
-    bool lost = false;
-    int w_recv = 0;
-    float2 a[C::EPT];
-    for (; tile < ntiles; tile += nclusters) {
-        const int next = tile + nclusters;
-        const bool ok = mbar_wait_bounded(&bar_early, (uint32_t)(w_early & 1)) &&
-                        mbar_wait_bounded(&bar_late, (uint32_t)(w_late & 1));
-        const int lost_here = __syncthreads_or((ok ? 0 : 1) | lost_recv);
-        if (tid == 0) {
-            if (!lost_recv)
-                mbar_arrive_expect_tx(&bar_recv, GC::XBYTES);
-            lost_flag[b] = lost_here;
-            *cluster.map_shared_rank(lost_flag + b, b ^ 1) = lost_here;
-        }
-        if (!lost_here) {
-            w_early++;
-            w_late++;
-            // group 0: u_b[m] from the first-half map (m < N/4 local rows)
-            // or the second-half map at slot 2^L - 1 - m
-#pragma unroll
-            for (int v = 0; v < G0::V; v++) {
-                const int u = tid + v * C::T;
-                const int hib = (u >> C::KW) & ((1 << G0::HB) - 1);
-#pragma unroll
-                for (int r = 0; r < G0::R; r++) {
-                    const int top = brev_c(r, G0::G) << G0::HB;   // compile-time
-                    a[v * G0::R + r] = top < D::HALF_ROWS
-                                           ? pref[(top | hib) * C::W + w]
-                                           : sm[(C::N - 1 - (top | hib)) * C::W + w];
-                }
-            }
-#pragma unroll
-            for (int v = 0; v < G0::V; v++)
-                run_stages<C, 0, false, true>(a, v, 0, stw, C::L);
-            fence_proxy_async_smem();
-            if (tid == 0)
-                bulk_wait_read_all();   // the previous tile's stores have read the staging
-            __syncthreads();            // both halves have been read
-            if (tid == 0 && next < ntiles)
-                issue_early(next);
-            if (next < ntiles)
-                n_early++;
-#pragma unroll
-            for (int v = 0; v < G0::V; v++) {
-                const int u = tid + v * C::T;
-                const int hib = (u >> C::KW) & ((1 << G0::HB) - 1);
-                const int hi = brev_rt(hib, G0::HB);
-#pragma unroll
-                for (int r = 0; r < G0::R; r++)
-                    sm[sidx<C>(0, r | (hi << G0::G), w)] = a[v * G0::R + r];
-            }
-            __syncthreads();
-            group_smem<C, 1, false, false, true>(a, sm, stw, C::L);
-            __syncthreads();
-            group_last_read<C>(a, sm);
-            __syncthreads();   // the tile region is free
-        }
-        cluster_arrive_release();   // A0: receive region free, mbarrier armed, flags sent
-        float2 wk[16];
-        if (!lost_here) {
-#pragma unroll
-            for (int v = 0; v < Gl::V; v++) {
-                const int u = tid + v * C::T;
-                const int lo = (u >> C::KW) & ((1 << Gl::S0) - 1);
-                run_stages<C, C::NG - 1, false, true>(a, v, lo, stw, C::L);
-            }
-            group_round_send<C, 0>(a, sendb, b);
-            fence_proxy_async_smem();
-        }
-        __syncthreads();
-        group_round_twiddles<C, 0>(wk, tw, b * (Gl::R / 2));
-        cluster_wait_acquire();
-        if (lost_flag[0] | lost_flag[1]) {
-            lost = true;
-            break;
-        }
-        if (tid == 0)
-            bulk_copy_to_peer(peer_recv, sendb, GC::XBYTES, peer_bar);
-        lost_recv = mbar_wait_bounded(&bar_recv, (uint32_t)(w_recv & 1)) ? 0 : 1;
-        if (!lost_recv)
-            w_recv++;
-        cluster_arrive_release();   // B0: the partner's send buffer has been read
-        // stage L+1: a[t 16 + v 8 + i] = Z[k + 2^L t], k = lo_v + 2^S0 (8b + i)
-        group_round_compute<C, 0>(a, recvb, wk, b);
-        // the rotations (cos, sin)(pi k / (2N)) of this CTA's k, early
-        float2 cs[16];
-#pragma unroll
-        for (int v = 0; v < Gl::V; v++) {
-            const int lo = ((tid + v * C::T) >> C::KW) & ((1 << Gl::S0) - 1);
-#pragma unroll
-            for (int i = 0; i < 8; i++)
-                cs[v * 8 + i] = __ldg(post + (lo | ((8 * b + i) << Gl::S0)));
-        }
-        fence_proxy_async_smem();
-        __syncthreads();   // the receive buffer has been read
-        if (tid == 0 && !lost_recv)
-            mbar_arrive_expect_tx(&bar_recv, GC::XBYTES);
-        cluster_wait_acquire();   // B0: this CTA's send buffer is free
-        // the second range Z[k + 2^L] to the partner, each value in the slot
-        // of the partner thread that holds N - (k + 2^L): unit 256 - lo
-#pragma unroll
-        for (int v = 0; v < Gl::V; v++) {
-            const int lo = ((tid + v * C::T) >> C::KW) & ((1 << Gl::S0) - 1);
-            const int lo_r = (256 - lo) & 255;
-            const int u_r = (lo_r << C::KW) | w;
-            const int tid_r = u_r & (C::T - 1), v_r = u_r / C::T;
-#pragma unroll
-            for (int i = 0; i < 8; i++) {
-                const int i_r = lo != 0 ? 7 - i : 8 - i;
-                if (lo == 0 && i == 0)
-                    continue;   // Z[2^L] (CTA 0) or Z[N - 2^(L-1)] (CTA 1): kept
-                sendb[(v_r * 8 + i_r) * C::T + tid_r] = a[16 + v * 8 + i];
-            }
-        }
-        fence_proxy_async_smem();
-        __syncthreads();
-        cluster_arrive_release();   // A1: every receive region free and armed
-        cluster_wait_acquire();
-        if (tid == 0)
-            bulk_copy_to_peer(peer_recv, sendb, GC::XBYTES, peer_bar);
-        {
-            const int lr = mbar_wait_bounded(&bar_recv, (uint32_t)(w_recv & 1)) ? 0 : 1;
-            if (!lr)
-                w_recv++;
-            lost_recv |= lr;
-        }
-        cluster_arrive_release();   // B1: the partner's send buffer has been read
-        // the outputs: X[k] staged, X[N - k] stored per thread
-        float2 *dst = out + (long long)tile * C::W + w;
-#pragma unroll
-        for (int v = 0; v < Gl::V; v++) {
-            const int lo = ((tid + v * C::T) >> C::KW) & ((1 << Gl::S0) - 1);
-#pragma unroll
-            for (int i = 0; i < 8; i++) {
-                const int k = lo | ((8 * b + i) << Gl::S0);
-                const float2 zk = a[v * 8 + i];
-                float2 zp = recvb[(v * 8 + i) * C::T + tid];
-                if (lo == 0 && i == 0)
-                    zp = b == 0 ? zk : a[16 + v * 8];   // k = 0 pairs with itself
-                float2 xk, xp;
-                dct_pair(zk, zp, cs[v * 8 + i], scale, xk, xp);
-                a[v * 8 + i] = xk;
-                if (!(lo == 0 && i == 0 && b == 0))
-                    st_stream(dst + (long long)(N - k) * ld, xp);
-            }
-        }
-        if (b == 0 && tid < C::W) {
-            // k = N/2 pairs with itself: Z[2^L] is this thread's second-range value
-            float2 xk, xp;
-            dct_pair(a[16], a[16], __ldg(post + N / 2), scale, xk, xp);
-            st_stream(dst + (long long)(N / 2) * ld, xk);
-        }
-        fence_proxy_async_smem();
-        __syncthreads();   // the receive buffer has been read
-        if (tid == 0 && next < ntiles)
-            issue_late(next);
-        if (next < ntiles)
-            n_late++;
-        cluster_wait_acquire();   // B1: this CTA's send buffer is free for staging
-#pragma unroll
-        for (int v = 0; v < Gl::V; v++) {
-            const int lo = ((tid + v * C::T) >> C::KW) & ((1 << Gl::S0) - 1);
-#pragma unroll
-            for (int i = 0; i < 8; i++)
-                sendb[((i << Gl::S0) | lo) * C::W + w] = a[v * 8 + i];
-        }
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            tma_store_3d(&omap, tile * C::W, 0, b * (C::N / 2 / S::BOX), sendb);
-            bulk_commit();
-        }
-    }
-
-    if (__syncthreads_or((lost || lost_recv) ? 1 : 0)) {
-        if (tid == 0)
-            atomicExch(err, kDevErrTmaTimeout);
-        if (n_early > w_early)
-            mbar_wait_bounded(&bar_early, (uint32_t)(w_early & 1));
-        if (n_late > w_late)
-            mbar_wait_bounded(&bar_late, (uint32_t)(w_late & 1));
-        if (lost_recv)
-            mbar_wait_bounded(&bar_recv, (uint32_t)(w_recv & 1));
-    }
-    if (tid == 0)
-        bulk_wait_all();
-}
-
-// The pair kernel for forward DCT columns of 8192 points when the image
-// allows it; cudaErrorNotSupported otherwise (the caller then runs the
-// plain kernel).
-cudaError_t dct_col_pair_launch(const DctIO &d, const float2 *tw, const float2 *post, float scale,
-                                int *err, int withhold, cudaStream_t s)
-{
-    using C = LineCfg<12, 2, 0, 32>;
-    using S = TmaSplit<C>;
-    using D = DctPair<C>;
-    const long long cc = d.cols / 2;   // complex columns
-    if (!err || d.rows != 2 * C::N || cc % C::W != 0 || (reinterpret_cast<uintptr_t>(d.in) & 15) ||
-        (reinterpret_cast<uintptr_t>(d.out) & 15) || (reinterpret_cast<uintptr_t>(tw) & 15) ||
-        (cc * 8) % 16 != 0 || !tensor_maps_available())
-        return cudaErrorNotSupported;
-    const float2 *in = reinterpret_cast<const float2 *>(d.in);
-    float2 *out = reinterpret_cast<float2 *>(d.out);
-    CUtensorMap em[2], lm[2], om;
-    for (int b = 0; b < 2; b++)
-        if (!encode_col_map(&em[b], in + 2 * b * cc, D::HALF_ROWS, (int)cc, 4 * cc, C::W, S::BOX,
-                            D::NBH) ||
-            !encode_col_map(&lm[b], in + (3 - 2 * b) * cc, D::HALF_ROWS, (int)cc, 4 * cc, C::W,
-                            S::BOX, D::NBH))
-            return cudaErrorNotSupported;
-    if (!encode_col_map(&om, out, d.rows, (int)cc, cc, C::W, S::BOX, D::NBH))
-        return cudaErrorNotSupported;
-    auto k = col_dct_pair_kernel<C>;
-    constexpr int SMEM = S::SMEM_BYTES;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 2;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(C::T);
-    cfg.dynamicSmemBytes = SMEM;
-    cfg.stream = s;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    static DeviceCache pairs;
-    const int dev = device_current();
-    if (!pairs.get(dev)) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-        if (e != cudaSuccess)
-            return e;
-        cfg.gridDim = dim3((unsigned)(2 * (device_sm_count() / 2)));
-        int n = 0;
-        e = cudaOccupancyMaxActiveClusters(&n, k, &cfg);
-        if (e != cudaSuccess)
-            return e;
-        pairs.set(dev, n > 0 ? n : 1);
-    }
-    const int ntiles = (int)(cc / C::W);
-    const int np = pairs.get(dev) < ntiles ? pairs.get(dev) : ntiles;
-    cfg.gridDim = dim3((unsigned)(2 * np));
-    return cudaLaunchKernelEx(&cfg, k, em[0], em[1], lm[0], lm[1], om, out, cc, ntiles, tw, post,
-                              scale, err, withhold);
-}
-
 // Forward DCT columns of 16384 points on the four-CTA cluster kernel with
 // the exchange through L2 (col_dct_l2_kernel, one complex line per real
-// column); cudaErrorNotSupported (nothing launched) when the image does not
-// allow it.  The kernel runs in place: its tiles are 4 real columns, so
+// column), for widths of 4 mod 8 real columns (the packed kernel above takes
+// multiples of 8); cudaErrorNotSupported (nothing launched) when the image
+// does not allow it.  The kernel runs in place: its tiles are 4 real columns, so
 // every access is half of a 32-byte sector, and a store merges into a
 // sector that the load of the same tile (and of the neighbouring tile, in
 // flight at the same time) has just brought into L2.  Out of place the
@@ -1333,6 +1005,78 @@ cudaError_t dct_col_quad_launch(const DctIO &din, const float2 *tw, const float2
     }
     void *xbuf = nullptr;
     cudaError_t e = scratch_take(&xbuf, (size_t)ng * GC::L2_SCRATCH_VALS * sizeof(float2), s);
+    if (e != cudaSuccess)
+        return e;
+    cfg.gridDim = dim3((unsigned)(CS * ng));
+    e = cudaLaunchKernelEx(&cfg, k, m, tw, post, ntiles, scale, err, withhold,
+                           static_cast<float2 *>(xbuf));
+    const cudaError_t f = cudaFreeAsync(xbuf, s);
+    return e != cudaSuccess ? e : f;
+}
+
+// Forward DCT columns of 2^(12+CL) points (8192: a CTA pair, 16384: four
+// CTAs) with two real columns per complex line on the cluster kernel with
+// the exchange through L2 (col_dct_pack_l2_kernel): tiles of 8 real
+// columns, 32-byte rows, in place or out of place; cudaErrorNotSupported
+// (nothing launched) when the image does not allow it.
+template <int CL>
+cudaError_t dct_col_pack_launch(const DctIO &d, const float2 *tw, const float2 *post,
+                                float scale, int *err, int withhold, cudaStream_t s)
+{
+    using C = LineCfg<12, 2, 0, 64, 6>;
+    using S = TmaSplit<C>;
+    using GC = GroupCol<C, CL>;
+    constexpr int CS = GC::CS;
+    const long long cc = d.cols / 2;   // complex columns: pairs of real columns
+    if (!err || d.rows != (long long)CS * C::N || d.cols % (2 * C::W) != 0 ||
+        (reinterpret_cast<uintptr_t>(d.in) & 15) || (reinterpret_cast<uintptr_t>(d.out) & 15) ||
+        (reinterpret_cast<uintptr_t>(tw) & 15) || !tensor_maps_available())
+        return cudaErrorNotSupported;
+    const float2 *in = reinterpret_cast<const float2 *>(d.in);
+    float2 *out = reinterpret_cast<float2 *>(d.out);
+    constexpr int HALF = C::N / 2;   // rows of each half of a CTA's local line
+    DctPackMaps m;
+    for (int r = 0; r < CS; r++)
+        if (!encode_col_map(&m.early[r], in + 2 * r * cc, HALF, (int)cc, 2 * CS * cc, C::W, S::BOX,
+                            HALF / S::BOX) ||
+            !encode_col_map(&m.late[r], in + (2 * CS - 1 - 2 * r) * cc, HALF, (int)cc, 2 * CS * cc,
+                            C::W, S::BOX, HALF / S::BOX))
+            return cudaErrorNotSupported;
+    if (!encode_col_map(&m.out, out, (int)d.rows, (int)cc, cc, C::W, S::BOX, GC::OUT_BOX_Z) ||
+        !encode_map_xyz(&m.out2, out, cc, (int)d.rows, 1, cc, cc * d.rows, C::W, S::BOX, 1))
+        return cudaErrorNotSupported;
+    m.mid_row = out + (d.rows / 2) * cc;
+    auto k = col_dct_pack_l2_kernel<C, CL>;
+    constexpr int SMEM = S::SMEM_BYTES;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(C::T);
+    cfg.dynamicSmemBytes = SMEM;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    static DeviceCache groups;
+    const int dev = device_current();
+    if (!groups.get(dev)) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (e != cudaSuccess)
+            return e;
+        cfg.gridDim = dim3((unsigned)(CS * (device_sm_count() / CS)));
+        int n = 0;
+        e = cudaOccupancyMaxActiveClusters(&n, k, &cfg);
+        if (e != cudaSuccess)
+            return e;
+        groups.set(dev, n > 0 ? n : 1);
+    }
+    const int ntiles = (int)(cc / C::W);
+    const int ng = groups.get(dev) < ntiles ? groups.get(dev) : ntiles;
+    void *xbuf = nullptr;
+    cudaError_t e = scratch_take(
+        &xbuf, (size_t)ng * (size_t)(GC::L2_SCRATCH_VALS + GC::MIRROR_VALS) * sizeof(float2), s);
     if (e != cudaSuccess)
         return e;
     cfg.gridDim = dim3((unsigned)(CS * ng));
@@ -2087,10 +1831,14 @@ cudaError_t dct_dispatch(bool row, bool inverse, const DctIO &d, const float2 *t
                                                                                err, 1, s);
         if constexpr (L == 13)
             return inverse ? idct_col_pair_launch(d, tw, post, scale, err, 1, s)
-                           : dct_col_pair_launch(d, tw, post, scale, err, 1, s);
-        if constexpr (L == 14)
-            return inverse ? idct_col_quad_launch(d, tw, post, scale, err, 1, s)
-                           : dct_col_quad_launch(d, tw, post, scale, err, 1, s);
+                           : dct_col_pack_launch<1>(d, tw, post, scale, err, 1, s);
+        if constexpr (L == 14) {
+            if (inverse)
+                return idct_col_quad_launch(d, tw, post, scale, err, 1, s);
+            const cudaError_t e = dct_col_pack_launch<2>(d, tw, post, scale, err, 1, s);
+            return e != cudaErrorNotSupported ? e
+                                              : dct_col_quad_launch(d, tw, post, scale, err, 1, s);
+        }
         return cudaErrorNotSupported;
     }
     if (inverse) {
@@ -2129,8 +1877,8 @@ cudaError_t dct_dispatch(bool row, bool inverse, const DctIO &d, const float2 *t
         if (e != cudaErrorNotSupported)
             return e;
     }
-    if constexpr (L == 13) {
-        const cudaError_t e = dct_col_pair_launch(d, tw, post, scale, err, 0, s);
+    if constexpr (L == 13 || L == 14) {
+        const cudaError_t e = dct_col_pack_launch<L - 12>(d, tw, post, scale, err, 0, s);
         if (e != cudaErrorNotSupported)
             return e;
     }

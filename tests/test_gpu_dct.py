@@ -85,15 +85,18 @@ def test_dct_small_shapes(env, rows, cols):
 @pytest.mark.parametrize("rows,cols", [(64, 256), (256, 64), (2, 1024), (1024, 2),
                                        (512, 512), (128, 2048), (1024, 1024),
                                        (2048, 64), (4096, 32), (2048, 8), (4096, 4),
-                                       (8192, 16), (8192, 4), (16384, 4)])
+                                       (8192, 16), (8192, 8), (8192, 4), (16384, 8),
+                                       (16384, 32), (16384, 4)])
 def test_dct_whole_outputs(env, rows, cols):
     """Non-square and wide/tall images spanning several CTAs and a partly
     filled last CTA (2 rows: one complex line), whole outputs compared.
     Columns of 2048 and 4096 rows run on the TMA-fed column kernel when the
     image is at least two tiles wide (64 and 32 columns here) and on the
-    plain kernel otherwise (8 and 4 columns); columns of 8192 rows on the
-    CTA-pair kernel (16 columns: two tiles) or the plain kernel (4); forward
-    columns of 16384 rows on the four-CTA kernel (4 real columns: one tile)."""
+    plain kernel otherwise (8 and 4 columns).  Forward columns of 8192 and
+    16384 rows run on the cluster kernels with two real columns per complex
+    line when the width is a multiple of 8 (one to four 8-column tiles
+    here); otherwise on the plain kernel (8192 x 4) or the four-CTA kernel
+    with one complex line per real column (16384 x 4)."""
     _, _, orc = env
     x = synth.gray_real(rows, cols, seed=7)
     err = rel(gpu_dct(env, x), orc.dct2d(x))
