@@ -98,3 +98,22 @@ def test_noalloc_single_line_shapes(env, shape):
         torch.cuda.synchronize()
         assert rel(out.cpu().numpy(), want) <= TOL
         assert rel(dx.cpu().numpy(), want) <= TOL
+
+
+@pytest.mark.parametrize("shape,direction", [((4096, 4096), -1), ((256, 1024), 1), ((2048, 32), -1)],
+                         ids=["4096x4096_fwd", "256x1024_inv", "2048x32_fwd"])
+def test_noalloc_matches_oracle(env, orc, shape, direction):
+    """The entry point's rotation factors are computed on the device, not
+    taken from the plan's FP64 tables, so it is also compared with the FP64
+    oracle of eqs. 2-3 directly (inverse scaled by 1/(rows*cols))."""
+    torch, fft = env
+    R, C = shape
+    x = synth.uniform_complex(R, C, seed=R + C)
+    dx = torch.from_numpy(x).cuda()
+    out = torch.empty_like(dx)
+    fft.fft2d_exec_noalloc(R, C, fft.FFT2D_FORWARD if direction < 0 else fft.FFT2D_INVERSE, dx, out)
+    torch.cuda.synchronize()
+    want = orc.fft2d(x, inverse=direction > 0, threads=8)
+    err = rel(out.cpu().numpy(), want)
+    print(f"[noalloc] {R}x{C} dir={direction}: rel_l2 vs oracle = {err:.2e}")
+    assert err <= TOL
