@@ -637,6 +637,10 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
     __shared__ int lost_flag[2][CS];       // [tile parity][slot p: written by CTA p]
     __shared__ int cmax[2][CS][C::W];      // half2: [tile parity][CTA p's partial column maxima]
     __shared__ int cmax_local[C::W];
+    // DCT == 3: (cos, sin)(pi B / (2N)) of the block starts B = NL t + k_base
+    // + 2^S0 i of this CTA's paired outputs (t < CS/2); a thread multiplies
+    // them by its own (cos, sin)(pi lo / (2N)) (within a few ulp of the table)
+    __shared__ float2 rot_base[DCT == 3 ? (1 << CL) / 2 * (Grp<C, C::NG - 1>::R >> CL) : 1];
     cg::cluster_group cluster = cg::this_cluster();
     const int q = (int)cluster.block_rank();
     const int tid = threadIdx.x;
@@ -708,6 +712,13 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
         mbar_init(&bar_early, 1);
         mbar_init(&bar_late, 1);
         fence_mbar_init();
+    }
+    float2 rot_lo = make_float2(1.f, 0.f);
+    if constexpr (DCT == 3) {
+        constexpr int KR = GC::KEEP_R;
+        for (int j = tid; j < CS / 2 * KR; j += C::T)
+            rot_base[j] = __ldg(post + ((j / KR) << C::L) + k_base + ((j % KR) << Gl::S0));
+        rot_lo = __ldg(post + ((tid >> C::KW) & ((1 << Gl::S0) - 1)));
     }
     if constexpr (H16) {
         // the factors of this CTA's rows CS m + rev_CL(q)
@@ -1085,7 +1096,6 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
             for (int t = 0; t < HT; t++) {
 #pragma unroll
                 for (int i = 0; i < KR; i++) {
-                    const int K = (t << C::L) + k_base + ((i << Gl::S0) | lo);
                     const float2 zk = a[t * KR + i];
                     float2 zp;
                     if (i == 0 && lo == 0 && q == 0)
@@ -1094,8 +1104,11 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
                         zp = r0[CS - 1 - t];             // k = NL/2 mirrors itself
                     else
                         zp = __ldcg(src + (t * KR + i) * C::T);
+                    const float2 rb = rot_base[t * KR + i];
+                    const float2 cs = make_float2(rb.x * rot_lo.x - rb.y * rot_lo.y,
+                                                  rb.x * rot_lo.y + rb.y * rot_lo.x);
                     float2 xk, xp;
-                    dct_pair(zk, zp, __ldg(post + K), scale, xk, xp);
+                    dct_pair(zk, zp, cs, scale, xk, xp);
                     a[t * KR + i] = xk;
                     a[(t + HT) * KR + i] = xp;
                 }
