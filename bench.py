@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--requests", type=int, default=20000, help="serving workload: requests")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving workload: mean req/s")
     ap.add_argument("--workload", choices=["fft4096", "batched", "fp16", "serve", "dct", "sizes",
-                                           "passes"],
+                                           "passes", "cpu"],
                     default="fft4096",
                     help="fft4096: the 4096x4096 forward+inverse benchmark (default); "
                          "batched: 64 uneven images through the grouped executor; "
@@ -53,7 +53,9 @@ def parse():
                          "dct: real 2D DCT-II at 4096^2 and 8192^2 beside the complex FFT; "
                          "sizes: forward+inverse at the paper's Table 1 image sizes; "
                          "passes: the default row and column kernels of one --shape image "
-                         "(--dtype c64 or h16), timed one pass at a time (for profiling)")
+                         "(--dtype c64 or h16), timed one pass at a time (for profiling); "
+                         "cpu: the CPU baseline (FP64 oracle, one thread and all cores) at "
+                         "256^2, 1024^2, 4096^2 and 8192^2 beside the GPU's time")
     ap.add_argument("--shape", default="16384x512", help="passes workload: RxC")
     ap.add_argument("--dtype", choices=["c64", "h16"], default="c64",
                     help="passes workload: complex64 or half2 storage")
@@ -209,8 +211,9 @@ class ClockSampler:
 
 # ------------------------------------------------------------- CPU oracle
 def cpu_oracle_sample(side, seconds, threads):
-    """Forward+inverse 4096^2 transforms by the FP64 oracle on host threads,
-    repeated while the wall-clock bound allows (at least one pair)."""
+    """Forward+inverse transforms of one side^2 blob image by the FP64 oracle
+    on host threads, repeated while the wall-clock bound allows (at least
+    one pair)."""
     import synth
     from oracle import oracle
     orc = oracle.get()
@@ -1255,6 +1258,64 @@ def run_passes(args):
                       "reps": reps, "passes": out}), flush=True)
 
 
+# ------------------------------------------- CPU baseline at several sizes
+def run_cpu(args):
+    """The CPU baseline (the FP64 oracle as it stands, on one thread and on
+    all host cores) at the sizes of the plain, blob and large-image
+    workloads, each beside the GPU's device time for the same forward +
+    inverse pair (one image at a time, a rotation of images larger than L2)."""
+    sides = (256, 1024, 4096, 8192)
+    th = host_cores()
+    cpu = {}
+    for side in sides:   # the oracle first, before any GPU work
+        v, n, dt = cpu_oracle_sample(side, args.cpu_seconds, th)
+        v1, n1, dt1 = cpu_oracle_sample(side, args.cpu_seconds, 1)
+        cpu[side] = {"all_cores": {"value": v, "unit": UNIT, "cores": th,
+                                   "sample": f"{n} transforms, {dt:.1f} s"},
+                     "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                                       "sample": f"{n1} transforms, {dt1:.1f} s"}}
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1505_08019_gb300 as fft
+    import synth
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    out = {}
+    for side in sides:
+        nimg = max(2, int(2 * 129e6 // (side * side * 8)) + 1)
+        x = torch.from_numpy(synth.blob_image(side, side, seed=0)).cuda()
+        xs = [x.clone() for _ in range(nimg)]
+        ys = [torch.empty_like(x) for _ in range(nimg)]
+        pf = fft.fft2d_plan(side, side, fft.FFT2D_C64, fft.FFT2D_FORWARD)
+        pi = fft.fft2d_plan(side, side, fft.FFT2D_C64, fft.FFT2D_INVERSE)
+        reps = max(40, 4 * nimg)
+        for i in range(reps + 5):
+            if i == 5:
+                torch.cuda.synchronize()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+            fft.fft2d_exec(pf, xs[i % nimg], ys[i % nimg], sptr)
+            fft.fft2d_exec(pi, ys[i % nimg], ys[i % nimg], sptr)
+        b.record(stream)
+        torch.cuda.synchronize()
+        gpu = 2 * reps / (a.elapsed_time(b) / 1e3)
+        fft.fft2d_destroy(pf)
+        fft.fft2d_destroy(pi)
+        del xs, ys, x
+        torch.cuda.empty_cache()
+        out[f"{side}x{side}"] = {"gpu": {"value": gpu, "unit": UNIT,
+                                         "call": "fft2d_exec forward + inverse, one stream"},
+                                 "cpu_baseline": dict(cpu[side], kind="oracle"),
+                                 "gpu_over_all_cores": gpu / cpu[side]["all_cores"]["value"]}
+    print(json.dumps({"metric": "2D FFT transforms/s, FP64 oracle on the host beside the GPU",
+                      "unit": UNIT, "workload": "cpu", "cpu_model": cpu_model(), "cores": th,
+                      "input": "blob image (seeded), forward + inverse pairs",
+                      "per_size": out}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1271,6 +1332,8 @@ def main():
         run_sizes(args)
     elif args.workload == "passes":
         run_passes(args)
+    elif args.workload == "cpu":
+        run_cpu(args)
     else:
         run_ours(args)
 

@@ -203,10 +203,28 @@ __device__ __forceinline__ void group_round_twiddles(float2 (&wk)[NW],
     }
 }
 
-// The same two steps of round J with the exchanged values in global memory:
-// slot j of this thread at at(j), written and read through L2 only.
-template <class C, int J, class At, int NA>
-__device__ __forceinline__ void group_round_send_g(const float2 (&s)[NA], At at, int bitj)
+// Slot pair m (slots 2m and 2m + 1) of this thread in an exchange region of
+// global memory: rt is the region's start plus threadIdx.x, and the pair is
+// the 16 bytes at float2 offset 2 (m T + tid), contiguous over the threads.
+template <class C>
+__device__ __forceinline__ float4 *slot_pair(float2 *rt, int m)
+{
+    return reinterpret_cast<float4 *>(rt + 2 * m * C::T + threadIdx.x);
+}
+template <class C>
+__device__ __forceinline__ const float4 *slot_pair(const float2 *rt, int m)
+{
+    return reinterpret_cast<const float4 *>(rt + 2 * m * C::T + threadIdx.x);
+}
+
+// The same two steps of round J with the exchanged values in global memory
+// (region rt = its start plus threadIdx.x), written and read through L2
+// only: slot j of this thread at rt + j T (8-byte accesses), or with VEC
+// two slots per 16-byte access (slot_pair).  Measured: VEC speeds up the
+// half2 kernels (16384^2 FP16 transform 2.51 -> 2.31 ms) and slows the
+// complex64 ones down (8192^2 column pass 0.317 -> 0.326 ms, more spills).
+template <class C, int J, bool VEC, int NA>
+__device__ __forceinline__ void group_round_send_g(const float2 (&s)[NA], float2 *rt, int bitj)
 {
     using Gl = Grp<C, C::NG - 1>;
     constexpr int NT = 1 << J;
@@ -217,19 +235,30 @@ __device__ __forceinline__ void group_round_send_g(const float2 (&s)[NA], At at,
     for (int t = 0; t < NT; t++) {
 #pragma unroll
         for (int v = 0; v < Gl::V; v++) {
+            if constexpr (VEC) {
 #pragma unroll
-            for (int ih = 0; ih < NH; ih++) {
-                const int j = (t * Gl::V + v) * NH + ih;
-                const float2 lo_half = s[(t * Gl::V + v) * NK + ih];
-                const float2 hi_half = s[(t * Gl::V + v) * NK + NH + ih];
-                __stcg(at(j), bitj == 0 ? hi_half : lo_half);
+                for (int ih = 0; ih < NH; ih += 2) {
+                    const int j = (t * Gl::V + v) * NH + ih;
+                    const int b = (t * Gl::V + v) * NK + ih;
+                    const float2 x0 = bitj == 0 ? s[b + NH] : s[b];
+                    const float2 x1 = bitj == 0 ? s[b + NH + 1] : s[b + 1];
+                    __stcg(slot_pair<C>(rt, j / 2), make_float4(x0.x, x0.y, x1.x, x1.y));
+                }
+            } else {
+#pragma unroll
+                for (int ih = 0; ih < NH; ih++) {
+                    const int j = (t * Gl::V + v) * NH + ih;
+                    const float2 lo_half = s[(t * Gl::V + v) * NK + ih];
+                    const float2 hi_half = s[(t * Gl::V + v) * NK + NH + ih];
+                    __stcg(rt + j * C::T, bitj == 0 ? hi_half : lo_half);
+                }
             }
         }
     }
 }
 
-template <class C, int J, class At, int NA, int NW>
-__device__ __forceinline__ void group_round_compute_g(float2 (&s)[NA], At at,
+template <class C, int J, bool VEC, int NA, int NW>
+__device__ __forceinline__ void group_round_compute_g(float2 (&s)[NA], const float2 *rt,
                                                       const float2 (&wk)[NW], int bitj)
 {
     using Gl = Grp<C, C::NG - 1>;
@@ -237,6 +266,7 @@ __device__ __forceinline__ void group_round_compute_g(float2 (&s)[NA], At at,
     constexpr int NK = Gl::R >> J;
     constexpr int NH = NK / 2;
     static_assert(NA == C::EPT && NW >= NT * Gl::V * NH, "a thread's values and factors");
+    static_assert(NH % 2 == 0, "whole slot pairs");
     float2 n[NA];
 #pragma unroll
     for (int t = 0; t < NT; t++) {
@@ -248,7 +278,13 @@ __device__ __forceinline__ void group_round_compute_g(float2 (&s)[NA], At at,
                 const float2 lo_half = s[(t * Gl::V + v) * NK + ih];
                 const float2 hi_half = s[(t * Gl::V + v) * NK + NH + ih];
                 const float2 mine = bitj == 0 ? lo_half : hi_half;
-                const float2 theirs = __ldcg(at(j));
+                float2 theirs;
+                if constexpr (VEC) {
+                    const float4 tp = __ldcg(slot_pair<C>(rt, j / 2));
+                    theirs = (j & 1) ? make_float2(tp.z, tp.w) : make_float2(tp.x, tp.y);
+                } else {
+                    theirs = __ldcg(rt + j * C::T);
+                }
                 float2 x0 = bitj == 0 ? mine : theirs;
                 float2 x1 = bitj == 0 ? theirs : mine;
                 butterfly_w(x0, x1, wk[j]);
@@ -698,6 +734,7 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
     // four CTAs exchange once per tile (both cross stages, radix 4); slots
     // [tile parity][source][destination][KEEP_V values][T]
     constexpr bool R4 = CL == 2;
+    constexpr bool VEC = H16;   // 16-byte exchange slots (see group_round_send_g)
     constexpr int R4V = GC::KEEP_V;                       // values per source and destination
     constexpr long long XSTRIDE = GC::L2_SCRATCH_VALS + (DCT == 3 ? GC::MIRROR_VALS : 0);
     float2 *xb = xbuf + (long long)cid * XSTRIDE + tid;
@@ -960,20 +997,35 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
                 // value r of unit v goes to the CTA whose final rows hold k's
                 // top bits r: p = bit G-1 of r | bit G-2 of r << 1
                 float2 *src = xb + par * (CS * CS * R4V * C::T) + q * (CS * R4V * C::T);
+                static_assert(GC::KEEP_R % 2 == 0, "whole slot pairs");
 #pragma unroll
                 for (int v = 0; v < Gl::V; v++) {
+                    if constexpr (VEC) {
 #pragma unroll
-                    for (int r = 0; r < Gl::R; r++) {
-                        const int p = ((r >> (Gl::G - 1)) & 1) | (((r >> (Gl::G - 2)) & 1) << 1);
-                        if (p != q)
-                            __stcg(src + (p * R4V + v * GC::KEEP_R + (r & (GC::KEEP_R - 1))) *
-                                             C::T,
-                                   a[v * Gl::R + r]);
+                        for (int r = 0; r < Gl::R; r += 2) {
+                            const int p =
+                                ((r >> (Gl::G - 1)) & 1) | (((r >> (Gl::G - 2)) & 1) << 1);
+                            const int sl = p * R4V + v * GC::KEEP_R + (r & (GC::KEEP_R - 1));
+                            const float2 x0 = a[v * Gl::R + r], x1 = a[v * Gl::R + r + 1];
+                            if (p != q)
+                                __stcg(slot_pair<C>(src, sl / 2),
+                                       make_float4(x0.x, x0.y, x1.x, x1.y));
+                        }
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < Gl::R; r++) {
+                            const int p =
+                                ((r >> (Gl::G - 1)) & 1) | (((r >> (Gl::G - 2)) & 1) << 1);
+                            if (p != q)
+                                __stcg(src + (p * R4V + v * GC::KEEP_R + (r & (GC::KEEP_R - 1))) *
+                                                 C::T,
+                                       a[v * Gl::R + r]);
+                        }
                     }
                 }
             } else {
                 float2 *mine = x0 + q * XV;
-                group_round_send_g<C, 0>(a, [&](int j) { return mine + j * C::T; }, q & 1);
+                group_round_send_g<C, 0, VEC>(a, mine, q & 1);
             }
         }
         // round 0 barrier: the flags and the values given away are visible
@@ -1014,21 +1066,43 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
             // X_t = a[t * R4V + v * KEEP_R + i] at rows k + 2^L t
             const float pq = -ld_tw<false>(tw + 2).y;
             const float2 *base = xb + par * (CS * CS * R4V * C::T) + q * (R4V * C::T);
+            // this CTA's own rows: r = rk_end + i, rk_end = (q & 1) R/2 + (q >> 1) R/4
+            auto own = [&](int v, int i) {
+                const float2 o0 = a[v * Gl::R + 0 * (Gl::R / 4) + i];
+                const float2 o1 = a[v * Gl::R + 2 * (Gl::R / 4) + i];
+                const float2 o2 = a[v * Gl::R + 1 * (Gl::R / 4) + i];
+                const float2 o3 = a[v * Gl::R + 3 * (Gl::R / 4) + i];
+                return q == 0 ? o0 : q == 1 ? o1 : q == 2 ? o2 : o3;
+            };
             float2 y[4][R4V];
+            if constexpr (VEC) {
 #pragma unroll
-            for (int v = 0; v < Gl::V; v++) {
+                for (int v = 0; v < Gl::V; v++) {
 #pragma unroll
-                for (int i = 0; i < GC::KEEP_R; i++) {
-                    const int jj = v * GC::KEEP_R + i;
-                    // this CTA's own rows: r = rk_end + i, rk_end = (q & 1) R/2 + (q >> 1) R/4
-                    const float2 o0 = a[v * Gl::R + 0 * (Gl::R / 4) + i];
-                    const float2 o1 = a[v * Gl::R + 2 * (Gl::R / 4) + i];
-                    const float2 o2 = a[v * Gl::R + 1 * (Gl::R / 4) + i];
-                    const float2 o3 = a[v * Gl::R + 3 * (Gl::R / 4) + i];
-                    const float2 own = q == 0 ? o0 : q == 1 ? o1 : q == 2 ? o2 : o3;
+                    for (int i = 0; i < GC::KEEP_R; i += 2) {
+                        const int jj = v * GC::KEEP_R + i;
+                        const float2 own0 = own(v, i), own1 = own(v, i + 1);
 #pragma unroll
-                    for (int t = 0; t < CS; t++)
-                        y[t][jj] = t == q ? own : __ldcg(base + (t * CS * R4V + jj) * C::T);
+                        for (int t = 0; t < CS; t++) {
+                            float4 tp = make_float4(0.f, 0.f, 0.f, 0.f);
+                            if (t != q)
+                                tp = __ldcg(slot_pair<C>(base, (t * CS * R4V + jj) / 2));
+                            y[t][jj] = t == q ? own0 : make_float2(tp.x, tp.y);
+                            y[t][jj + 1] = t == q ? own1 : make_float2(tp.z, tp.w);
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < Gl::V; v++) {
+#pragma unroll
+                    for (int i = 0; i < GC::KEEP_R; i++) {
+                        const int jj = v * GC::KEEP_R + i;
+                        const float2 o = own(v, i);
+#pragma unroll
+                        for (int t = 0; t < CS; t++)
+                            y[t][jj] = t == q ? o : __ldcg(base + (t * CS * R4V + jj) * C::T);
+                    }
                 }
             }
 #pragma unroll
@@ -1045,7 +1119,7 @@ __device__ __forceinline__ void col_group_l2_body(const CUtensorMap *lmap, const
             }
         } else {
             const float2 *theirs = x0 + (q ^ 1) * XV;
-            group_round_compute_g<C, 0>(a, [&](int j) { return theirs + j * C::T; }, wk, q & 1);
+            group_round_compute_g<C, 0, VEC>(a, theirs, wk, q & 1);
         }
         if constexpr (DCT == 3) {
             constexpr int NN = C::N << CL;   // line length
