@@ -115,7 +115,8 @@ cudaError_t h16_launch_col_group(const H16PassArgs &a, cudaStream_t s)
 {
     // local engine: two groups of 6 stages for the pair (0.484 against 0.510
     // ms per 8192^2 transform), three of 4 for four CTAs (2.47 against 2.53
-    // ms per 16384^2 transform)
+    // ms per 16384^2 transform; 2.33 against 2.44 ms with 16-byte exchange
+    // slots)
     using C = typename std::conditional<CL == 1, LineCfg<12, 2, 0, 64, 6>, LineCfg<12, 2, 0, 32>>::type;
     using GH = GroupH16<C>;
     using GC = GroupCol<C, CL>;
