@@ -920,6 +920,234 @@ cudaError_t dct_col_tma_launch(const DctIO &d, const float2 *tw, const float2 *p
 }
 
 // ---------------------------------------------------------------------------
+// Forward DCT columns of 4096 points on the engine of the complex column
+// pass (two groups of 6 stages, 256 threads x 64 values), two real columns
+// per complex line, tiles of W complex = 2W real columns.  The even rows
+// (v[0..N/2)) arrive in the prefetch region and the odd rows (v[N/2..N),
+// reversed) in the first half of the tile region, as two TMA loads.
+// After the last group thread (lo, w) holds Z[k], k = lo + 64 r.  The
+// mirror N - k lies in thread 64 - lo at index 63 - r (lo != 0) or in the
+// same thread at 64 - r (lo = 0), so each thread with lo != 0 hands its
+// values r >= 32 through the staging half of shared memory to the thread
+// that pairs them, and every thread forms X[k] and X[N-k] for its r < 32
+// (dct_pair); k = N/2 pairs with itself.  X[k] (rows 0..N/2-1) and X[N-k]
+// (rows N/2..N-1; k = 0 has no mirror row) leave by one TMA store each.
+template <class C>
+__global__ void __launch_bounds__(C::T, 1) col_dct_tma64_kernel(
+    const __grid_constant__ CUtensorMap me, const __grid_constant__ CUtensorMap mo,
+    const __grid_constant__ CUtensorMap omap, int ntiles, const float2 *__restrict__ tw,
+    const float2 *__restrict__ post, float scale, int *err, int withhold)
+{
+    using S = TmaSplit<C>;
+    using G0 = Grp<C, 0>;
+    using Gl = Grp<C, C::NG - 1>;
+    constexpr int N = C::N, HALF = N / 2, R = Gl::R;
+    static_assert(C::NG == 2 && Gl::V == 1 && C::T == (1 << (Gl::S0 + C::KW)) &&
+                      (R << Gl::S0) == N,
+                  "one unit of R values per thread, k = lo + 2^S0 r");
+    extern __shared__ __align__(1024) float2 sm[];
+    __shared__ __align__(8) uint64_t bar_early, bar_late;
+    __shared__ float2 rot_base[R / 2];   // (cos, sin)(pi 2^S0 r / (2N)), r < R/2
+    const int tid = threadIdx.x;
+    float2 *stw = sm + S::TW_OFF;
+    float2 *stage = sm + C::E / 2;
+    const int w = tid & (C::W - 1);
+    const int lo = tid >> C::KW;
+    auto issue_early = [&](int t) {
+        mbar_arrive_expect_tx(&bar_early, S::EARLY_BYTES);
+        tma_load_3d(sm + C::E, &me, t * C::W, 0, 0, &bar_early);
+    };
+    auto issue_late = [&](int t) {
+        mbar_arrive_expect_tx(&bar_late, S::LATE_BYTES);
+        tma_load_3d(sm, &mo, t * C::W, 0, 0, &bar_late);
+    };
+    if (tid == 0) {
+        mbar_init(&bar_early, 1);
+        mbar_init(&bar_late, 1);
+        fence_mbar_init();
+    }
+    for (int j = tid; j < R / 2; j += C::T)
+        rot_base[j] = __ldg(post + (j << Gl::S0));
+    const float2 rot_lo = __ldg(post + lo);
+    __syncthreads();
+    int tile = (int)blockIdx.x;
+    int n_early = 0, n_late = 0, w_early = 0, w_late = 0;
+    if (tile < ntiles) {
+        if (tid == 0) {
+            mbar_expect_tx(&bar_early, S::TW_BYTES);
+            bulk_load(stw, tw, S::TW_BYTES, &bar_early);
+            issue_early(tile);
+            if (!(withhold && blockIdx.x == 0))   // self-test: the first odd rows never come
+                issue_late(tile);
+        }
+        n_early = n_late = 1;
+    }
+    bool lost = false;
+    float2 a[C::EPT];
+    for (; tile < ntiles; tile += gridDim.x) {
+        const int next = tile + gridDim.x;
+        const bool ok = mbar_wait_bounded(&bar_early, (uint32_t)(w_early & 1)) &&
+                        mbar_wait_bounded(&bar_late, (uint32_t)(w_late & 1));
+        if (__syncthreads_or(ok ? 0 : 1)) {
+            lost = true;
+            break;
+        }
+        w_early++;
+        w_late++;
+        // group 0: scrambled gather of the reordered line (odd rows backwards)
+        {
+            const float2 *pref = sm + C::E;
+#pragma unroll
+            for (int v = 0; v < G0::V; v++) {
+                const int u = tid + v * C::T;
+                const int hib = (u >> C::KW) & ((1 << G0::HB) - 1);
+#pragma unroll
+                for (int r = 0; r < G0::R; r++) {
+                    const int top = brev_c(r, G0::G) << G0::HB;   // compile-time
+                    a[v * G0::R + r] = top < HALF ? pref[(top | hib) * C::W + w]
+                                                  : sm[(N - 1 - (top | hib)) * C::W + w];
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < G0::V; v++)
+            run_stages<C, 0, false, true>(a, v, 0, stw, C::L);
+        fence_proxy_async_smem();
+        if (tid == 0)
+            bulk_wait_read_all();   // the previous tile's stores have read the staging half
+        __syncthreads();            // both input regions have been read
+        if (tid == 0 && next < ntiles)
+            issue_early(next);
+        if (next < ntiles)
+            n_early++;
+#pragma unroll
+        for (int v = 0; v < G0::V; v++) {
+            const int u = tid + v * C::T;
+            const int hib = (u >> C::KW) & ((1 << G0::HB) - 1);
+            const int hi = brev_rt(hib, G0::HB);
+#pragma unroll
+            for (int r = 0; r < G0::R; r++)
+                sm[sidx<C>(0, r | (hi << G0::G), w)] = a[v * G0::R + r];
+        }
+        __syncthreads();
+        group_last_read<C>(a, sm);
+        fence_proxy_async_smem();
+        __syncthreads();   // the tile region is free: the next tile's odd rows
+        if (tid == 0 && next < ntiles)
+            issue_late(next);
+        if (next < ntiles)
+            n_late++;
+        run_stages<C, C::NG - 1, false, true>(a, 0, lo, stw, C::L);
+        // values r >= R/2 to the thread that pairs them: N - k is thread
+        // 2^S0 - lo, index R - 1 - r
+        if (lo != 0) {
+            const int tid_r = (((1 << Gl::S0) - lo) << C::KW) | w;
+#pragma unroll
+            for (int r = R / 2; r < R; r++)
+                stage[(R - 1 - r) * C::T + tid_r] = a[r];
+        }
+        __syncthreads();
+        float2 xmid = make_float2(0.f, 0.f);
+        if (lo == 0) {   // k = N/2 pairs with itself
+            float2 xq;
+            dct_pair(a[R / 2], a[R / 2], __ldg(post + HALF), scale, xmid, xq);
+        }
+#pragma unroll
+        for (int r = 0; r < R / 2; r++) {
+            const float2 zk = a[r];
+            const float2 zp = lo != 0 ? stage[r * C::T + tid] : (r == 0 ? zk : a[R - r]);
+            const float2 rb = rot_base[r];
+            const float2 cs = make_float2(rb.x * rot_lo.x - rb.y * rot_lo.y,
+                                          rb.x * rot_lo.y + rb.y * rot_lo.x);
+            float2 xk, xp;
+            dct_pair(zk, zp, cs, scale, xk, xp);
+            a[r] = xk;
+            a[r == 0 ? R / 2 : R - r] = xp;   // the slot zp came from (lo = 0)
+        }
+        __syncthreads();   // the handed values have been read
+        // X[k], rows k < N/2
+#pragma unroll
+        for (int r = 0; r < R / 2; r++)
+            stage[((r << Gl::S0) | lo) * C::W + w] = a[r];
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tma_store_3d(&omap, tile * C::W, 0, 0, stage);
+            bulk_commit();
+            bulk_wait_read_all();
+        }
+        __syncthreads();
+        // X[N - k] at rows N/2 + s, s = N/2 - k; X[N/2] at s = 0
+#pragma unroll
+        for (int r = 0; r < R / 2; r++)
+            if (lo != 0 || r != 0)
+                stage[(HALF - ((r << Gl::S0) | lo)) * C::W + w] = a[r == 0 ? R / 2 : R - r];
+        if (lo == 0)
+            stage[w] = xmid;
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tma_store_3d(&omap, tile * C::W, 0, HALF / 256, stage);
+            bulk_commit();
+        }
+    }
+    if (__syncthreads_or(lost ? 1 : 0)) {
+        if (tid == 0)
+            atomicExch(err, kDevErrTmaTimeout);
+        // let transfers still in flight land before the CTA leaves
+        if (n_early > w_early)
+            mbar_wait_bounded(&bar_early, (uint32_t)(w_early & 1));
+        if (n_late > w_late)
+            mbar_wait_bounded(&bar_late, (uint32_t)(w_late & 1));
+    }
+    if (tid == 0)
+        bulk_wait_all();   // shared memory stays valid until the stores are done
+}
+
+// The kernel above for forward DCT columns of 4096 points when the image
+// allows it; cudaErrorNotSupported (nothing launched) otherwise.
+cudaError_t dct_col_tma64_launch(const DctIO &d, const float2 *tw, const float2 *post,
+                                 float scale, int *err, int withhold, cudaStream_t s)
+{
+    using C = LineCfg<12, 2, 0, 64, 6>;
+    using S = TmaSplit<C>;
+    constexpr int HALF = C::N / 2;
+    const long long cc = d.cols / 2;   // complex columns
+    if (!err || d.rows != C::N || cc % C::W != 0 || (reinterpret_cast<uintptr_t>(d.in) & 15) ||
+        (reinterpret_cast<uintptr_t>(d.out) & 15) || (reinterpret_cast<uintptr_t>(tw) & 15) ||
+        !tensor_maps_available())
+        return cudaErrorNotSupported;
+    const float2 *in = reinterpret_cast<const float2 *>(d.in);
+    float2 *out = reinterpret_cast<float2 *>(d.out);
+    CUtensorMap me, mo, omap;
+    if (!encode_map_xyz(&me, in, cc, 256, HALF / 256, 2 * cc, 2 * cc * 256, C::W, 256,
+                        HALF / 256) ||
+        !encode_map_xyz(&mo, in + cc, cc, 256, HALF / 256, 2 * cc, 2 * cc * 256, C::W, 256,
+                        HALF / 256) ||
+        !encode_map_xyz(&omap, out, cc, 256, C::N / 256, cc, cc * 256, C::W, 256, HALF / 256))
+        return cudaErrorNotSupported;
+    static_assert((uint32_t)HALF * C::W * 8u == S::EARLY_BYTES &&
+                      S::EARLY_BYTES == S::LATE_BYTES,
+                  "each parity fills one half of the split");
+    auto k = col_dct_tma64_kernel<C>;
+    constexpr int SMEM = S::SMEM_BYTES;
+    static DeviceCache attr_set;
+    const int dev = device_current();
+    if (!attr_set.get(dev)) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (e != cudaSuccess)
+            return e;
+        attr_set.set(dev, 1);
+    }
+    const int ntiles = (int)(cc / C::W);
+    int grid = device_sm_count();
+    if (grid > ntiles)
+        grid = ntiles;
+    k<<<grid, C::T, SMEM, s>>>(me, mo, omap, ntiles, tw, post, scale, err, withhold);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Tile geometry of the inverse DCT column pass over a CTA pair (below): the
 // local engine's 2^L rows in two halves of whole 256-row blocks.
 template <class C>
@@ -1824,6 +2052,9 @@ cudaError_t dct_dispatch(bool row, bool inverse, const DctIO &d, const float2 *t
     if (withhold) {   // the self-test runs on the TMA-fed column kernels only
         if (row)
             return cudaErrorNotSupported;
+        if constexpr (L == 12)
+            if (!inverse)
+                return dct_col_tma64_launch(d, tw, post, scale, err, 1, s);
         if constexpr (L == 11 || L == 12)
             return inverse ? idct_col_tma_launch<LineCfg<L, col_kw(L), 0, 32>>(d, tw, post, scale,
                                                                                 err, 1, s)
@@ -1871,7 +2102,12 @@ cudaError_t dct_dispatch(bool row, bool inverse, const DctIO &d, const float2 *t
             return row_dct_launch<LineCfg<L, 0, row_kb(L), 32>>(d, tw, post, d.rows / 2, scale, s);
         return dct_launch<LineCfg<L, 0, row_kb(L)>, true>(d, tw, post, d.rows / 2, scale, s);
     }
-    if constexpr (L == 11 || L == 12) {
+    if constexpr (L == 12) {
+        const cudaError_t e = dct_col_tma64_launch(d, tw, post, scale, err, 0, s);
+        if (e != cudaErrorNotSupported)
+            return e;
+    }
+    if constexpr (L == 11) {
         const cudaError_t e =
             dct_col_tma_launch<LineCfg<L, col_kw(L), 0, 32>>(d, tw, post, scale, err, 0, s);
         if (e != cudaErrorNotSupported)
