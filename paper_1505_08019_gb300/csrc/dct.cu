@@ -31,7 +31,9 @@
 //  * row_dct_kernel / row_idct_kernel: rows of 2^10 .. 2^14 points, 32
 //    values per thread, loads, pairing and stores in registers;
 //  * col_dct_tma_kernel / col_idct_tma_kernel: persistent TMA-fed column
-//    passes for columns of 2^11 and 2^12 points;
+//    passes for columns of 2^11 points (forward) and 2^11, 2^12 (inverse);
+//  * col_dct_tma64_kernel: forward columns of 2^12 points on the 6-stage
+//    engine of the complex column pass;
 //  * col_dct_pack_l2_kernel (col_group.cuh): forward columns of 2^13 and
 //    2^14 points on a cluster of 2 or 4 CTAs, two real columns per complex
 //    line; col_idct_pair_kernel and col_idct_l2_kernel: the inverse.
