@@ -31,9 +31,9 @@
 //  * row_dct_kernel / row_idct_kernel: rows of 2^10 .. 2^14 points, 32
 //    values per thread, loads, pairing and stores in registers;
 //  * col_dct_tma_kernel / col_idct_tma_kernel: persistent TMA-fed column
-//    passes for columns of 2^11 points (forward) and 2^11, 2^12 (inverse);
-//  * col_dct_tma64_kernel: forward columns of 2^12 points on the 6-stage
-//    engine of the complex column pass;
+//    passes for columns of 2^11 points;
+//  * col_dct_tma64_kernel / col_idct_tma64_kernel: columns of 2^12 points on
+//    the 6-stage engine of the complex column pass;
 //  * col_dct_pack_l2_kernel (col_group.cuh): forward columns of 2^13 and
 //    2^14 points on a cluster of 2 or 4 CTAs, two real columns per complex
 //    line; col_idct_pair_kernel and col_idct_l2_kernel: the inverse.
@@ -1150,6 +1150,192 @@ cudaError_t dct_col_tma64_launch(const DctIO &d, const float2 *tw, const float2 
 }
 
 // ---------------------------------------------------------------------------
+// Inverse DCT columns of 4096 points on the same engine, two real columns per
+// complex line: with (c, s) = (cos, sin)(pi k / (2N)) and X' = X[N - k]
+// (X[N] = 0), V_a = (c + i s)(X_a - i X'_a), V_b likewise, Z = V_a + i V_b,
+// and v_a + i v_b = IDFT(Z) (the plan's conjugate factors).  The tile arrives
+// in natural order (rows 0..N/2-1 in the prefetch region, the others in the
+// tile region), so group 0 reads X[k] and X[N-k] of its scrambled positions
+// straight from shared memory.  Outputs: x[2n] = v[n] (n < N/2) and
+// x[2n+1] = v[N-1-n], one TMA store over the even rows and one over the odd
+// rows (reversed in staging).
+template <class C>
+__global__ void __launch_bounds__(C::T, 1) col_idct_tma64_kernel(
+    const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap oe,
+    const __grid_constant__ CUtensorMap oo, int ntiles, const float2 *__restrict__ tw,
+    const float2 *__restrict__ post, float scale, int *err, int withhold)
+{
+    using S = TmaSplit<C>;
+    using G0 = Grp<C, 0>;
+    using Gl = Grp<C, C::NG - 1>;
+    constexpr int N = C::N, HALF = N / 2, R = Gl::R;
+    static_assert(C::NG == 2 && Gl::V == 1 && G0::V == 1 && C::T == (1 << (Gl::S0 + C::KW)) &&
+                      (R << Gl::S0) == N && G0::R == R,
+                  "one unit of R values per thread in both groups");
+    extern __shared__ __align__(1024) float2 sm[];
+    __shared__ __align__(8) uint64_t bar_early, bar_late;
+    __shared__ float2 rot_top[G0::R];   // (cos, sin)(pi top(r) / (2N)), top(r) = rev(r) 2^HB
+    const int tid = threadIdx.x;
+    float2 *stw = sm + S::TW_OFF;
+    float2 *stage = sm + C::E / 2;
+    const float2 *pref = sm + C::E;
+    const int w = tid & (C::W - 1);
+    const int hib = (tid >> C::KW) & ((1 << G0::HB) - 1);
+    const int lo = (tid >> C::KW) & ((1 << Gl::S0) - 1);
+    if (tid == 0) {
+        mbar_init(&bar_early, 1);
+        mbar_init(&bar_late, 1);
+        fence_mbar_init();
+    }
+    for (int j = tid; j < G0::R; j += C::T) {
+        const int top = brev_rt(j, G0::G) << G0::HB;
+        const float2 p = __ldg(post + (top <= HALF ? top : N - top));
+        rot_top[j] = top <= HALF ? p : make_float2(p.y, p.x);
+    }
+    const float2 rot_hib = __ldg(post + hib);
+    __syncthreads();
+    int tile = (int)blockIdx.x;
+    int n_early = 0, n_late = 0, w_early = 0, w_late = 0;
+    if (tile < ntiles) {
+        if (tid == 0) {
+            mbar_expect_tx(&bar_early, S::TW_BYTES);
+            bulk_load(stw, tw, S::TW_BYTES, &bar_early);
+            split_issue_early<C>(sm, &map, tile * C::W, &bar_early);
+            if (!(withhold && blockIdx.x == 0))   // self-test: the first second half never comes
+                split_issue_late<C>(sm, &map, tile * C::W, &bar_late);
+        }
+        n_early = n_late = 1;
+    }
+    bool lost = false;
+    float2 a[C::EPT];
+    auto xrow = [&](int k) { return k < HALF ? pref[k * C::W + w] : sm[(k - HALF) * C::W + w]; };
+    for (; tile < ntiles; tile += gridDim.x) {
+        const int next = tile + gridDim.x;
+        const bool ok = mbar_wait_bounded(&bar_early, (uint32_t)(w_early & 1)) &&
+                        mbar_wait_bounded(&bar_late, (uint32_t)(w_late & 1));
+        if (__syncthreads_or(ok ? 0 : 1)) {
+            lost = true;
+            break;
+        }
+        w_early++;
+        w_late++;
+        // group 0: scrambled gather of the spectrum rows k and N - k,
+        // pre-rotated into Z[k]
+#pragma unroll
+        for (int r = 0; r < G0::R; r++) {
+            const int k = (brev_c(r, G0::G) << G0::HB) | hib;
+            const float2 xn = xrow(k);
+            float2 xm = xrow((N - k) & (N - 1));
+            if (k == 0)
+                xm = make_float2(0.f, 0.f);   // X[N] = 0
+            const float2 rt = rot_top[r];
+            const float c = rt.x * rot_hib.x - rt.y * rot_hib.y;
+            const float sn = rt.x * rot_hib.y + rt.y * rot_hib.x;
+            a[r] = make_float2(c * xn.x + sn * xm.x - sn * xn.y + c * xm.y,
+                               sn * xn.x - c * xm.x + c * xn.y + sn * xm.y);
+        }
+        run_stages<C, 0, false, true>(a, 0, 0, stw, C::L);
+        fence_proxy_async_smem();
+        if (tid == 0)
+            bulk_wait_read_all();   // the previous tile's stores have read the staging half
+        __syncthreads();            // both input regions have been read
+        if (tid == 0 && next < ntiles)
+            split_issue_early<C>(sm, &map, next * C::W, &bar_early);
+        if (next < ntiles)
+            n_early++;
+        {
+            const int hi = brev_rt(hib, G0::HB);
+#pragma unroll
+            for (int r = 0; r < G0::R; r++)
+                sm[sidx<C>(0, r | (hi << G0::G), w)] = a[r];
+        }
+        __syncthreads();
+        group_last_read<C>(a, sm);
+        fence_proxy_async_smem();
+        __syncthreads();   // the tile region is free: the next tile's second half
+        if (tid == 0 && next < ntiles)
+            split_issue_late<C>(sm, &map, next * C::W, &bar_late);
+        if (next < ntiles)
+            n_late++;
+        run_stages<C, C::NG - 1, false, true>(a, 0, lo, stw, C::L);
+        // v[k], k = lo + 2^S0 r: the even rows take k < N/2 in order
+#pragma unroll
+        for (int r = 0; r < R / 2; r++)
+            stage[((r << Gl::S0) | lo) * C::W + w] = make_float2(a[r].x * scale, a[r].y * scale);
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tma_store_3d(&oe, tile * C::W, 0, 0, stage);
+            bulk_commit();
+            bulk_wait_read_all();
+        }
+        __syncthreads();
+        // the odd rows take k >= N/2 at slot N - 1 - k
+#pragma unroll
+        for (int r = R / 2; r < R; r++)
+            stage[(N - 1 - ((r << Gl::S0) | lo)) * C::W + w] =
+                make_float2(a[r].x * scale, a[r].y * scale);
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tma_store_3d(&oo, tile * C::W, 0, 0, stage);
+            bulk_commit();
+        }
+    }
+    if (__syncthreads_or(lost ? 1 : 0)) {
+        if (tid == 0)
+            atomicExch(err, kDevErrTmaTimeout);
+        // let transfers still in flight land before the CTA leaves
+        if (n_early > w_early)
+            mbar_wait_bounded(&bar_early, (uint32_t)(w_early & 1));
+        if (n_late > w_late)
+            mbar_wait_bounded(&bar_late, (uint32_t)(w_late & 1));
+    }
+    if (tid == 0)
+        bulk_wait_all();   // shared memory stays valid until the stores are done
+}
+
+// The kernel above for inverse DCT columns of 4096 points when the image
+// allows it; cudaErrorNotSupported (nothing launched) otherwise.
+cudaError_t idct_col_tma64_launch(const DctIO &d, const float2 *tw, const float2 *post,
+                                  float scale, int *err, int withhold, cudaStream_t s)
+{
+    using C = LineCfg<12, 2, 0, 64, 6>;
+    using S = TmaSplit<C>;
+    constexpr int HALF = C::N / 2;
+    const long long cc = d.cols / 2;   // complex columns
+    if (!err || d.rows != C::N || cc % C::W != 0 || (reinterpret_cast<uintptr_t>(d.in) & 15) ||
+        (reinterpret_cast<uintptr_t>(d.out) & 15) || (reinterpret_cast<uintptr_t>(tw) & 15) ||
+        !tensor_maps_available())
+        return cudaErrorNotSupported;
+    const float2 *in = reinterpret_cast<const float2 *>(d.in);
+    float2 *out = reinterpret_cast<float2 *>(d.out);
+    CUtensorMap map, oe, oo;
+    if (!encode_col_map(&map, in, C::N, (int)cc, cc, C::W, S::BOX, S::NB) ||
+        !encode_map_xyz(&oe, out, cc, 256, HALF / 256, 2 * cc, 2 * cc * 256, C::W, 256,
+                        HALF / 256) ||
+        !encode_map_xyz(&oo, out + cc, cc, 256, HALF / 256, 2 * cc, 2 * cc * 256, C::W, 256,
+                        HALF / 256))
+        return cudaErrorNotSupported;
+    auto k = col_idct_tma64_kernel<C>;
+    constexpr int SMEM = S::SMEM_BYTES;
+    static DeviceCache attr_set;
+    const int dev = device_current();
+    if (!attr_set.get(dev)) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (e != cudaSuccess)
+            return e;
+        attr_set.set(dev, 1);
+    }
+    const int ntiles = (int)(cc / C::W);
+    int grid = device_sm_count();
+    if (grid > ntiles)
+        grid = ntiles;
+    k<<<grid, C::T, SMEM, s>>>(map, oe, oo, ntiles, tw, post, scale, err, withhold);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Tile geometry of the inverse DCT column pass over a CTA pair (below): the
 // local engine's 2^L rows in two halves of whole 256-row blocks.
 template <class C>
@@ -2055,8 +2241,8 @@ cudaError_t dct_dispatch(bool row, bool inverse, const DctIO &d, const float2 *t
         if (row)
             return cudaErrorNotSupported;
         if constexpr (L == 12)
-            if (!inverse)
-                return dct_col_tma64_launch(d, tw, post, scale, err, 1, s);
+            return inverse ? idct_col_tma64_launch(d, tw, post, scale, err, 1, s)
+                           : dct_col_tma64_launch(d, tw, post, scale, err, 1, s);
         if constexpr (L == 11 || L == 12)
             return inverse ? idct_col_tma_launch<LineCfg<L, col_kw(L), 0, 32>>(d, tw, post, scale,
                                                                                 err, 1, s)
@@ -2081,7 +2267,12 @@ cudaError_t dct_dispatch(bool row, bool inverse, const DctIO &d, const float2 *t
                                                                      scale, s);
             return idct_launch<LineCfg<L, 0, row_kb(L)>, true>(d, tw, post, d.rows / 2, scale, s);
         }
-        if constexpr (L == 11 || L == 12) {
+        if constexpr (L == 12) {
+            const cudaError_t e = idct_col_tma64_launch(d, tw, post, scale, err, 0, s);
+            if (e != cudaErrorNotSupported)
+                return e;
+        }
+        if constexpr (L == 11) {
             const cudaError_t e =
                 idct_col_tma_launch<LineCfg<L, col_kw(L), 0, 32>>(d, tw, post, scale, err, 0, s);
             if (e != cudaErrorNotSupported)
