@@ -302,7 +302,7 @@ def test_dct_round_trip(env, rows, cols):
     assert err <= TOL, err
 
 
-@pytest.mark.parametrize("rows,inverse", [(4096, False), (2048, True), (8192, False),
+@pytest.mark.parametrize("rows,inverse", [(4096, False), (2048, True), (4096, True), (8192, False),
                                           (8192, True), (16384, False), (16384, True)])
 def test_dct_withheld_load_times_out_cleanly(env, rows, inverse):
     """Failure path of the TMA-fed DCT column kernels: CTA 0 never issues the
