@@ -106,10 +106,11 @@ FFT2D_API fft2d_status fft2d_plan(int rows, int cols, int dtype, int dir, fft2d_
  * line (even samples ascending, odd samples descending) followed by a
  * rotation by exp(-i pi k / (2N)) (Makhoul, 1980); the inverse rotates
  * first, then runs the inverse DFT and undoes the reordering.  Two real
- * lines share one complex line, except in the column pass of 16384 rows
- * (both directions), where each real column is its own complex line and the
- * pass runs in place: called out of place it first copies `in` to `out` on
- * the stream.  The plan also holds the
+ * lines share one complex line, except in the inverse column pass of 16384
+ * rows, and in the forward one when cols is not a multiple of 8: there each
+ * real column is its own complex line and the pass runs in place (called
+ * out of place it first copies `in` to `out` on the stream).  The plan also
+ * holds the
  * (cos, sin)(pi k / (2N)) tables, built in FP64 and rounded to FP32.
  * Errors: FFT2D_ERR_UNSUPPORTED for a side of 1.  The other entry points
  * reject these plans with FFT2D_ERR_ARG, except fft2d_exec_host,
@@ -207,8 +208,8 @@ FFT2D_API fft2d_status fft2d_plan_info(fft2d_plan_t plan, int *rows, int *cols, 
  * Once the plan has run on its device (the first launch of each kernel sets
  * its shared-memory limit), the call may be captured in a CUDA graph on
  * `stream`.  It makes no allocation then, except that the column pass of
- * 8192 or 16384 rows (and the DCT column pass of 16384 rows) takes a
- * scratch block (about 20 MB) for the exchange
+ * 8192 or 16384 rows (and the DCT column pass of 8192 and 16384 rows)
+ * takes a scratch block (about 20 to 50 MB) for the exchange
  * between the CTAs of a cluster stream-ordered from the library's own
  * device memory pool and returns it on `stream` after the launch
  * (cudaMallocFromPoolAsync / cudaFreeAsync: no device synchronisation; the
