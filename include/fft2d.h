@@ -208,8 +208,8 @@ FFT2D_API fft2d_status fft2d_plan_info(fft2d_plan_t plan, int *rows, int *cols, 
  * Once the plan has run on its device (the first launch of each kernel sets
  * its shared-memory limit), the call may be captured in a CUDA graph on
  * `stream`.  It makes no allocation then, except that the column pass of
- * 8192 or 16384 rows (and the DCT column pass of 8192 and 16384 rows)
- * takes a scratch block (about 20 to 50 MB) for the exchange
+ * 8192 or 16384 rows (and the DCT column passes of 16384 rows and the
+ * forward one of 8192 rows) takes a scratch block (about 20 to 50 MB) for the exchange
  * between the CTAs of a cluster stream-ordered from the library's own
  * device memory pool and returns it on `stream` after the launch
  * (cudaMallocFromPoolAsync / cudaFreeAsync: no device synchronisation; the
